@@ -1,0 +1,514 @@
+"""FP64 CPU oracle for one semi-implicit step of the 1D3V electron BTE (arXiv 2502.16555).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline leg may import this module. It shares no code with the CUDA path (``csrc/``) and never
+reads anything that path produced.
+
+What it computes (Section 3.4, eqs. "bte_semi_implicit"): one step of the split scheme
+
+    F^{n+1} = S_x  S_v(E(t_n + dt/2))  S_x  F^n
+
+where S_x solves (I + dt/2 A_x (x) D_x) per ordinate with zero-inflow rows (Algorithm 1, via the
+eigen-decomposition of M_v^{-1} G_v), and S_v solves (I - dt P_O (C + E_i A_v) P_S) at every
+collocation point i (eq. "vspace_batched_system") by a dense LU solve. Every sub-step is a
+non-singular linear solve, so the result is unique; the paper's GMRES reaches the same solution
+to its tolerance, this oracle reaches it directly.
+
+Layout: F has shape (Nx, Ntheta, Nr), float64: x slowest, radial B-spline index fastest. The
+velocity index inside a point is v = a*Nr + k (ordinate a, B-spline k).
+
+Readings of points the paper leaves open (the full list with reasons is in the design notes):
+  - collision weak form uses v^3 sigma (test measure v^2 times speed v);
+  - ionization releases two electrons, each at (eps - eps_ion)/2, gain factor 2;
+  - excitation: one electron at eps - eps_th;
+  - heavy-temperature term: -(n0 kB T0/m0) int v^3 sigma_el phi_p' phi_k' dv on the (0,0) block;
+  - field operator derived from the strong form (eE/m_e)[mu d_v f + (1-mu^2)/v d_mu f]
+    with the Legendre recurrences (only A_M(l) = l/sqrt(4l^2-1) of the printed table survives);
+  - T_S carries the azimuthal 2*pi, so T_S T_O = I;
+  - zero-inflow boundary rows replace the Chebyshev row at x=0 (mu >= 0) or x=L (mu < 0);
+  - Algorithm 1's last contraction acts on the updated Y (not on F^n);
+  - the field of the velocity step is taken at t_n + dt/2.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# CODATA 2018 / SI 2019
+E_CHARGE = 1.602176634e-19
+M_E = 9.1093837015e-31
+K_B = 1.380649e-23
+AMU = 1.66053906660e-27
+TORR_PA = 101325.0 / 760.0
+
+
+# --------------------------------------------------------------------------------------------
+# basic conversions
+
+def speed_of_energy(eps_eV):
+    return np.sqrt(2.0 * E_CHARGE * np.asarray(eps_eV, dtype=np.float64) / M_E)
+
+
+def energy_of_speed(v):
+    v = np.asarray(v, dtype=np.float64)
+    return 0.5 * M_E * v * v / E_CHARGE
+
+
+def neutral_density(p_Torr, T0_K):
+    """Ideal-gas neutral density n0 = p / (kB T0) (Table "model parameters")."""
+    return p_Torr * TORR_PA / (K_B * T0_K)
+
+
+# --------------------------------------------------------------------------------------------
+# x: Chebyshev-Gauss-Lobatto collocation (Section 3.3 / 3.4)
+
+def cheb_points(nx, L):
+    """x_i = (L/2)(1 - cos(pi i/(Nx-1))), ascending from 0 to L."""
+    i = np.arange(nx)
+    x = 0.5 * L * (1.0 - np.cos(np.pi * i / (nx - 1)))
+    x[0], x[-1] = 0.0, L
+    return x
+
+
+def cheb_diff(x):
+    """Collocation derivative matrix on the points x via the barycentric formula.
+
+    For Chebyshev-Gauss-Lobatto points the barycentric weights are (-1)^j, halved at both ends;
+    D_ij = (w_j/w_i)/(x_i - x_j) off the diagonal and D_ii = -sum_{j != i} D_ij."""
+    n = x.size
+    w = (-1.0) ** np.arange(n)
+    w[0] *= 0.5
+    w[-1] *= 0.5
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                D[i, j] = (w[j] / w[i]) / (x[i] - x[j])
+        D[i, i] = -np.sum(D[i, :])
+    return D
+
+
+# --------------------------------------------------------------------------------------------
+# theta: Gauss-Legendre ordinates and real spherical harmonics Y_l0 (eqs. "sph_harmonics",
+# "proj_ops")
+
+def ordinates(ntheta):
+    """mu_a = cos(theta_a) at Gauss-Legendre nodes (ascending) and their weights on [-1, 1]."""
+    mu, w = np.polynomial.legendre.leggauss(ntheta)
+    return mu, w
+
+
+def legendre_P(lmax, mu):
+    """P_0..P_lmax at mu by the three-term recurrence; shape (lmax+1, len(mu))."""
+    mu = np.asarray(mu, dtype=np.float64)
+    P = np.zeros((lmax + 1, mu.size))
+    P[0] = 1.0
+    if lmax >= 1:
+        P[1] = mu
+    for l in range(1, lmax):
+        P[l + 1] = ((2 * l + 1) * mu * P[l] - l * P[l - 1]) / (l + 1)
+    return P
+
+
+def angular_ops(ntheta, nl):
+    """T_O[a, l] = Y_l(mu_a) and T_S[l, a] = 2 pi w_a Y_l(mu_a), Y_l = sqrt((2l+1)/4pi) P_l."""
+    mu, w = ordinates(ntheta)
+    P = legendre_P(nl - 1, mu)
+    c = np.sqrt((2.0 * np.arange(nl) + 1.0) / (4.0 * np.pi))
+    Y = c[:, None] * P                      # (nl, ntheta)
+    T_O = Y.T.copy()                        # (ntheta, nl)
+    T_S = 2.0 * np.pi * w[None, :] * Y      # (nl, ntheta)
+    return mu, w, T_O, T_S
+
+
+# --------------------------------------------------------------------------------------------
+# v: clamped cubic B-splines on a uniform grid in speed (eq. "f_expansion")
+
+def bspline_knots(nr, vmax):
+    """Open (clamped) uniform knot vector with Nr cubic functions on [0, vmax]."""
+    if nr < 4:
+        raise ValueError("need at least 4 cubic B-splines")
+    inner = np.linspace(0.0, vmax, nr - 2)
+    inner[-1] = vmax
+    return np.concatenate([[0.0] * 3, inner, [vmax] * 3])
+
+
+def bspline_eval(t, v, deriv=0):
+    """All cubic B-splines (Cox-de Boor recursion) or their first derivatives at points v.
+
+    Returns shape (len(v), Nr) with Nr = len(t) - 4. The interval containing the right end of the
+    support is closed, so phi_{Nr-1}(vmax) = 1. Points outside [t_0, t_last] give zeros."""
+    v = np.atleast_1d(np.asarray(v, dtype=np.float64))
+    nt = t.size
+    B = np.zeros((v.size, nt - 1))
+    last = nt - 2
+    while t[last] == t[last + 1]:
+        last -= 1
+    for m in range(nt - 1):
+        if t[m] < t[m + 1]:
+            inside = (v >= t[m]) & (v < t[m + 1])
+            if m == last:
+                inside |= v == t[m + 1]
+            B[inside, m] = 1.0
+    for p in range(1, 4):
+        use_deriv = deriv == 1 and p == 3
+        Bn = np.zeros((v.size, nt - 1 - p))
+        for m in range(nt - 1 - p):
+            d1 = t[m + p] - t[m]
+            d2 = t[m + p + 1] - t[m + 1]
+            acc = np.zeros(v.size)
+            if use_deriv:
+                if d1 > 0:
+                    acc += p / d1 * B[:, m]
+                if d2 > 0:
+                    acc -= p / d2 * B[:, m + 1]
+            else:
+                if d1 > 0:
+                    acc += (v - t[m]) / d1 * B[:, m]
+                if d2 > 0:
+                    acc += (t[m + p + 1] - v) / d2 * B[:, m + 1]
+            Bn[:, m] = acc
+        B = Bn
+    return B
+
+
+def gauss_composite(breaks, nq):
+    """Composite Gauss-Legendre nodes/weights on the sub-intervals between sorted breakpoints."""
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    b = np.unique(np.asarray(breaks, dtype=np.float64))
+    lo, hi = b[:-1], b[1:]
+    keep = hi > lo
+    lo, hi = lo[keep], hi[keep]
+    x = 0.5 * (lo + hi)[:, None] + 0.5 * (hi - lo)[:, None] * xg[None, :]
+    w = 0.5 * (hi - lo)[:, None] * wg[None, :]
+    return x.ravel(), w.ravel()
+
+
+# --------------------------------------------------------------------------------------------
+# cross sections (Section 3.2; analytic stand-ins for the argon set)
+
+def sigma_of_speed(proc, v):
+    """Cross section (m^2) of one process at speeds v, including its scale factor."""
+    v = np.asarray(v, dtype=np.float64)
+    eps = energy_of_speed(v)
+    th = proc["threshold_eV"]
+    s0 = proc["sigma0"]
+    form = proc["form"]
+    if form == "const":
+        s = np.full(v.shape, s0)
+    elif form == "linear":
+        s = np.where(eps > th, s0 * (1.0 - th / np.where(eps > th, eps, 1.0)), 0.0)
+    elif form == "log":
+        r = np.where(eps > th, eps / th, 1.0)
+        s = np.where(eps > th, s0 * np.log(r) / r, 0.0)
+    elif form == "nu":
+        s = s0 / np.where(v > 0, v, 1.0)
+        s = np.where(v > 0, s, 0.0)
+    elif form == "table":
+        e_tab = np.asarray(proc["eps_eV"])
+        s_tab = np.asarray(proc["sigma_m2"])
+        s = np.interp(eps, e_tab, s_tab, left=0.0, right=0.0)
+        if th > 0:
+            s = np.where(eps > th, s, 0.0)
+    else:
+        raise ValueError(form)
+    return proc["scale"] * s
+
+
+def _sigma_breaks(proc):
+    """Speeds where a cross section is not smooth (threshold, table points)."""
+    out = []
+    if proc["threshold_eV"] > 0:
+        out.append(float(speed_of_energy(proc["threshold_eV"])))
+    if proc["form"] == "table":
+        out += [float(speed_of_energy(e)) for e in proc["eps_eV"] if e > 0]
+    return out
+
+
+class PostCollision:
+    """Post-collision speed map u(v) of one process, and its inverse v(u) with dv/du.
+
+    elastic:    u = alpha v, alpha = sqrt(1 - 2 m_e/m0)      (gain factor 1)
+    excitation: u = sqrt(v^2 - c), c = 2 e eps_th / m_e        (gain factor 1)
+    ionization: u = sqrt((v^2 - c)/2), c = 2 e eps_ion / m_e   (gain factor 2: both electrons)
+    """
+
+    def __init__(self, proc, m0):
+        self.kind = proc["kind"]
+        self.c = 2.0 * E_CHARGE * proc["threshold_eV"] / M_E
+        if self.kind == "elastic":
+            self.alpha = np.sqrt(1.0 - 2.0 * M_E / m0)
+            self.g = 1.0
+        elif self.kind == "excitation":
+            self.g = 1.0
+        else:
+            self.g = 2.0
+
+    def u_of_v(self, v):
+        v = np.asarray(v, dtype=np.float64)
+        if self.kind == "elastic":
+            return self.alpha * v
+        if self.kind == "excitation":
+            return np.sqrt(np.maximum(v * v - self.c, 0.0))
+        return np.sqrt(np.maximum(0.5 * (v * v - self.c), 0.0))
+
+    def v_of_u(self, u):
+        u = np.asarray(u, dtype=np.float64)
+        if self.kind == "elastic":
+            return u / self.alpha, np.full(u.shape, 1.0 / self.alpha)
+        if self.kind == "excitation":
+            v = np.sqrt(u * u + self.c)
+            return v, u / v
+        v = np.sqrt(2.0 * u * u + self.c)
+        return v, 2.0 * u / v
+
+
+# --------------------------------------------------------------------------------------------
+# velocity-space Galerkin matrices (eqs. "c_en_mat_1d", "c_T0_mat_1d", "adv_v_ws", "A_x")
+
+def radial_matrices(t, nq=16):
+    """M_v = int v^2 phi_p phi_k, G_v = int v^3 phi_p phi_k, Dv = int v^2 phi_p phi_k',
+    M1 = int v phi_p phi_k (all polynomial on each knot interval, so Gauss is exact)."""
+    v, w = gauss_composite(t, nq)
+    P = bspline_eval(t, v)
+    dP = bspline_eval(t, v, deriv=1)
+    M = (P * (w * v**2)[:, None]).T @ P
+    G = (P * (w * v**3)[:, None]).T @ P
+    Dv = (P * (w * v**2)[:, None]).T @ dP
+    M1 = (P * (w * v)[:, None]).T @ P
+    return M, G, Dv, M1
+
+
+def collision_loss(t, proc, n0, nq=32):
+    """-n0 int v^3 sigma phi_p phi_k dv (every l)."""
+    vmax = t[-1]
+    br = [b for b in list(t) + _sigma_breaks(proc) if 0.0 <= b <= vmax]
+    v, w = gauss_composite(br, nq)
+    P = bspline_eval(t, v)
+    wt = w * v**3 * sigma_of_speed(proc, v)
+    return -n0 * (P * wt[:, None]).T @ P
+
+
+def collision_gain(t, proc, n0, m0, nq=32):
+    """g n0 int v^3 sigma(v) phi_k(v) phi_p(u(v)) dv, (q, l) = (0, 0) block only.
+
+    Integrated in the post-collision speed u (dv = (dv/du) du), so that the threshold's square-root
+    behaviour becomes smooth; sub-intervals split at the knots in u and at the images u(t_m) of
+    the knots and of the cross-section breakpoints."""
+    vmax = t[-1]
+    pc = PostCollision(proc, m0)
+    umax = float(pc.u_of_v(vmax))
+    if umax <= 0.0:
+        return np.zeros((t.size - 4, t.size - 4))
+    pre = [b for b in list(t) + _sigma_breaks(proc) if b <= vmax]
+    br = [0.0, umax] + [b for b in t if b <= umax]
+    for b in pre:
+        if pc.kind == "elastic" or b * b > pc.c:
+            br.append(float(pc.u_of_v(b)))
+    br = [b for b in br if 0.0 <= b <= umax]
+    u, w = gauss_composite(br, nq)
+    v, dvdu = pc.v_of_u(u)
+    v = np.minimum(v, vmax)
+    Pu = bspline_eval(t, u)       # test function phi_p at the post-collision speed
+    Pv = bspline_eval(t, v)       # trial function phi_k at the pre-collision speed
+    wt = w * dvdu * v**3 * sigma_of_speed(proc, v)
+    return pc.g * n0 * (Pu * wt[:, None]).T @ Pv
+
+
+def collision_T0(t, procs, n0, T0, m0, nq=16):
+    """-(n0 kB T0/m0) int v^3 sigma_el phi_p' phi_k' dv, (0, 0) block, elastic processes."""
+    vmax = t[-1]
+    nr = t.size - 4
+    out = np.zeros((nr, nr))
+    for proc in procs:
+        if proc["kind"] != "elastic":
+            continue
+        br = [b for b in list(t) + _sigma_breaks(proc) if 0.0 <= b <= vmax]
+        v, w = gauss_composite(br, nq)
+        dP = bspline_eval(t, v, deriv=1)
+        wt = w * v**3 * sigma_of_speed(proc, v)
+        out -= (n0 * K_B * T0 / m0) * (dP * wt[:, None]).T @ dP
+    return out
+
+
+def a_coef(l):
+    """a_l = l / sqrt(4 l^2 - 1): mu Y_l = a_{l+1} Y_{l+1} + a_l Y_{l-1}."""
+    return l / np.sqrt(4.0 * l * l - 1.0) if l > 0 else 0.0
+
+
+def field_blocks(Dv, M1, nl):
+    """Field operator A_v (unscaled) as blocks A[q, l] (Nr x Nr), factor e/m_e included.
+
+    From (eE/m_e)[mu d_v f + (1 - mu^2)/v d_mu f] tested with phi_p Y_q (measure v^2 dv dOmega):
+      l = q-1:  a_q     * int v^2 phi_p (phi_k' - (q-1) phi_k / v)
+      l = q+1:  a_{q+1} * int v^2 phi_p (phi_k' + (q+2) phi_k / v)."""
+    nr = Dv.shape[0]
+    A = np.zeros((nl, nl, nr, nr))
+    f = E_CHARGE / M_E
+    for q in range(nl):
+        if q - 1 >= 0:
+            A[q, q - 1] = f * a_coef(q) * (Dv - (q - 1) * M1)
+        if q + 1 < nl:
+            A[q, q + 1] = f * a_coef(q + 1) * (Dv + (q + 2) * M1)
+    return A
+
+
+# --------------------------------------------------------------------------------------------
+# full operator set
+
+class Operators:
+    """Everything one discharge needs: grids, K_C, K_A, the x-step eigen-decomposition, moments."""
+
+    def __init__(self, cfg, nq_gain=32):
+        self.cfg = cfg
+        nx, nr, nt = cfg["nx"], cfg["nr"], cfg["ntheta"]
+        nl = cfg.get("nl") or nt
+        if nl > nt:
+            raise ValueError("nl must not exceed ntheta")
+        self.nx, self.nr, self.nt, self.nl = nx, nr, nt, nl
+        self.nv = nr * nt
+        self.L = cfg["L_m"]
+        self.dt = cfg["dt_s"]
+        self.n0 = neutral_density(cfg["p_Torr"], cfg["T0_K"])
+        self.m0 = cfg["m0_amu"] * AMU
+        self.T0 = cfg["T0_K"]
+        self.vmax = float(speed_of_energy(cfg["vmax_eV"]))
+        self.procs = cfg["processes"]
+
+        self.x = cheb_points(nx, self.L)
+        self.Dx = cheb_diff(self.x)
+        self.mu, self.wmu, self.T_O, self.T_S = angular_ops(nt, nl)
+        self.knots = bspline_knots(nr, self.vmax)
+        M, G, Dv, M1 = radial_matrices(self.knots)
+        self.M, self.G, self.Dv, self.M1 = M, G, Dv, M1
+
+        # collisions: C[l] (l-block diagonal); gain and T0 term only on l = 0
+        loss = np.zeros((nr, nr))
+        gain = np.zeros((nr, nr))
+        for p in self.procs:
+            loss += collision_loss(self.knots, p, self.n0)
+            gain += collision_gain(self.knots, p, self.n0, self.m0, nq=nq_gain)
+        cT = collision_T0(self.knots, self.procs, self.n0, self.T0, self.m0)
+        self.C_raw = np.array([loss + (gain + cT if l == 0 else 0.0) for l in range(nl)])
+        self.A_raw = field_blocks(Dv, M1, nl)
+
+        # mass scaling (Section 3.4: operators scaled by the Galerkin mass matrices)
+        Minv = np.linalg.inv(M)
+        self.Cs = np.einsum("pq,lqk->lpk", Minv, self.C_raw)
+        self.As = np.einsum("pr,qlrk->qlpk", Minv, self.A_raw)
+        # K_C = P_O C P_S, K_A = P_O A_v P_S in the ordinate layout v = a*Nr + k
+        self.KC = np.einsum("al,lpk,lb->apbk", self.T_O, self.Cs, self.T_S).reshape(self.nv, self.nv)
+        self.KA = np.einsum("aq,qlpk,lb->apbk", self.T_O, self.As, self.T_S).reshape(self.nv, self.nv)
+
+        # x-step: generalized symmetric eigenproblem G_v u = lambda M_v u, M_v^{-1} G_v = U Lam U^-1
+        R = np.linalg.cholesky(M)
+        Rinv = np.linalg.inv(R)
+        lam, Z = np.linalg.eigh(Rinv @ G @ Rinv.T)
+        self.lam = lam
+        self.U = Rinv.T @ Z
+        self.Uinv = Z.T @ R.T          # = U^T M_v
+
+        # moment vectors (per x point: n_e = sum_{a,k} u[a,k] F[a,k], etc.)
+        vq, wq = gauss_composite(self.knots, 16)
+        P = bspline_eval(self.knots, vq)
+        ang = 2.0 * np.pi * self.wmu
+        self.mom_n = np.outer(ang, (P * (wq * vq**2)[:, None]).sum(0))
+        self.mom_e = np.outer(ang, (P * (wq * vq**2 * energy_of_speed(vq))[:, None]).sum(0))
+        self.mom_r = []
+        for p in self.procs:
+            br = [b for b in list(self.knots) + _sigma_breaks(p) if 0 <= b <= self.vmax]
+            vr, wr = gauss_composite(br, 32)
+            Pr = bspline_eval(self.knots, vr)
+            self.mom_r.append(np.outer(ang, (Pr * (wr * vr**3 * sigma_of_speed(p, vr))[:, None]).sum(0)))
+
+    # ---- field
+    def field(self, t, V0=None, freq=None):
+        """E_i at time t: (V0/L) sin(2 pi f t), uniform in x (the workloads' specified field)."""
+        V0 = self.cfg["V0"] if V0 is None else V0
+        freq = self.cfg["freq_Hz"] if freq is None else freq
+        return np.full(self.nx, V0 / self.L * np.sin(2.0 * np.pi * freq * t))
+
+    # ---- sub-steps
+    def inflow_row(self, a):
+        """Zero-incoming-flux row: x = 0 for theta <= pi/2 (mu >= 0), x = L otherwise."""
+        return 0 if self.mu[a] >= 0.0 else self.nx - 1
+
+    def x_halfstep(self, F):
+        """Backward-Euler half step of the x-advection (eq. "bte_semi_implicit_xspace0"/"...1")
+        through Algorithm 1: Y = U^-1 F, Y_i <- (I + dt/2 lam_i mu_a D_x)^-1 Y_i, F = U Y."""
+        out = np.empty_like(F)
+        I = np.eye(self.nx)
+        for a in range(self.nt):
+            Y = F[:, a, :] @ self.Uinv.T          # (nx, nr): column i = eigen-coefficient i
+            r = self.inflow_row(a)
+            for i in range(self.nr):
+                B = I + 0.5 * self.dt * self.lam[i] * self.mu[a] * self.Dx
+                B[r, :] = 0.0
+                B[r, r] = 1.0
+                rhs = Y[:, i].copy()
+                rhs[r] = 0.0
+                Y[:, i] = np.linalg.solve(B, rhs)
+            out[:, a, :] = Y @ self.U.T
+        return out
+
+    def v_matrix(self, E_i):
+        return np.eye(self.nv) - self.dt * (self.KC + E_i * self.KA)
+
+    def v_step(self, F, E):
+        """Backward-Euler velocity step (eq. "vspace_batched_system"): one dense solve per point."""
+        out = np.empty_like(F)
+        for i in range(self.nx):
+            out[i] = np.linalg.solve(self.v_matrix(E[i]), F[i].reshape(-1)).reshape(self.nt, self.nr)
+        return out
+
+    def step(self, F, t, E=None):
+        """One semi-implicit step from t to t + dt (eqs. "bte_semi_implicit")."""
+        if E is None:
+            E = self.field(t + 0.5 * self.dt)
+        F1 = self.x_halfstep(F)
+        F2 = self.v_step(F1, E)
+        return self.x_halfstep(F2)
+
+    # ---- moments
+    def moments(self, F):
+        """n_e [m^-3], mean energy [eV], rate coefficients k_j [m^3/s] per x point
+        (n_e = int f dv; k_j = int |v| sigma_j f dv / n_e; eq. "glow_hybrid"). Where n_e == 0
+        the ratios are defined as 0."""
+        Ff = F.reshape(self.nx, -1)
+        ne = Ff @ self.mom_n.reshape(-1)
+        en = Ff @ self.mom_e.reshape(-1)
+        safe = np.where(ne != 0.0, ne, 1.0)
+        mean = np.where(ne != 0.0, en / safe, 0.0)
+        rates = np.array([np.where(ne != 0.0, (Ff @ r.reshape(-1)) / safe, 0.0) for r in self.mom_r])
+        return ne, mean, rates
+
+    # ---- initial condition
+    def maxwellian_coeffs(self, Te_eV):
+        """Galerkin (v^2-weighted) projection of a unit-density Maxwellian at Te onto the splines."""
+        vth = np.sqrt(2.0 * E_CHARGE * Te_eV / M_E)
+        v, w = gauss_composite(self.knots, 32)
+        P = bspline_eval(self.knots, v)
+        fM = np.exp(-(v / vth) ** 2) / (np.pi**1.5 * vth**3)
+        b = (P * (w * v**2 * fM)[:, None]).sum(0)
+        return np.linalg.solve(self.M, b)
+
+    def initial_state(self, Te_eV=None, ne_peak=None):
+        """F(0) = n_e(x) f_M(v; Te), n_e = ne_peak (1 - xi^2), xi = 2x/L - 1, same for all ordinates."""
+        ic = self.cfg.get("ic", {})
+        Te = ic.get("Te_eV", 2.0) if Te_eV is None else Te_eV
+        npk = ic.get("ne_peak", 1e15) if ne_peak is None else ne_peak
+        xi = 2.0 * self.x / self.L - 1.0
+        ne = npk * (1.0 - xi * xi)
+        c = self.maxwellian_coeffs(Te)
+        F = ne[:, None, None] * np.broadcast_to(c, (self.nt, self.nr))[None, :, :]
+        return np.ascontiguousarray(F)
+
+
+def run(cfg, steps=None, F0=None, t0=0.0):
+    """March a workload for ``steps`` steps from its initial state; returns (F, t, ops)."""
+    ops = Operators(cfg)
+    F = ops.initial_state() if F0 is None else np.array(F0, dtype=np.float64)
+    t = t0
+    for _ in range(cfg["steps"] if steps is None else steps):
+        F = ops.step(F, t)
+        t += ops.dt
+    return F, t, ops

@@ -1,0 +1,493 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: closed forms, invariants,
+brute-force assemblies at tiny sizes, values the paper prints, or an independent quadrature.
+"""
+import os
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import bte as O
+from paper_2502_16555_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def tiny_cfg(nx=6, nr=5, nt=4, nl=None, procs=None, **kw):
+    c = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=nt)
+    c["nl"] = nt if nl is None else nl
+    if procs is not None:
+        c["processes"] = procs
+    c.update(kw)
+    return c
+
+
+# ------------------------------------------------------------------------------------ golden
+
+def test_golden_neutral_density_table():
+    """Table "model parameters": n0 = (0.322, 1.61, 3.22, 6.44) e22 m^-3 at 0.1/0.5/1/2 Torr."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "model_parameters.txt"))
+            if l.strip() and not l.startswith("#")]
+    for p, n0 in rows:
+        got = O.neutral_density(float(p), 300.0) / 1e22
+        assert abs(got - float(n0)) / float(n0) < 3e-3, (p, got, n0)
+
+
+def test_golden_rf_period():
+    """Section 3.4.1 quotes the 13.56 MHz period as 7.374e-8 s (four digits, last one truncated)."""
+    assert abs(1.0 / W.RF_FREQ_HZ - 7.374e-8) < 1e-11
+
+
+# ------------------------------------------------------------------------------------ x grid
+
+@pytest.mark.parametrize("nx", [5, 16, 33])
+def test_cheb_diff_exact_on_polynomials(nx):
+    L = 2.54e-2
+    x = O.cheb_points(nx, L)
+    D = O.cheb_diff(x)
+    s = x / L                       # work in units of L to keep powers O(1)
+    for m in range(nx):
+        f = s**m
+        df = m * s ** max(m - 1, 0) / L if m > 0 else np.zeros_like(s)
+        err = np.max(np.abs(D @ f - df)) * L
+        assert err < 1e-10 * max(1, m) ** 2, (m, err)
+
+
+def test_cheb_points_endpoints_and_symmetry():
+    x = O.cheb_points(9, 2.0)
+    assert x[0] == 0.0 and x[-1] == 2.0
+    assert np.allclose(x + x[::-1], 2.0, atol=1e-15)
+    assert np.all(np.diff(x) > 0)
+
+
+def test_cheb_spectral_convergence():
+    errs = []
+    for nx in (8, 16, 24):
+        x = O.cheb_points(nx, 2.0) - 1.0
+        D = O.cheb_diff(x + 1.0)
+        f = np.exp(np.sin(2 * x))
+        errs.append(np.max(np.abs(D @ f - 2 * np.cos(2 * x) * f)))
+    assert errs[1] < 1e-3 * errs[0] and errs[2] < 1e-3 * errs[1]
+
+
+# ------------------------------------------------------------------------------------ B-splines
+
+def test_bspline_partition_of_unity_and_knot_values():
+    t = O.bspline_knots(10, 3.0)
+    v = np.linspace(0.0, 3.0, 1001)
+    P = O.bspline_eval(t, v)
+    assert np.allclose(P.sum(1), 1.0, atol=1e-14)
+    assert np.all(P >= -1e-15)
+    # interior uniform cubic B-spline at its knots: 1/6, 2/3, 1/6
+    h = t[4] - t[3]
+    k = 5
+    knots_k = t[k:k + 5]
+    vals = O.bspline_eval(t, knots_k[1:4])[:, k]
+    assert np.allclose(vals, [1 / 6, 2 / 3, 1 / 6], atol=1e-14)
+    # phi_{Nr-1}(vmax) = 1 and phi_0(0) = 1 (clamped ends)
+    assert O.bspline_eval(t, [3.0])[0, -1] == 1.0
+    assert O.bspline_eval(t, [0.0])[0, 0] == 1.0
+    # integral of an interior uniform cubic B-spline is h
+    vq, wq = O.gauss_composite(t, 8)
+    assert abs((O.bspline_eval(t, vq)[:, k] * wq).sum() - h) < 1e-14
+
+
+def test_bspline_derivative_matches_difference_quotient():
+    t = O.bspline_knots(9, 1.0)
+    v = np.linspace(0.013, 0.987, 57)
+    eps = 1e-6
+    d_num = (O.bspline_eval(t, v + eps) - O.bspline_eval(t, v - eps)) / (2 * eps)
+    assert np.max(np.abs(O.bspline_eval(t, v, deriv=1) - d_num)) < 1e-6
+
+
+def test_marsden_quadratic_reproduction():
+    """Cubic splines reproduce v^2 exactly: its Galerkin projection is exact at every point."""
+    t = O.bspline_knots(12, 2.0)
+    M, _, _, _ = O.radial_matrices(t)
+    vq, wq = O.gauss_composite(t, 16)
+    P = O.bspline_eval(t, vq)
+    b = (P * (wq * vq**2 * vq**2)[:, None]).sum(0)
+    w = np.linalg.solve(M, b)
+    v = np.linspace(0, 2.0, 301)
+    assert np.max(np.abs(O.bspline_eval(t, v) @ w - v**2)) < 1e-11
+
+
+def test_radial_matrices_mass_and_eigs():
+    vmax = 3.2e6
+    t = O.bspline_knots(16, vmax)
+    M, G, Dv, M1 = O.radial_matrices(t)
+    assert np.allclose(M, M.T, rtol=0, atol=1e-14 * np.abs(M).max())
+    assert np.all(np.linalg.eigvalsh(M) > 0)
+    # int v^2 sum_k phi_k = vmax^3 / 3
+    assert abs(M.sum() - vmax**3 / 3) < 1e-13 * vmax**3
+    lam = np.linalg.eigvals(np.linalg.solve(M, G))
+    assert np.max(np.abs(lam.imag)) < 1e-8 * vmax
+    assert np.all(lam.real > 0) and np.all(lam.real <= vmax * (1 + 1e-12))
+    # sum_{p,k} int v^2 phi_p phi_k' = int v^2 (sum phi)' = 0
+    assert abs(Dv.sum()) < 1e-12 * np.abs(Dv).max()
+
+
+# ------------------------------------------------------------------------------------ angular
+
+@pytest.mark.parametrize("nt,nl", [(4, 4), (8, 3), (16, 16), (5, 5)])
+def test_angular_projections(nt, nl):
+    mu, w, T_O, T_S = O.angular_ops(nt, nl)
+    assert np.allclose(T_S @ T_O, np.eye(nl), atol=1e-13)
+    if nl == nt:
+        assert np.allclose(T_O @ T_S, np.eye(nt), atol=1e-13)
+    # closed-form Y_2(mu) = sqrt(5/4pi) (3 mu^2 - 1)/2
+    if nl > 2:
+        assert np.allclose(T_O[:, 2], np.sqrt(5 / (4 * np.pi)) * (3 * mu**2 - 1) / 2, atol=1e-14)
+    assert abs(2 * np.pi * w.sum() - 4 * np.pi) < 1e-13
+
+
+# ------------------------------------------------------------------------------------ collisions
+
+def _ops(cfg):
+    return O.Operators(cfg)
+
+
+def test_collision_particle_conservation_elastic_excitation():
+    cfg = tiny_cfg(nr=12, procs=[W.P1_ELASTIC, W.P2_EXC, W.P4_EXC])
+    ops = _ops(cfg)
+    C0 = ops.C_raw[0]
+    scale = np.abs(C0).max()
+    assert np.max(np.abs(C0.sum(0))) < 1e-12 * scale
+
+
+def test_collision_ionization_source_is_rate():
+    """1^T C_ion = n0 int v^3 sigma_ion phi_k (two out, one in), i.e. minus the loss column sum."""
+    cfg = tiny_cfg(nr=12, procs=[W.P3_ION])
+    ops = _ops(cfg)
+    loss = O.collision_loss(ops.knots, W.P3_ION, ops.n0)
+    assert np.allclose(ops.C_raw[0].sum(0), -loss.sum(0), rtol=1e-11, atol=1e-12 * np.abs(loss).max())
+
+
+@pytest.mark.parametrize("proc", [W.P1_ELASTIC, W.P2_EXC, W.P3_ION, W.P4_EXC])
+def test_collision_energy_moment(proc):
+    """Energy identity: with sum_p w_p phi_p = v^2 (exact for cubics), the energy moment of the
+    collision operator equals n0 int v^3 sigma phi_k (g u(v)^2 - v^2): elastic loses the fraction
+    2 m_e/m0 of v^2, excitation/ionization remove exactly the threshold energy per collision."""
+    cfg = tiny_cfg(nr=14, procs=[proc])
+    ops = _ops(cfg)
+    vq, wq = O.gauss_composite(ops.knots, 16)
+    P = O.bspline_eval(ops.knots, vq)
+    w = np.linalg.solve(ops.M, (P * (wq * vq**4)[:, None]).sum(0))
+    loss = O.collision_loss(ops.knots, proc, ops.n0)     # -n0 int v^3 sigma phi_p phi_k
+    gain = O.collision_gain(ops.knots, proc, ops.n0, ops.m0)
+    lhs = w @ (loss + gain)
+    rate = -loss.sum(0)                                   # n0 int v^3 sigma phi_k
+    if proc["kind"] == "elastic":
+        # g u^2 - v^2 = -(2 m_e/m0) v^2: compare with -(2 m_e/m0) n0 int v^5 sigma phi_k
+        r5 = -(w @ loss)
+        rhs = -(2 * O.M_E / ops.m0) * r5
+    else:
+        c = 2 * O.E_CHARGE * proc["threshold_eV"] / O.M_E
+        rhs = -c * rate
+    assert np.allclose(lhs, rhs, rtol=1e-9, atol=1e-10 * np.abs(rhs).max())
+
+
+@pytest.mark.parametrize("proc", [W.P2_EXC, W.P3_ION, W.P1_ELASTIC])
+def test_collision_gain_against_direct_quadrature(proc):
+    """The gain integral done in the post-collision speed agrees with a brute-force, heavily
+    subdivided quadrature in the pre-collision speed (which never uses the change of variables)."""
+    cfg = tiny_cfg(nr=7, procs=[proc])
+    ops = _ops(cfg)
+    got = O.collision_gain(ops.knots, proc, ops.n0, ops.m0)
+    pc = O.PostCollision(proc, ops.m0)
+    vth = np.sqrt(pc.c) if proc["kind"] != "elastic" else 0.0
+    # geometric grading toward the threshold (square-root behaviour there), then uniform
+    edges = [vth + (ops.vmax - vth) * 2.0**-k for k in range(40, 0, -1)] + list(np.linspace(vth, ops.vmax, 4001))
+    v, wq = O.gauss_composite([vth] + edges, 12)
+    Pv = O.bspline_eval(ops.knots, v)
+    Pu = O.bspline_eval(ops.knots, pc.u_of_v(v))
+    wt = wq * v**3 * O.sigma_of_speed(proc, v)
+    ref = pc.g * ops.n0 * (Pu * wt[:, None]).T @ Pv
+    assert np.max(np.abs(got - ref)) < 1e-7 * np.abs(ref).max()
+
+
+def test_gain_quadrature_converged():
+    cfg = tiny_cfg(nr=16, procs=[W.P3_ION, W.P2_EXC])
+    ops = _ops(cfg)
+    for proc in cfg["processes"]:
+        a = O.collision_gain(ops.knots, proc, ops.n0, ops.m0, nq=32)
+        b = O.collision_gain(ops.knots, proc, ops.n0, ops.m0, nq=64)
+        assert np.max(np.abs(a - b)) < 1e-13 * np.abs(b).max()
+
+
+def test_vstep_conserves_particles_without_field():
+    cfg = tiny_cfg(nx=3, nr=10, nt=6, procs=[W.P1_ELASTIC, W.P2_EXC])
+    ops = _ops(cfg)
+    F = W.random_state(3, 6, 10, seed=3)
+    F1 = ops.v_step(F, np.zeros(3))
+    ne0, _, _ = ops.moments(F)
+    ne1, _, _ = ops.moments(F1)
+    assert np.allclose(ne1, ne0, rtol=1e-12)
+
+
+def test_vstep_ionization_growth():
+    """Backward Euler: n_e(F*) - n_e(F) = dt * n0 * (ionization-rate moment of F*)."""
+    cfg = tiny_cfg(nx=3, nr=10, nt=6, procs=[W.P1_ELASTIC, W.P3_ION])
+    ops = _ops(cfg)
+    F = W.random_state(3, 6, 10, seed=4)
+    F1 = ops.v_step(F, np.zeros(3))
+    ne0, _, _ = ops.moments(F)
+    ne1, _, k1 = ops.moments(F1)
+    src = ops.dt * ops.n0 * k1[1] * ne1
+    assert np.allclose(ne1 - ne0, src, rtol=1e-9)
+    assert np.all(ne1 > ne0)
+
+
+@pytest.mark.parametrize("nt,nl", [(6, 6), (6, 3)])
+def test_relaxation_constant_frequency(nt, nl):
+    """Elastic, constant collision frequency nu (sigma = nu/(n0 v)), m0 -> inf, E = 0: the isotropic
+    part is a fixed point and every l >= 1 harmonic decays by 1/(1 + nu dt) per backward-Euler step;
+    ordinate content outside range(P_O) (when N_l < N_theta) is untouched."""
+    nu = 2.5e9
+    n0 = O.neutral_density(1.0, 300.0)
+    proc = W.process("elastic", "nu", nu / n0)
+    cfg = tiny_cfg(nx=2, nr=8, nt=nt, nl=nl, procs=[proc], m0_amu=1e40)
+    ops = _ops(cfg)
+    F = W.random_state(2, nt, 8, seed=5)
+    F1 = ops.v_step(F, np.zeros(2))
+    d = np.array([1.0] + [1.0 / (1.0 + nu * ops.dt)] * (nl - 1))
+    T_O, T_S = ops.T_O, ops.T_S
+    Pmat = T_O @ T_S                                       # projector onto range(P_O)
+    expect = np.einsum("al,l,lb,xbk->xak", T_O, d, T_S, F) + np.einsum("ab,xbk->xak", np.eye(nt) - Pmat, F)
+    assert np.allclose(F1, expect, rtol=1e-11, atol=1e-12 * np.abs(F).max())
+
+
+# ------------------------------------------------------------------------------------ field
+
+def test_field_number_balance_is_boundary_flux():
+    """Only the l=1 -> l=0 coupling changes the particle count, and it equals the speed-space flux
+    through vmax: sum_p A[0,1][p,k] = (e/m_e) a_1 vmax^2 phi_k(vmax)."""
+    cfg = tiny_cfg(nr=9, nt=6)
+    ops = _ops(cfg)
+    col = ops.A_raw[0, 1].sum(0)
+    phi_end = O.bspline_eval(ops.knots, [ops.vmax])[0]
+    expect = O.E_CHARGE / O.M_E * (1 / np.sqrt(3)) * ops.vmax**2 * phi_end
+    assert np.allclose(col, expect, rtol=1e-11, atol=1e-12 * np.abs(expect).max())
+    for l in range(2, ops.nl):
+        assert np.all(ops.A_raw[0, l] == 0.0)
+
+
+def test_field_operator_matches_strong_form_projection():
+    """A_v against a direct 2-D Galerkin projection of (e/m_e)[mu d_v f + (1-mu^2)/v d_mu f] for
+    f = phi_k(v) Y_l(mu), computed with its own Legendre derivative (no recurrence identities)."""
+    nr, nl = 7, 5
+    cfg = tiny_cfg(nr=nr, nt=nl)
+    ops = _ops(cfg)
+    vq, wv = O.gauss_composite(ops.knots, 12)
+    mq, wm = np.polynomial.legendre.leggauss(24)
+    P = O.bspline_eval(ops.knots, vq)
+    dP = O.bspline_eval(ops.knots, vq, deriv=1)
+    leg = [np.polynomial.legendre.Legendre.basis(l) for l in range(nl)]
+    c = np.sqrt((2 * np.arange(nl) + 1) / (4 * np.pi))
+    Y = np.array([c[l] * leg[l](mq) for l in range(nl)])
+    dY = np.array([c[l] * leg[l].deriv()(mq) for l in range(nl)])
+    ef = O.E_CHARGE / O.M_E
+    for q in range(nl):
+        for l in range(nl):
+            # int dOmega Y_q [mu Y_l] and int dOmega Y_q (1 - mu^2) Y_l'
+            a1 = 2 * np.pi * np.sum(wm * Y[q] * mq * Y[l])
+            a2 = 2 * np.pi * np.sum(wm * Y[q] * (1 - mq**2) * dY[l])
+            ref = ef * (a1 * (P * (wv * vq**2)[:, None]).T @ dP + a2 * (P * (wv * vq)[:, None]).T @ P)
+            assert np.allclose(ops.A_raw[q, l], ref, rtol=1e-11, atol=1e-12 * np.abs(ops.A_raw).max()), (q, l)
+
+
+def test_field_drift_sign():
+    """Force is -eE: with E > 0 an isotropic Maxwellian acquires a flux toward -x (mu < 0)."""
+    cfg = tiny_cfg(nx=3, nr=16, nt=8, procs=[])
+    ops = _ops(cfg)
+    F = ops.initial_state()
+    F1 = ops.v_step(F, np.full(3, 5e3))
+    vq, wq = O.gauss_composite(ops.knots, 16)
+    P = O.bspline_eval(ops.knots, vq)
+    m3 = (P * (wq * vq**3)[:, None]).sum(0)
+    flux = np.einsum("a,xak,k->x", 2 * np.pi * ops.wmu * ops.mu, F1, m3)
+    assert flux[1] < 0
+
+
+# ------------------------------------------------------------------------------------ x-step
+
+def _x_bruteforce(ops, F):
+    """Dense (Nr Nx)^2 solve per ordinate of (I + dt/2 mu_a G (x) D_x) with inflow rows = identity."""
+    G = np.linalg.solve(ops.M, ops.G)
+    out = np.empty_like(F)
+    nx, nr = ops.nx, ops.nr
+    for a in range(ops.nt):
+        B = np.eye(nx * nr) + 0.5 * ops.dt * ops.mu[a] * np.kron(ops.Dx, G)   # index x*nr + k
+        r = ops.inflow_row(a)
+        rhs = F[:, a, :].reshape(-1).copy()
+        for k in range(nr):
+            row = r * nr + k
+            B[row, :] = 0.0
+            B[row, row] = 1.0
+            rhs[row] = 0.0
+        out[:, a, :] = np.linalg.solve(B, rhs).reshape(nx, nr)
+    return out
+
+
+def test_xstep_equals_bruteforce():
+    cfg = tiny_cfg(nx=9, nr=6, nt=4)
+    ops = _ops(cfg)
+    F = W.random_state(9, 4, 6, seed=7)
+    assert np.allclose(ops.x_halfstep(F), _x_bruteforce(ops, F), rtol=1e-12, atol=1e-13 * np.abs(F).max())
+
+
+def test_xstep_inflow_rows_zero():
+    cfg = tiny_cfg(nx=9, nr=6, nt=4)
+    ops = _ops(cfg)
+    F1 = ops.x_halfstep(W.random_state(9, 4, 6, seed=8))
+    for a in range(ops.nt):
+        assert np.all(F1[ops.inflow_row(a), a, :] == 0.0)
+
+
+def test_free_streaming_first_order_in_time():
+    """Collisions and field off: one eigen-mode g(x) U[:, i] advects at speed lam_i mu_a; repeated
+    half steps converge at first order in dt to the characteristic solution g(x - lam_i mu_a t)."""
+    cfg = tiny_cfg(nx=48, nr=6, nt=4, procs=[])
+    ops = _ops(cfg)
+    a, i = 3, 2
+    speed = ops.lam[i] * ops.mu[a]
+    L = ops.L
+    T = 0.15 * L / speed
+    g = lambda x: np.exp(-((x - 0.35 * L) / (0.06 * L)) ** 2)
+    errs = []
+    for n in (80, 160, 320):
+        ops.dt = 2 * T / n                 # each half step advances dt/2 = T/n
+        F = np.zeros((ops.nx, ops.nt, ops.nr))
+        F[:, a, :] = np.outer(g(ops.x), ops.U[:, i])
+        for _ in range(n):
+            F = ops.x_halfstep(F)
+        y = F[:, a, :] @ ops.Uinv.T
+        errs.append(np.max(np.abs(y[:, i] - g(ops.x - speed * T))))
+    order = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+    assert all(0.9 < o < 1.1 for o in order), (errs, order)
+
+
+# ------------------------------------------------------------------------------------ full step
+
+def test_full_step_bruteforce_tiny():
+    """Assemble each sub-step as a full (Nx Nv)^2 matrix with Kronecker products in the harmonic
+    basis (independent of the K_C/K_A einsums) and compose S_x S_v S_x."""
+    cfg = tiny_cfg(nx=6, nr=4, nt=4, procs=[W.P1_ELASTIC, W.P2_EXC, W.P3_ION])
+    cfg["V0"] = 400.0
+    ops = _ops(cfg)
+    nx, nr, nt, nl, nv = ops.nx, ops.nr, ops.nt, ops.nl, ops.nv
+    F = W.random_state(nx, nt, nr, seed=9)
+    t = 0.2 / W.RF_FREQ_HZ
+    E = ops.field(t + 0.5 * ops.dt)
+    # harmonic-space operators, layout (l, k)
+    Cfull = np.zeros((nl * nr, nl * nr))
+    Afull = np.zeros((nl * nr, nl * nr))
+    for q in range(nl):
+        Cfull[q * nr:(q + 1) * nr, q * nr:(q + 1) * nr] = ops.C_raw[q]
+        for l in range(nl):
+            Afull[q * nr:(q + 1) * nr, l * nr:(l + 1) * nr] = ops.A_raw[q, l]
+    Minv_full = np.kron(np.eye(nl), np.linalg.inv(ops.M))
+    PS = np.kron(ops.T_S, np.eye(nr))      # (l,k) <- (a,k)
+    PO = np.kron(ops.T_O, np.eye(nr))      # (a,k) <- (l,k)
+    Sv = np.zeros((nx * nv, nx * nv))
+    for i in range(nx):
+        Ki = PO @ Minv_full @ (Cfull + E[i] * Afull) @ PS
+        Sv[i * nv:(i + 1) * nv, i * nv:(i + 1) * nv] = np.linalg.inv(np.eye(nv) - ops.dt * Ki)
+    # x-step as a full matrix: apply the brute-force per-ordinate solve to unit vectors
+    Sx = np.zeros((nx * nv, nx * nv))
+    for j in range(nx * nv):
+        e = np.zeros(nx * nv)
+        e[j] = 1.0
+        Sx[:, j] = _x_bruteforce(ops, e.reshape(nx, nt, nr)).reshape(-1)
+    ref = (Sx @ Sv @ Sx @ F.reshape(-1)).reshape(nx, nt, nr)
+    got = ops.step(F, t)
+    assert np.allclose(got, ref, rtol=1e-11, atol=1e-12 * np.abs(F).max())
+
+
+# ------------------------------------------------------------------------------------ moments
+
+def _truncated_rates(Te, emax, proc):
+    """Maxwellian rate coefficient of sigma truncated at emax (closed forms)."""
+    vbar = np.sqrt(8 * O.E_CHARGE * Te / (np.pi * O.M_E))
+    s0, th = proc["sigma0"], proc["threshold_eV"]
+    # k = vbar / Te^2 * int sigma(eps) eps exp(-eps/Te) d eps
+    if proc["form"] == "const":
+        I = Te * Te * (1 - np.exp(-emax / Te) * (1 + emax / Te))
+        return vbar * s0 * I / Te**2
+    if proc["form"] == "linear":
+        d = emax - th
+        I = Te * np.exp(-th / Te) * (Te - (d + Te) * np.exp(-d / Te))
+        return vbar * s0 * I / Te**2
+    if proc["form"] == "log":
+        I = th * (-Te * np.exp(-emax / Te) * np.log(emax / th)
+                  + Te * (special.exp1(th / Te) - special.exp1(emax / Te)))
+        return vbar * s0 * I / Te**2
+    raise ValueError
+
+
+def test_moments_of_maxwellian_closed_forms():
+    """Mean energy -> 3/2 Te and Maxwellian rate coefficients of the analytic cross sections,
+    truncated at vmax, up to the B-spline projection error (which must shrink with Nr)."""
+    Te = 2.0
+    res = []
+    for nr in (24, 48, 96):
+        cfg = tiny_cfg(nx=3, nr=nr, nt=4, procs=[W.P1_ELASTIC, W.P2_EXC, W.P3_ION])
+        ops = _ops(cfg)
+        F = np.broadcast_to(ops.maxwellian_coeffs(Te), (3, 4, nr)).copy()
+        ne, mean, rates = ops.moments(F)
+        emax = cfg["vmax_eV"]
+        # truncated Maxwellian: number and energy fractions below emax
+        x = emax / Te
+        frac_n = special.gammainc(1.5, x)
+        frac_e = special.gammainc(2.5, x)
+        e_expect = 1.5 * Te * frac_e / frac_n
+        errs = [abs(ne[0] - frac_n) / frac_n, abs(mean[0] - e_expect) / e_expect]
+        for j, p in enumerate(cfg["processes"]):
+            k_exp = _truncated_rates(Te, emax, p) / frac_n
+            errs.append(abs(rates[j, 0] - k_exp) / k_exp)
+        res.append(max(errs))
+    assert res[-1] < 1e-6 and res[2] < res[0], res
+
+
+def test_moments_zero_density_rule():
+    ops = _ops(tiny_cfg(nx=3, nr=6, nt=4))
+    F = np.zeros((3, 4, 6))
+    ne, mean, rates = ops.moments(F)
+    assert np.all(ne == 0) and np.all(mean == 0) and np.all(rates == 0)
+
+
+def test_initial_state_profile():
+    ops = _ops(tiny_cfg(nx=9, nr=20, nt=4))
+    F = ops.initial_state()
+    ne, _, _ = ops.moments(F)
+    xi = 2 * ops.x / ops.L - 1
+    assert np.all(F[0] == 0) and np.all(F[-1] == 0)
+    frac = special.gammainc(1.5, 30.0 / 2.0)
+    assert np.allclose(ne, 1e15 * (1 - xi**2) * frac, rtol=1e-5, atol=1.0)
+
+
+# ------------------------------------------------------------------------------------ convergence
+
+@pytest.mark.slow
+def test_spectral_self_convergence_shape():
+    """Specified-field runs at three resolutions: the n_e(x) differences shrink (the shape of the
+    paper's self-convergence study, Section 4.1)."""
+    ne = []
+    grids = [(12, 8, 8), (24, 16, 16), (48, 32, 32)]
+    xs = np.linspace(0.05, 0.95, 15)
+    for nx, nr, nt in grids:
+        cfg = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=nt)
+        F, t, ops = O.run(cfg, steps=4)
+        n, _, _ = ops.moments(F)
+        # evaluate the Chebyshev interpolant at common points (barycentric)
+        xh = xs * ops.L
+        w = (-1.0) ** np.arange(nx)
+        w[0] *= 0.5
+        w[-1] *= 0.5
+        d = xh[:, None] - ops.x[None, :]
+        ne.append(((w / d) @ n) / (w / d).sum(1))
+    e1 = np.max(np.abs(ne[0] - ne[2])) / np.max(np.abs(ne[2]))
+    e2 = np.max(np.abs(ne[1] - ne[2])) / np.max(np.abs(ne[2]))
+    assert e2 < 0.5 * e1, (e1, e2)
