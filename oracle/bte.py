@@ -352,6 +352,16 @@ def field_blocks(Dv, M1, nl):
     return A
 
 
+def lower_triangular_inverse(R):
+    """Inverse of a lower-triangular matrix by forward substitution, row by row."""
+    n = R.shape[0]
+    X = np.zeros_like(R)
+    I = np.eye(n)
+    for i in range(n):
+        X[i] = (I[i] - R[i, :i] @ X[:i]) / R[i, i]
+    return X
+
+
 # --------------------------------------------------------------------------------------------
 # full operator set
 
@@ -391,8 +401,12 @@ class Operators:
         self.C_raw = np.array([loss + (gain + cT if l == 0 else 0.0) for l in range(nl)])
         self.A_raw = field_blocks(Dv, M1, nl)
 
-        # mass scaling (Section 3.4: operators scaled by the Galerkin mass matrices)
-        Minv = np.linalg.inv(M)
+        # mass scaling (Section 3.4: operators scaled by the Galerkin mass matrices). M_v = R R^T;
+        # R^-1 by triangular substitution (a general-LU inverse of R loses ~1e-13 here, M_v being
+        # graded by the v^2 weight), M_v^-1 = R^-T R^-1.
+        R = np.linalg.cholesky(M)
+        Rinv = lower_triangular_inverse(R)
+        Minv = Rinv.T @ Rinv
         self.Cs = np.einsum("pq,lqk->lpk", Minv, self.C_raw)
         self.As = np.einsum("pr,qlrk->qlpk", Minv, self.A_raw)
         # K_C = P_O C P_S, K_A = P_O A_v P_S in the ordinate layout v = a*Nr + k
@@ -400,9 +414,8 @@ class Operators:
         self.KA = np.einsum("aq,qlpk,lb->apbk", self.T_O, self.As, self.T_S).reshape(self.nv, self.nv)
 
         # x-step: generalized symmetric eigenproblem G_v u = lambda M_v u, M_v^{-1} G_v = U Lam U^-1
-        R = np.linalg.cholesky(M)
-        Rinv = np.linalg.inv(R)
-        lam, Z = np.linalg.eigh(Rinv @ G @ Rinv.T)
+        S = Rinv @ G @ Rinv.T
+        lam, Z = np.linalg.eigh(0.5 * (S + S.T))
         self.lam = lam
         self.U = Rinv.T @ Z
         self.Uinv = Z.T @ R.T          # = U^T M_v
