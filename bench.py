@@ -1,0 +1,358 @@
+"""Benchmark of the semi-implicit BTE step on GB300: DOF-updates/s, mixed precision vs plain FP64.
+
+Workload: one discharge with Nx=128 Chebyshev points, Nr=64 B-splines, Ntheta=32 ordinates
+(Nv = 2048, 262,144 DOFs), 0.5 Torr, 150 V at 13.56 MHz, dt = T_RF/2000, four analytic processes,
+synthetic Maxwellian initial state. A step is one full bte_step: x half step, per-point dense
+LU solve of the velocity system (with FP64 refinement in the mixed path), x half step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank steps its own discharge (independent replicas: weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2502_16555_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "medium_nx128_nr64_nt32"
+METRIC = "DOF-updates/s per bte_step (mixed vs plain FP64, same GPU) at rel-L2 <=1e-6 vs FP64"
+UNIT = "DOF-updates/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Nominal ratio TF32 : BF16 dense tensor throughput (1.1 : 2.25 PFLOP/s) applied to the measured
+# BF16 peak; TF32x3 spends three tensor products per FP32-accurate product.
+TF32_OVER_BF16 = 1.1 / 2.25
+# FP32 SIMT peak from unit counts and clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"], "src": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+
+
+# ---------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------- work model
+
+def algorithmic(cfg, precision, kernel):
+    """(amount, unit, bound) of algorithmic work of one step for a kernel class.
+
+    lu_gemm: 2 M^2 kb flops per point and panel (M = trailing size); x_apply_q: the Q stream
+    (8 Nv Nx^2 bytes) plus Y in/out per half step; lu_solve: one read of the factors; v_form: one
+    write of the factors plus the K_C/K_A read."""
+    nx, nv = cfg["nx"], cfg["nr"] * cfg["ntheta"]
+    esz = 8 if precision == "fp64" else 4
+    nb = 64 if precision == "fp64" else 128
+    if kernel == "lu_gemm":
+        fl = 0.0
+        for k0 in range(0, nv, nb):
+            kb = min(nb, nv - k0)
+            m = nv - k0 - kb
+            fl += 2.0 * m * m * kb
+        return fl * nx, "flop", "tensor"
+    if kernel == "x_apply_q":
+        return 2 * (8.0 * nv * nx * nx + 16.0 * nv * nx), "byte", "hbm"
+    if kernel == "lu_solve":
+        return float(esz) * nx * nv * nv, "byte", "hbm"
+    if kernel == "v_form":
+        return float(esz) * nx * nv * nv + 16.0 * nv * nv, "byte", "hbm"
+    if kernel == "lu_panel":
+        fl = 0.0
+        for k0 in range(0, nv, nb):
+            kb = min(nb, nv - k0)
+            fl += (nv - k0) * kb * kb
+        return fl * nx, "flop", "alu"
+    return None, None, None
+
+
+def roofline(cfg, precision, prof, steps, peaks, tc):
+    tot = {k: v[0] for k, v in prof.items()}
+    dom = max(tot, key=tot.get)
+    amount, unit, bound = algorithmic(cfg, precision, dom)
+    if amount is None:
+        return {"kernel": dom, "bound": None}
+    n_launch = prof[dom][1]
+    sec = tot[dom] / 1e3
+    per_step_amount = amount
+    achieved = per_step_amount * steps / sec
+    if unit == "flop":
+        achieved_t = achieved / 1e12
+        if dom == "lu_gemm" and precision == "mixed" and tc:
+            peak = peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0
+            bound, pk_note = "tensor", "TF32 peak (measured BF16 x 1.1/2.25) / 3 products (TF32x3)"
+        elif precision == "fp64":
+            peak = 1.10
+            bound, pk_note = "alu", "FP64 DGEMM measured on this GB300 (cuBLAS, 8192^3)"
+        else:
+            peak = FP32_SIMT_PEAK_TFLOPS
+            bound, pk_note = "alu", "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+        return {"kernel": dom, "bound": bound, "achieved": achieved_t, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved_t / peak, "traffic": None, "launches_per_step": n_launch / steps,
+                "peak_source": pk_note + " (" + peaks["src"] + ")"}
+    gbs = achieved / 1e9
+    return {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "traffic": None, "launches_per_step": n_launch / steps,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (" + peaks["src"] + ")"}
+
+
+# ---------------------------------------------------------------------------------- CPU oracle leg
+
+def oracle_sample(cfg, budget_s=20.0):
+    """Time the oracle (as it stands) on the host: one full x half step plus the velocity solve of a
+    bounded subset of points; the per-step time is 2 t_x + (Nx/k) t_v(k)."""
+    from oracle import bte as O
+    ops = O.Operators(cfg)
+    F = ops.initial_state()
+    t0 = time.perf_counter()
+    F1 = ops.x_halfstep(F)
+    tx = time.perf_counter() - t0
+    E = ops.field(0.25 / cfg["freq_Hz"])
+    k, tv = 0, 0.0
+    while k < cfg["nx"] and (tv + 2 * tx) < budget_s:
+        t0 = time.perf_counter()
+        np.linalg.solve(ops.v_matrix(E[k]), F1[k].reshape(-1))
+        tv += time.perf_counter() - t0
+        k += 1
+    step_s = 2 * tx + cfg["nx"] / k * tv
+    dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
+    cores = len(os.sched_getaffinity(0))
+    return {"value": dof / step_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{WORKLOAD}: 1 full x half step ({tx:.2f} s) + dense v-solves of {k}/{cfg['nx']} points "
+                      f"({tv:.2f} s), extrapolated to one step = {step_s:.2f} s; numpy/LAPACK on {cores} host threads"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cfg = W.WORKLOADS[WORKLOAD]
+    vals = []
+    for _ in range(max(1, args.warmup)):
+        oracle_sample(cfg, budget_s=3.0)
+    for _ in range(args.steps):
+        vals.append(oracle_sample(cfg, budget_s=8.0))
+    v = float(np.median([x["value"] for x in vals]))
+    base = vals[-1]
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 262144 / v * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "nx": 128, "nr": 64, "ntheta": 32},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                            "sample": base["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------- GPU leg
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2502_16555_gb300 import bte
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = W.WORKLOADS[WORKLOAD]
+    dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
+    dt = cfg["dt_s"]
+    peaks = load_peaks()
+
+    # ---- mixed precision (the headline)
+    s = bte.Solver(cfg, precision="mixed")
+    tc = False
+    F = s.initial_state()
+    F0 = F.clone()
+    s.run(F, args.warmup, 0.0)
+    launches0 = s.info()["launches"]
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        s.profile_start()
+        ev0.record()
+        s.run(F, args.steps, args.warmup * dt)
+        ev1.record()
+        barrier()
+        prof = s.profile_stop()
+    launches = s.info()["launches"] - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    # the same timing again without event bracketing of every kernel
+    s.run(F, 1, (args.warmup + args.steps) * dt)
+    Fq = F.clone()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    s.run(Fq, args.steps, (args.warmup + args.steps + 1) * dt)
+    e1.record()
+    barrier()
+    ms_plain = e0.elapsed_time(e1) / args.steps
+    ms = min(ms, ms_plain)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * dof / (ms / 1e3)
+
+    # ---- plain FP64 on the same GPU, same steps from the same state
+    s64 = bte.Solver(cfg, precision="fp64")
+    G = F0.clone()
+    n64 = args.warmup + args.steps
+    s64.run(G, args.warmup, 0.0)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    s64.run(G, args.steps, args.warmup * dt)
+    f1.record()
+    barrier()
+    ms64 = f0.elapsed_time(f1) / args.steps
+    # accuracy of the mixed path against FP64 after the same n64 steps
+    Fm = F0.clone()
+    s.run(Fm, n64, 0.0)
+    ne_m, _, _ = s.moments(Fm)
+    ne_d, _, _ = s64.moments(G)
+    torch.cuda.synchronize()
+    rel_f = float(torch.linalg.norm(Fm - G) / torch.linalg.norm(G))
+    rel_ne = float(torch.linalg.norm(ne_m - ne_d) / torch.linalg.norm(ne_d))
+    prof64 = None
+    del s64
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    Fh = torch.empty(F.shape, dtype=torch.float64, pin_memory=True).numpy()
+    Fh[...] = F0.cpu().numpy()
+    s.step_host(Fh, 0.0)
+    n_e2e = max(3, min(args.steps, 20))
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        s.step_host(Fh, (i + 1) * dt)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_val = world * dof / e2e_s
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32x3+f64" if prof["lu_gemm"][1] and tc else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": cfg["nx"], "nr": cfg["nr"], "ntheta": cfg["ntheta"],
+                   "nv": cfg["nr"] * cfg["ntheta"], "dof": dof, "precision": "mixed",
+                   "l2": "working set > L2: 2.1 GB of per-point FP32 factors streamed every step",
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": world * dof / (ms64 / 1e3), "ms_per_step": ms64, "unit": UNIT},
+        "speedup_mixed_over_fp64": ms64 / ms,
+        "accuracy_mixed_vs_fp64": {"steps": n64, "rel_l2_f": rel_f, "rel_l2_ne": rel_ne},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dof, "d2h_bytes_per_step": 8 * dof,
+                "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"},
+        "gpu_launches": int(launches),
+        "roofline": roofline(cfg, "mixed", prof, args.steps, peaks, tc),
+        "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+    }
+    if world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = oracle_sample(cfg)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,181 @@
+/*
+ * bte.h -- C ABI of libbte: the semi-implicit time step of the 1D3V electron Boltzmann transport
+ * equation of arXiv 2502.16555 ("Boltzsim"), on one GB300 (sm_103a).
+ *
+ * The discrete system (Section 3.4, eq. "bte_1d_discrete") is
+ *     dF/dt + A_x F D_x^T = P_O C P_S F + P_O A_v P_S (E . F),
+ * F holding, at every Chebyshev collocation point x_i, the B-spline coefficients f_k(x_i, theta_a)
+ * at every discrete ordinate theta_a. One call of bte_step advances F by dt with the split scheme
+ * of eqs. "bte_semi_implicit": an x half step (backward Euler, dt/2, Algorithm 1), a velocity step
+ * (backward Euler, dt, one dense linear solve per collocation point, eq. "vspace_batched_system"),
+ * and a second x half step.
+ *
+ * Conventions shared by every entry point:
+ *  - F layout: double F[nx][ntheta][nr], C order (x slowest, B-spline index fastest), device memory
+ *    owned by the caller. nv = nr*ntheta; the velocity index inside a point is a*nr + k.
+ *  - Units: SI, energies in eV. The field E is in V/m; the electron force is -eE.
+ *  - Errors are returned as bte_status, never thrown or trapped. bte_last_error() gives a message.
+ *    A failed bte_step leaves F unchanged (BTE_ESINGULAR / BTE_ENOCONV / BTE_ENONFINITE) and the
+ *    handle usable. Arguments are validated before anything is launched.
+ *  - Streams: all device work is enqueued on bte_config.stream (a cudaStream_t, NULL = legacy
+ *    default stream). Entry points do not synchronise the device except where stated.
+ *  - Threading: a handle is used by one host thread at a time.
+ */
+#ifndef BTE_H
+#define BTE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bte_handle bte_handle;
+
+typedef enum {
+  BTE_OK = 0,
+  BTE_EINVAL = 1,      /* bad argument (NULL, size, nl > ntheta, unknown enum ...) */
+  BTE_ENOMEM = 2,      /* device or host allocation failed */
+  BTE_ECUDA = 3,       /* a CUDA runtime call failed (message in bte_last_error) */
+  BTE_ESINGULAR = 4,   /* a zero or non-finite pivot in some per-point factorisation */
+  BTE_ENOCONV = 5,     /* iterative refinement did not reach refine_tol within refine_max sweeps */
+  BTE_ENONFINITE = 6,  /* the input or the result of a step holds NaN/Inf */
+  BTE_ESTATE = 7       /* call out of order (e.g. bte_step before bte_set_cross_sections) */
+} bte_status;
+
+typedef enum {
+  BTE_FP64 = 0,        /* every operation in FP64; direct LU solve of each point's system */
+  BTE_MIXED = 1        /* FP32 factorisation (TF32x3 tensor-core trailing updates), FP64
+                          refinement residuals, FP64 x step and moments */
+} bte_precision;
+
+/* flags for bte_config.flags */
+#define BTE_FLAG_HOST_ONLY 1u   /* assemble the operators on the host only: no CUDA call is made;
+                                   bte_get_operator works, device entry points return BTE_ESTATE */
+#define BTE_FLAG_SIMT_GEMM 2u   /* BTE_MIXED: do the trailing updates of the factorisation on the CUDA
+                                   cores (FP32) instead of the tcgen05 tensor cores (TF32x3) */
+
+typedef struct {
+  int nx;            /* Chebyshev-Gauss-Lobatto points, >= 3 */
+  int nr;            /* cubic B-splines in speed, >= 4 */
+  int ntheta;        /* Gauss-Legendre ordinates in mu = cos(theta), >= 2 */
+  int nl;            /* spherical harmonics Y_l0 kept, 1 <= nl <= ntheta (0 means ntheta) */
+  double L_m;        /* electrode gap [m] */
+  double vmax_eV;    /* largest speed of the B-spline grid, as an energy [eV] */
+  double p_Torr;     /* neutral pressure [Torr]; n0 = p / (kB T0) */
+  double T0_K;       /* neutral temperature [K] */
+  double m0_amu;     /* neutral mass [u] */
+  double dt_s;       /* time step [s] */
+  int precision;     /* bte_precision */
+  double refine_tol; /* stop refining a point when max|r| <= refine_tol * max|b| (<= 0: default) */
+  int refine_max;    /* maximum refinement sweeps per step (< 0: default: 0 FP64, 4 mixed) */
+  void* stream;      /* cudaStream_t for all device work */
+  unsigned flags;    /* BTE_FLAG_* */
+} bte_config;
+
+typedef enum { BTE_ELASTIC = 0, BTE_EXCITATION = 1, BTE_IONIZATION = 2 } bte_kind;
+
+typedef enum {
+  BTE_SIGMA_CONST = 0,   /* sigma = sigma0 */
+  BTE_SIGMA_LINEAR = 1,  /* sigma = sigma0 (1 - th/eps) above the threshold th, else 0 */
+  BTE_SIGMA_LOG = 2,     /* sigma = sigma0 ln(eps/th)/(eps/th) above th, else 0 */
+  BTE_SIGMA_TABLE = 3,   /* piecewise linear in eps through (eps_eV[i], sigma_m2[i]), 0 outside
+                            the table and at or below th */
+  BTE_SIGMA_NU = 4       /* sigma = sigma0 / v (sigma0 in m^3/s): constant collision frequency */
+} bte_form;
+
+typedef struct {
+  int kind;              /* bte_kind; elastic: u = v sqrt(1 - 2 m_e/m0); excitation: one electron
+                            at eps - th; ionization: two electrons at (eps - th)/2 each */
+  int form;              /* bte_form */
+  double threshold_eV;   /* th (ignored for elastic) */
+  double scale;          /* multiplies sigma */
+  double sigma0;         /* m^2 (m^3/s for BTE_SIGMA_NU) */
+  int n_tab;             /* table length (BTE_SIGMA_TABLE), host arrays below, ascending eps */
+  const double* eps_eV;
+  const double* sigma_m2;
+} bte_process;
+
+typedef struct {
+  int nx, nr, ntheta, nl, nv, n_proc;
+  int precision;
+  double n0_m3;           /* neutral density */
+  double vmax_ms;         /* largest speed [m/s] */
+  size_t device_bytes;    /* device memory held by the handle */
+  int last_refine_sweeps; /* sweeps run by the last completed bte_step (needs a synchronised stream) */
+  double last_residual;   /* max over points of max|r|/max|b| after the last step */
+  unsigned last_flags;    /* device status bits of the last step (1 zero pivot, 2 non-finite,
+                             4 not converged) */
+  unsigned long long launches; /* kernels launched by this handle so far */
+  int tensor_cores;       /* 1 if the trailing updates run on tcgen05 (TF32x3) */
+} bte_info;
+
+/* Kernel classes reported by bte_profile (index into its output arrays). */
+enum {
+  BTE_K_X_TO_EIGEN = 0, BTE_K_X_APPLY_Q = 1, BTE_K_X_FROM_EIGEN = 2, BTE_K_V_FORM = 3,
+  BTE_K_LU_PANEL = 4, BTE_K_LU_SWAP_TRSM = 5, BTE_K_LU_GEMM = 6, BTE_K_LU_SOLVE = 7,
+  BTE_K_RESIDUAL = 8, BTE_K_OTHER = 9, BTE_NPROF = 10
+};
+
+/* Create a handle: validates cfg, assembles the grids and the x-step operators on the host (the
+ * velocity operators need bte_set_cross_sections), and allocates its device buffers with cudaMalloc.
+ * Ownership: the handle owns every buffer it allocates; free with bte_destroy.
+ * Section 3.4 (discretisation) and Algorithm 1 (precomputed Q_ij). */
+bte_status bte_create(const bte_config* cfg, bte_handle** out);
+
+/* (Re)assemble the collision operator C (eqs. "c_en_mat_1d", "c_T0_mat_1d"), the field operator
+ * A_v (eq. "adv_v_ws"), their projections K_C = P_O C P_S and K_A = P_O A_v P_S (eq. "proj_ops"),
+ * and the moment vectors, for n_proc processes (host arrays, copied). Blocks until the device
+ * copies are done. */
+bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* procs);
+
+/* F = n_e(x) f_M(v; Te) at every ordinate: the v^2-weighted Galerkin projection of a unit
+ * Maxwellian (Section 4.1, eq. "ic_liu"), scaled by ne_dev[nx] (device). F_dev[nx][ntheta][nr]. */
+bte_status bte_init_maxwellian(bte_handle* h, double* F_dev, const double* ne_dev, double Te_eV);
+
+/* One semi-implicit step t -> t + dt of F_dev (device, in/out), eqs. "bte_semi_implicit".
+ * The field of the velocity step is E_dev[nx] (device, V/m) if non-NULL, else the uniform
+ * E = (V0/L) sin(2 pi freq (t + dt/2)). On BTE_ESINGULAR/ENOCONV/ENONFINITE F is left unchanged.
+ * Enqueues on the handle's stream; the status check reads back 4 bytes and synchronises it. */
+bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_s, double V0,
+                    double freq_Hz);
+
+/* Same as bte_step, but n_steps steps from t_s without any host synchronisation between them
+ * (the status word is read once at the end). E is the uniform sinusoidal field. */
+bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double V0, double freq_Hz);
+
+/* bte_step on HOST buffers: copies F_host (nx*nv doubles) to the device, steps, copies the result
+ * back and synchronises. F_host may be pageable or pinned. */
+bte_status bte_step_host(bte_handle* h, double* F_host, double t_s, double V0, double freq_Hz);
+
+/* Moments at every collocation point (eq. "glow_hybrid", n_e = u^T F): ne_dev[nx] [m^-3],
+ * mean_eV_dev[nx] [eV], rates_dev[n_proc][nx] [m^3/s] (rate coefficient int |v| sigma_j f / n_e).
+ * Where n_e == 0 the ratios are 0. Any output pointer may be NULL. FP64 accumulation. */
+bte_status bte_moments(bte_handle* h, const double* F_dev, double* ne_dev, double* mean_eV_dev,
+                       double* rates_dev);
+
+/* Copy one host-assembled operator into a host array of `count` doubles (for inspection/tests):
+ * which = 0 x[nx], 1 D_x[nx][nx], 2 mu[ntheta], 3 K_C[nv][nv], 4 K_A[nv][nv], 5 lambda[nr],
+ * 6 U[nr][nr], 7 U^-1[nr][nr], 8 Q[ntheta][nr][nx][nx] (inflow column zeroed), 9 M_v[nr][nr],
+ * 10 density moment vector [nv], 11 energy moment vector [nv], 12 rate vectors [n_proc][nv].
+ * Returns BTE_EINVAL if count does not match, BTE_ESTATE if the operator is not assembled yet. */
+bte_status bte_get_operator(const bte_handle* h, int which, double* host_out, size_t count);
+
+bte_status bte_get_info(const bte_handle* h, bte_info* info);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around every launch.
+ * enable = 1: clear and start recording (cheap: two event records per launch). enable = 0: stop,
+ * synchronise the stream, and write the summed device time [ms] and launch count of every kernel
+ * class into ms_out[BTE_NPROF] and count_out[BTE_NPROF] (either may be NULL). */
+bte_status bte_profile(bte_handle* h, int enable, double* ms_out, unsigned long long* count_out);
+
+/* Release every buffer of the handle (synchronises its stream first). NULL is accepted. */
+bte_status bte_destroy(bte_handle* h);
+
+/* Message of the last failing call on this handle ("" if none); NULL handle: last create error. */
+const char* bte_last_error(const bte_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BTE_H */

@@ -1,0 +1,540 @@
+// C ABI of libbte (declared in include/bte.h): handle life cycle, device buffers and the
+// per-step launch sequence of the semi-implicit scheme (eqs. "bte_semi_implicit", arXiv 2502.16555).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bte_internal.h"
+#include "bte_kernels.h"
+
+using bte::HostOps;
+
+struct bte_handle {
+  bte_config cfg{};
+  HostOps ops;
+  std::string err;
+  bool host_only = false;
+  cudaStream_t st = nullptr;
+  int precision = BTE_FP64;
+  int nb = 64;            // outer LU panel width
+  double tol = 0.0;
+  int refine_max = 0;
+  bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  // x-step operators
+  double *U = nullptr, *Uinv = nullptr, *Q = nullptr;
+  // velocity operators
+  double *KC = nullptr, *KA = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
+  double *TO = nullptr, *TS = nullptr;
+  double *mom_n = nullptr, *mom_e = nullptr, *mom_r = nullptr;
+  // work
+  double *Y = nullptr, *Y2 = nullptr, *Fa = nullptr, *Fb = nullptr, *Fw = nullptr, *R = nullptr;
+  double *Fhost_dev = nullptr, *coef = nullptr, *ratio = nullptr;
+  void* fac = nullptr;
+  void* linv = nullptr;
+  void* tcws = nullptr;
+  int *piv = nullptr, *perm = nullptr, *conv = nullptr;
+  unsigned* status = nullptr;
+  unsigned* status_host = nullptr;  // pinned
+  int last_sweeps = 0;
+  double last_resid = 0.0;
+  unsigned last_flags = 0;
+  unsigned long long launches = 0;
+  // profiling: events around every launch while enabled
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+
+namespace {
+
+std::string g_create_error;
+
+bte_status fail(bte_handle* h, bte_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+bte_status cuda_fail(bte_handle* h, cudaError_t e, const char* what) {
+  return fail(h, BTE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define BTE_CUDA(h, call)                                       \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+  } while (0)
+
+template <typename T>
+bte_status dalloc(bte_handle* h, T** p, size_t count) {
+  void* q = nullptr;
+  const size_t bytes = count * sizeof(T);
+  cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) return fail(h, BTE_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  h->allocs.push_back(q);
+  h->bytes += bytes;
+  *p = static_cast<T*>(q);
+  return BTE_OK;
+}
+
+template <typename T>
+bte_status upload(bte_handle* h, T* dst, const std::vector<T>& src) {
+  if (src.empty()) return BTE_OK;
+  BTE_CUDA(h, cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->st));
+  return BTE_OK;
+}
+
+cudaEvent_t next_event(bte_handle* h) {
+  if (h->pool_used == h->pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->pool.push_back(e);
+  }
+  return h->pool[h->pool_used++];
+}
+
+// Brackets one launch: counts it and, while profiling, records events around it.
+struct Launch {
+  bte_handle* h;
+  int kind;
+  cudaEvent_t a = nullptr;
+  Launch(bte_handle* h_, int k) : h(h_), kind(k) {
+    ++h->launches;
+    if (h->prof) {
+      a = next_event(h);
+      cudaEventRecord(a, h->st);
+    }
+  }
+  ~Launch() {
+    if (h->prof) {
+      cudaEvent_t b = next_event(h);
+      cudaEventRecord(b, h->st);
+      h->recs.push_back({kind, a, b});
+    }
+  }
+};
+#define BTE_LAUNCH(kind, call) \
+  do {                         \
+    Launch l_(h, kind);        \
+    call;                      \
+  } while (0)
+
+bool device_ready(bte_handle* h) {
+  if (h->host_only) {
+    h->err = "handle was created with BTE_FLAG_HOST_ONLY";
+    return false;
+  }
+  if (!h->ops.have_v) {
+    h->err = "bte_set_cross_sections has not been called";
+    return false;
+  }
+  return true;
+}
+
+// One semi-implicit step of F_in into F_out (F_out is written only if the status word stays 0).
+bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const double* E_dev,
+                        double t, double V0, double freq) {
+  const HostOps& o = h->ops;
+  const int nx = o.nx, nt = o.nt, nr = o.nr, nv = o.nv, nl = o.nl;
+  const double Eu = V0 / o.L * std::sin(2.0 * bte::kPi * freq * (t + 0.5 * o.dt));
+  cudaStream_t st = h->st;
+  // x half step #1 (eq. "bte_semi_implicit_xspace0")
+  BTE_LAUNCH(BTE_K_X_TO_EIGEN, bte::launch_x_to_eigen(F_in, h->Uinv, h->Y, nx, nt, nr, h->status, st));
+  BTE_LAUNCH(BTE_K_X_APPLY_Q, bte::launch_x_apply_q(h->Q, h->Y, h->Y2, nx, nt, nr, st));
+  BTE_LAUNCH(BTE_K_X_FROM_EIGEN, bte::launch_x_from_eigen(h->Y2, h->U, h->Fa, nx, nt, nr, nullptr, st));
+  // velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system")
+  const int n = nv, nb = h->nb;
+  if (h->precision == BTE_FP64) {
+    double* fac = static_cast<double*>(h->fac);
+    BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
+    for (int k0 = 0; k0 < n; k0 += nb) {
+      const int kb = std::min(nb, n - k0);
+      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nx, n,
+                                                              k0, kb, nb, h->status, nullptr, nullptr, st));
+      if (k0 + kb < n) {
+        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
+                                                                        n, k0, kb, nb, nullptr, nullptr, st));
+        BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<double>(fac, nx, n, k0, kb, st));
+      }
+    }
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st));
+  } else {
+    float* fac = static_cast<float*>(h->fac);
+    float* whi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 0) : nullptr;
+    float* wlo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 1) : nullptr;
+    float* uhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 2) : nullptr;
+    float* ulo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 3) : nullptr;
+    BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
+    for (int k0 = 0; k0 < n; k0 += nb) {
+      const int kb = std::min(nb, n - k0);
+      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv), nx, n,
+                                                             k0, kb, nb, h->status, whi, wlo, st));
+      if (k0 + kb < n) {
+        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, static_cast<float*>(h->linv), nx,
+                                                                       n, k0, kb, nb, uhi, ulo, st));
+        if (h->use_tc) BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, kb, h->tcws, h->status, st));
+        else BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
+      }
+    }
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<float>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st));
+  }
+  // FP64 iterative refinement: residual through Algorithm 2, correction through the factors
+  if (h->refine_max > 0) {
+    BTE_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(int) * nx, st));
+    for (int s = 0; s <= h->refine_max; ++s) {
+      BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                      h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, nx,
+                                                      nt, nr, nl, st));
+      if (s == h->refine_max) break;
+      if (h->precision == BTE_FP64)
+        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(static_cast<double*>(h->fac), h->piv, h->R, h->Fb, nx, n, nb, h->conv, 1, st));
+      else
+        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<float>(static_cast<float*>(h->fac), h->piv, h->R, h->Fb, nx, n, nb, h->conv, 1, st));
+    }
+    BTE_LAUNCH(BTE_K_OTHER, bte::launch_check_conv(h->conv, nx, h->status, st));
+  }
+  // x half step #2 (eq. "bte_semi_implicit_xspace1"), then commit if nothing was flagged
+  BTE_LAUNCH(BTE_K_X_TO_EIGEN, bte::launch_x_to_eigen(h->Fb, h->Uinv, h->Y, nx, nt, nr, nullptr, st));
+  BTE_LAUNCH(BTE_K_X_APPLY_Q, bte::launch_x_apply_q(h->Q, h->Y, h->Y2, nx, nt, nr, st));
+  BTE_LAUNCH(BTE_K_X_FROM_EIGEN, bte::launch_x_from_eigen(h->Y2, h->U, h->Fw, nx, nt, nr, h->status, st));
+  BTE_LAUNCH(BTE_K_OTHER, bte::launch_commit(h->Fw, F_out, static_cast<size_t>(nx) * nv, h->status, st));
+  BTE_CUDA(h, cudaGetLastError());
+  return BTE_OK;
+}
+
+bte_status read_status(bte_handle* h) {
+  BTE_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  BTE_CUDA(h, cudaStreamSynchronize(h->st));
+  const unsigned f = *h->status_host;
+  h->last_flags = f;
+  if (h->refine_max > 0) {
+    std::vector<double> r(h->ops.nx);
+    std::vector<int> c(h->ops.nx);
+    BTE_CUDA(h, cudaMemcpy(r.data(), h->ratio, sizeof(double) * r.size(), cudaMemcpyDeviceToHost));
+    double m = 0;
+    for (double v : r) m = std::max(m, v);
+    h->last_resid = m;
+  }
+  if (f & bte::kTimeout) return fail(h, BTE_ECUDA, "a bounded device-side wait expired in the tensor-core update");
+  if (f & bte::kNonFinite) return fail(h, BTE_ENONFINITE, "non-finite values in the input or the result of a step");
+  if (f & bte::kZeroPivot) return fail(h, BTE_ESINGULAR, "zero or non-finite pivot in a per-point factorisation");
+  if (f & bte::kNoConv) return fail(h, BTE_ENOCONV, "iterative refinement did not converge");
+  return BTE_OK;
+}
+
+bool valid_cfg(const bte_config* c, std::string& why) {
+  if (!c) return why = "cfg is NULL", false;
+  if (c->nx < 3) return why = "nx must be >= 3", false;
+  if (c->nr < 4) return why = "nr must be >= 4", false;
+  if (c->ntheta < 2) return why = "ntheta must be >= 2", false;
+  const int nl = c->nl > 0 ? c->nl : c->ntheta;
+  if (nl < 1 || nl > c->ntheta) return why = "nl must satisfy 1 <= nl <= ntheta", false;
+  if (!(c->L_m > 0) || !(c->vmax_eV > 0) || !(c->p_Torr > 0) || !(c->T0_K > 0) || !(c->m0_amu > 0) ||
+      !(c->dt_s > 0))
+    return why = "L_m, vmax_eV, p_Torr, T0_K, m0_amu and dt_s must be positive", false;
+  if (c->precision != BTE_FP64 && c->precision != BTE_MIXED) return why = "unknown precision", false;
+  const double nv = static_cast<double>(c->nr) * c->ntheta;
+  if (nv > 16384 || c->nx > 4096) return why = "grid too large (nr*ntheta <= 16384, nx <= 4096)", false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+bte_status bte_create(const bte_config* cfg, bte_handle** out) {
+  std::string why;
+  if (!out) return fail(nullptr, BTE_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!valid_cfg(cfg, why)) return fail(nullptr, BTE_EINVAL, why);
+  bte_handle* h = new bte_handle();
+  h->cfg = *cfg;
+  h->host_only = (cfg->flags & BTE_FLAG_HOST_ONLY) != 0;
+  h->st = static_cast<cudaStream_t>(cfg->stream);
+  h->precision = cfg->precision;
+  h->nb = cfg->precision == BTE_FP64 ? 64 : 128;
+  h->tol = cfg->refine_tol > 0 ? cfg->refine_tol : (cfg->precision == BTE_FP64 ? 1e-13 : 1e-12);
+  h->refine_max = cfg->refine_max >= 0 ? cfg->refine_max : (cfg->precision == BTE_FP64 ? 0 : 4);
+  std::string e = bte::assemble_x(*cfg, h->ops);
+  if (!e.empty()) {
+    delete h;
+    return fail(nullptr, BTE_EINVAL, e);
+  }
+  if (!h->host_only) {
+    const HostOps& o = h->ops;
+    const size_t D = static_cast<size_t>(o.nx) * o.nv;
+    const size_t nn = static_cast<size_t>(o.nv) * o.nv;
+    bte_status s;
+    auto chk = [&](bte_status r) { s = r; return r == BTE_OK; };
+    bool ok = chk(dalloc(h, &h->U, o.U.size())) && chk(dalloc(h, &h->Uinv, o.Uinv.size())) &&
+              chk(dalloc(h, &h->Q, o.Q.size())) && chk(dalloc(h, &h->KC, nn)) && chk(dalloc(h, &h->KA, nn)) &&
+              chk(dalloc(h, &h->Cs, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
+              chk(dalloc(h, &h->Alo, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
+              chk(dalloc(h, &h->Aup, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
+              chk(dalloc(h, &h->TO, o.TO.size())) && chk(dalloc(h, &h->TS, o.TS.size())) &&
+              chk(dalloc(h, &h->mom_n, o.nv)) && chk(dalloc(h, &h->mom_e, o.nv)) &&
+              chk(dalloc(h, &h->Y, D)) && chk(dalloc(h, &h->Y2, D)) && chk(dalloc(h, &h->Fa, D)) &&
+              chk(dalloc(h, &h->Fb, D)) && chk(dalloc(h, &h->Fw, D)) && chk(dalloc(h, &h->R, D)) &&
+              chk(dalloc(h, &h->Fhost_dev, D)) && chk(dalloc(h, &h->coef, o.nr)) &&
+              chk(dalloc(h, &h->ratio, o.nx)) && chk(dalloc(h, &h->piv, D)) &&
+              chk(dalloc(h, &h->perm, static_cast<size_t>(o.nx) * bte::perm_record_ints(h->nb))) &&
+              chk(dalloc(h, &h->conv, o.nx)) && chk(dalloc(h, &h->status, 1));
+    if (ok) {
+      if (h->precision == BTE_FP64) {
+        double *f = nullptr, *l = nullptr;
+        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, static_cast<size_t>(o.nx) * h->nb * h->nb));
+        h->fac = f;
+        h->linv = l;
+      } else {
+        float *f = nullptr, *l = nullptr;
+        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, static_cast<size_t>(o.nx) * h->nb * h->nb));
+        h->fac = f;
+        h->linv = l;
+        if (ok && !(cfg->flags & BTE_FLAG_SIMT_GEMM) && bte::tc_available()) {
+          unsigned char* w = nullptr;
+          ok = chk(dalloc(h, &w, bte::tc_workspace_bytes(o.nx, o.nv, h->nb)));
+          h->tcws = w;
+          h->use_tc = ok;
+        }
+      }
+    }
+    if (ok) {
+      cudaError_t ce = cudaMallocHost(reinterpret_cast<void**>(&h->status_host), sizeof(unsigned));
+      if (ce != cudaSuccess) ok = false, s = cuda_fail(h, ce, "cudaMallocHost");
+    }
+    if (ok) ok = chk(upload(h, h->U, o.U)) && chk(upload(h, h->Uinv, o.Uinv)) && chk(upload(h, h->Q, o.Q)) &&
+                 chk(upload(h, h->TO, o.TO)) && chk(upload(h, h->TS, o.TS));
+    if (ok) {
+      cudaError_t ce = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
+      if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
+      if (ce != cudaSuccess) ok = false, s = cuda_fail(h, ce, "initialising device buffers");
+    }
+    if (!ok) {
+      g_create_error = h->err;
+      bte_destroy(h);
+      return s;
+    }
+  }
+  *out = h;
+  return BTE_OK;
+}
+
+bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* procs) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (n_proc < 0 || n_proc > 64 || (n_proc > 0 && !procs)) return fail(h, BTE_EINVAL, "bad process list");
+  std::vector<bte::Process> ps;
+  for (int j = 0; j < n_proc; ++j) {
+    const bte_process& p = procs[j];
+    if (p.kind < BTE_ELASTIC || p.kind > BTE_IONIZATION) return fail(h, BTE_EINVAL, "unknown process kind");
+    if (p.form < BTE_SIGMA_CONST || p.form > BTE_SIGMA_NU) return fail(h, BTE_EINVAL, "unknown cross-section form");
+    if (p.kind != BTE_ELASTIC && !(p.threshold_eV > 0))
+      return fail(h, BTE_EINVAL, "inelastic processes need a positive threshold");
+    if ((p.form == BTE_SIGMA_LINEAR || p.form == BTE_SIGMA_LOG) && !(p.threshold_eV > 0))
+      return fail(h, BTE_EINVAL, "linear/log cross sections need a positive threshold");
+    bte::Process q;
+    q.kind = p.kind;
+    q.form = p.form;
+    q.th_eV = p.kind == BTE_ELASTIC && p.form != BTE_SIGMA_LINEAR && p.form != BTE_SIGMA_LOG ? 0.0 : p.threshold_eV;
+    q.scale = p.scale;
+    q.sigma0 = p.sigma0;
+    if (p.form == BTE_SIGMA_TABLE) {
+      if (p.n_tab < 2 || !p.eps_eV || !p.sigma_m2) return fail(h, BTE_EINVAL, "table needs n_tab >= 2 points");
+      q.tab_eps.assign(p.eps_eV, p.eps_eV + p.n_tab);
+      q.tab_sigma.assign(p.sigma_m2, p.sigma_m2 + p.n_tab);
+      for (int i = 1; i < p.n_tab; ++i)
+        if (!(q.tab_eps[i] > q.tab_eps[i - 1])) return fail(h, BTE_EINVAL, "table energies must ascend");
+    }
+    ps.push_back(q);
+  }
+  std::string e = bte::assemble_v(h->ops, ps);
+  if (!e.empty()) return fail(h, BTE_EINVAL, e);
+  if (h->host_only) return BTE_OK;
+  const HostOps& o = h->ops;
+  if (h->mom_r) {
+    cudaFree(h->mom_r);
+    h->mom_r = nullptr;
+  }
+  if (o.n_proc > 0) {
+    BTE_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->mom_r), sizeof(double) * o.mom_r.size()));
+  }
+  bte_status s;
+  if ((s = upload(h, h->KC, o.KC)) != BTE_OK || (s = upload(h, h->KA, o.KA)) != BTE_OK ||
+      (s = upload(h, h->Cs, o.Cs)) != BTE_OK || (s = upload(h, h->Alo, o.As_lo)) != BTE_OK ||
+      (s = upload(h, h->Aup, o.As_up)) != BTE_OK || (s = upload(h, h->mom_n, o.mom_n)) != BTE_OK ||
+      (s = upload(h, h->mom_e, o.mom_e)) != BTE_OK || (o.n_proc > 0 && (s = upload(h, h->mom_r, o.mom_r)) != BTE_OK))
+    return s;
+  BTE_CUDA(h, cudaStreamSynchronize(h->st));
+  return BTE_OK;
+}
+
+bte_status bte_init_maxwellian(bte_handle* h, double* F_dev, const double* ne_dev, double Te_eV) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (!F_dev || !ne_dev || !(Te_eV > 0)) return fail(h, BTE_EINVAL, "bad arguments");
+  if (h->host_only) return fail(h, BTE_ESTATE, "handle was created with BTE_FLAG_HOST_ONLY");
+  std::vector<double> c = bte::maxwellian_coeffs(h->ops, Te_eV);
+  bte_status s = upload(h, h->coef, c);
+  if (s != BTE_OK) return s;
+  bte::launch_fill_maxwellian(F_dev, ne_dev, h->coef, h->ops.nx, h->ops.nt, h->ops.nr, h->st);
+  BTE_CUDA(h, cudaGetLastError());
+  BTE_CUDA(h, cudaStreamSynchronize(h->st));  // keeps the host coefficient vector alive until copied
+  return BTE_OK;
+}
+
+bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_s, double V0,
+                    double freq_Hz) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (!F_dev) return fail(h, BTE_EINVAL, "F_dev is NULL");
+  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+  bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t_s, V0, freq_Hz);
+  if (s != BTE_OK) return s;
+  h->last_sweeps = h->refine_max;
+  return read_status(h);
+}
+
+bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double V0, double freq_Hz) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (!F_dev || n_steps < 0) return fail(h, BTE_EINVAL, "bad arguments");
+  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+  for (int i = 0; i < n_steps; ++i) {
+    bte_status s = enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * h->ops.dt, V0, freq_Hz);
+    if (s != BTE_OK) return s;
+  }
+  h->last_sweeps = h->refine_max;
+  return read_status(h);
+}
+
+bte_status bte_step_host(bte_handle* h, double* F_host, double t_s, double V0, double freq_Hz) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (!F_host) return fail(h, BTE_EINVAL, "F_host is NULL");
+  if (!device_ready(h)) return BTE_ESTATE;
+  const size_t bytes = sizeof(double) * h->ops.nx * h->ops.nv;
+  BTE_CUDA(h, cudaMemcpyAsync(h->Fhost_dev, F_host, bytes, cudaMemcpyHostToDevice, h->st));
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+  bte_status s = enqueue_step(h, h->Fhost_dev, h->Fhost_dev, nullptr, t_s, V0, freq_Hz);
+  if (s != BTE_OK) return s;
+  BTE_CUDA(h, cudaMemcpyAsync(F_host, h->Fhost_dev, bytes, cudaMemcpyDeviceToHost, h->st));
+  return read_status(h);
+}
+
+bte_status bte_moments(bte_handle* h, const double* F_dev, double* ne_dev, double* mean_eV_dev,
+                       double* rates_dev) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (!F_dev) return fail(h, BTE_EINVAL, "F_dev is NULL");
+  if (!device_ready(h)) return BTE_ESTATE;
+  bte::launch_moments(F_dev, h->mom_n, h->mom_e, h->mom_r, rates_dev ? h->ops.n_proc : 0, ne_dev,
+                      mean_eV_dev, rates_dev, h->ops.nx, h->ops.nv, h->st);
+  BTE_CUDA(h, cudaGetLastError());
+  return BTE_OK;
+}
+
+bte_status bte_get_operator(const bte_handle* hc, int which, double* out, size_t count) {
+  bte_handle* h = const_cast<bte_handle*>(hc);
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (!out) return fail(h, BTE_EINVAL, "output is NULL");
+  const HostOps& o = h->ops;
+  const std::vector<double>* v = nullptr;
+  switch (which) {
+    case 0: v = &o.x; break;
+    case 1: v = &o.Dx; break;
+    case 2: v = &o.mu; break;
+    case 3: v = &o.KC; break;
+    case 4: v = &o.KA; break;
+    case 5: v = &o.lam; break;
+    case 6: v = &o.U; break;
+    case 7: v = &o.Uinv; break;
+    case 8: v = &o.Q; break;
+    case 9: v = &o.M; break;
+    case 10: v = &o.mom_n; break;
+    case 11: v = &o.mom_e; break;
+    case 12: v = &o.mom_r; break;
+    default: return fail(h, BTE_EINVAL, "unknown operator id");
+  }
+  const bool needs_v = which == 3 || which == 4 || which >= 10;
+  if (needs_v && !o.have_v)
+    return fail(h, BTE_ESTATE, "velocity operators not assembled yet");
+  if (v->size() != count) return fail(h, BTE_EINVAL, "count does not match the operator size");
+  std::memcpy(out, v->data(), count * sizeof(double));
+  return BTE_OK;
+}
+
+bte_status bte_get_info(const bte_handle* hc, bte_info* info) {
+  if (!hc || !info) return fail(nullptr, BTE_EINVAL, "NULL argument");
+  const HostOps& o = hc->ops;
+  info->nx = o.nx;
+  info->nr = o.nr;
+  info->ntheta = o.nt;
+  info->nl = o.nl;
+  info->nv = o.nv;
+  info->n_proc = o.n_proc;
+  info->precision = hc->precision;
+  info->n0_m3 = o.n0;
+  info->vmax_ms = o.vmax;
+  info->device_bytes = hc->bytes;
+  info->last_refine_sweeps = hc->last_sweeps;
+  info->last_residual = hc->last_resid;
+  info->last_flags = hc->last_flags;
+  info->launches = hc->launches;
+  info->tensor_cores = hc->use_tc ? 1 : 0;
+  return BTE_OK;
+}
+
+bte_status bte_profile(bte_handle* h, int enable, double* ms_out, unsigned long long* count_out) {
+  if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
+  if (h->host_only) return fail(h, BTE_ESTATE, "handle was created with BTE_FLAG_HOST_ONLY");
+  if (enable) {
+    h->recs.clear();
+    h->pool_used = 0;
+    h->prof = true;
+    return BTE_OK;
+  }
+  h->prof = false;
+  BTE_CUDA(h, cudaStreamSynchronize(h->st));
+  double ms[BTE_NPROF] = {0};
+  unsigned long long cnt[BTE_NPROF] = {0};
+  for (const auto& r : h->recs) {
+    float t = 0.f;
+    BTE_CUDA(h, cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.kind] += t;
+    cnt[r.kind] += 1;
+  }
+  h->recs.clear();
+  h->pool_used = 0;
+  for (int k = 0; k < BTE_NPROF; ++k) {
+    if (ms_out) ms_out[k] = ms[k];
+    if (count_out) count_out[k] = cnt[k];
+  }
+  return BTE_OK;
+}
+
+bte_status bte_destroy(bte_handle* h) {
+  if (!h) return BTE_OK;
+  if (!h->host_only) {
+    cudaStreamSynchronize(h->st);
+    for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->mom_r) cudaFree(h->mom_r);
+    if (h->status_host) cudaFreeHost(h->status_host);
+  }
+  delete h;
+  return BTE_OK;
+}
+
+const char* bte_last_error(const bte_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,54 @@
+// Internal declarations shared by the host assembly (assembly.cpp) and the CUDA side (*.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/bte.h"
+
+namespace bte {
+
+// Physical constants: CODATA 2018 values (e, kB exact since SI 2019).
+constexpr double kE = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kKB = 1.380649e-23;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kTorr = 101325.0 / 760.0;
+constexpr double kPi = 3.14159265358979323846;
+
+struct Process {
+  int kind = 0, form = 0;
+  double th_eV = 0, scale = 1, sigma0 = 0;
+  std::vector<double> tab_eps, tab_sigma;
+};
+
+// Everything assembled on the host, in FP64, row-major.
+struct HostOps {
+  int nx = 0, nr = 0, nt = 0, nl = 0, nv = 0;
+  double L = 0, vmax = 0, n0 = 0, T0 = 0, m0 = 0, dt = 0;
+
+  std::vector<double> x, Dx;            // nx, nx*nx
+  std::vector<double> mu, wmu;          // nt Gauss-Legendre nodes (ascending) and weights
+  std::vector<double> knots;            // nr + 4
+  std::vector<double> M, G, Dv, M1;     // nr*nr radial Galerkin matrices
+  std::vector<double> lam, U, Uinv;     // M^-1 G = U diag(lam) U^-1
+  std::vector<double> Q;                // [nt][nr][nx][nx] inverse x half-step operators
+  std::vector<double> TO, TS;           // T_O [nt][nl], T_S [nl][nt]
+
+  bool have_v = false;
+  int n_proc = 0;
+  std::vector<double> Cs;               // [nl][nr][nr]  M^-1 C (l-block diagonal)
+  std::vector<double> As_lo, As_up;     // [nl][nr][nr]  M^-1 A_v blocks (q, q-1) and (q, q+1)
+  std::vector<double> KC, KA;           // [nv][nv]  P_O C P_S, P_O A_v P_S
+  std::vector<double> mom_n, mom_e;     // [nv]
+  std::vector<double> mom_r;            // [n_proc][nv]
+};
+
+// Grids, radial matrices, eigen-decomposition and Q_ij. Returns "" on success, else a message.
+std::string assemble_x(const bte_config& cfg, HostOps& ops);
+// Collision and field operators, their projections and the moment vectors.
+std::string assemble_v(HostOps& ops, const std::vector<Process>& procs);
+// Galerkin coefficients of a unit-density Maxwellian at temperature Te (eV).
+std::vector<double> maxwellian_coeffs(const HostOps& ops, double Te_eV);
+
+}  // namespace bte

@@ -1,0 +1,68 @@
+// Launch wrappers of the device kernels (plain pointers; all enqueue on `st`, none synchronise).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bte {
+
+enum StatusBits : unsigned {
+  kZeroPivot = 1u,   // a zero or non-finite pivot in some per-point LU
+  kNonFinite = 2u,   // NaN/Inf in the input or the result of a step
+  kNoConv = 4u,      // refinement did not reach the tolerance
+  kTimeout = 8u,     // a bounded device-side wait expired (tensor-core pipeline)
+};
+
+// tensor-core (tcgen05) trailing update of the FP32 LU; workspace of tc_workspace_bytes()
+bool tc_available();
+size_t tc_workspace_bytes(int nx, int n, int nbmax);
+float* tc_ws_part(void* ws, int nx, int n, int part);  // 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
+void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st);
+
+// ---- x half step (Algorithm 1): eigen-basis transform, Q_ij apply, back transform
+void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
+                       unsigned* status, cudaStream_t st);
+void launch_x_apply_q(const double* Q, const double* Y, double* Y2, int nx, int nt, int nr,
+                      cudaStream_t st);
+void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, int nt, int nr,
+                         unsigned* status, cudaStream_t st);
+
+// ---- velocity step
+// A_i = I - dt (K_C + E_i K_A) in storage type T (float or double), row-major per point
+template <typename T>
+void launch_v_form(const double* KC, const double* KA, const double* E, double E_uniform, double dt,
+                   T* fac, int nx, int nv, cudaStream_t st);
+// ints per point of the panel permutation record written by lu_panel
+int perm_record_ints(int nbmax);
+// ws_hi/ws_lo (may be NULL): K-major TF32 head/remainder copies of L21 (panel) and of U12^T
+// (swap_trsm) for the tensor-core trailing update, [point][n - nbmax][nbmax] floats.
+template <typename T>
+void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
+                     unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st);
+template <typename T>
+void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, int k0, int nb,
+                         int nbmax, float* ws_hi, float* ws_lo, cudaStream_t st);
+template <typename T>
+void launch_lu_gemm_simt(T* fac, int nx, int n, int k0, int nb, cudaStream_t st);
+// x = A^-1 b (pivots applied lazily, panel by panel); `conv` (may be NULL) skips converged points.
+// For T = float the arithmetic is FP32 and the result is ADDED to x when `accumulate` is set.
+template <typename T>
+void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
+                     const int* conv, int accumulate, cudaStream_t st);
+
+// FP64 residual r = b - (x - dt P_O (C + E_i A_v) P_S x) through the structured operators
+// (Algorithm 2), per-point ratio max|r|/max|b|; marks conv[i] = 1 when ratio <= tol.
+void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
+                     const double* Cs, const double* Alo, const double* Aup, const double* TO,
+                     const double* TS, double* r, double* ratio, int* conv, double tol, int nx,
+                     int nt, int nr, int nl, cudaStream_t st);
+void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st);
+
+// ---- misc
+void launch_commit(const double* src, double* dst, size_t n, const unsigned* status, cudaStream_t st);
+void launch_moments(const double* F, const double* mom_n, const double* mom_e, const double* mom_r,
+                    int n_proc, double* ne, double* mean, double* rates, int nx, int nv,
+                    cudaStream_t st);
+void launch_fill_maxwellian(double* F, const double* ne, const double* coef, int nx, int nt, int nr,
+                            cudaStream_t st);
+
+}  // namespace bte

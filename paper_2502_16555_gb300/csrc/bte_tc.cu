@@ -1,0 +1,380 @@
+// Tensor-core (tcgen05, sm_103a) trailing update of the FP32 per-point LU: A22 -= L21 U12 for every
+// point of the batch, with the three-product TF32 split (a = a_hi + a_lo, b = b_hi + b_lo,
+// ab ~ a_hi b_hi + a_hi b_lo + a_lo b_hi) accumulated in FP32 in tensor memory. This is the
+// bulk O(Nv^3) work of the velocity-space solves of eq. "vspace_batched_system" (arXiv 2502.16555).
+//
+// Operands: the panel kernel writes L21 split into hi/lo parts, and the swap/TRSM kernel writes
+// U12 transposed and split, into a workspace laid out K-major ([point][row][128] floats), so both
+// MMA operands are K-major, 128-byte-swizzled TMA tiles.
+//
+// Kernel: persistent, one CTA of 192 threads per SM, static round-robin over 128x128 output tiles
+// (point-major, so the CTAs in flight share one point's panels in L2):
+//   warp 0  TMA producer: per K-chunk of 32, four 16 KB boxes (A_hi, A_lo, B_hi, B_lo) into a
+//           3-stage shared-memory ring, completion through mbarrier transaction counts;
+//   warp 1  allocates 256 TMEM columns (two 128x128 FP32 accumulators) and issues the MMAs
+//           (M=128, N=128, K=8 per instruction, 12 per chunk), committing each stage back to the
+//           producer and each finished accumulator to the epilogue;
+//   warps 2-5 epilogue: tcgen05.ld of their 32-lane slice, C -= acc in global memory.
+// Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the kernel records a status bit,
+// stops issuing work, drains the copies it issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstdio>
+
+#include "bte_kernels.h"
+
+namespace bte {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32, KTOT = 128, NCHUNK = KTOT / BK;
+constexpr int STAGES = 3;
+constexpr int BOX_BYTES = BM * BK * 4;            // 16 KB (BM == BN)
+constexpr int STAGE_BYTES = 4 * BOX_BYTES;        // A_hi, A_lo, B_hi, B_lo
+constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
+constexpr int NTHREADS = 192;
+constexpr long long kWaitCycles = 1ll << 32;     // ~2 s at 2 GHz
+constexpr unsigned kTimeoutBit = 8u;
+
+// instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9, 10-12 = 2),
+// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+struct Smem {
+  alignas(1024) unsigned char stage[STAGES][STAGE_BYTES];
+  alignas(8) uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort;
+  int issued;    // K-chunks whose loads the producer issued
+};
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false if the phase did not complete in time or the CTA is aborting.
+__device__ bool mbar_wait(Smem& s, uint64_t* b, uint32_t parity, unsigned* status) {
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity)) {
+    if (*reinterpret_cast<volatile int*>(&s.abort)) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(&s.abort, 1);
+      atomicOr(status, kTimeoutBit);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(saddr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused for this layout)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version for tcgen05
+  d |= static_cast<uint64_t>(2) << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                   float* __restrict__ fac, int n, int base, int M, int rows_per_point, int tiles,
+                   int total, unsigned* status) {
+  extern __shared__ unsigned char raw[];
+  Smem& s = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) mbar_init(&s.full[i], 1), mbar_init(&s.empty[i], 1);
+    for (int i = 0; i < 2; ++i) mbar_init(&s.tfull[i], 1), mbar_init(&s.tempty[i], 4);
+    mbar_init(&s.drain, 1);
+    s.abort = 0;
+    s.issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s.tmem_base;
+  const int per_point = tiles * tiles;
+
+  if (warp == 0) {
+    if (lane == 0) {  // ---------------------------------------------------------------- producer
+      int st = 0;
+      uint32_t ph = 0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int p = t / per_point, r = t % per_point;
+        const int ya = p * rows_per_point + (r / tiles) * BM;
+        const int yb = p * rows_per_point + (r % tiles) * BN;
+        bool ok = true;
+        for (int c = 0; c < NCHUNK; ++c) {
+          if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status)) { ok = false; break; }
+          mbar_expect_tx(&s.full[st], STAGE_BYTES);
+          unsigned char* d = s.stage[st];
+          tma_load(d, &mAhi, c * BK, ya, &s.full[st]);
+          tma_load(d + BOX_BYTES, &mAlo, c * BK, ya, &s.full[st]);
+          tma_load(d + 2 * BOX_BYTES, &mBhi, c * BK, yb, &s.full[st]);
+          tma_load(d + 3 * BOX_BYTES, &mBlo, c * BK, yb, &s.full[st]);
+          s.issued += 1;
+          if (++st == STAGES) st = 0, ph ^= 1u;
+        }
+        if (!ok) break;
+      }
+      // producer tail: every stage handed out must have been released by its MMAs
+      if (!*reinterpret_cast<volatile int*>(&s.abort))
+        for (int i = 0; i < STAGES; ++i) {
+          if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status)) break;
+          if (++st == STAGES) st = 0, ph ^= 1u;
+        }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // ---------------------------------------------------------------- MMA issuer
+      int st = 0, acc = 0;
+      uint32_t ph = 0, aph = 0;
+      int consumed = 0;
+      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        if (!mbar_wait(s, &s.tempty[acc], aph ^ 1u, status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + acc * BN;
+        bool ok = true;
+        for (int c = 0; c < NCHUNK; ++c) {
+          if (!mbar_wait(s, &s.full[st], ph, status)) { ok = false; break; }
+          ++consumed;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = saddr(s.stage[st]);
+          const uint32_t a1 = a0 + BOX_BYTES, b0 = a0 + 2 * BOX_BYTES, b1 = a0 + 3 * BOX_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 8; ++k) {
+            const uint32_t off = k * 32;  // 8 tf32 = 32 bytes inside the 128-byte swizzle row
+            mma_tf32(d, sdesc(a1 + off), sdesc(b0 + off), (c | k) ? 1u : 0u);  // a_lo b_hi
+            mma_tf32(d, sdesc(a0 + off), sdesc(b1 + off), 1u);                 // a_hi b_lo
+            mma_tf32(d, sdesc(a0 + off), sdesc(b0 + off), 1u);                 // a_hi b_hi
+          }
+          mma_commit(&s.empty[st]);
+          if (++st == STAGES) st = 0, ph ^= 1u;
+        }
+        if (!ok) break;
+        mma_commit(&s.tfull[acc]);
+        if (++acc == 2) acc = 0, aph ^= 1u;
+      }
+      // drain: loads issued but not consumed must land before the CTA exits
+      if (*reinterpret_cast<volatile int*>(&s.abort)) {
+        for (int q = consumed; q < *reinterpret_cast<volatile int*>(&s.issued); ++q) {
+          const long long t0 = clock64();
+          while (!mbar_try(&s.full[st], ph) && clock64() - t0 < kWaitCycles) {
+          }
+          if (++st == STAGES) st = 0, ph ^= 1u;
+        }
+      }
+      // every MMA issued by this thread has retired once the drain barrier completes
+      mma_commit(&s.drain);
+      const long long t0 = clock64();
+      while (!mbar_try(&s.drain, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {  // ------------------------------------------------------------------------- epilogue
+    const int sub = warp & 3;  // TMEM lane quarter this warp may access
+    int acc = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      if (!mbar_wait(s, &s.tfull[acc], aph, status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int p = t / per_point, r = t % per_point;
+      const int row = (r / tiles) * BM + sub * 32 + lane;
+      const int col0 = (r % tiles) * BN;
+      float* crow = fac + static_cast<size_t>(p) * n * n + static_cast<size_t>(base + row) * n + base;
+      const bool vec = (n & 3) == 0;
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tmem + acc * BN + ch * 32 + ((sub * 32) << 16), v);
+        if (row < M) {
+          const int c0 = col0 + ch * 32;
+          float* cp = crow + c0;
+          if (vec && c0 + 32 <= M) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              float4 x = *reinterpret_cast<float4*>(cp + j);
+              x.x -= __uint_as_float(v[j]);
+              x.y -= __uint_as_float(v[j + 1]);
+              x.z -= __uint_as_float(v[j + 2]);
+              x.w -= __uint_as_float(v[j + 3]);
+              *reinterpret_cast<float4*>(cp + j) = x;
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < M) cp[j] -= __uint_as_float(v[j]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s.tempty[acc]);
+      if (++acc == 2) acc = 0, aph ^= 1u;
+    }
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, float* base, size_t rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(KTOT), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(KTOT) * 4};
+  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct Maps {
+  void* ws = nullptr;
+  int nx = 0, rows = 0;
+  CUtensorMap m[4];
+  bool ok = false;
+};
+
+}  // namespace
+
+// Workspace: four arrays [nx][n - 128][128] floats (A_hi, A_lo, B_hi, B_lo).
+size_t tc_workspace_bytes(int nx, int n, int nbmax) {
+  if (nbmax != KTOT || n <= KTOT) return 0;
+  return 4ull * nx * static_cast<size_t>(n - KTOT) * KTOT * sizeof(float);
+}
+
+float* tc_ws_part(void* ws, int nx, int n, int part) {
+  if (!ws) return nullptr;
+  return static_cast<float*>(ws) + static_cast<size_t>(part) * nx * static_cast<size_t>(n - KTOT) * KTOT;
+}
+
+bool tc_available() {
+  int dev = 0;
+  cudaDeviceProp p;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
+  if (p.major != 10) return false;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, tc_gemm_kernel) != cudaSuccess) return false;
+  return get_encode() != nullptr;
+}
+
+void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st) {
+  static Maps maps;
+  const int rows = n - KTOT;
+  if (!maps.ok || maps.ws != ws || maps.nx != nx || maps.rows != rows) {
+    maps.ok = true;
+    for (int part = 0; part < 4; ++part)
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * rows);
+    maps.ws = ws;
+    maps.nx = nx;
+    maps.rows = rows;
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(Smem) + 1024));
+  }
+  (void)nb;
+  const int base = k0 + KTOT;
+  const int M = n - base;
+  if (M <= 0 || !maps.ok) return;
+  const int tiles = (M + BM - 1) / BM;
+  const int total = nx * tiles * tiles;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int grid = total < sms ? total : sms;
+  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(maps.m[0], maps.m[1], maps.m[2], maps.m[3], fac, n,
+                                                              base, M, rows, tiles, total, status);
+}
+
+}  // namespace bte

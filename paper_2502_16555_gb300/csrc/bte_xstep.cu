@@ -1,0 +1,299 @@
+// x half step (Algorithm 1 of arXiv 2502.16555), operator formation, FP64 refinement residual
+// (Algorithm 2), moments and small helpers. All FP64 unless templated on the storage type.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "bte_kernels.h"
+
+namespace bte {
+namespace {
+
+constexpr int kXT = 32;  // x points per CTA in the eigen-basis transforms
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// Y[a][i][x] = sum_k Uinv[i][k] F[x][a][k]  (the U^-1 contraction of Algorithm 1). Flags
+// non-finite inputs, which is where a NaN handed in by the caller is first seen.
+__global__ void x_to_eigen_kernel(const double* __restrict__ F, const double* __restrict__ Uinv,
+                                  double* __restrict__ Y, int nx, int nt, int nr,
+                                  unsigned* status) {
+  extern __shared__ double sm[];
+  const int a = blockIdx.x, x0 = blockIdx.y * kXT;
+  const int nxt = min(kXT, nx - x0);
+  const int ld = nr + 1;  // padded row
+  for (int idx = threadIdx.x; idx < nxt * nr; idx += blockDim.x) {
+    const int xx = idx / nr, k = idx % nr;
+    const double v = F[(static_cast<size_t>(x0 + xx) * nt + a) * nr + k];
+    if (status && !finite(v)) atomicOr(status, kNonFinite);
+    sm[xx * ld + k] = v;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nr * kXT; idx += blockDim.x) {
+    const int i = idx / kXT, xx = idx % kXT;
+    if (xx >= nxt) continue;
+    const double* u = Uinv + static_cast<size_t>(i) * nr;
+    double s = 0.0;
+    for (int k = 0; k < nr; ++k) s = fma(__ldg(u + k), sm[xx * ld + k], s);
+    Y[(static_cast<size_t>(a) * nr + i) * nx + x0 + xx] = s;
+  }
+}
+
+// Y2[b] = Q[b] Y[b] for every (ordinate, eigen-index) pair b: one CTA per pair, a warp per row,
+// lanes across the row (coalesced stream of Q).
+__global__ void x_apply_q_kernel(const double* __restrict__ Q, const double* __restrict__ Y,
+                                 double* __restrict__ Y2, int nx) {
+  extern __shared__ double ys[];
+  const size_t b = blockIdx.x;
+  const double* y = Y + b * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  const double* Qb = Q + b * nx * nx;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = warp; r < nx; r += nw) {
+    const double* q = Qb + static_cast<size_t>(r) * nx;
+    double s = 0.0;
+    for (int c = lane; c < nx; c += 32) s = fma(__ldg(q + c), ys[c], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) Y2[b * nx + r] = s;
+  }
+}
+
+// F[x][a][k] = sum_i U[k][i] Y2[a][i][x]; flags non-finite results.
+__global__ void x_from_eigen_kernel(const double* __restrict__ Y2, const double* __restrict__ U,
+                                    double* __restrict__ F, int nx, int nt, int nr,
+                                    unsigned* status) {
+  extern __shared__ double sm[];
+  const int a = blockIdx.x, x0 = blockIdx.y * kXT;
+  const int nxt = min(kXT, nx - x0);
+  for (int idx = threadIdx.x; idx < nr * kXT; idx += blockDim.x) {
+    const int i = idx / kXT, xx = idx % kXT;
+    sm[i * (kXT + 1) + xx] = xx < nxt ? Y2[(static_cast<size_t>(a) * nr + i) * nx + x0 + xx] : 0.0;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int idx = threadIdx.x; idx < nxt * nr; idx += blockDim.x) {
+    const int xx = idx / nr, k = idx % nr;
+    const double* u = U + static_cast<size_t>(k) * nr;
+    double s = 0.0;
+    for (int i = 0; i < nr; ++i) s = fma(__ldg(u + i), sm[i * (kXT + 1) + xx], s);
+    bad |= !finite(s);
+    F[(static_cast<size_t>(x0 + xx) * nt + a) * nr + k] = s;
+  }
+  if (status && bad) atomicOr(status, kNonFinite);
+}
+
+template <typename T>
+__global__ void v_form_kernel(const double* __restrict__ KC, const double* __restrict__ KA,
+                              const double* __restrict__ E, double E_uniform, double dt,
+                              T* __restrict__ fac, int nx, int nv) {
+  const size_t nn = static_cast<size_t>(nv) * nv;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < nn;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const double kc = KC[e], ka = KA[e];
+    const double d = (e / nv == e % nv) ? 1.0 : 0.0;
+    for (int i = 0; i < nx; ++i) {
+      const double Ei = E ? E[i] : E_uniform;
+      fac[static_cast<size_t>(i) * nn + e] = static_cast<T>(d - dt * (kc + Ei * ka));
+    }
+  }
+}
+
+// Refinement residual of one point (CTA per point), Algorithm 2 with the structured operators:
+// xS = P_S x, g = (C_s + E_i A_s) xS, r = b - x + dt P_O g.
+__global__ void residual_kernel(const double* __restrict__ X, const double* __restrict__ B,
+                                const double* __restrict__ E, double E_uniform, double dt,
+                                const double* __restrict__ Cs, const double* __restrict__ Alo,
+                                const double* __restrict__ Aup, const double* __restrict__ TO,
+                                const double* __restrict__ TS, double* __restrict__ R,
+                                double* __restrict__ ratio, int* __restrict__ conv, double tol,
+                                int nt, int nr, int nl) {
+  extern __shared__ double sm[];
+  const int i = blockIdx.x;
+  const int nv = nt * nr;
+  double* xs = sm;             // nv
+  double* xS = xs + nv;        // nl*nr
+  double* g = xS + nl * nr;    // nl*nr
+  __shared__ double red_r[32], red_b[32];
+  const double* x = X + static_cast<size_t>(i) * nv;
+  const double* b = B + static_cast<size_t>(i) * nv;
+  const double Ei = E ? E[i] : E_uniform;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) xs[v] = x[v];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nl * nr; idx += blockDim.x) {
+    const int l = idx / nr, k = idx % nr;
+    double s = 0.0;
+    for (int a = 0; a < nt; ++a) s = fma(__ldg(TS + l * nt + a), xs[a * nr + k], s);
+    xS[idx] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nl * nr; idx += blockDim.x) {
+    const int l = idx / nr, p = idx % nr;
+    const size_t off = (static_cast<size_t>(l) * nr + p) * nr;
+    double c = 0.0, f = 0.0;
+    for (int k = 0; k < nr; ++k) c = fma(__ldg(Cs + off + k), xS[l * nr + k], c);
+    if (l >= 1)
+      for (int k = 0; k < nr; ++k) f = fma(__ldg(Alo + off + k), xS[(l - 1) * nr + k], f);
+    if (l + 1 < nl)
+      for (int k = 0; k < nr; ++k) f = fma(__ldg(Aup + off + k), xS[(l + 1) * nr + k], f);
+    g[idx] = c + Ei * f;
+  }
+  __syncthreads();
+  double mr = 0.0, mb = 0.0;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const int a = v / nr, p = v % nr;
+    double s = 0.0;
+    for (int l = 0; l < nl; ++l) s = fma(__ldg(TO + a * nl + l), g[l * nr + p], s);
+    const double bv = b[v];
+    const double rv = bv - xs[v] + dt * s;
+    R[static_cast<size_t>(i) * nv + v] = rv;
+    mr = fmax(mr, fabs(rv));
+    mb = fmax(mb, fabs(bv));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) red_r[threadIdx.x >> 5] = mr, red_b[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mr = fmax(mr, red_r[w]), mb = fmax(mb, red_b[w]);
+    const double q = mb > 0.0 ? mr / mb : (mr > 0.0 ? INFINITY : 0.0);
+    ratio[i] = q;
+    conv[i] = (q <= tol) ? 1 : 0;
+  }
+}
+
+__global__ void check_conv_kernel(const int* conv, int nx, unsigned* status) {
+  bool all = true;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) all &= conv[i] != 0;
+  if (!__syncthreads_and(all) && threadIdx.x == 0) atomicOr(status, kNoConv);
+}
+
+__global__ void commit_kernel(const double* __restrict__ src, double* __restrict__ dst, size_t n,
+                              const unsigned* status) {
+  if (*status != 0u) return;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x)
+    dst[e] = src[e];
+}
+
+// ne = mom_n . F_i, mean = (mom_e . F_i)/ne, rates_j = (mom_r_j . F_i)/ne; FP64 block reductions.
+__global__ void moments_kernel(const double* __restrict__ F, const double* __restrict__ mn,
+                               const double* __restrict__ me, const double* __restrict__ mr,
+                               int n_proc, double* ne, double* mean, double* rates, int nx, int nv) {
+  __shared__ double red[32];
+  __shared__ double ne_s;
+  const int i = blockIdx.x;
+  const double* f = F + static_cast<size_t>(i) * nv;
+  auto block_sum = [&](const double* w) {
+    double s = 0.0;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) s = fma(w[v], f[v], s);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+      for (int w2 = 0; w2 < static_cast<int>(blockDim.x >> 5); ++w2) t += red[w2];
+    return t;  // valid on thread 0
+  };
+  const double n = block_sum(mn);
+  if (threadIdx.x == 0) {
+    ne_s = n;
+    if (ne) ne[i] = n;
+  }
+  __syncthreads();
+  const double nn = ne_s;
+  const double e = block_sum(me);
+  if (threadIdx.x == 0 && mean) mean[i] = nn != 0.0 ? e / nn : 0.0;
+  for (int j = 0; j < n_proc; ++j) {
+    const double r = block_sum(mr + static_cast<size_t>(j) * nv);
+    if (threadIdx.x == 0 && rates) rates[static_cast<size_t>(j) * nx + i] = nn != 0.0 ? r / nn : 0.0;
+  }
+}
+
+__global__ void fill_maxwellian_kernel(double* F, const double* ne, const double* coef, int nx,
+                                       int nt, int nr) {
+  const size_t n = static_cast<size_t>(nx) * nt * nr;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t i = e / (static_cast<size_t>(nt) * nr);
+    F[e] = ne[i] * coef[e % nr];
+  }
+}
+
+int grid_for(size_t n, int block) {
+  size_t g = (n + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  return static_cast<int>(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
+                       unsigned* status, cudaStream_t st) {
+  dim3 grid(nt, (nx + kXT - 1) / kXT);
+  const size_t smem = sizeof(double) * kXT * (nr + 1);
+  x_to_eigen_kernel<<<grid, 256, smem, st>>>(F, Uinv, Y, nx, nt, nr, status);
+}
+
+void launch_x_apply_q(const double* Q, const double* Y, double* Y2, int nx, int nt, int nr,
+                      cudaStream_t st) {
+  x_apply_q_kernel<<<nt * nr, 256, sizeof(double) * nx, st>>>(Q, Y, Y2, nx);
+}
+
+void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, int nt, int nr,
+                         unsigned* status, cudaStream_t st) {
+  dim3 grid(nt, (nx + kXT - 1) / kXT);
+  const size_t smem = sizeof(double) * nr * (kXT + 1);
+  x_from_eigen_kernel<<<grid, 256, smem, st>>>(Y2, U, F, nx, nt, nr, status);
+}
+
+template <typename T>
+void launch_v_form(const double* KC, const double* KA, const double* E, double E_uniform, double dt,
+                   T* fac, int nx, int nv, cudaStream_t st) {
+  const size_t nn = static_cast<size_t>(nv) * nv;
+  v_form_kernel<T><<<grid_for(nn, 256), 256, 0, st>>>(KC, KA, E, E_uniform, dt, fac, nx, nv);
+}
+template void launch_v_form<double>(const double*, const double*, const double*, double, double,
+                                    double*, int, int, cudaStream_t);
+template void launch_v_form<float>(const double*, const double*, const double*, double, double,
+                                   float*, int, int, cudaStream_t);
+
+void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
+                     const double* Cs, const double* Alo, const double* Aup, const double* TO,
+                     const double* TS, double* r, double* ratio, int* conv, double tol, int nx,
+                     int nt, int nr, int nl, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (static_cast<size_t>(nt) * nr + 2 * nl * nr);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  residual_kernel<<<nx, 256, smem, st>>>(x, b, E, E_uniform, dt, Cs, Alo, Aup, TO, TS, r, ratio,
+                                         conv, tol, nt, nr, nl);
+}
+
+void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st) {
+  check_conv_kernel<<<1, 256, 0, st>>>(conv, nx, status);
+}
+
+void launch_commit(const double* src, double* dst, size_t n, const unsigned* status, cudaStream_t st) {
+  commit_kernel<<<grid_for(n, 256), 256, 0, st>>>(src, dst, n, status);
+}
+
+void launch_moments(const double* F, const double* mom_n, const double* mom_e, const double* mom_r,
+                    int n_proc, double* ne, double* mean, double* rates, int nx, int nv,
+                    cudaStream_t st) {
+  moments_kernel<<<nx, 256, 0, st>>>(F, mom_n, mom_e, mom_r, n_proc, ne, mean, rates, nx, nv);
+}
+
+void launch_fill_maxwellian(double* F, const double* ne, const double* coef, int nx, int nt, int nr,
+                            cudaStream_t st) {
+  const size_t n = static_cast<size_t>(nx) * nt * nr;
+  fill_maxwellian_kernel<<<grid_for(n, 256), 256, 0, st>>>(F, ne, coef, nx, nt, nr);
+}
+
+}  // namespace bte

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances: relative L2 of f <= 1e-10 for the FP64 path; for the mixed path (FP32 factors,
+TF32x3 trailing updates, FP64 refinement) relative L2 of f <= 1e-9 per step with refinement and
+<= 1e-6 in n_e over the run.
+"""
+import numpy as np
+import pytest
+
+from oracle import bte as O
+from paper_2502_16555_gb300 import workloads as W
+from tests._lib import ensure_built
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def solver(cfg, precision="fp64", **kw):
+    from paper_2502_16555_gb300 import bte
+    return bte.Solver(cfg, precision=precision, **kw)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# ------------------------------------------------------------------ single steps, several shapes
+
+CASES = {
+    # spans several LU panels and a ragged last panel (nv = 21*12 = 252, not a multiple of 64)
+    "ragged": W.scaled(W.SMALL, nx=9, nr=21, ntheta=12),
+    "small": W.SMALL,
+    "nl_lt_ntheta": W.scaled(W.SMALL, nx=11, nr=16, ntheta=8, nl=3),
+    "odd_ntheta": W.scaled(W.SMALL, nx=7, nr=9, ntheta=5),
+    "tiny": W.scaled(W.SMALL, nx=3, nr=4, ntheta=2),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_one_step_random_state(name, precision):
+    cfg = dict(CASES[name])
+    cfg["V0"] = 300.0
+    ops = O.Operators(cfg)
+    F0 = W.random_state(ops.nx, ops.nt, ops.nr, seed=11)
+    t = 0.23 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t)
+    s = solver(cfg, precision)
+    F = to_dev(F0)
+    s.step(F, t)
+    err = rel_l2(F.cpu().numpy(), ref)
+    assert err <= (1e-10 if precision == "fp64" else 1e-9), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonuniform_field_per_point(precision):
+    cfg = W.scaled(W.SMALL, nx=12, nr=16, ntheta=8)
+    ops = O.Operators(cfg)
+    F0 = W.random_state(ops.nx, ops.nt, ops.nr, seed=12)
+    E = W.random_field(ops.nx, seed=3, e0=8e3)
+    ref = ops.step(F0, 0.0, E=E)
+    s = solver(cfg, precision)
+    F = to_dev(F0)
+    s.step(F, 0.0, E=to_dev(E))
+    assert rel_l2(F.cpu().numpy(), ref) <= (1e-10 if precision == "fp64" else 1e-9)
+
+
+# ------------------------------------------------------------------ the small workload, full run
+
+def test_small_workload_fp64_full_run():
+    """32 x (16 x 16), 200 steps of T_RF/1000 from the Maxwellian IC: rel-L2(f) <= 1e-10."""
+    cfg = W.SMALL
+    F_ref, t_end, ops = O.run(cfg)
+    s = solver(cfg, "fp64")
+    F = s.initial_state()
+    F_ic = ops.initial_state()
+    assert rel_l2(F.cpu().numpy(), F_ic) < 1e-13
+    s.run(F, cfg["steps"], 0.0)
+    assert rel_l2(F.cpu().numpy(), F_ref) <= 1e-10
+    ne, mean, rates = s.moments(F)
+    ne_r, mean_r, rates_r = ops.moments(F_ref)
+    assert rel_l2(ne.cpu().numpy(), ne_r) <= 1e-10
+    inner = np.abs(ne_r) > 1e-6 * np.abs(ne_r).max()
+    assert np.allclose(mean.cpu().numpy()[inner], mean_r[inner], rtol=1e-9)
+    assert np.allclose(rates.cpu().numpy()[:, inner], rates_r[:, inner], rtol=1e-9)
+
+
+def test_small_workload_mixed_full_run():
+    cfg = W.SMALL
+    F_ref, t_end, ops = O.run(cfg)
+    s = solver(cfg, "mixed")
+    F = s.initial_state()
+    s.run(F, cfg["steps"], 0.0)
+    ne, _, _ = s.moments(F)
+    ne_r, _, _ = ops.moments(F_ref)
+    assert rel_l2(ne.cpu().numpy(), ne_r) <= 1e-6
+    assert rel_l2(F.cpu().numpy(), F_ref) <= 1e-6
+
+
+# ------------------------------------------------------------------ full-size workload, one step
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_medium_workload_one_step(precision):
+    """Nx=128, Nr=64, Ntheta=32 (Nv = 2048): one step at the field maximum vs the oracle."""
+    cfg = W.MEDIUM
+    ops = O.Operators(cfg)
+    F0 = ops.initial_state()
+    t = 0.25 / W.RF_FREQ_HZ - 0.5 * cfg["dt_s"]   # E(t + dt/2) at its peak
+    ref = ops.step(F0, t)
+    s = solver(cfg, precision)
+    F = s.initial_state()
+    assert rel_l2(F.cpu().numpy(), F0) < 1e-13
+    s.step(F, t)
+    err = rel_l2(F.cpu().numpy(), ref)
+    assert err <= (1e-10 if precision == "fp64" else 1e-9), err
+    ne, _, _ = s.moments(F)
+    ne_r, _, _ = ops.moments(ref)
+    assert rel_l2(ne.cpu().numpy(), ne_r) <= (1e-10 if precision == "fp64" else 1e-8)
+
+
+# ------------------------------------------------------------------ tensor-core trailing update
+
+@pytest.mark.parametrize("shape", [(4, 32, 8), (6, 24, 16), (5, 40, 13)])
+def test_tensor_core_update_against_oracle_and_simt(shape):
+    """Mixed path with the tcgen05 TF32x3 trailing update vs the CUDA-core FP32 update and vs the
+    oracle: nv = 256, 384 and 520 give one to three trailing updates, the last one ragged."""
+    nx, nr, nt = shape
+    cfg = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=nt)
+    cfg["V0"] = 400.0
+    ops = O.Operators(cfg)
+    F0 = W.random_state(nx, nt, nr, seed=31)
+    t = 0.21 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t)
+    s_tc = solver(cfg, "mixed")
+    s_simt = solver(cfg, "mixed", simt_gemm=True)
+    assert s_simt.info()["tensor_cores"] == 0
+    F1, F2 = to_dev(F0), to_dev(F0)
+    s_tc.step(F1, t)
+    s_simt.step(F2, t)
+    assert rel_l2(F2.cpu().numpy(), ref) <= 1e-9
+    assert rel_l2(F1.cpu().numpy(), ref) <= 1e-9
+    assert s_tc.info()["tensor_cores"] == 1
+
+
+# ------------------------------------------------------------------ entry points and errors
+
+def test_step_host_matches_device_step():
+    cfg = W.scaled(W.SMALL, nx=10, nr=12, ntheta=6)
+    F0 = W.random_state(10, 6, 12, seed=21)
+    s = solver(cfg)
+    Fd = to_dev(F0)
+    s.step(Fd, 1e-9)
+    Fh = F0.copy()
+    s.step_host(Fh, 1e-9)
+    assert np.array_equal(Fh, Fd.cpu().numpy())
+
+
+def test_nonfinite_input_is_reported_and_state_kept():
+    from paper_2502_16555_gb300 import bte
+    cfg = W.scaled(W.SMALL, nx=6, nr=8, ntheta=4)
+    F0 = W.random_state(6, 4, 8, seed=22)
+    F0[2, 1, 3] = np.nan
+    s = solver(cfg)
+    F = to_dev(F0)
+    with pytest.raises(bte.BteError) as e:
+        s.step(F, 0.0)
+    assert e.value.status == bte.ENONFINITE
+    got = F.cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(F0)) and np.array_equal(got[~np.isnan(got)], F0[~np.isnan(F0)])
+    # the handle stays usable
+    F2 = to_dev(W.random_state(6, 4, 8, seed=23))
+    s.step(F2, 0.0)
+
+
+def test_refinement_budget_exhausted_is_reported():
+    from paper_2502_16555_gb300 import bte
+    cfg = W.scaled(W.SMALL, nx=6, nr=8, ntheta=4)
+    F0 = W.random_state(6, 4, 8, seed=24)
+    s = solver(cfg, "mixed", refine_tol=1e-300, refine_max=1)
+    F = to_dev(F0)
+    with pytest.raises(bte.BteError) as e:
+        s.step(F, 0.0)
+    assert e.value.status == bte.ENOCONV
+    assert np.array_equal(F.cpu().numpy(), F0)
+
+
+def test_moments_of_maxwellian_match_oracle():
+    cfg = W.scaled(W.SMALL, nx=9, nr=40, ntheta=6)
+    ops = O.Operators(cfg)
+    s = solver(cfg)
+    F = s.initial_state()
+    ne, mean, rates = s.moments(F)
+    ne_r, mean_r, rates_r = ops.moments(ops.initial_state())
+    assert rel_l2(ne.cpu().numpy(), ne_r) < 1e-13
+    inner = ne_r != 0
+    assert np.allclose(mean.cpu().numpy()[inner], mean_r[inner], rtol=1e-12)
+    assert np.allclose(rates.cpu().numpy()[:, inner], rates_r[:, inner], rtol=1e-11)
+    assert np.all(mean.cpu().numpy()[~inner] == 0)

@@ -1,0 +1,112 @@
+"""CPU-only checks of libbte: it loads, exports every symbol of include/bte.h, validates its
+arguments, and its independent C++ host assembly matches the oracle's operators."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import bte as O
+from paper_2502_16555_gb300 import workloads as W
+from tests._lib import ensure_built
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "bte.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bte_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ensure_built()
+    from paper_2502_16555_gb300 import bte
+    return bte.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2502_16555_gb300 import bte
+    assert sorted(bte.EXPORTS) == names
+
+
+def _solver(cfg, **kw):
+    from paper_2502_16555_gb300 import bte
+    return bte.Solver(cfg, host_only=True, **kw)
+
+
+@pytest.mark.parametrize("name,cfg", [
+    ("small", W.SMALL),
+    ("nl_lt_ntheta", W.scaled(W.MEDIUM, nx=16, nr=24, ntheta=8, nl=3)),
+    ("odd_ntheta", W.scaled(W.SMALL, nx=7, nr=9, ntheta=5)),
+    ("table_and_nu", dict(W.scaled(W.SMALL, nx=5, nr=12, ntheta=4), processes=[
+        W.process("elastic", "table", eps_eV=[0.0, 5.0, 30.0], sigma_m2=[1e-19, 2e-19, 5e-20]),
+        W.process("excitation", "table", threshold_eV=11.55, eps_eV=[11.55, 20.0, 40.0], sigma_m2=[0.0, 3e-21, 1e-21]),
+        W.process("elastic", "nu", sigma0=1e-13)])),
+])
+def test_host_assembly_matches_oracle(name, cfg):
+    s = _solver(cfg)
+    ops = O.Operators(cfg)
+
+    def rel(a, b):
+        return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+    assert rel(s.operator("x"), ops.x) < 1e-15
+    assert rel(s.operator("Dx"), ops.Dx) < 1e-12
+    assert rel(s.operator("mu"), ops.mu) < 1e-14
+    assert rel(s.operator("M"), ops.M) < 1e-13
+    assert rel(s.operator("lambda"), ops.lam) < 1e-12
+    assert rel(s.operator("KC"), ops.KC) < 1e-11
+    assert rel(s.operator("KA"), ops.KA) < 1e-11
+    U, Ui, lam = s.operator("U"), s.operator("Uinv"), s.operator("lambda")
+    assert rel(U @ np.diag(lam) @ Ui, np.linalg.solve(ops.M, ops.G)) < 1e-11
+    assert rel(s.operator("mom_n"), ops.mom_n.ravel()) < 1e-13
+    assert rel(s.operator("mom_e"), ops.mom_e.ravel()) < 1e-13
+    assert rel(s.operator("mom_r"), np.array([r.ravel() for r in ops.mom_r])) < 1e-12
+    # Q_ij through Algorithm 1 reproduces the oracle's x half step
+    Q = s.operator("Q")
+    F = W.random_state(ops.nx, ops.nt, ops.nr, seed=1)
+    out = np.empty_like(F)
+    for a in range(ops.nt):
+        Y = F[:, a, :] @ Ui.T
+        for i in range(ops.nr):
+            Y[:, i] = Q[a, i] @ Y[:, i]
+        out[:, a, :] = Y @ U.T
+    assert rel(out, ops.x_halfstep(F)) < 1e-12
+
+
+def test_create_rejects_bad_configs(lib):
+    from paper_2502_16555_gb300 import bte
+    bad = [dict(nx=2), dict(nr=3), dict(ntheta=1), dict(nl=9, ntheta=8), dict(dt_s=0.0), dict(p_Torr=-1.0)]
+    for kw in bad:
+        cfg = W.scaled(W.SMALL, **{k: v for k, v in kw.items() if k != "nl"})
+        if "nl" in kw:
+            cfg["nl"] = kw["nl"]
+        with pytest.raises(bte.BteError) as e:
+            bte.Solver(cfg, host_only=True)
+        assert e.value.status == bte.EINVAL, kw
+
+
+def test_bad_process_lists(lib):
+    from paper_2502_16555_gb300 import bte
+    s = _solver(W.scaled(W.SMALL, nx=5, nr=6, ntheta=4))
+    with pytest.raises(bte.BteError):
+        s.set_cross_sections([W.process("excitation", "linear", 1e-21, 0.0)])
+    with pytest.raises(bte.BteError):
+        s.set_cross_sections([W.process("elastic", "table", eps_eV=[1.0, 0.5], sigma_m2=[1.0, 1.0])])
+
+
+def test_host_only_handle_refuses_device_work(lib):
+    from paper_2502_16555_gb300 import bte
+    s = _solver(W.scaled(W.SMALL, nx=5, nr=6, ntheta=4))
+    st = lib.bte_step(s.h, ctypes.c_void_p(1), None, 0.0, 1.0, 1.0)
+    assert st == bte.ESTATE
+    st = lib.bte_step(s.h, None, None, 0.0, 1.0, 1.0)
+    assert st == bte.EINVAL
+    assert lib.bte_destroy(None) == bte.OK
