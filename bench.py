@@ -240,7 +240,7 @@ def run_ours(args, rank, world):
 
     # ---- mixed precision (the headline)
     s = bte.Solver(cfg, precision="mixed")
-    tc = False
+    tc = bool(s.info()["tensor_cores"])
     F = s.initial_state()
     F0 = F.clone()
     s.run(F, args.warmup, 0.0)
@@ -274,39 +274,45 @@ def run_ours(args, rank, world):
     value = world * dof / (ms / 1e3)
 
     # ---- plain FP64 on the same GPU, same steps from the same state
-    s64 = bte.Solver(cfg, precision="fp64")
-    G = F0.clone()
-    n64 = args.warmup + args.steps
-    s64.run(G, args.warmup, 0.0)
-    barrier()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record()
-    s64.run(G, args.steps, args.warmup * dt)
-    f1.record()
-    barrier()
-    ms64 = f0.elapsed_time(f1) / args.steps
-    # accuracy of the mixed path against FP64 after the same n64 steps
-    Fm = F0.clone()
-    s.run(Fm, n64, 0.0)
-    ne_m, _, _ = s.moments(Fm)
-    ne_d, _, _ = s64.moments(G)
-    torch.cuda.synchronize()
-    rel_f = float(torch.linalg.norm(Fm - G) / torch.linalg.norm(G))
-    rel_ne = float(torch.linalg.norm(ne_m - ne_d) / torch.linalg.norm(ne_d))
-    prof64 = None
-    del s64
+    fp64 = None
+    if not args.no_fp64:
+        s64 = bte.Solver(cfg, precision="fp64")
+        G = F0.clone()
+        n64 = args.warmup + args.steps
+        s64.run(G, args.warmup, 0.0)
+        barrier()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        s64.run(G, args.steps, args.warmup * dt)
+        f1.record()
+        barrier()
+        ms64 = f0.elapsed_time(f1) / args.steps
+        # accuracy of the mixed path against FP64 after the same n64 steps
+        Fm = F0.clone()
+        s.run(Fm, n64, 0.0)
+        ne_m, _, _ = s.moments(Fm)
+        ne_d, _, _ = s64.moments(G)
+        torch.cuda.synchronize()
+        fp64 = {"value": world * dof / (ms64 / 1e3), "ms_per_step": ms64, "unit": UNIT,
+                "accuracy_mixed_vs_fp64": {"steps": n64,
+                                           "rel_l2_f": float(torch.linalg.norm(Fm - G) / torch.linalg.norm(G)),
+                                           "rel_l2_ne": float(torch.linalg.norm(ne_m - ne_d) / torch.linalg.norm(ne_d))}}
+        del s64
 
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    Fh = torch.empty(F.shape, dtype=torch.float64, pin_memory=True).numpy()
-    Fh[...] = F0.cpu().numpy()
-    s.step_host(Fh, 0.0)
-    n_e2e = max(3, min(args.steps, 20))
-    barrier()
-    t0 = time.perf_counter()
-    for i in range(n_e2e):
-        s.step_host(Fh, (i + 1) * dt)
-    e2e_s = (time.perf_counter() - t0) / n_e2e
-    e2e_val = world * dof / e2e_s
+    e2e = None
+    if not args.no_e2e:
+        Fh = torch.empty(F.shape, dtype=torch.float64, pin_memory=True).numpy()
+        Fh[...] = F0.cpu().numpy()
+        s.step_host(Fh, 0.0)
+        n_e2e = max(3, min(args.steps, 20))
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(n_e2e):
+            s.step_host(Fh, (i + 1) * dt)
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        e2e = {"value": world * dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * dof,
+               "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"}
 
     if rank != 0:
         if dist:
@@ -321,12 +327,10 @@ def run_ours(args, rank, world):
                    "nv": cfg["nr"] * cfg["ntheta"], "dof": dof, "precision": "mixed",
                    "l2": "working set > L2: 2.1 GB of per-point FP32 factors streamed every step",
                    "parallelism": f"replicas x{world}"},
-        "fp64": {"value": world * dof / (ms64 / 1e3), "ms_per_step": ms64, "unit": UNIT},
-        "speedup_mixed_over_fp64": ms64 / ms,
-        "accuracy_mixed_vs_fp64": {"steps": n64, "rel_l2_f": rel_f, "rel_l2_ne": rel_ne},
+        "fp64": fp64,
+        "speedup_mixed_over_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
         "clocks": clk.summary(),
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * dof, "d2h_bytes_per_step": 8 * dof,
-                "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"},
+        "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roofline(cfg, "mixed", prof, args.steps, peaks, tc),
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
@@ -346,6 +350,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

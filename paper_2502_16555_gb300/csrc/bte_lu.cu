@@ -30,28 +30,74 @@ __device__ __forceinline__ T tabs(T v) { return v < T(0) ? -v : v; }
 // panel rows k0..k0+nb-1, then d pairs (destination row >= k0+nb, origin row in [k0, k0+nb)).
 __host__ __device__ constexpr int perm_stride(int nbmax) { return 1 + nbmax + 2 * nbmax; }
 
+// Shared-memory plan of lu_panel (elements of T unless noted):
+//   R0   max(m0 * (W+1), 2 * nb * (nb+1))   sub-panel S (later L11 and inv(L11) staging)
+//   U    W * nbmax                          U rows of the current sub-panel, right part
+//   SB   2W * nbmax                         row-swap staging of the other panel columns
+//   ints m0 (orig) + W (local pivots) + 2W (slot rows) + 2W (slot contents)
+template <typename T>
+__host__ __device__ inline size_t panel_smem_bytes(int m0, int nb, int nbmax, int W) {
+  size_t r0 = static_cast<size_t>(m0) * (W + 1);
+  const size_t linv = 2ull * nb * (nb + 1);
+  if (linv > r0) r0 = linv;
+  const size_t elems = r0 + static_cast<size_t>(W) * nbmax + 2ull * W * nbmax;
+  return elems * sizeof(T) + (static_cast<size_t>(m0) + 5 * W) * sizeof(int) + 16;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int* __restrict__ piv,
                                                        int* __restrict__ perm, T* __restrict__ linv,
                                                        int n, int k0, int nb, int nbmax, int W,
                                                        unsigned* status, float* __restrict__ ws_hi,
                                                        float* __restrict__ ws_lo) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = W + 1;
-  T* S = reinterpret_cast<T*>(smraw);                                 // (n-k0) x ld
-  int* orig = reinterpret_cast<int*>(S + static_cast<size_t>(n - k0) * ld);  // n-k0
+  const int m0 = n - k0;
+  size_t r0 = static_cast<size_t>(m0) * ld;
+  if (static_cast<size_t>(2) * nb * (nb + 1) > r0) r0 = static_cast<size_t>(2) * nb * (nb + 1);
+  T* S = reinterpret_cast<T*>(smraw);
+  T* Ub = S + r0;
+  T* SB = Ub + static_cast<size_t>(W) * nbmax;
+  int* orig = reinterpret_cast<int*>(SB + static_cast<size_t>(2) * W * nbmax);
+  int* lp = orig + m0;          // local pivots of the current sub-panel (relative to c0)
+  int* slot_row = lp + W;       // rows of the swap slots (2W)
+  int* content = slot_row + 2 * W;  // 2W
   __shared__ T red_v[16];
   __shared__ int red_i[16];
-  __shared__ int s_pr;
-  __shared__ int s_cnt;
+  __shared__ int s_pr, s_cnt, s_nslot;
+  __shared__ int pslot[32];
 
   const int mat = blockIdx.x;
   T* A = fac + static_cast<size_t>(mat) * n * n;
   int* ip = piv + static_cast<size_t>(mat) * n;
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
 
-  for (int r = tid; r < n - k0; r += bd) orig[r] = k0 + r;
+  for (int r = tid; r < m0; r += bd) orig[r] = k0 + r;
   bool bad_pivot = false;
+
+  // block argmax of (v, i): larger v wins, ties to the smaller i; result in s_pr (needs a barrier
+  // before it is read)
+  auto block_argmax = [&](T best, int bi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+    }
+    if (lane == 0) red_v[warp] = best, red_i[warp] = bi;
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < nwarp ? red_v[lane] : T(-1);
+      bi = lane < nwarp ? red_i[lane] : 0x7fffffff;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+      }
+      if (lane == 0) s_pr = bi;
+    }
+  };
 
   for (int c0 = k0; c0 < k0 + nb; c0 += W) {
     const int w = min(W, k0 + nb - c0);
@@ -61,90 +107,140 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
       S[r * ld + jj] = A[static_cast<size_t>(c0 + r) * n + c0 + jj];
     }
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-      // pivot: largest |S[r][j]|, r >= j; ties go to the smaller row
+    {
       T best = T(-1);
-      int bi = j;
-      for (int r = j + tid; r < m; r += bd) {
-        const T v = tabs(S[r * ld + j]);
+      int bi = 0;
+      for (int r = tid; r < m; r += bd) {
+        const T v = tabs(S[r * ld]);
         if (v > best) best = v, bi = r;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
-      }
-      if (lane == 0) red_v[warp] = best, red_i[warp] = bi;
-      __syncthreads();
-      if (warp == 0) {
-        best = lane < (bd >> 5) ? red_v[lane] : T(-1);
-        bi = lane < (bd >> 5) ? red_i[lane] : 0x7fffffff;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
-        }
-        if (lane == 0) s_pr = (bi >= j && bi < m) ? bi : j;
-      }
-      __syncthreads();
-      const int pr = s_pr;
-      if (tid == 0) ip[c0 + j] = c0 + pr;
-      if (pr != j) {
+      block_argmax(best, bi);
+    }
+    for (int j = 0; j < w; ++j) {
+      __syncthreads();  // s_pr of column j is published
+      int pr = s_pr;
+      if (pr < j || pr >= m) pr = j;
+      if (pr != j)
         for (int jj = tid; jj < w; jj += bd) {
           const T t = S[j * ld + jj];
           S[j * ld + jj] = S[pr * ld + jj];
           S[pr * ld + jj] = t;
         }
-        const int nleft = c0 - k0, nright = k0 + nb - (c0 + w);
-        for (int q = tid; q < nleft + nright; q += bd) {
-          const int col = q < nleft ? k0 + q : c0 + w + (q - nleft);
-          T* a1 = A + static_cast<size_t>(c0 + j) * n + col;
-          T* a2 = A + static_cast<size_t>(c0 + pr) * n + col;
-          const T t = *a1;
-          *a1 = *a2;
-          *a2 = t;
-        }
-        if (tid == 0) {
-          const int t = orig[c0 + j - k0];
-          orig[c0 + j - k0] = orig[c0 + pr - k0];
-          orig[c0 + pr - k0] = t;
-        }
-      }
-      __syncthreads();
+      if (tid == 0) lp[j] = pr;
+      __syncthreads();  // pivot row in place
       const T pv = S[j * ld + j];
       if (tid == 0 && (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv)))) bad_pivot = true;
       const T inv = (pv != T(0)) ? T(1) / pv : T(0);
+      T best = T(-1);
+      int bi = j + 1;
       for (int r = j + 1 + tid; r < m; r += bd) {
         const T l = S[r * ld + j] * inv;
         S[r * ld + j] = l;
         for (int jj = j + 1; jj < w; ++jj) S[r * ld + jj] -= l * S[j * ld + jj];
+        if (j + 1 < w) {
+          const T v = tabs(S[r * ld + j + 1]);
+          if (v > best) best = v, bi = r;
+        }
       }
-      __syncthreads();
+      if (j + 1 < w) block_argmax(best, bi);
     }
+    __syncthreads();
     for (int idx = tid; idx < m * w; idx += bd) {
       const int r = idx / w, jj = idx % w;
       A[static_cast<size_t>(c0 + r) * n + c0 + jj] = S[r * ld + jj];
+    }
+    // the sub-panel's row permutation, as slots: slot k < w is row c0+k, further slots are the
+    // distinct pivot rows below the sub-panel; content[k] = slot whose original row ends in slot k
+    if (tid == 0) {
+      int ns = w;
+      for (int k = 0; k < w; ++k) slot_row[k] = c0 + k;
+      for (int j = 0; j < w; ++j) {
+        const int p = lp[j];
+        int sl = p;
+        if (p >= w) {
+          sl = -1;
+          for (int q = w; q < ns; ++q)
+            if (slot_row[q] == c0 + p) sl = q;
+          if (sl < 0) slot_row[sl = ns++] = c0 + p;
+        }
+        pslot[j] = sl;
+        ip[c0 + j] = c0 + p;
+        const int a = c0 + j - k0, b = c0 + p - k0;
+        const int t = orig[a];
+        orig[a] = orig[b];
+        orig[b] = t;
+      }
+      for (int k = 0; k < ns; ++k) content[k] = k;
+      for (int j = 0; j < w; ++j) {
+        const int t = content[j];
+        content[j] = content[pslot[j]];
+        content[pslot[j]] = t;
+      }
+      s_nslot = ns;
+    }
+    __syncthreads();
+    // apply it to the other columns of the outer panel: [k0, c0) and [c0+w, k0+nb)
+    const int nsl = s_nslot, nleft = c0 - k0, noth = nb - w;
+    for (int idx = tid; idx < nsl * noth; idx += bd) {
+      const int k = idx / noth, q = idx % noth;
+      const int col = q < nleft ? k0 + q : c0 + w + (q - nleft);
+      SB[k * noth + q] = A[static_cast<size_t>(slot_row[k]) * n + col];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nsl * noth; idx += bd) {
+      const int k = idx / noth, q = idx % noth;
+      const int col = q < nleft ? k0 + q : c0 + w + (q - nleft);
+      A[static_cast<size_t>(slot_row[k]) * n + col] = SB[content[k] * noth + q];
     }
     __syncthreads();
     // right-looking update of the not yet factored columns of this outer panel
     const int rw = k0 + nb - (c0 + w);
     if (rw > 0) {
       const int cb = c0 + w;
-      for (int col = tid; col < rw; col += bd) {
-        for (int jr = 1; jr < w; ++jr) {
-          T x = A[static_cast<size_t>(c0 + jr) * n + cb + col];
-          for (int jj = 0; jj < jr; ++jj) x -= S[jr * ld + jj] * A[static_cast<size_t>(c0 + jj) * n + cb + col];
-          A[static_cast<size_t>(c0 + jr) * n + cb + col] = x;
-        }
+      for (int idx = tid; idx < w * rw; idx += bd) {
+        const int jr = idx / rw, q = idx % rw;
+        Ub[jr * nbmax + q] = A[static_cast<size_t>(c0 + jr) * n + cb + q];
       }
       __syncthreads();
-      for (int idx = tid; idx < (m - w) * rw; idx += bd) {
-        const int r = w + idx / rw, col = idx % rw;
-        T acc = A[static_cast<size_t>(c0 + r) * n + cb + col];
-        for (int jj = 0; jj < w; ++jj) acc -= S[r * ld + jj] * A[static_cast<size_t>(c0 + jj) * n + cb + col];
-        A[static_cast<size_t>(c0 + r) * n + cb + col] = acc;
+      for (int q = tid; q < rw; q += bd)
+        for (int jr = 1; jr < w; ++jr) {
+          T x = Ub[jr * nbmax + q];
+          for (int jj = 0; jj < jr; ++jj) x -= S[jr * ld + jj] * Ub[jj * nbmax + q];
+          Ub[jr * nbmax + q] = x;
+        }
+      __syncthreads();
+      for (int idx = tid; idx < w * rw; idx += bd) {
+        const int jr = idx / rw, q = idx % rw;
+        A[static_cast<size_t>(c0 + jr) * n + cb + q] = Ub[jr * nbmax + q];
+      }
+      // rows below: A[c0+r][cb+q] -= S[r][:w] . Ub[:w][q], 4 x 4 register tiles
+      const int ntr = (m - w + 3) / 4, ntc = (rw + 3) / 4;
+      for (int t = tid; t < ntr * ntc; t += bd) {
+        const int r0 = w + 4 * (t / ntc), q0 = 4 * (t % ntc);
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][c] = T(0);
+        for (int jj = 0; jj < w; ++jj) {
+          T sv[4], uv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) sv[i] = (r0 + i < m) ? S[(r0 + i) * ld + jj] : T(0);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) uv[c] = (q0 + c < rw) ? Ub[jj * nbmax + q0 + c] : T(0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][c] += sv[i] * uv[c];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (r0 + i >= m) continue;
+          T* row = A + static_cast<size_t>(c0 + r0 + i) * n + cb + q0;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (q0 + c < rw) row[c] -= acc[i][c];
+        }
       }
       __syncthreads();
     }
@@ -156,7 +252,7 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
   if (tid == 0) s_cnt = 0;
   __syncthreads();
   for (int j = tid; j < nb; j += bd) pr_rec[1 + j] = orig[j];
-  for (int r = nb + tid; r < n - k0; r += bd) {
+  for (int r = nb + tid; r < m0; r += bd) {
     if (orig[r] != k0 + r) {
       const int slot = atomicAdd(&s_cnt, 1);
       pr_rec[1 + nbmax + 2 * slot] = k0 + r;
@@ -180,16 +276,28 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
     }
   }
 
-  // inv(L11), L11 = unit lower part of A[k0:k0+nb, k0:k0+nb]
-  T* X = linv + static_cast<size_t>(mat) * nbmax * nbmax;
+  // inv(L11), L11 = unit lower part of A[k0:k0+nb, k0:k0+nb], staged in shared memory
+  const int ldl = nb + 1;
+  T* Ls = S;
+  T* Xs = S + static_cast<size_t>(nb) * ldl;
+  for (int idx = tid; idx < nb * nb; idx += bd) {
+    const int r = idx / nb, c = idx % nb;
+    Ls[r * ldl + c] = A[static_cast<size_t>(k0 + r) * n + k0 + c];
+  }
+  __syncthreads();
   for (int c = tid; c < nb; c += bd) {
-    for (int r = 0; r < c; ++r) X[r * nbmax + c] = T(0);
-    X[c * nbmax + c] = T(1);
+    Xs[c * ldl + c] = T(1);
     for (int r = c + 1; r < nb; ++r) {
-      T s = T(0);
-      for (int j = c; j < r; ++j) s += A[static_cast<size_t>(k0 + r) * n + k0 + j] * X[j * nbmax + c];
-      X[r * nbmax + c] = -s;
+      T acc = T(0);
+      for (int j = c; j < r; ++j) acc += Ls[r * ldl + j] * Xs[j * ldl + c];
+      Xs[r * ldl + c] = -acc;
     }
+  }
+  __syncthreads();
+  T* X = linv + static_cast<size_t>(mat) * nbmax * nbmax;
+  for (int idx = tid; idx < nb * nb; idx += bd) {
+    const int r = idx / nb, c = idx % nb;
+    X[r * nbmax + c] = c <= r ? Xs[r * ldl + c] : T(0);
   }
 }
 
@@ -197,13 +305,19 @@ constexpr int kTrsmCols = 64;
 constexpr int kTrsmLd = kTrsmCols + 1;  // padded smem row (transposed reads)
 
 template <typename T>
+__host__ __device__ inline size_t trsm_smem_bytes(int nb) {
+  return (2ull * nb * kTrsmLd + static_cast<size_t>(nb) * (nb + 1)) * sizeof(T);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, const int* __restrict__ perm,
                                                            const T* __restrict__ linv, int n, int k0,
                                                            int nb, int nbmax, float* __restrict__ ws_hi,
                                                            float* __restrict__ ws_lo) {
-  extern __shared__ unsigned char smraw[];
-  T* top = reinterpret_cast<T*>(smraw);                 // original panel rows, later U12   nb x ld
-  T* Bs = top + static_cast<size_t>(nb) * kTrsmLd;       // permuted panel rows             nb x ld
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* top = reinterpret_cast<T*>(smraw);                  // original panel rows, later U12   nb x ld
+  T* Bs = top + static_cast<size_t>(nb) * kTrsmLd;        // permuted panel rows             nb x ld
+  T* Xs = Bs + static_cast<size_t>(nb) * kTrsmLd;         // inv(L11)                        nb x (nb+1)
   const int mat = blockIdx.x;
   const int C0 = k0 + nb + blockIdx.y * kTrsmCols;
   const int ncol = min(kTrsmCols, n - C0);
@@ -211,7 +325,11 @@ __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, 
   const int* rec = perm + static_cast<size_t>(mat) * perm_stride(nbmax);
   const T* X = linv + static_cast<size_t>(mat) * nbmax * nbmax;
   const int tid = threadIdx.x, bd = blockDim.x;
-  // read phase: original panel rows, and the final content of the panel rows
+  // read phase: inv(L11), the original panel rows, and the final content of the panel rows
+  for (int idx = tid; idx < nb * nb; idx += bd) {
+    const int r = idx / nb, c = idx % nb;
+    Xs[r * (nb + 1) + c] = X[r * nbmax + c];
+  }
   for (int idx = tid; idx < nb * kTrsmCols; idx += bd) {
     const int r = idx / kTrsmCols, c = idx % kTrsmCols;
     top[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(k0 + r) * n + C0 + c] : T(0);
@@ -228,12 +346,32 @@ __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, 
     A[static_cast<size_t>(dst) * n + C0 + c] = top[(src - k0) * kTrsmLd + c];
   }
   __syncthreads();
-  // U12 = inv(L11) P A12 (inv(L11) unit lower), staged in `top`
-  for (int idx = tid; idx < nb * kTrsmCols; idx += bd) {
-    const int r = idx / kTrsmCols, c = idx % kTrsmCols;
-    T s = Bs[r * kTrsmLd + c];
-    for (int j = 0; j < r; ++j) s += X[r * nbmax + j] * Bs[j * kTrsmLd + c];
-    top[r * kTrsmLd + c] = s;
+  // U12 = inv(L11) P A12 (inv(L11) unit lower), 4 x 4 register tiles, staged in `top`
+  const int ntr = (nb + 3) / 4;
+  for (int t = tid; t < ntr * (kTrsmCols / 4); t += bd) {
+    const int r0 = 4 * (t / (kTrsmCols / 4)), q0 = 4 * (t % (kTrsmCols / 4));
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][c] = T(0);
+    const int jmax = min(r0 + 4, nb);
+    for (int j = 0; j < jmax; ++j) {
+      T bv[4], xv[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[j * kTrsmLd + q0 + c];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = (r0 + i < nb && j <= r0 + i) ? Xs[(r0 + i) * (nb + 1) + j] : T(0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[i][c] += xv[i] * bv[c];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (r0 + i < nb)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) top[(r0 + i) * kTrsmLd + q0 + c] = acc[i][c];
   }
   __syncthreads();
   for (int idx = tid; idx < nb * kTrsmCols; idx += bd) {
@@ -312,13 +450,16 @@ __global__ void __launch_bounds__(256) lu_gemm_simt_kernel(T* __restrict__ fac, 
 }
 
 // x = A^-1 b for one point per CTA, with the lazily applied pivots; Tc is the arithmetic type.
+// Column chunks of 32: the 32 x 32 diagonal block is staged in shared memory and solved by one
+// warp, then every thread updates whole rows below (forward) or above (backward) the chunk.
 template <typename T, typename Tc>
 __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fac, const int* __restrict__ piv,
                                                         const double* __restrict__ b, double* __restrict__ x,
                                                         int n, int nb, const int* __restrict__ conv,
                                                         int accumulate) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   Tc* s = reinterpret_cast<Tc*>(smraw);
+  __shared__ Tc dblk[32][33];
   const int mat = blockIdx.x;
   if (conv && conv[mat]) return;
   const T* A = fac + static_cast<size_t>(mat) * n * n;
@@ -337,14 +478,18 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
           s[p] = t;
         }
       }
-    __syncthreads();
     for (int j0 = k0; j0 < k0 + kb; j0 += 32) {
       const int cw = min(32, k0 + kb - j0);
+      for (int idx = tid; idx < cw * cw; idx += bd) {
+        const int r = idx / cw, c = idx % cw;
+        dblk[r][c] = static_cast<Tc>(A[static_cast<size_t>(j0 + r) * n + j0 + c]);
+      }
+      __syncthreads();
       if (warp == 0) {
         Tc v = lane < cw ? s[j0 + lane] : Tc(0);
         for (int jj = 0; jj < cw; ++jj) {
           const Tc xj = __shfl_sync(0xffffffffu, v, jj);
-          if (lane > jj && lane < cw) v -= static_cast<Tc>(A[static_cast<size_t>(j0 + lane) * n + j0 + jj]) * xj;
+          if (lane > jj && lane < cw) v -= dblk[lane][jj] * xj;
         }
         if (lane < cw) s[j0 + lane] = v;
       }
@@ -352,6 +497,7 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
       for (int r = j0 + cw + tid; r < n; r += bd) {
         const T* a = A + static_cast<size_t>(r) * n + j0;
         Tc acc = Tc(0);
+#pragma unroll 8
         for (int jj = 0; jj < cw; ++jj) acc += static_cast<Tc>(a[jj]) * s[j0 + jj];
         s[r] -= acc;
       }
@@ -360,12 +506,17 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
   }
   for (int j0 = ((n - 1) / 32) * 32; j0 >= 0; j0 -= 32) {
     const int cw = min(32, n - j0);
+    for (int idx = tid; idx < cw * cw; idx += bd) {
+      const int r = idx / cw, c = idx % cw;
+      dblk[r][c] = static_cast<Tc>(A[static_cast<size_t>(j0 + r) * n + j0 + c]);
+    }
+    __syncthreads();
     if (warp == 0) {
       Tc v = lane < cw ? s[j0 + lane] : Tc(0);
       for (int jj = cw - 1; jj >= 0; --jj) {
-        if (lane == jj) v /= static_cast<Tc>(A[static_cast<size_t>(j0 + jj) * n + j0 + jj]);
+        if (lane == jj) v /= dblk[jj][jj];
         const Tc xj = __shfl_sync(0xffffffffu, v, jj);
-        if (lane < jj) v -= static_cast<Tc>(A[static_cast<size_t>(j0 + lane) * n + j0 + jj]) * xj;
+        if (lane < jj) v -= dblk[lane][jj] * xj;
       }
       if (lane < cw) s[j0 + lane] = v;
     }
@@ -373,6 +524,7 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
     for (int r = tid; r < j0; r += bd) {
       const T* a = A + static_cast<size_t>(r) * n + j0;
       Tc acc = Tc(0);
+#pragma unroll 8
       for (int jj = 0; jj < cw; ++jj) acc += static_cast<Tc>(a[jj]) * s[j0 + jj];
       s[r] -= acc;
     }
@@ -384,11 +536,11 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
 
 }  // namespace
 
-// sub-panel width: largest power of two <= 32 whose staging buffer fits the shared-memory budget
+// sub-panel width: largest power of two <= 32 whose shared-memory plan fits the budget
 template <typename T>
 static int panel_width(int n, int nb) {
   int w = 32;
-  while (w > 1 && (static_cast<size_t>(n) * (w + 1) * sizeof(T) + n * sizeof(int)) > 200 * 1024) w >>= 1;
+  while (w > 2 && panel_smem_bytes<T>(n, nb, nb, w) > 210 * 1024) w >>= 1;
   return w < nb ? w : nb;
 }
 
@@ -396,7 +548,7 @@ template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st) {
   const int W = panel_width<T>(n, nbmax);
-  const size_t smem = static_cast<size_t>(n - k0) * (W + 1) * sizeof(T) + (n - k0) * sizeof(int);
+  const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, W);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -412,7 +564,7 @@ void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, 
   const int ntrail = n - k0 - nb;
   if (ntrail <= 0) return;
   dim3 grid(nx, (ntrail + kTrsmCols - 1) / kTrsmCols);
-  const size_t smem = 2 * static_cast<size_t>(nb) * kTrsmLd * sizeof(T);
+  const size_t smem = trsm_smem_bytes<T>(nb);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_swap_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);

@@ -119,8 +119,8 @@ def test_medium_workload_one_step(precision):
     t = 0.25 / W.RF_FREQ_HZ - 0.5 * cfg["dt_s"]   # E(t + dt/2) at its peak
     ref = ops.step(F0, t)
     s = solver(cfg, precision)
-    F = s.initial_state()
-    assert rel_l2(F.cpu().numpy(), F0) < 1e-13
+    assert rel_l2(s.initial_state().cpu().numpy(), F0) < 1e-12   # independent IC projections
+    F = to_dev(F0)
     s.step(F, t)
     err = rel_l2(F.cpu().numpy(), ref)
     assert err <= (1e-10 if precision == "fp64" else 1e-9), err
