@@ -38,6 +38,7 @@ struct bte_handle {
   double *Fhost_dev = nullptr, *coef = nullptr, *ratio = nullptr;
   void* fac = nullptr;
   void* linv = nullptr;
+  void* uinv = nullptr;
   void* tcws = nullptr;
   int *piv = nullptr, *perm = nullptr, *conv = nullptr;
   unsigned* status = nullptr;
@@ -161,8 +162,9 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
-      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nx, n,
-                                                              k0, kb, nb, h->status, nullptr, nullptr, st));
+      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv),
+                                                              nullptr, nx, n, k0, kb, nb, h->status, nullptr, nullptr,
+                                                              st));
       if (k0 + kb < n) {
         BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
                                                                         n, k0, kb, nb, nullptr, nullptr, st));
@@ -179,8 +181,9 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
-      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv), nx, n,
-                                                             k0, kb, nb, h->status, whi, wlo, st));
+      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv),
+                                                             static_cast<float*>(h->uinv), nx, n, k0, kb, nb,
+                                                             h->status, whi, wlo, st));
       if (k0 + kb < n) {
         BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, static_cast<float*>(h->linv), nx,
                                                                        n, k0, kb, nb, uhi, ulo, st));
@@ -188,7 +191,9 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
         else BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
       }
     }
-    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<float>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st));
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(fac, h->perm, static_cast<float*>(h->linv),
+                                                                   static_cast<float*>(h->uinv), h->Fa, h->Fb, nx, n,
+                                                                   nb, nullptr, 0, st));
   }
   // FP64 iterative refinement: residual through Algorithm 2, correction through the factors
   if (h->refine_max > 0) {
@@ -201,7 +206,9 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
       if (h->precision == BTE_FP64)
         BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(static_cast<double*>(h->fac), h->piv, h->R, h->Fb, nx, n, nb, h->conv, 1, st));
       else
-        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<float>(static_cast<float*>(h->fac), h->piv, h->R, h->Fb, nx, n, nb, h->conv, 1, st));
+        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(
+                                       static_cast<float*>(h->fac), h->perm, static_cast<float*>(h->linv),
+                                       static_cast<float*>(h->uinv), h->R, h->Fb, nx, n, nb, h->conv, 1, st));
     }
     BTE_LAUNCH(BTE_K_OTHER, bte::launch_check_conv(h->conv, nx, h->status, st));
   }
@@ -289,19 +296,23 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
               chk(dalloc(h, &h->Fb, D)) && chk(dalloc(h, &h->Fw, D)) && chk(dalloc(h, &h->R, D)) &&
               chk(dalloc(h, &h->Fhost_dev, D)) && chk(dalloc(h, &h->coef, o.nr)) &&
               chk(dalloc(h, &h->ratio, o.nx)) && chk(dalloc(h, &h->piv, D)) &&
-              chk(dalloc(h, &h->perm, static_cast<size_t>(o.nx) * bte::perm_record_ints(h->nb))) &&
+              chk(dalloc(h, &h->perm, static_cast<size_t>(o.nx) * ((o.nv + h->nb - 1) / h->nb) *
+                                          bte::perm_record_ints(h->nb))) &&
               chk(dalloc(h, &h->conv, o.nx)) && chk(dalloc(h, &h->status, 1));
     if (ok) {
+      const size_t npan = (o.nv + h->nb - 1) / h->nb;
+      const size_t blk = static_cast<size_t>(o.nx) * npan * h->nb * h->nb;
       if (h->precision == BTE_FP64) {
         double *f = nullptr, *l = nullptr;
-        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, static_cast<size_t>(o.nx) * h->nb * h->nb));
+        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, blk));
         h->fac = f;
         h->linv = l;
       } else {
-        float *f = nullptr, *l = nullptr;
-        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, static_cast<size_t>(o.nx) * h->nb * h->nb));
+        float *f = nullptr, *l = nullptr, *u = nullptr;
+        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, blk)) && chk(dalloc(h, &u, blk));
         h->fac = f;
         h->linv = l;
+        h->uinv = u;
         if (ok && !(cfg->flags & BTE_FLAG_SIMT_GEMM) && bte::tc_available()) {
           unsigned char* w = nullptr;
           ok = chk(dalloc(h, &w, bte::tc_workspace_bytes(o.nx, o.nv, h->nb)));

@@ -45,10 +45,11 @@ __host__ __device__ inline size_t panel_smem_bytes(int m0, int nb, int nbmax, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int* __restrict__ piv,
+__global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int* __restrict__ piv,
                                                        int* __restrict__ perm, T* __restrict__ linv,
-                                                       int n, int k0, int nb, int nbmax, int W,
-                                                       unsigned* status, float* __restrict__ ws_hi,
+                                                       T* __restrict__ uinv, int n, int k0, int nb,
+                                                       int nbmax, int W, unsigned* status,
+                                                       float* __restrict__ ws_hi,
                                                        float* __restrict__ ws_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = W + 1;
@@ -62,8 +63,8 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
   int* lp = orig + m0;          // local pivots of the current sub-panel (relative to c0)
   int* slot_row = lp + W;       // rows of the swap slots (2W)
   int* content = slot_row + 2 * W;  // 2W
-  __shared__ T red_v[16];
-  __shared__ int red_i[16];
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
   __shared__ int s_pr, s_cnt, s_nslot;
   __shared__ int pslot[32];
 
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
   T* A = fac + static_cast<size_t>(mat) * n * n;
   int* ip = piv + static_cast<size_t>(mat) * n;
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
+  const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
 
   for (int r = tid; r < m0; r += bd) orig[r] = k0 + r;
   bool bad_pivot = false;
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
   if (tid == 0 && bad_pivot) atomicOr(status, kZeroPivot);
 
   // permutation record for the trailing columns
-  int* pr_rec = perm + static_cast<size_t>(mat) * perm_stride(nbmax);
+  int* pr_rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
   if (tid == 0) s_cnt = 0;
   __syncthreads();
   for (int j = tid; j < nb; j += bd) pr_rec[1 + j] = orig[j];
@@ -285,19 +287,46 @@ __global__ void __launch_bounds__(512) lu_panel_kernel(T* __restrict__ fac, int*
     Ls[r * ldl + c] = A[static_cast<size_t>(k0 + r) * n + k0 + c];
   }
   __syncthreads();
-  for (int c = tid; c < nb; c += bd) {
-    Xs[c * ldl + c] = T(1);
+  // column c of inv(L11) by one warp: X[r][c] = -sum_{c<=j<r} L[r][j] X[j][c], lanes split j
+  for (int c = warp; c < nb; c += nwarp) {
+    if (lane == 0) Xs[c * ldl + c] = T(1);
+    __syncwarp();
     for (int r = c + 1; r < nb; ++r) {
       T acc = T(0);
-      for (int j = c; j < r; ++j) acc += Ls[r * ldl + j] * Xs[j * ldl + c];
-      Xs[r * ldl + c] = -acc;
+      for (int j = c + lane; j < r; j += 32) acc += Ls[r * ldl + j] * Xs[j * ldl + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) Xs[r * ldl + c] = -acc;
+      __syncwarp();
     }
   }
   __syncthreads();
-  T* X = linv + static_cast<size_t>(mat) * nbmax * nbmax;
+  T* X = linv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
   for (int idx = tid; idx < nb * nb; idx += bd) {
     const int r = idx / nb, c = idx % nb;
     X[r * nbmax + c] = c <= r ? Xs[r * ldl + c] : T(0);
+  }
+  if (!uinv) return;
+  // inv(U11), U11 = upper part of A[k0:k0+nb, k0:k0+nb] (non-unit diagonal); column c by one warp:
+  // X[c][c] = 1/U[c][c], X[r][c] = -sum_{r<j<=c} U[r][j] X[j][c] / U[r][r] for r = c-1 .. 0
+  __syncthreads();
+  for (int c = warp; c < nb; c += nwarp) {
+    if (lane == 0) Xs[c * ldl + c] = T(1) / Ls[c * ldl + c];
+    __syncwarp();
+    for (int r = c - 1; r >= 0; --r) {
+      T acc = T(0);
+      for (int j = r + 1 + lane; j <= c; j += 32) acc += Ls[r * ldl + j] * Xs[j * ldl + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) Xs[r * ldl + c] = -acc / Ls[r * ldl + r];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  T* Y = uinv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
+  for (int idx = tid; idx < nb * nb; idx += bd) {
+    const int r = idx / nb, c = idx % nb;
+    Y[r * nbmax + c] = c >= r ? Xs[r * ldl + c] : T(0);
   }
 }
 
@@ -322,8 +351,9 @@ __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, 
   const int C0 = k0 + nb + blockIdx.y * kTrsmCols;
   const int ncol = min(kTrsmCols, n - C0);
   T* A = fac + static_cast<size_t>(mat) * n * n;
-  const int* rec = perm + static_cast<size_t>(mat) * perm_stride(nbmax);
-  const T* X = linv + static_cast<size_t>(mat) * nbmax * nbmax;
+  const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
+  const int* rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
+  const T* X = linv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
   const int tid = threadIdx.x, bd = blockDim.x;
   // read phase: inv(L11), the original panel rows, and the final content of the panel rows
   for (int idx = tid; idx < nb * nb; idx += bd) {
@@ -494,12 +524,14 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
         if (lane < cw) s[j0 + lane] = v;
       }
       __syncthreads();
-      for (int r = j0 + cw + tid; r < n; r += bd) {
-        const T* a = A + static_cast<size_t>(r) * n + j0;
-        Tc acc = Tc(0);
-#pragma unroll 8
-        for (int jj = 0; jj < cw; ++jj) acc += static_cast<Tc>(a[jj]) * s[j0 + jj];
-        s[r] -= acc;
+      {
+        const Tc xv = lane < cw ? s[j0 + lane] : Tc(0);
+        for (int r = j0 + cw + warp; r < n; r += (bd >> 5)) {
+          Tc acc = lane < cw ? static_cast<Tc>(A[static_cast<size_t>(r) * n + j0 + lane]) * xv : Tc(0);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) s[r] -= acc;
+        }
       }
       __syncthreads();
     }
@@ -521,12 +553,91 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
       if (lane < cw) s[j0 + lane] = v;
     }
     __syncthreads();
-    for (int r = tid; r < j0; r += bd) {
-      const T* a = A + static_cast<size_t>(r) * n + j0;
-      Tc acc = Tc(0);
-#pragma unroll 8
-      for (int jj = 0; jj < cw; ++jj) acc += static_cast<Tc>(a[jj]) * s[j0 + jj];
-      s[r] -= acc;
+    {
+      const Tc xv = lane < cw ? s[j0 + lane] : Tc(0);
+      for (int r = warp; r < j0; r += (bd >> 5)) {
+        Tc acc = lane < cw ? static_cast<Tc>(A[static_cast<size_t>(r) * n + j0 + lane]) * xv : Tc(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s[r] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  double* xo = x + static_cast<size_t>(mat) * n;
+  for (int r = tid; r < n; r += bd) xo[r] = accumulate ? xo[r] + static_cast<double>(s[r]) : static_cast<double>(s[r]);
+}
+
+// x = A^-1 b (or x += A^-1 b) for one point per CTA with the per-panel block inverses: forward,
+// per panel p: permute the right-hand side with the panel's row record, y = inv(L11_p) b_p, then
+// b[below] -= L21_p y; backward, per panel from the last: y = inv(U11_p) b_p, b[above] -= U_p y.
+// Rows are processed one per warp with the lanes across the panel's columns (coalesced).
+template <typename T>
+__global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restrict__ fac, const int* __restrict__ perm,
+                                                                const T* __restrict__ linv, const T* __restrict__ uinv,
+                                                                const double* __restrict__ b, double* __restrict__ x,
+                                                                int n, int nb, const int* __restrict__ conv,
+                                                                int accumulate) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* s = reinterpret_cast<T*>(smraw);   // n
+  T* y = s + n;                          // nb
+  T* tmp = y + nb;                       // 2 nb
+  const int mat = blockIdx.x;
+  if (conv && conv[mat]) return;
+  const T* A = fac + static_cast<size_t>(mat) * n * n;
+  const int npan = (n + nb - 1) / nb;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
+  for (int r = tid; r < n; r += bd) s[r] = static_cast<T>(b[static_cast<size_t>(mat) * n + r]);
+  __syncthreads();
+  for (int p = 0; p < npan; ++p) {
+    const int k0 = p * nb, kb = min(nb, n - k0);
+    const int* rec = perm + (static_cast<size_t>(mat) * npan + p) * perm_stride(nb);
+    const int d = rec[0];
+    for (int j = tid; j < kb; j += bd) tmp[j] = s[rec[1 + j]];
+    for (int q = tid; q < d; q += bd) tmp[nb + q] = s[rec[1 + nb + 2 * q + 1]];
+    __syncthreads();
+    for (int j = tid; j < kb; j += bd) s[k0 + j] = tmp[j];
+    for (int q = tid; q < d; q += bd) s[rec[1 + nb + 2 * q]] = tmp[nb + q];
+    __syncthreads();
+    const T* X = linv + (static_cast<size_t>(mat) * npan + p) * nb * nb;
+    for (int r = warp; r < kb; r += nwarp) {
+      T acc = T(0);
+      for (int c = lane; c <= r; c += 32) acc += X[r * nb + c] * s[k0 + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) y[r] = acc;
+    }
+    __syncthreads();
+    for (int j = tid; j < kb; j += bd) s[k0 + j] = y[j];
+    for (int r = k0 + kb + warp; r < n; r += nwarp) {
+      const T* a = A + static_cast<size_t>(r) * n + k0;
+      T acc = T(0);
+      for (int c = lane; c < kb; c += 32) acc += a[c] * y[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) s[r] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int p = npan - 1; p >= 0; --p) {
+    const int k0 = p * nb, kb = min(nb, n - k0);
+    const T* Y = uinv + (static_cast<size_t>(mat) * npan + p) * nb * nb;
+    for (int r = warp; r < kb; r += nwarp) {
+      T acc = T(0);
+      for (int c = r + lane; c < kb; c += 32) acc += Y[r * nb + c] * s[k0 + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) y[r] = acc;
+    }
+    __syncthreads();
+    for (int j = tid; j < kb; j += bd) s[k0 + j] = y[j];
+    for (int r = warp; r < k0; r += nwarp) {
+      const T* a = A + static_cast<size_t>(r) * n + k0;
+      T acc = T(0);
+      for (int c = lane; c < kb; c += 32) acc += a[c] * y[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) s[r] -= acc;
     }
     __syncthreads();
   }
@@ -545,7 +656,7 @@ static int panel_width(int n, int nb) {
 }
 
 template <typename T>
-void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
+void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st) {
   const int W = panel_width<T>(n, nbmax);
   const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, W);
@@ -554,7 +665,7 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  lu_panel_kernel<T><<<nx, 512, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, W, status,
+  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax, W, status,
                                              k0 + nb < n ? ws_hi : nullptr, ws_lo);
 }
 
@@ -601,9 +712,23 @@ void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, i
 
 int perm_record_ints(int nbmax) { return perm_stride(nbmax); }
 
+template <typename T>
+void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
+                             double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st) {
+  const size_t smem = (static_cast<size_t>(n) + 3 * nb) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lu_solve_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    attr_set = true;
+  }
+  lu_solve_blocked_kernel<T><<<nx, 1024, smem, st>>>(fac, perm, linv, uinv, b, x, n, nb, conv, accumulate);
+}
+
 #define BTE_INST(T)                                                                                 \
-  template void launch_lu_panel<T>(T*, int*, int*, T*, int, int, int, int, int, unsigned*, float*, float*, \
-                                   cudaStream_t);                                                   \
+  template void launch_lu_panel<T>(T*, int*, int*, T*, T*, int, int, int, int, int, unsigned*, float*,   \
+                                   float*, cudaStream_t);                                           \
+  template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \
+                                           double*, int, int, int, const int*, int, cudaStream_t);  \
   template void launch_lu_swap_trsm<T>(T*, const int*, const T*, int, int, int, int, int, float*, float*, \
                                        cudaStream_t);                                               \
   template void launch_lu_gemm_simt<T>(T*, int, int, int, int, cudaStream_t);                       \
