@@ -163,8 +163,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv),
-                                                              nullptr, nx, n, k0, kb, nb, h->status, nullptr, nullptr,
-                                                              st));
+                                                              nx, n, k0, kb, nb, h->status, nullptr, nullptr, st));
       if (k0 + kb < n) {
         BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
                                                                         n, k0, kb, nb, nullptr, nullptr, st));
@@ -182,8 +181,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv),
-                                                             static_cast<float*>(h->uinv), nx, n, k0, kb, nb,
-                                                             h->status, whi, wlo, st));
+                                                             nx, n, k0, kb, nb, h->status, whi, wlo, st));
       if (k0 + kb < n) {
         BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, static_cast<float*>(h->linv), nx,
                                                                        n, k0, kb, nb, uhi, ulo, st));
@@ -191,6 +189,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
         else BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
       }
     }
+    BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));
     BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(fac, h->perm, static_cast<float*>(h->linv),
                                                                    static_cast<float*>(h->uinv), h->Fa, h->Fb, nx, n,
                                                                    nb, nullptr, 0, st));

@@ -35,11 +35,14 @@ void launch_v_form(const double* KC, const double* KA, const double* E, double E
 int perm_record_ints(int nbmax);
 // ws_hi/ws_lo (may be NULL): K-major TF32 head/remainder copies of L21 (panel) and of U12^T
 // (swap_trsm) for the tensor-core trailing update, [point][n - nbmax][nbmax] floats.
-// Per-point, per-panel records ([point][panel] ...): perm (perm_record_ints each), inv(L11) and,
-// if uinv != NULL, inv(U11) (nbmax x nbmax each).
+// Per-point, per-panel records ([point][panel] ...): perm (perm_record_ints each) and inv(L11)
+// (nbmax x nbmax each).
 template <typename T>
-void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
+void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st);
+// inv(U11) of every panel of every point, once the factorisation is complete ([point][panel]).
+template <typename T>
+void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_t st);
 // x = A^-1 b (x += when accumulate) through the per-panel block inverses; T is the arithmetic type.
 template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,

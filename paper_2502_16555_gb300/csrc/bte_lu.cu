@@ -44,42 +44,90 @@ __host__ __device__ inline size_t panel_smem_bytes(int m0, int nb, int nbmax, in
   return elems * sizeof(T) + (static_cast<size_t>(m0) + 5 * W) * sizeof(int) + 16;
 }
 
+constexpr int kColWarps = 8;  // warps running the column-by-column elimination of a sub-panel
+constexpr int kLoadBatch = 8; // independent global loads in flight per thread in copy loops
+
+// inv(L) for a unit-lower (kUnit) or inv(U) for an upper triangular nb x nb matrix held in shared
+// memory (row stride ldl), by row blocks of 16: X[R,:] = D_RR^-1 (I[R,:] - D[R,rest] X[rest,:]),
+// rest = the rows already inverted (above R for L, below R for U). All threads of the block.
+template <typename T, bool kLower>
+__device__ void tri_inverse_smem(const T* D, T* X, int nb, int ldl) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int idx = tid; idx < nb * nb; idx += bd) X[(idx / nb) * ldl + idx % nb] = T(0);
+  __syncthreads();
+  const int nblk = (nb + 15) / 16;
+  for (int bi = 0; bi < nblk; ++bi) {
+    const int blk = kLower ? bi : nblk - 1 - bi;
+    const int r0 = 16 * blk, r1 = min(nb, r0 + 16), rb = r1 - r0;
+    // columns that can be non-zero in these rows: [0, r1) for L, [r0, nb) for U
+    const int c_lo = kLower ? 0 : r0, c_hi = kLower ? r1 : nb, ncol = c_hi - c_lo;
+    for (int idx = tid; idx < rb * ncol; idx += bd) {
+      const int r = r0 + idx / ncol, c = c_lo + idx % ncol;
+      T acc = (r == c) ? T(1) : T(0);
+      if (kLower) {
+        for (int k = c; k < r0; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
+      } else {
+        for (int k = r1; k <= c; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
+      }
+      X[r * ldl + c] = acc;
+    }
+    __syncthreads();
+    for (int c = c_lo + tid; c < c_hi; c += bd) {
+      if (kLower) {
+        for (int r = r0 + 1; r < r1; ++r) {
+          T acc = X[r * ldl + c];
+          for (int k = r0; k < r; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
+          X[r * ldl + c] = acc;
+        }
+      } else {
+        for (int r = r1 - 1; r >= r0; --r) {
+          T acc = X[r * ldl + c];
+          for (int k = r + 1; k < r1; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
+          X[r * ldl + c] = acc / D[r * ldl + r];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int* __restrict__ piv,
                                                        int* __restrict__ perm, T* __restrict__ linv,
-                                                       T* __restrict__ uinv, int n, int k0, int nb,
-                                                       int nbmax, int W, unsigned* status,
-                                                       float* __restrict__ ws_hi,
+                                                       int n, int k0, int nb, int nbmax, int W,
+                                                       unsigned* status, float* __restrict__ ws_hi,
                                                        float* __restrict__ ws_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = W + 1;
   const int m0 = n - k0;
-  size_t r0 = static_cast<size_t>(m0) * ld;
-  if (static_cast<size_t>(2) * nb * (nb + 1) > r0) r0 = static_cast<size_t>(2) * nb * (nb + 1);
+  size_t r0sz = static_cast<size_t>(m0) * ld;
+  if (static_cast<size_t>(2) * nb * (nb + 1) > r0sz) r0sz = static_cast<size_t>(2) * nb * (nb + 1);
   T* S = reinterpret_cast<T*>(smraw);
-  T* Ub = S + r0;
+  T* Ub = S + r0sz;
   T* SB = Ub + static_cast<size_t>(W) * nbmax;
   int* orig = reinterpret_cast<int*>(SB + static_cast<size_t>(2) * W * nbmax);
-  int* lp = orig + m0;          // local pivots of the current sub-panel (relative to c0)
-  int* slot_row = lp + W;       // rows of the swap slots (2W)
+  int* lp = orig + m0;              // local pivots of the current sub-panel (relative to c0)
+  int* slot_row = lp + W;           // rows of the swap slots (2W)
   int* content = slot_row + 2 * W;  // 2W
-  __shared__ T red_v[32];
-  __shared__ int red_i[32];
+  __shared__ T red_v[kColWarps];
+  __shared__ int red_i[kColWarps];
   __shared__ int s_pr, s_cnt, s_nslot;
   __shared__ int pslot[32];
 
   const int mat = blockIdx.x;
   T* A = fac + static_cast<size_t>(mat) * n * n;
   int* ip = piv + static_cast<size_t>(mat) * n;
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
   const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
+  constexpr int kColThreads = kColWarps * 32;
 
   for (int r = tid; r < m0; r += bd) orig[r] = k0 + r;
   bool bad_pivot = false;
 
-  // block argmax of (v, i): larger v wins, ties to the smaller i; result in s_pr (needs a barrier
-  // before it is read)
-  auto block_argmax = [&](T best, int bi) {
+  // argmax over the column warps: larger |v| wins, ties to the smaller row; result in s_pr,
+  // published by the next column barrier
+  auto col_sync = []() { asm volatile("bar.sync 1, %0;" ::"r"(kColThreads) : "memory"); };
+  auto col_argmax = [&](T best, int bi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const T ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -87,10 +135,10 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
       if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
     }
     if (lane == 0) red_v[warp] = best, red_i[warp] = bi;
-    __syncthreads();
+    col_sync();
     if (warp == 0) {
-      best = lane < nwarp ? red_v[lane] : T(-1);
-      bi = lane < nwarp ? red_i[lane] : 0x7fffffff;
+      best = lane < kColWarps ? red_v[lane] : T(-1);
+      bi = lane < kColWarps ? red_i[lane] : 0x7fffffff;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -104,47 +152,58 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
   for (int c0 = k0; c0 < k0 + nb; c0 += W) {
     const int w = min(W, k0 + nb - c0);
     const int m = n - c0;
-    for (int idx = tid; idx < m * w; idx += bd) {
-      const int r = idx / w, jj = idx % w;
-      S[r * ld + jj] = A[static_cast<size_t>(c0 + r) * n + c0 + jj];
+    for (int base = tid; base < m * w; base += bd * kLoadBatch) {
+      T v[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = base + u * bd;
+        v[u] = idx < m * w ? A[static_cast<size_t>(c0 + idx / w) * n + c0 + idx % w] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = base + u * bd;
+        if (idx < m * w) S[(idx / w) * ld + idx % w] = v[u];
+      }
     }
     __syncthreads();
-    {
-      T best = T(-1);
-      int bi = 0;
-      for (int r = tid; r < m; r += bd) {
-        const T v = tabs(S[r * ld]);
-        if (v > best) best = v, bi = r;
-      }
-      block_argmax(best, bi);
-    }
-    for (int j = 0; j < w; ++j) {
-      __syncthreads();  // s_pr of column j is published
-      int pr = s_pr;
-      if (pr < j || pr >= m) pr = j;
-      if (pr != j)
-        for (int jj = tid; jj < w; jj += bd) {
-          const T t = S[j * ld + jj];
-          S[j * ld + jj] = S[pr * ld + jj];
-          S[pr * ld + jj] = t;
-        }
-      if (tid == 0) lp[j] = pr;
-      __syncthreads();  // pivot row in place
-      const T pv = S[j * ld + j];
-      if (tid == 0 && (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv)))) bad_pivot = true;
-      const T inv = (pv != T(0)) ? T(1) / pv : T(0);
-      T best = T(-1);
-      int bi = j + 1;
-      for (int r = j + 1 + tid; r < m; r += bd) {
-        const T l = S[r * ld + j] * inv;
-        S[r * ld + j] = l;
-        for (int jj = j + 1; jj < w; ++jj) S[r * ld + jj] -= l * S[j * ld + jj];
-        if (j + 1 < w) {
-          const T v = tabs(S[r * ld + j + 1]);
+    if (warp < kColWarps) {
+      {
+        T best = T(-1);
+        int bi = 0;
+        for (int r = tid; r < m; r += kColThreads) {
+          const T v = tabs(S[r * ld]);
           if (v > best) best = v, bi = r;
         }
+        col_argmax(best, bi);
       }
-      if (j + 1 < w) block_argmax(best, bi);
+      for (int j = 0; j < w; ++j) {
+        col_sync();  // s_pr of column j is published
+        int pr = s_pr;
+        if (pr < j || pr >= m) pr = j;
+        if (pr != j)
+          for (int jj = tid; jj < w; jj += kColThreads) {
+            const T t = S[j * ld + jj];
+            S[j * ld + jj] = S[pr * ld + jj];
+            S[pr * ld + jj] = t;
+          }
+        if (tid == 0) lp[j] = pr;
+        col_sync();  // pivot row in place
+        const T pv = S[j * ld + j];
+        if (tid == 0 && (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv)))) bad_pivot = true;
+        const T inv = (pv != T(0)) ? T(1) / pv : T(0);
+        T best = T(-1);
+        int bi = j + 1;
+        for (int r = j + 1 + tid; r < m; r += kColThreads) {
+          const T l = S[r * ld + j] * inv;
+          S[r * ld + j] = l;
+          for (int jj = j + 1; jj < w; ++jj) S[r * ld + jj] -= l * S[j * ld + jj];
+          if (j + 1 < w) {
+            const T v = tabs(S[r * ld + j + 1]);
+            if (v > best) best = v, bi = r;
+          }
+        }
+        if (j + 1 < w) col_argmax(best, bi);
+      }
     }
     __syncthreads();
     for (int idx = tid; idx < m * w; idx += bd) {
@@ -215,28 +274,29 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
         const int jr = idx / rw, q = idx % rw;
         A[static_cast<size_t>(c0 + jr) * n + cb + q] = Ub[jr * nbmax + q];
       }
-      // rows below: A[c0+r][cb+q] -= S[r][:w] . Ub[:w][q], 4 x 4 register tiles
-      const int ntr = (m - w + 3) / 4, ntc = (rw + 3) / 4;
+      // rows below: A[c0+r][cb+q] -= S[r][:w] . Ub[:w][q], TR x 4 register tiles
+      constexpr int TR = sizeof(T) == 4 ? 8 : 4;
+      const int ntr = (m - w + TR - 1) / TR, ntc = (rw + 3) / 4;
       for (int t = tid; t < ntr * ntc; t += bd) {
-        const int r0 = w + 4 * (t / ntc), q0 = 4 * (t % ntc);
-        T acc[4][4];
+        const int r0 = w + TR * (t / ntc), q0 = 4 * (t % ntc);
+        T acc[TR][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
           for (int c = 0; c < 4; ++c) acc[i][c] = T(0);
         for (int jj = 0; jj < w; ++jj) {
-          T sv[4], uv[4];
+          T sv[TR], uv[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) sv[i] = (r0 + i < m) ? S[(r0 + i) * ld + jj] : T(0);
+          for (int i = 0; i < TR; ++i) sv[i] = (r0 + i < m) ? S[(r0 + i) * ld + jj] : T(0);
 #pragma unroll
           for (int c = 0; c < 4; ++c) uv[c] = (q0 + c < rw) ? Ub[jj * nbmax + q0 + c] : T(0);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < TR; ++i)
 #pragma unroll
             for (int c = 0; c < 4; ++c) acc[i][c] += sv[i] * uv[c];
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < TR; ++i) {
           if (r0 + i >= m) continue;
           T* row = A + static_cast<size_t>(c0 + r0 + i) * n + cb + q0;
 #pragma unroll
@@ -269,12 +329,23 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
     const int M = n - k0 - nb;
     float* hi = ws_hi + static_cast<size_t>(mat) * (n - nbmax) * nbmax;
     float* lo = ws_lo + static_cast<size_t>(mat) * (n - nbmax) * nbmax;
-    for (int idx = tid; idx < M * nb; idx += bd) {
-      const int r = idx / nb, k = idx % nb;
-      float h, l;
-      split_tf32(static_cast<float>(A[static_cast<size_t>(k0 + nb + r) * n + k0 + k]), h, l);
-      hi[static_cast<size_t>(r) * nbmax + k] = h;
-      lo[static_cast<size_t>(r) * nbmax + k] = l;
+    for (int base = tid; base < M * nb; base += bd * kLoadBatch) {
+      float v[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = base + u * bd;
+        v[u] = idx < M * nb ? static_cast<float>(A[static_cast<size_t>(k0 + nb + idx / nb) * n + k0 + idx % nb]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int idx = base + u * bd;
+        if (idx < M * nb) {
+          float h, l;
+          split_tf32(v[u], h, l);
+          hi[static_cast<size_t>(idx / nb) * nbmax + idx % nb] = h;
+          lo[static_cast<size_t>(idx / nb) * nbmax + idx % nb] = l;
+        }
+      }
     }
   }
 
@@ -287,46 +358,35 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
     Ls[r * ldl + c] = A[static_cast<size_t>(k0 + r) * n + k0 + c];
   }
   __syncthreads();
-  // column c of inv(L11) by one warp: X[r][c] = -sum_{c<=j<r} L[r][j] X[j][c], lanes split j
-  for (int c = warp; c < nb; c += nwarp) {
-    if (lane == 0) Xs[c * ldl + c] = T(1);
-    __syncwarp();
-    for (int r = c + 1; r < nb; ++r) {
-      T acc = T(0);
-      for (int j = c + lane; j < r; j += 32) acc += Ls[r * ldl + j] * Xs[j * ldl + c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) Xs[r * ldl + c] = -acc;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
+  tri_inverse_smem<T, true>(Ls, Xs, nb, ldl);
   T* X = linv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
   for (int idx = tid; idx < nb * nb; idx += bd) {
     const int r = idx / nb, c = idx % nb;
-    X[r * nbmax + c] = c <= r ? Xs[r * ldl + c] : T(0);
+    X[r * nbmax + c] = Xs[r * ldl + c];
   }
-  if (!uinv) return;
-  // inv(U11), U11 = upper part of A[k0:k0+nb, k0:k0+nb] (non-unit diagonal); column c by one warp:
-  // X[c][c] = 1/U[c][c], X[r][c] = -sum_{r<j<=c} U[r][j] X[j][c] / U[r][r] for r = c-1 .. 0
-  __syncthreads();
-  for (int c = warp; c < nb; c += nwarp) {
-    if (lane == 0) Xs[c * ldl + c] = T(1) / Ls[c * ldl + c];
-    __syncwarp();
-    for (int r = c - 1; r >= 0; --r) {
-      T acc = T(0);
-      for (int j = r + 1 + lane; j <= c; j += 32) acc += Ls[r * ldl + j] * Xs[j * ldl + c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) Xs[r * ldl + c] = -acc / Ls[r * ldl + r];
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  T* Y = uinv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
-  for (int idx = tid; idx < nb * nb; idx += bd) {
+}
+
+// inv(U11) of every panel of every point, after the factorisation (one CTA per point and panel).
+template <typename T>
+__global__ void __launch_bounds__(256) lu_uinv_kernel(const T* __restrict__ fac, T* __restrict__ uinv, int n,
+                                                      int nbmax) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int npan = (n + nbmax - 1) / nbmax;
+  const int mat = blockIdx.x / npan, pan = blockIdx.x % npan;
+  const int k0 = pan * nbmax, nb = min(nbmax, n - k0), ldl = nb + 1;
+  T* Us = reinterpret_cast<T*>(smraw);
+  T* Xs = Us + static_cast<size_t>(nb) * ldl;
+  const T* A = fac + static_cast<size_t>(mat) * n * n;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
     const int r = idx / nb, c = idx % nb;
-    Y[r * nbmax + c] = c >= r ? Xs[r * ldl + c] : T(0);
+    Us[r * ldl + c] = A[static_cast<size_t>(k0 + r) * n + k0 + c];
+  }
+  __syncthreads();
+  tri_inverse_smem<T, false>(Us, Xs, nb, ldl);
+  T* Y = uinv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx / nb, c = idx % nb;
+    Y[r * nbmax + c] = Xs[r * ldl + c];
   }
 }
 
@@ -656,7 +716,7 @@ static int panel_width(int n, int nb) {
 }
 
 template <typename T>
-void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
+void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st) {
   const int W = panel_width<T>(n, nbmax);
   const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, W);
@@ -665,7 +725,7 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int 
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax, W, status,
+  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, W, status,
                                              k0 + nb < n ? ws_hi : nullptr, ws_lo);
 }
 
@@ -713,6 +773,18 @@ void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, i
 int perm_record_ints(int nbmax) { return perm_stride(nbmax); }
 
 template <typename T>
+void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_t st) {
+  const int npan = (n + nbmax - 1) / nbmax;
+  const size_t smem = 2ull * nbmax * (nbmax + 1) * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lu_uinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  lu_uinv_kernel<T><<<nx * npan, 256, smem, st>>>(fac, uinv, n, nbmax);
+}
+
+template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
                              double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st) {
   const size_t smem = (static_cast<size_t>(n) + 3 * nb) * sizeof(T);
@@ -725,8 +797,9 @@ void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const
 }
 
 #define BTE_INST(T)                                                                                 \
-  template void launch_lu_panel<T>(T*, int*, int*, T*, T*, int, int, int, int, int, unsigned*, float*,   \
+  template void launch_lu_panel<T>(T*, int*, int*, T*, int, int, int, int, int, unsigned*, float*,       \
                                    float*, cudaStream_t);                                           \
+  template void launch_lu_uinv<T>(const T*, T*, int, int, int, cudaStream_t);                        \
   template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \
                                            double*, int, int, int, const int*, int, cudaStream_t);  \
   template void launch_lu_swap_trsm<T>(T*, const int*, const T*, int, int, int, int, int, float*, float*, \
