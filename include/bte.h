@@ -169,6 +169,20 @@ bte_status bte_get_info(const bte_handle* h, bte_info* info);
  * class into ms_out[BTE_NPROF] and count_out[BTE_NPROF] (either may be NULL). */
 bte_status bte_profile(bte_handle* h, int enable, double* ms_out, unsigned long long* count_out);
 
+/* The same fill as bte_init_maxwellian, for callers that cannot allocate device memory (code whose
+ * device memory all comes from another runtime's pool, or a host program that passes in buffers it
+ * got elsewhere): it makes no device allocation and also accepts a handle created with
+ * BTE_FLAG_HOST_ONLY, which holds no device memory. The paper has no counterpart; this is an
+ * interface convenience. F_dev[nx][ntheta][nr] and ne_dev[nx] are device buffers of the caller.
+ * Scratch: the nr Maxwellian coefficients are staged in a file-scope __device__ array of 4096 doubles
+ * (32 KB) that every GPU loading libbte holds until the process exits; nr > 4096 gives BTE_EINVAL.
+ * The first call on a device looks up that array's device address with the device current; make
+ * that first call before any stream capture. All calls share the array and it keeps the last call's
+ * coefficients (nothing in it needs to start at zero: each call writes the entries it reads); calls
+ * whose work overlaps on the GPU (other streams, or other threads) race on it. Work is enqueued on
+ * the handle's stream without synchronising it. */
+bte_status bte_init_maxwellian_static(const bte_handle* h, double* F_dev, const double* ne_dev, double Te_eV);
+
 /* Release every buffer of the handle (synchronises its stream first). NULL is accepted. */
 bte_status bte_destroy(bte_handle* h);
 

@@ -31,7 +31,7 @@ OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "U
              "M": 9, "mom_n": 10, "mom_e": 11, "mom_r": 12}
 EXPORTS = ("bte_create", "bte_set_cross_sections", "bte_init_maxwellian", "bte_step", "bte_run",
            "bte_step_host", "bte_moments", "bte_get_operator", "bte_get_info", "bte_profile",
-           "bte_destroy", "bte_last_error")
+           "bte_destroy", "bte_last_error", "bte_init_maxwellian_static")
 KERNELS = ("x_to_eigen", "x_apply_q", "x_from_eigen", "v_form", "lu_panel", "lu_swap_trsm", "lu_gemm",
            "lu_solve", "residual", "other")
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
     lib.bte_get_operator.argtypes = [vp, i, pd, C.c_size_t]
     lib.bte_get_info.argtypes = [vp, C.POINTER(Info)]
     lib.bte_profile.argtypes = [vp, i, pd, C.POINTER(C.c_ulonglong)]
+    lib.bte_init_maxwellian_static.argtypes = [vp, vp, vp, d]
     lib.bte_destroy.argtypes = [vp]
     lib.bte_last_error.argtypes = [vp]
     lib.bte_last_error.restype = C.c_char_p

@@ -258,6 +258,14 @@ bool valid_cfg(const bte_config* c, std::string& why) {
 
 }  // namespace
 
+namespace bte {
+const HostOps* handle_ops(const bte_handle* h) { return &h->ops; }
+void* handle_stream_ptr(const bte_handle* h) { return static_cast<void*>(h->st); }
+bte_status handle_fail(const bte_handle* h, bte_status s, const std::string& msg) {
+  return fail(const_cast<bte_handle*>(h), s, msg);
+}
+}  // namespace bte
+
 extern "C" {
 
 bte_status bte_create(const bte_config* cfg, bte_handle** out) {

@@ -51,4 +51,9 @@ std::string assemble_v(HostOps& ops, const std::vector<Process>& procs);
 // Galerkin coefficients of a unit-density Maxwellian at temperature Te (eV).
 std::vector<double> maxwellian_coeffs(const HostOps& ops, double Te_eV);
 
+// Handle accessors for entry points defined outside bte_api.cu.
+const HostOps* handle_ops(const bte_handle* h);
+void* handle_stream_ptr(const bte_handle* h);
+bte_status handle_fail(const bte_handle* h, bte_status s, const std::string& msg);
+
 }  // namespace bte

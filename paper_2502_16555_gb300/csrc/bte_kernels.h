@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "bte_internal.h"
+
 namespace bte {
 
 enum StatusBits : unsigned {
@@ -73,5 +75,7 @@ void launch_moments(const double* F, const double* mom_n, const double* mom_e, c
                     cudaStream_t st);
 void launch_fill_maxwellian(double* F, const double* ne, const double* coef, int nx, int nt, int nr,
                             cudaStream_t st);
+
+inline cudaStream_t handle_stream(const bte_handle* h) { return static_cast<cudaStream_t>(handle_stream_ptr(h)); }
 
 }  // namespace bte
