@@ -163,7 +163,8 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv),
-                                                              nx, n, k0, kb, nb, h->status, nullptr, nullptr, st));
+                                                              nx, n, k0, kb, nb, h->status, nullptr, nullptr,
+                                                              nullptr, nullptr, st));
       if (k0 + kb < n) {
         BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
                                                                         n, k0, kb, nb, nullptr, nullptr, st));
@@ -177,16 +178,23 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     float* wlo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 1) : nullptr;
     float* uhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 2) : nullptr;
     float* ulo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 3) : nullptr;
+    float* lhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 4) : nullptr;
+    float* llo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 5) : nullptr;
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv),
-                                                             nx, n, k0, kb, nb, h->status, whi, wlo, st));
+                                                             nx, n, k0, kb, nb, h->status, whi, wlo, lhi, llo, st));
       if (k0 + kb < n) {
-        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, static_cast<float*>(h->linv), nx,
-                                                                       n, k0, kb, nb, uhi, ulo, st));
-        if (h->use_tc) BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, kb, h->tcws, h->status, st));
-        else BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
+        if (h->use_tc) {
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, kb, nb, uhi, ulo, st));
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, h->tcws, h->status, st));
+          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, kb, h->tcws, h->status, st));
+        } else {
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, static_cast<float*>(h->linv),
+                                                                         nx, n, k0, kb, nb, nullptr, nullptr, st));
+          BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
+        }
       }
     }
     BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));

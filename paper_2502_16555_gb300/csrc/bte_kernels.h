@@ -19,6 +19,9 @@ bool tc_available();
 size_t tc_workspace_bytes(int nx, int n, int nbmax);
 float* tc_ws_part(void* ws, int nx, int n, int part);  // 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
 void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st);
+// U12 = inv(L11) (P A12) on the tensor cores, written into the matrix and (transposed, split) into
+// the B operand of the following trailing update.
+void tc_lu_u12(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
 
 // ---- x half step (Algorithm 1): eigen-basis transform, Q_ij apply, back transform
 void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
@@ -39,9 +42,13 @@ int perm_record_ints(int nbmax);
 // (swap_trsm) for the tensor-core trailing update, [point][n - nbmax][nbmax] floats.
 // Per-point, per-panel records ([point][panel] ...): perm (perm_record_ints each) and inv(L11)
 // (nbmax x nbmax each).
+// li_hi/li_lo (may be NULL): TF32 split of inv(L11) for the tensor-core U12 formation.
 template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
-                     unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st);
+                     unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st);
+// Tensor-core path: displaced-row writes of the panel permutation and the split (P A12)^T operand.
+void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,
+                         float* bt_lo, cudaStream_t st);
 // inv(U11) of every panel of every point, once the factorisation is complete ([point][panel]).
 template <typename T>
 void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_t st);

@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
                                                        int* __restrict__ perm, T* __restrict__ linv,
                                                        int n, int k0, int nb, int nbmax, int W,
                                                        unsigned* status, float* __restrict__ ws_hi,
-                                                       float* __restrict__ ws_lo) {
+                                                       float* __restrict__ ws_lo, float* __restrict__ li_hi,
+                                                       float* __restrict__ li_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int ld = W + 1;
   const int m0 = n - k0;
@@ -364,6 +365,16 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
     const int r = idx / nb, c = idx % nb;
     X[r * nbmax + c] = Xs[r * ldl + c];
   }
+  // inv(L11) split for the tensor-core formation of U12 ([point][nbmax][nbmax])
+  if (li_hi) {
+    for (int idx = tid; idx < nbmax * nbmax; idx += bd) {
+      const int r = idx / nbmax, c = idx % nbmax;
+      float h = 0.f, l = 0.f;
+      if (r < nb && c < nb) split_tf32(static_cast<float>(Xs[r * ldl + c]), h, l);
+      li_hi[static_cast<size_t>(mat) * nbmax * nbmax + idx] = h;
+      li_lo[static_cast<size_t>(mat) * nbmax * nbmax + idx] = l;
+    }
+  }
 }
 
 // inv(U11) of every panel of every point, after the factorisation (one CTA per point and panel).
@@ -480,6 +491,47 @@ __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, 
       ws_hi[o] = h;
       ws_lo[o] = l;
     }
+  }
+}
+
+// Tensor-core path: apply the panel's row permutation to the trailing columns (displaced rows only)
+// and write (P A12)^T, split into TF32 head/remainder, as the K-major B operand of the U12 GEMM.
+__global__ void __launch_bounds__(256) lu_swap_pack_kernel(float* __restrict__ fac, const int* __restrict__ perm,
+                                                           int n, int k0, int nb, int nbmax,
+                                                           float* __restrict__ bt_hi, float* __restrict__ bt_lo) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* top = reinterpret_cast<float*>(smraw);            // original panel rows  nb x ld
+  float* Bs = top + static_cast<size_t>(nb) * kTrsmLd;      // permuted panel rows nb x ld
+  const int mat = blockIdx.x;
+  const int C0 = k0 + nb + blockIdx.y * kTrsmCols;
+  const int ncol = min(kTrsmCols, n - C0);
+  float* A = fac + static_cast<size_t>(mat) * n * n;
+  const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
+  const int* rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
+  const int tid = threadIdx.x, bd = blockDim.x;
+  for (int idx = tid; idx < nb * kTrsmCols; idx += bd) {
+    const int r = idx / kTrsmCols, c = idx % kTrsmCols;
+    top[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(k0 + r) * n + C0 + c] : 0.f;
+    const int o = rec[1 + r];
+    Bs[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(o) * n + C0 + c] : 0.f;
+  }
+  __syncthreads();
+  const int d = rec[0];
+  for (int idx = tid; idx < d * kTrsmCols; idx += bd) {
+    const int q = idx / kTrsmCols, c = idx % kTrsmCols;
+    if (c >= ncol) continue;
+    const int dst = rec[1 + nbmax + 2 * q], src = rec[1 + nbmax + 2 * q + 1];
+    A[static_cast<size_t>(dst) * n + C0 + c] = top[(src - k0) * kTrsmLd + c];
+  }
+  const size_t off = static_cast<size_t>(mat) * (n - nbmax) * nbmax;
+  for (int idx = tid; idx < kTrsmCols * nbmax; idx += bd) {
+    const int c = idx / nbmax, r = idx % nbmax;
+    if (c >= ncol) continue;
+    float h = 0.f, l = 0.f;
+    if (r < nb) split_tf32(Bs[r * kTrsmLd + c], h, l);
+    const size_t o = off + static_cast<size_t>(C0 - (k0 + nb) + c) * nbmax + r;
+    bt_hi[o] = h;
+    bt_lo[o] = l;
   }
 }
 
@@ -717,7 +769,7 @@ static int panel_width(int n, int nb) {
 
 template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
-                     unsigned* status, float* ws_hi, float* ws_lo, cudaStream_t st) {
+                     unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
   const int W = panel_width<T>(n, nbmax);
   const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, W);
   static bool attr_set = false;
@@ -725,8 +777,9 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
+  const bool trail = k0 + nb < n;
   lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, W, status,
-                                             k0 + nb < n ? ws_hi : nullptr, ws_lo);
+                                             trail ? ws_hi : nullptr, ws_lo, trail ? li_hi : nullptr, li_lo);
 }
 
 template <typename T>
@@ -742,6 +795,20 @@ void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, 
     attr_set = true;
   }
   lu_swap_trsm_kernel<T><<<grid, 256, smem, st>>>(fac, perm, linv, n, k0, nb, nbmax, ws_hi, ws_lo);
+}
+
+void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,
+                         float* bt_lo, cudaStream_t st) {
+  const int ntrail = n - k0 - nb;
+  if (ntrail <= 0) return;
+  dim3 grid(nx, (ntrail + kTrsmCols - 1) / kTrsmCols);
+  const size_t smem = 2ull * nb * kTrsmLd * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lu_swap_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  lu_swap_pack_kernel<<<grid, 256, smem, st>>>(fac, perm, n, k0, nb, nbmax, bt_hi, bt_lo);
 }
 
 template <typename T>
@@ -798,7 +865,7 @@ void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const
 
 #define BTE_INST(T)                                                                                 \
   template void launch_lu_panel<T>(T*, int*, int*, T*, int, int, int, int, int, unsigned*, float*,       \
-                                   float*, cudaStream_t);                                           \
+                                   float*, float*, float*, cudaStream_t);                           \
   template void launch_lu_uinv<T>(const T*, T*, int, int, int, cudaStream_t);                        \
   template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \
                                            double*, int, int, int, const int*, int, cudaStream_t);  \

@@ -15,6 +15,10 @@
 //           (M=128, N=128, K=8 per instruction, 12 per chunk), committing each stage back to the
 //           producer and each finished accumulator to the epilogue;
 //   warps 2-5 epilogue: tcgen05.ld of their 32-lane slice, C -= acc in global memory.
+// A second epilogue mode forms U12 = inv(L11) P A12 for the same factorisation step: A = inv(L11)
+// (split, 128 x 128), B = (P A12)^T (split, written by the swap/pack kernel); the epilogue stores U12
+// into the panel rows of the matrix and its transposed TF32 split over the B operand, where the
+// trailing update then reads it.
 // Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the kernel records a status bit,
 // stops issuing work, drains the copies it issued, frees its TMEM and returns.
 #include <cuda.h>
@@ -138,11 +142,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+struct TcArgs {
+  float* fac;        // per-point matrices, n x n row-major
+  int n;
+  int row0, col0;    // origin of C inside each point's matrix
+  int M, N;          // extent of C
+  int tiles_m, tiles_n, total;
+  int rows_a, rows_b;  // rows per point of the A and B operand arrays
+  int mode;          // 0: C -= A B^T;  1: C = A B^T and (bt_hi, bt_lo)[point][col][row] = split(C)
+  float* bt_hi;
+  float* bt_lo;
+  unsigned* status;
+};
+
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                   float* __restrict__ fac, int n, int base, int M, int rows_per_point, int tiles,
-                   int total, unsigned* status) {
+                   const TcArgs args) {
+  float* __restrict__ fac = args.fac;
+  const int n = args.n, M = args.M, N = args.N, total = args.total;
+  unsigned* status = args.status;
   extern __shared__ unsigned char raw[];
   Smem& s = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -165,7 +184,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s.tmem_base;
-  const int per_point = tiles * tiles;
+  const int per_point = args.tiles_m * args.tiles_n;
 
   if (warp == 0) {
     if (lane == 0) {  // ---------------------------------------------------------------- producer
@@ -173,8 +192,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t ph = 0;
       for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int p = t / per_point, r = t % per_point;
-        const int ya = p * rows_per_point + (r / tiles) * BM;
-        const int yb = p * rows_per_point + (r % tiles) * BN;
+        const int ya = p * args.rows_a + (r / args.tiles_n) * BM;
+        const int yb = p * args.rows_b + (r % args.tiles_n) * BN;
         bool ok = true;
         for (int c = 0; c < NCHUNK; ++c) {
           if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status)) { ok = false; break; }
@@ -249,31 +268,56 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!mbar_wait(s, &s.tfull[acc], aph, status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int p = t / per_point, r = t % per_point;
-      const int row = (r / tiles) * BM + sub * 32 + lane;
-      const int col0 = (r % tiles) * BN;
-      float* crow = fac + static_cast<size_t>(p) * n * n + static_cast<size_t>(base + row) * n + base;
-      const bool vec = (n & 3) == 0;
+      const int row = (r / args.tiles_n) * BM + sub * 32 + lane;
+      const int col0 = (r % args.tiles_n) * BN;
+      float* crow = fac + static_cast<size_t>(p) * n * n + static_cast<size_t>(args.row0 + row) * n + args.col0;
+      const bool vec = (n & 3) == 0 && (args.col0 & 3) == 0;
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ++ch) {
         uint32_t v[32];
         tmem_ld32(tmem + acc * BN + ch * 32 + ((sub * 32) << 16), v);
+        const int c0 = col0 + ch * 32;
         if (row < M) {
-          const int c0 = col0 + ch * 32;
           float* cp = crow + c0;
-          if (vec && c0 + 32 <= M) {
+          if (args.mode == 0) {
+            if (vec && c0 + 32 <= N) {
 #pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              float4 x = *reinterpret_cast<float4*>(cp + j);
-              x.x -= __uint_as_float(v[j]);
-              x.y -= __uint_as_float(v[j + 1]);
-              x.z -= __uint_as_float(v[j + 2]);
-              x.w -= __uint_as_float(v[j + 3]);
-              *reinterpret_cast<float4*>(cp + j) = x;
+              for (int j = 0; j < 32; j += 4) {
+                float4 x = *reinterpret_cast<float4*>(cp + j);
+                x.x -= __uint_as_float(v[j]);
+                x.y -= __uint_as_float(v[j + 1]);
+                x.z -= __uint_as_float(v[j + 2]);
+                x.w -= __uint_as_float(v[j + 3]);
+                *reinterpret_cast<float4*>(cp + j) = x;
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (c0 + j < N) cp[j] -= __uint_as_float(v[j]);
             }
           } else {
+            if (vec && c0 + 32 <= N) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (c0 + j < M) cp[j] -= __uint_as_float(v[j]);
+              for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4*>(cp + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                                 __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j)
+                if (c0 + j < N) cp[j] = __uint_as_float(v[j]);
+            }
+            // transposed split: lanes are consecutive rows, so each column's store is coalesced
+            float* bh = args.bt_hi + static_cast<size_t>(p) * args.rows_b * KTOT + row;
+            float* bl = args.bt_lo + static_cast<size_t>(p) * args.rows_b * KTOT + row;
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) {
+              if (c0 + j >= N) break;
+              uint32_t h;
+              const float x = __uint_as_float(v[j]);
+              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+              bh[static_cast<size_t>(c0 + j) * KTOT] = __uint_as_float(h);
+              bl[static_cast<size_t>(c0 + j) * KTOT] = x - __uint_as_float(h);
+            }
           }
         }
       }
@@ -319,22 +363,58 @@ bool make_map(CUtensorMap* m, float* base, size_t rows) {
 
 struct Maps {
   void* ws = nullptr;
-  int nx = 0, rows = 0;
-  CUtensorMap m[4];
+  int nx = 0, n = 0;
+  CUtensorMap m[6];
   bool ok = false;
 };
 
+Maps& maps_for(void* ws, int nx, int n) {
+  static Maps maps;
+  if (!maps.ok || maps.ws != ws || maps.nx != nx || maps.n != n) {
+    const size_t rows = static_cast<size_t>(nx) * (n - KTOT);
+    maps.ok = true;
+    for (int part = 0; part < 4; ++part)
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), rows);
+    for (int part = 4; part < 6; ++part)
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KTOT);
+    maps.ws = ws;
+    maps.nx = nx;
+    maps.n = n;
+    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(Smem) + 1024));
+  }
+  return maps;
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return sms;
+}
+
+void launch(const Maps& mp, int ia, int ib, const TcArgs& a, cudaStream_t st) {
+  const int grid = a.total < sm_count() ? a.total : sm_count();
+  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1], a);
+}
+
 }  // namespace
 
-// Workspace: four arrays [nx][n - 128][128] floats (A_hi, A_lo, B_hi, B_lo).
+// Workspace: four arrays [nx][n - 128][128] floats (A_hi, A_lo, B_hi, B_lo) and two [nx][128][128]
+// (inv(L11) hi, lo).
 size_t tc_workspace_bytes(int nx, int n, int nbmax) {
   if (nbmax != KTOT || n <= KTOT) return 0;
-  return 4ull * nx * static_cast<size_t>(n - KTOT) * KTOT * sizeof(float);
+  return (4ull * nx * static_cast<size_t>(n - KTOT) * KTOT + 2ull * nx * KTOT * KTOT) * sizeof(float);
 }
 
 float* tc_ws_part(void* ws, int nx, int n, int part) {
   if (!ws) return nullptr;
-  return static_cast<float*>(ws) + static_cast<size_t>(part) * nx * static_cast<size_t>(n - KTOT) * KTOT;
+  const size_t big = static_cast<size_t>(nx) * (n - KTOT) * KTOT, small = static_cast<size_t>(nx) * KTOT * KTOT;
+  float* f = static_cast<float*>(ws);
+  return part < 4 ? f + part * big : f + 4 * big + (part - 4) * small;
 }
 
 bool tc_available() {
@@ -348,33 +428,46 @@ bool tc_available() {
 }
 
 void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st) {
-  static Maps maps;
-  const int rows = n - KTOT;
-  if (!maps.ok || maps.ws != ws || maps.nx != nx || maps.rows != rows) {
-    maps.ok = true;
-    for (int part = 0; part < 4; ++part)
-      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * rows);
-    maps.ws = ws;
-    maps.nx = nx;
-    maps.rows = rows;
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(sizeof(Smem) + 1024));
-  }
   (void)nb;
-  const int base = k0 + KTOT;
-  const int M = n - base;
-  if (M <= 0 || !maps.ok) return;
-  const int tiles = (M + BM - 1) / BM;
-  const int total = nx * tiles * tiles;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int grid = total < sms ? total : sms;
-  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(maps.m[0], maps.m[1], maps.m[2], maps.m[3], fac, n,
-                                                              base, M, rows, tiles, total, status);
+  Maps& mp = maps_for(ws, nx, n);
+  const int base = k0 + KTOT, M = n - base;
+  if (M <= 0 || !mp.ok) return;
+  TcArgs a{};
+  a.fac = fac;
+  a.n = n;
+  a.row0 = base;
+  a.col0 = base;
+  a.M = M;
+  a.N = M;
+  a.tiles_m = a.tiles_n = (M + BM - 1) / BM;
+  a.total = nx * a.tiles_m * a.tiles_n;
+  a.rows_a = a.rows_b = n - KTOT;
+  a.mode = 0;
+  a.status = status;
+  launch(mp, 0, 2, a, st);
+}
+
+void tc_lu_u12(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
+  Maps& mp = maps_for(ws, nx, n);
+  const int base = k0 + KTOT, N = n - base;
+  if (N <= 0 || !mp.ok) return;
+  TcArgs a{};
+  a.fac = fac;
+  a.n = n;
+  a.row0 = k0;
+  a.col0 = base;
+  a.M = KTOT;
+  a.N = N;
+  a.tiles_m = 1;
+  a.tiles_n = (N + BN - 1) / BN;
+  a.total = nx * a.tiles_n;
+  a.rows_a = KTOT;
+  a.rows_b = n - KTOT;
+  a.mode = 1;
+  a.bt_hi = tc_ws_part(ws, nx, n, 2);
+  a.bt_lo = tc_ws_part(ws, nx, n, 3);
+  a.status = status;
+  launch(mp, 4, 2, a, st);
 }
 
 }  // namespace bte
