@@ -377,6 +377,296 @@ __global__ void __launch_bounds__(1024) lu_panel_kernel(T* __restrict__ fac, int
   }
 }
 
+// 16-byte vector of T
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ void vload(const T* p, T* out) {
+  using V = typename Vec16<T>::type;
+  const V v = *reinterpret_cast<const V*>(p);
+  const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+  for (int i = 0; i < Vec16<T>::n; ++i) out[i] = e[i];
+}
+template <typename T>
+__device__ __forceinline__ void vstore(T* p, const T* in) {
+  using V = typename Vec16<T>::type;
+  V v;
+  T* e = reinterpret_cast<T*>(&v);
+#pragma unroll
+  for (int i = 0; i < Vec16<T>::n; ++i) e[i] = in[i];
+  *reinterpret_cast<V*>(p) = v;
+}
+
+// Register-resident panel factorisation (same contract as lu_panel_kernel). Thread t holds panel rows
+// t and t + 1024 (RPT rows) of the current W-wide column block in registers. Per block: load it,
+// apply the earlier blocks of this panel left-looking (U block by a W x W unit-lower solve, then the
+// rank-W update of every row below, streaming the earlier L columns), eliminate column by column
+// (two barriers per column: argmax partials, then the pivot/current rows through shared memory),
+// store it, and apply its row swaps to the other panel columns. All global row segments move as
+// 16-byte vectors. Requires n % (16/sizeof(T)) == 0, nb % W == 0 and n - k0 <= 1024 * RPT.
+template <typename T, int W, int RPT>
+__global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, int* __restrict__ piv,
+                                                          int* __restrict__ perm, T* __restrict__ linv,
+                                                          int n, int k0, int nb, int nbmax,
+                                                          unsigned* status, float* __restrict__ ws_hi,
+                                                          float* __restrict__ ws_lo, float* __restrict__ li_hi,
+                                                          float* __restrict__ li_lo) {
+  constexpr int NT = 1024, VE = Vec16<T>::n;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int m0 = n - k0;
+  T* LX = reinterpret_cast<T*>(smraw);                       // 2 nb (nb+1): L11 / inv(L11) staging
+  T* SB = LX + 2 * static_cast<size_t>(nb) * (nb + 1);      // 2W x nbmax: swap staging
+  int* orig = reinterpret_cast<int*>(SB + 2 * static_cast<size_t>(W) * nbmax);  // m0
+  __shared__ T Ublk[W][W + 1];
+  __shared__ T Lt[W][W + 1];
+  __shared__ T prow[W], orow[W];
+  __shared__ T red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int lp[W], pslot[W], slot_row[2 * W], content[2 * W];
+  __shared__ int s_cnt, s_nslot;
+
+  const int mat = blockIdx.x;
+  T* A = fac + static_cast<size_t>(mat) * n * n;
+  int* ip = piv + static_cast<size_t>(mat) * n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
+  for (int r = tid; r < m0; r += NT) orig[r] = k0 + r;
+  bool bad_pivot = false;
+  T a[RPT][W];
+
+  for (int s0 = 0; s0 < nb; s0 += W) {
+    const int c0 = k0 + s0;
+    // load the column block, every panel row
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = tid + q * NT;
+      if (r < m0) {
+#pragma unroll
+        for (int v = 0; v < W; v += VE) vload(A + static_cast<size_t>(k0 + r) * n + c0 + v, &a[q][v]);
+      }
+    }
+    // left-looking: the earlier blocks of this panel
+    for (int t0 = 0; t0 < s0; t0 += W) {
+      const int ct = k0 + t0;
+      if (tid >= t0 && tid < t0 + W) {
+#pragma unroll
+        for (int jj = 0; jj < W; ++jj) Ublk[tid - t0][jj] = a[0][jj];
+      }
+      if (tid < W * W) Lt[tid / W][tid % W] = A[static_cast<size_t>(ct + tid / W) * n + ct + tid % W];
+      __syncthreads();
+      if (tid < W) {
+        for (int i = 1; i < W; ++i) {
+          T x = Ublk[i][tid];
+          for (int k = 0; k < i; ++k) x -= Lt[i][k] * Ublk[k][tid];
+          Ublk[i][tid] = x;
+        }
+      }
+      __syncthreads();
+      if (tid >= t0 && tid < t0 + W) {
+#pragma unroll
+        for (int jj = 0; jj < W; ++jj) a[0][jj] = Ublk[tid - t0][jj];
+      }
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = tid + q * NT;
+        if (r >= t0 + W && r < m0) {
+          const T* lr = A + static_cast<size_t>(k0 + r) * n + ct;
+#pragma unroll
+          for (int kv = 0; kv < W; kv += VE) {
+            T l[VE];
+            vload(lr + kv, l);
+#pragma unroll
+            for (int u = 0; u < VE; ++u)
+#pragma unroll
+              for (int jj = 0; jj < W; ++jj) a[q][jj] -= l[u] * Ublk[kv + u][jj];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // column-by-column elimination of rows s0.. (panel-relative)
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int cur = s0 + j;
+      T best = T(-1);
+      int bi = 0x7fffffff;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = tid + q * NT;
+        if (r >= cur && r < m0) {
+          const T v = tabs(a[q][j]);
+          if (v > best || (v == best && r < bi)) best = v, bi = r;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+      }
+      if (lane == 0) red_v[warp] = best, red_i[warp] = bi;
+      __syncthreads();
+      best = red_v[lane];
+      bi = red_i[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+      }
+      const int pr = (bi >= cur && bi < m0) ? bi : cur;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = tid + q * NT;
+        if (r == pr) {
+#pragma unroll
+          for (int jj = 0; jj < W; ++jj) prow[jj] = a[q][jj];
+        }
+        if (r == cur) {
+#pragma unroll
+          for (int jj = 0; jj < W; ++jj) orow[jj] = a[q][jj];
+        }
+      }
+      if (tid == 0) lp[j] = pr - s0;
+      __syncthreads();
+      const T pv = prow[j];
+      if (tid == 0 && (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv)))) bad_pivot = true;
+      const T inv = (pv != T(0)) ? T(1) / pv : T(0);
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        const int r = tid + q * NT;
+        if (r == cur) {
+#pragma unroll
+          for (int jj = 0; jj < W; ++jj) a[q][jj] = prow[jj];
+        } else if (r == pr) {
+#pragma unroll
+          for (int jj = 0; jj < W; ++jj) a[q][jj] = orow[jj];
+        }
+        if (r > cur && r < m0) {
+          const T l = a[q][j] * inv;
+          a[q][j] = l;
+#pragma unroll
+          for (int jj = j + 1; jj < W; ++jj) a[q][jj] -= l * prow[jj];
+        }
+      }
+    }
+    // store the column block
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+      const int r = tid + q * NT;
+      if (r < m0) {
+#pragma unroll
+        for (int v = 0; v < W; v += VE) vstore(A + static_cast<size_t>(k0 + r) * n + c0 + v, &a[q][v]);
+      }
+    }
+    // the block's row permutation as slots (see lu_panel_kernel), applied to the other panel columns
+    if (tid == 0) {
+      int ns = W;
+      for (int k = 0; k < W; ++k) slot_row[k] = c0 + k;
+      for (int j = 0; j < W; ++j) {
+        const int pl = lp[j];
+        int sl = pl;
+        if (pl >= W) {
+          sl = -1;
+          for (int q = W; q < ns; ++q)
+            if (slot_row[q] == c0 + pl) sl = q;
+          if (sl < 0) slot_row[sl = ns++] = c0 + pl;
+        }
+        pslot[j] = sl;
+        ip[c0 + j] = c0 + pl;
+        const int x = c0 + j - k0, y = c0 + pl - k0;
+        const int t = orig[x];
+        orig[x] = orig[y];
+        orig[y] = t;
+      }
+      for (int k = 0; k < ns; ++k) content[k] = k;
+      for (int j = 0; j < W; ++j) {
+        const int t = content[j];
+        content[j] = content[pslot[j]];
+        content[pslot[j]] = t;
+      }
+      s_nslot = ns;
+    }
+    __syncthreads();
+    const int nsl = s_nslot, nleft = s0, noth = nb - W;
+    for (int idx = tid; idx < nsl * noth; idx += NT) {
+      const int k = idx / noth, q = idx % noth;
+      const int col = q < nleft ? k0 + q : c0 + W + (q - nleft);
+      SB[k * noth + q] = A[static_cast<size_t>(slot_row[k]) * n + col];
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nsl * noth; idx += NT) {
+      const int k = idx / noth, q = idx % noth;
+      const int col = q < nleft ? k0 + q : c0 + W + (q - nleft);
+      A[static_cast<size_t>(slot_row[k]) * n + col] = SB[content[k] * noth + q];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && bad_pivot) atomicOr(status, kZeroPivot);
+
+  // permutation record for the trailing columns
+  int* pr_rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
+  if (tid == 0) s_cnt = 0;
+  __syncthreads();
+  for (int j = tid; j < nb; j += NT) pr_rec[1 + j] = orig[j];
+  for (int r = nb + tid; r < m0; r += NT) {
+    if (orig[r] != k0 + r) {
+      const int slot = atomicAdd(&s_cnt, 1);
+      pr_rec[1 + nbmax + 2 * slot] = k0 + r;
+      pr_rec[1 + nbmax + 2 * slot + 1] = orig[r];
+    }
+  }
+  __syncthreads();
+  if (tid == 0) pr_rec[0] = s_cnt;
+
+  // L21 split for the tensor-core trailing update ([point][row][nbmax]), 16-byte vectors
+  if (ws_hi) {
+    const int M = n - k0 - nb, q4 = nb / VE;
+    float* hi = ws_hi + static_cast<size_t>(mat) * (n - nbmax) * nbmax;
+    float* lo = ws_lo + static_cast<size_t>(mat) * (n - nbmax) * nbmax;
+    for (int idx = tid; idx < M * q4; idx += NT) {
+      const int r = idx / q4, k = VE * (idx % q4);
+      T v[VE];
+      vload(A + static_cast<size_t>(k0 + nb + r) * n + k0 + k, v);
+      float h[VE], l[VE];
+#pragma unroll
+      for (int u = 0; u < VE; ++u) split_tf32(static_cast<float>(v[u]), h[u], l[u]);
+#pragma unroll
+      for (int u = 0; u < VE; ++u) {
+        hi[static_cast<size_t>(r) * nbmax + k + u] = h[u];
+        lo[static_cast<size_t>(r) * nbmax + k + u] = l[u];
+      }
+    }
+  }
+
+  // inv(L11) in shared memory (+ its split for the tensor-core U12 formation)
+  const int ldl = nb + 1;
+  T* Ls = LX;
+  T* Xs = LX + static_cast<size_t>(nb) * ldl;
+  for (int idx = tid; idx < nb * nb; idx += NT) Ls[(idx / nb) * ldl + idx % nb] = A[static_cast<size_t>(k0 + idx / nb) * n + k0 + idx % nb];
+  __syncthreads();
+  tri_inverse_smem<T, true>(Ls, Xs, nb, ldl);
+  T* X = linv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
+  for (int idx = tid; idx < nb * nb; idx += NT) X[(idx / nb) * nbmax + idx % nb] = Xs[(idx / nb) * ldl + idx % nb];
+  if (li_hi) {
+    for (int idx = tid; idx < nbmax * nbmax; idx += NT) {
+      const int r = idx / nbmax, c = idx % nbmax;
+      float h = 0.f, l = 0.f;
+      if (r < nb && c < nb) split_tf32(static_cast<float>(Xs[r * ldl + c]), h, l);
+      li_hi[static_cast<size_t>(mat) * nbmax * nbmax + idx] = h;
+      li_lo[static_cast<size_t>(mat) * nbmax * nbmax + idx] = l;
+    }
+  }
+}
+
+template <typename T, int W>
+__host__ inline size_t panel_rr_smem_bytes(int m0, int nb, int nbmax) {
+  return (2ull * nb * (nb + 1) + 2ull * W * nbmax) * sizeof(T) + static_cast<size_t>(m0) * sizeof(int) + 16;
+}
+
 // inv(U11) of every panel of every point, after the factorisation (one CTA per point and panel).
 template <typename T>
 __global__ void __launch_bounds__(256) lu_uinv_kernel(const T* __restrict__ fac, T* __restrict__ uinv, int n,
@@ -767,9 +1057,38 @@ static int panel_width(int n, int nb) {
   return w < nb ? w : nb;
 }
 
+template <typename T, int W, int RPT>
+static void launch_rr(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax, unsigned* status,
+                      float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lu_panel_rr_kernel<T, W, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  const size_t smem = panel_rr_smem_bytes<T, W>(n - k0, nb, nbmax);
+  lu_panel_rr_kernel<T, W, RPT><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, status, ws_hi, ws_lo,
+                                                       li_hi, li_lo);
+}
+
 template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
+  const bool trail = k0 + nb < n;
+  float* wh = trail ? ws_hi : nullptr;
+  float* lh = trail ? li_hi : nullptr;
+  // register-resident kernel when the shape allows it
+  constexpr int VE = 16 / sizeof(T);
+  constexpr int W2 = sizeof(T) == 4 ? 16 : 8, W4 = sizeof(T) == 4 ? 8 : 4;
+  if (n % VE == 0 && nbmax <= 128) {
+    if (n - k0 <= 2048 && nb % W2 == 0) {
+      launch_rr<T, W2, 2>(fac, piv, perm, linv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
+      return;
+    }
+    if (n - k0 <= 4096 && nb % W4 == 0) {
+      launch_rr<T, W4, 4>(fac, piv, perm, linv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
+      return;
+    }
+  }
   const int W = panel_width<T>(n, nbmax);
   const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, W);
   static bool attr_set = false;
@@ -777,9 +1096,7 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  const bool trail = k0 + nb < n;
-  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, W, status,
-                                             trail ? ws_hi : nullptr, ws_lo, trail ? li_hi : nullptr, li_lo);
+  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, W, status, wh, ws_lo, lh, li_lo);
 }
 
 template <typename T>
