@@ -47,43 +47,89 @@ __host__ __device__ inline size_t panel_smem_bytes(int m0, int nb, int nbmax, in
 constexpr int kColWarps = 8;  // warps running the column-by-column elimination of a sub-panel
 constexpr int kLoadBatch = 8; // independent global loads in flight per thread in copy loops
 
-// inv(L) for a unit-lower (kUnit) or inv(U) for an upper triangular nb x nb matrix held in shared
-// memory (row stride ldl), by row blocks of 16: X[R,:] = D_RR^-1 (I[R,:] - D[R,rest] X[rest,:]),
-// rest = the rows already inverted (above R for L, below R for U). All threads of the block.
+// inv(L) for a unit-lower (kLower) or inv(U) for an upper triangular nb x nb matrix held in shared
+// memory (row stride ldl), by row blocks R of 16: the 16 x 16 diagonal blocks are inverted first
+// (one warp each, lane = column, registers), then row block by row block (downwards for L, upwards
+// for U) X[R, rest] = -inv(D_RR) (D[R, between] X[between, rest]) as two parallel products.
+// All threads of the block; X must not alias D.
 template <typename T, bool kLower>
 __device__ void tri_inverse_smem(const T* D, T* X, int nb, int ldl) {
-  const int tid = threadIdx.x, bd = blockDim.x;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
+  const int nblk = (nb + 15) / 16;
   for (int idx = tid; idx < nb * nb; idx += bd) X[(idx / nb) * ldl + idx % nb] = T(0);
   __syncthreads();
-  const int nblk = (nb + 15) / 16;
-  for (int bi = 0; bi < nblk; ++bi) {
+  // diagonal blocks: X[R,R] = inv(D[R,R]); lanes 0..15 one block, 16..31 the next
+  for (int pb = warp * 2; pb < nblk; pb += nwarp * 2) {
+    const int blk = pb + (lane >> 4), c = lane & 15;
+    const int r0 = 16 * blk, rb = blk < nblk ? min(16, nb - r0) : 0;
+    T x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = T(0);
+    if (c < rb) {
+      if (kLower) {
+        x[c] = T(1);
+#pragma unroll
+        for (int r = 1; r < 16; ++r) {
+          if (r > c && r < rb) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              if (k >= c && k < r) acc += D[(r0 + r) * ldl + r0 + k] * x[k];
+            x[r] = -acc;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int r = 15; r >= 0; --r) {
+          if (r <= c) {
+            T acc = (r == c) ? T(1) : T(0);
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+              if (k > r && k <= c) acc -= D[(r0 + r) * ldl + r0 + k] * x[k];
+            x[r] = acc / D[(r0 + r) * ldl + r0 + r];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (r < rb) X[(r0 + r) * ldl + r0 + c] = x[r];
+    }
+  }
+  __syncthreads();
+  // off-diagonal row blocks; the product D[R, between] X[between, rest] is staged in T1, the rows
+  // of X below (L) or above (U) the diagonal blocks' area are still zero and serve as scratch
+  T* T1 = X;  // write target rows R of X directly after the second product
+  (void)T1;
+  for (int bi = 1; bi < nblk; ++bi) {
     const int blk = kLower ? bi : nblk - 1 - bi;
     const int r0 = 16 * blk, r1 = min(nb, r0 + 16), rb = r1 - r0;
-    // columns that can be non-zero in these rows: [0, r1) for L, [r0, nb) for U
-    const int c_lo = kLower ? 0 : r0, c_hi = kLower ? r1 : nb, ncol = c_hi - c_lo;
+    // columns of X in row block R still to fill: [0, r0) for L, [r1, nb) for U
+    const int c_lo = kLower ? 0 : r1, c_hi = kLower ? r0 : nb, ncol = c_hi - c_lo;
+    // acc[r][c] = sum over k between of D[r][k] X[k][c]; stored temporarily in X[r][c]
     for (int idx = tid; idx < rb * ncol; idx += bd) {
       const int r = r0 + idx / ncol, c = c_lo + idx % ncol;
-      T acc = (r == c) ? T(1) : T(0);
+      T acc = T(0);
       if (kLower) {
-        for (int k = c; k < r0; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
+        for (int k = c; k < r0; ++k) acc += D[r * ldl + k] * X[k * ldl + c];
       } else {
-        for (int k = r1; k <= c; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
+        for (int k = r1; k <= c; ++k) acc += D[r * ldl + k] * X[k * ldl + c];
       }
       X[r * ldl + c] = acc;
     }
     __syncthreads();
+    // X[R, cols] = -inv(D_RR) acc: each thread one column, the 16 rows in registers
     for (int c = c_lo + tid; c < c_hi; c += bd) {
-      if (kLower) {
-        for (int r = r0 + 1; r < r1; ++r) {
-          T acc = X[r * ldl + c];
-          for (int k = r0; k < r; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
-          X[r * ldl + c] = acc;
-        }
-      } else {
-        for (int r = r1 - 1; r >= r0; --r) {
-          T acc = X[r * ldl + c];
-          for (int k = r + 1; k < r1; ++k) acc -= D[r * ldl + k] * X[k * ldl + c];
-          X[r * ldl + c] = acc / D[r * ldl + r];
+      T v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = i < rb ? X[(r0 + i) * ldl + c] : T(0);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (i < rb) {
+          T acc = T(0);
+#pragma unroll
+          for (int k = 0; k < 16; ++k)
+            if (k < rb) acc += X[(r0 + i) * ldl + r0 + k] * v[k];
+          X[(r0 + i) * ldl + c] = -acc;
         }
       }
     }
@@ -417,8 +463,7 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
   constexpr int NT = 1024, VE = Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int m0 = n - k0;
-  T* LX = reinterpret_cast<T*>(smraw);                       // 2 nb (nb+1): L11 / inv(L11) staging
-  T* SB = LX + 2 * static_cast<size_t>(nb) * (nb + 1);      // 2W x nbmax: swap staging
+  T* SB = reinterpret_cast<T*>(smraw);                       // 2W x nbmax: swap staging
   int* orig = reinterpret_cast<int*>(SB + 2 * static_cast<size_t>(W) * nbmax);  // m0
   __shared__ T Ublk[W][W + 1];
   __shared__ T Lt[W][W + 1];
@@ -469,6 +514,7 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
 #pragma unroll
         for (int jj = 0; jj < W; ++jj) a[0][jj] = Ublk[tid - t0][jj];
       }
+      // rows below the block: a[q][:] -= L[r][ct:ct+W] Ublk
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid + q * NT;
@@ -622,6 +668,20 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
   __syncthreads();
   if (tid == 0) pr_rec[0] = s_cnt;
 
+}
+
+// After lu_panel_rr: the L21 split for the tensor-core trailing update and inv(L11) (+ its split).
+template <typename T>
+__global__ void __launch_bounds__(1024) lu_panel_tail_kernel(const T* __restrict__ fac, T* __restrict__ linv, int n,
+                                                            int k0, int nb, int nbmax, float* __restrict__ ws_hi,
+                                                            float* __restrict__ ws_lo, float* __restrict__ li_hi,
+                                                            float* __restrict__ li_lo) {
+  constexpr int NT = 1024, VE = Vec16<T>::n;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* LX = reinterpret_cast<T*>(smraw);
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const T* A = fac + static_cast<size_t>(mat) * n * n;
+  const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
   // L21 split for the tensor-core trailing update ([point][row][nbmax]), 16-byte vectors
   if (ws_hi) {
     const int M = n - k0 - nb, q4 = nb / VE;
@@ -634,10 +694,15 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
       float h[VE], l[VE];
 #pragma unroll
       for (int u = 0; u < VE; ++u) split_tf32(static_cast<float>(v[u]), h[u], l[u]);
+      if (VE == 4) {
+        *reinterpret_cast<float4*>(hi + static_cast<size_t>(r) * nbmax + k) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(lo + static_cast<size_t>(r) * nbmax + k) = make_float4(l[0], l[1], l[2], l[3]);
+      } else {
 #pragma unroll
-      for (int u = 0; u < VE; ++u) {
-        hi[static_cast<size_t>(r) * nbmax + k + u] = h[u];
-        lo[static_cast<size_t>(r) * nbmax + k + u] = l[u];
+        for (int u = 0; u < VE; ++u) {
+          hi[static_cast<size_t>(r) * nbmax + k + u] = h[u];
+          lo[static_cast<size_t>(r) * nbmax + k + u] = l[u];
+        }
       }
     }
   }
@@ -662,9 +727,11 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
   }
 }
 
+
 template <typename T, int W>
 __host__ inline size_t panel_rr_smem_bytes(int m0, int nb, int nbmax) {
-  return (2ull * nb * (nb + 1) + 2ull * W * nbmax) * sizeof(T) + static_cast<size_t>(m0) * sizeof(int) + 16;
+  (void)nb;
+  return 2ull * W * nbmax * sizeof(T) + static_cast<size_t>(m0) * sizeof(int) + 16;
 }
 
 // inv(U11) of every panel of every point, after the factorisation (one CTA per point and panel).
@@ -1065,9 +1132,16 @@ static void launch_rr(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k
     cudaFuncSetAttribute(lu_panel_rr_kernel<T, W, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  static bool attr_tail = false;
+  if (!attr_tail) {
+    cudaFuncSetAttribute(lu_panel_tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_tail = true;
+  }
   const size_t smem = panel_rr_smem_bytes<T, W>(n - k0, nb, nbmax);
   lu_panel_rr_kernel<T, W, RPT><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, status, ws_hi, ws_lo,
                                                        li_hi, li_lo);
+  const size_t smem_tail = 2ull * nb * (nb + 1) * sizeof(T);
+  lu_panel_tail_kernel<T><<<nx, 1024, smem_tail, st>>>(fac, linv, n, k0, nb, nbmax, ws_hi, ws_lo, li_hi, li_lo);
 }
 
 template <typename T>
