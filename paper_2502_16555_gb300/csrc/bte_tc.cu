@@ -14,7 +14,8 @@
 //   warp 1  allocates 256 TMEM columns (two 128x128 FP32 accumulators) and issues the MMAs
 //           (M=128, N=128, K=8 per instruction, 12 per chunk), committing each stage back to the
 //           producer and each finished accumulator to the epilogue;
-//   warps 2-5 epilogue: tcgen05.ld of their 32-lane slice, C -= acc in global memory.
+//   warps 2-5 epilogue: tcgen05.ld of their 32-lane slice, C -= acc in global memory; for full tile
+//           rows each thread fetches its 128 C values before the accumulator is ready.
 // A second epilogue mode forms U12 = inv(L11) P A12 for the same factorisation step: A = inv(L11)
 // (split, 128 x 128), B = (P A12)^T (split, written by the swap/pack kernel); the epilogue stores U12
 // into the panel rows of the matrix and its transposed TF32 split over the B operand, where the
@@ -265,21 +266,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int acc = 0;
     uint32_t aph = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
-      if (!mbar_wait(s, &s.tfull[acc], aph, status)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int p = t / per_point, r = t % per_point;
       const int row = (r / args.tiles_n) * BM + sub * 32 + lane;
       const int col0 = (r % args.tiles_n) * BN;
       float* crow = fac + static_cast<size_t>(p) * n * n + static_cast<size_t>(args.row0 + row) * n + args.col0;
       const bool vec = (n & 3) == 0 && (args.col0 & 3) == 0;
-#pragma unroll 1
+      // mode 0, full tile row: fetch this thread's 128 C values before the accumulator is ready, so
+      // the loads overlap the tile's MMAs
+      const bool pre = args.mode == 0 && vec && row < M && col0 + BN <= N;
+      float4 cv[BN / 4];
+      if (pre) {
+#pragma unroll
+        for (int j = 0; j < BN / 4; ++j) cv[j] = *reinterpret_cast<const float4*>(crow + col0 + 4 * j);
+      }
+      if (!mbar_wait(s, &s.tfull[acc], aph, status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
       for (int ch = 0; ch < BN / 32; ++ch) {
         uint32_t v[32];
         tmem_ld32(tmem + acc * BN + ch * 32 + ((sub * 32) << 16), v);
         const int c0 = col0 + ch * 32;
         if (row < M) {
           float* cp = crow + c0;
-          if (args.mode == 0) {
+          if (pre) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float4 x = cv[ch * 8 + j];
+              x.x -= __uint_as_float(v[4 * j]);
+              x.y -= __uint_as_float(v[4 * j + 1]);
+              x.z -= __uint_as_float(v[4 * j + 2]);
+              x.w -= __uint_as_float(v[4 * j + 3]);
+              *reinterpret_cast<float4*>(cp + 4 * j) = x;
+            }
+          } else if (args.mode == 0) {
             if (vec && c0 + 32 <= N) {
 #pragma unroll
               for (int j = 0; j < 32; j += 4) {
