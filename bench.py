@@ -36,6 +36,12 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TF32_OVER_BF16 = 1.1 / 2.25
 # FP32 SIMT peak from unit counts and clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 peak: cuBLAS DGEMM (8192^3) measured on this machine's GB300 with `bench.py --peaks`.
+FP64_PEAK_TFLOPS = 1.10
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernels from
+# one ncu capture of the command in profiles/, scaled from the captured (largest) launch to the
+# average launch by the algorithmic bytes; None once the kernel has changed since the capture.
+TRAFFIC = {}
 
 
 def load_peaks():
@@ -106,65 +112,71 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------------- work model
 
-def algorithmic(cfg, precision, kernel):
-    """(amount, unit, bound) of algorithmic work of one step for a kernel class.
-
-    lu_gemm: 2 M^2 kb flops per point and panel (M = trailing size); x_apply_q: the Q stream
-    (8 Nv Nx^2 bytes) plus Y in/out per half step; lu_solve: one read of the factors; v_form: one
-    write of the factors plus the K_C/K_A read."""
-    nx, nv = cfg["nx"], cfg["nr"] * cfg["ntheta"]
+def algorithmic(cfg, precision, kernel, tc):
+    """(amount, unit, bound) of the algorithmic work of one step for a kernel class (per-step sums
+    over its launches; per unit):
+      lu_panel     read + write of every outer panel once: 2 * 4 B * (Nv - k0) * 128 per point;
+      lu_gemm      trailing updates, 2 M^2 128 flop per point and panel (M = Nv - k0 - 128);
+      lu_swap_trsm U12 = inv(L11) P A12, 2 * 128 * M * 128 flop per point and panel;
+      lu_solve     one read of the FP32 factors per solve launch (4 B * Nv^2 per point);
+      x_apply_q    the FP64 Q stream (8 B Nv Nx^2) plus Y in/out, per half step;
+      v_form       write of the per-point matrices plus the K_C/K_A read;
+      residual     FP64 flops of the structured residual (Algorithm 2) per sweep."""
+    nx, nr, nt = cfg["nx"], cfg["nr"], cfg["ntheta"]
+    nv = nr * nt
+    nl = cfg.get("nl") or nt
     esz = 8 if precision == "fp64" else 4
     nb = 64 if precision == "fp64" else 128
+    panels = [(k0, min(nb, nv - k0)) for k0 in range(0, nv, nb)]
+    if kernel == "lu_panel":
+        return sum(2.0 * esz * (nv - k0) * kb for k0, kb in panels) * nx, "byte", "hbm"
     if kernel == "lu_gemm":
-        fl = 0.0
-        for k0 in range(0, nv, nb):
-            kb = min(nb, nv - k0)
-            m = nv - k0 - kb
-            fl += 2.0 * m * m * kb
-        return fl * nx, "flop", "tensor"
+        return sum(2.0 * (nv - k0 - kb) ** 2 * kb for k0, kb in panels) * nx, "flop", "tensor" if tc else "alu"
+    if kernel == "lu_swap_trsm":
+        return sum(2.0 * kb * (nv - k0 - kb) * kb for k0, kb in panels) * nx, "flop", "tensor" if tc else "alu"
+    if kernel == "lu_solve":
+        return float(esz) * nx * nv * nv, "byte/launch", "hbm"
     if kernel == "x_apply_q":
         return 2 * (8.0 * nv * nx * nx + 16.0 * nv * nx), "byte", "hbm"
-    if kernel == "lu_solve":
-        return float(esz) * nx * nv * nv, "byte", "hbm"
     if kernel == "v_form":
         return float(esz) * nx * nv * nv + 16.0 * nv * nv, "byte", "hbm"
-    if kernel == "lu_panel":
-        fl = 0.0
-        for k0 in range(0, nv, nb):
-            kb = min(nb, nv - k0)
-            fl += (nv - k0) * kb * kb
-        return fl * nx, "flop", "alu"
+    if kernel == "residual":
+        return 2.0 * nx * (2 * nl * nt * nr + 3 * nl * nr * nr), "flop/launch", "alu"
     return None, None, None
 
 
-def roofline(cfg, precision, prof, steps, peaks, tc):
-    tot = {k: v[0] for k, v in prof.items()}
-    dom = max(tot, key=tot.get)
-    amount, unit, bound = algorithmic(cfg, precision, dom)
-    if amount is None:
-        return {"kernel": dom, "bound": None}
-    n_launch = prof[dom][1]
-    sec = tot[dom] / 1e3
-    per_step_amount = amount
-    achieved = per_step_amount * steps / sec
-    if unit == "flop":
-        achieved_t = achieved / 1e12
-        if dom == "lu_gemm" and precision == "mixed" and tc:
-            peak = peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0
-            bound, pk_note = "tensor", "TF32 peak (measured BF16 x 1.1/2.25) / 3 products (TF32x3)"
-        elif precision == "fp64":
-            peak = 1.10
-            bound, pk_note = "alu", "FP64 DGEMM measured on this GB300 (cuBLAS, 8192^3)"
-        else:
-            peak = FP32_SIMT_PEAK_TFLOPS
-            bound, pk_note = "alu", "FP32 SIMT: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-        return {"kernel": dom, "bound": bound, "achieved": achieved_t, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved_t / peak, "traffic": None, "launches_per_step": n_launch / steps,
-                "peak_source": pk_note + " (" + peaks["src"] + ")"}
-    gbs = achieved / 1e9
-    return {"kernel": dom, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": gbs / peaks["hbm_gbs"], "traffic": None, "launches_per_step": n_launch / steps,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (" + peaks["src"] + ")"}
+def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc):
+    amount, unit, bound = algorithmic(cfg, precision, kernel, tc)
+    ms, launches = prof.get(kernel, (0.0, 0))
+    if amount is None or launches == 0 or ms <= 0:
+        return None
+    total = amount * (launches if unit.endswith("/launch") else steps)
+    rate = total / (ms / 1e3)
+    if bound == "hbm":
+        achieved, peak, u = rate / 1e9, peaks["hbm_gbs"], "GB/s"
+        src = "MEASURED_PEAKS.json hbm_gbs (" + peaks["src"] + ")"
+    elif bound == "tensor":
+        achieved, peak, u = rate / 1e12, peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0, "TFLOP/s"
+        src = "measured BF16 x 1.1/2.25 (TF32) / 3 products (" + peaks["src"] + ")"
+    elif precision == "fp64" or kernel == "residual":
+        achieved, peak, u = rate / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
+        src = "FP64 DGEMM measured on this GB300 (bench.py --peaks)"
+    else:
+        achieved, peak, u = rate / 1e12, FP32_SIMT_PEAK_TFLOPS, "TFLOP/s"
+        src = "FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
+            "frac": achieved / peak, "traffic": TRAFFIC.get(kernel), "launches_per_step": launches / steps,
+            "ms_per_step": ms / steps, "peak_source": src}
+
+
+def rooflines(cfg, precision, prof, steps, peaks, tc):
+    out = {}
+    for k in prof:
+        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc)
+        if r:
+            out[k] = r
+    dom = max(out, key=lambda k: out[k]["ms_per_step"])
+    return out[dom], out
 
 
 # ---------------------------------------------------------------------------------- CPU oracle leg
@@ -314,6 +326,7 @@ def run_ours(args, rank, world):
         e2e = {"value": world * dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * dof,
                "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"}
 
+    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -332,7 +345,8 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": roofline(cfg, "mixed", prof, args.steps, peaks, tc),
+        "roofline": rf_dom,
+        "rooflines": rf_all,
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
     }
     if world == 1 and not args.no_cpu:
@@ -340,6 +354,34 @@ def run_ours(args, rank, world):
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+    return 0
+
+
+def measure_peaks():
+    """Library GEMM throughput on this GPU (cuBLAS via torch.matmul, 8192^3, best of several): the
+    denominators for FP64 and TF32 work that MEASURED_PEAKS.json does not carry."""
+    import torch
+    out = {}
+    for name, dt, tf32, it in (("fp64", torch.float64, False, 3), ("fp32_simt", torch.float32, False, 5),
+                               ("tf32", torch.float32, True, 10), ("bf16", torch.bfloat16, False, 10)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(8192, 8192, device="cuda", dtype=dt)
+        b = torch.randn(8192, 8192, device="cuda", dtype=dt)
+        for _ in range(2):
+            a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(it):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name + "_tflops"] = 2 * 8192**3 / best / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -352,9 +394,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.peaks:
+        return measure_peaks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world)

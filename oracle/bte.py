@@ -17,7 +17,7 @@ to its tolerance, this oracle reaches it directly.
 Layout: F has shape (Nx, Ntheta, Nr), float64: x slowest, radial B-spline index fastest. The
 velocity index inside a point is v = a*Nr + k (ordinate a, B-spline k).
 
-Readings of points the paper leaves open (the full list with reasons is in the design notes):
+Readings of points the paper leaves open:
   - collision weak form uses v^3 sigma (test measure v^2 times speed v);
   - ionization releases two electrons, each at (eps - eps_ion)/2, gain factor 2;
   - excitation: one electron at eps - eps_th;

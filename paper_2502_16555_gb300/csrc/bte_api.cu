@@ -162,7 +162,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
-      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv),
+      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nullptr,
                                                               nx, n, k0, kb, nb, h->status, nullptr, nullptr,
                                                               nullptr, nullptr, st));
       if (k0 + kb < n) {
@@ -180,14 +180,17 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     float* ulo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 3) : nullptr;
     float* lhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 4) : nullptr;
     float* llo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 5) : nullptr;
+    const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb);
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
+      // the L21 split for the tensor cores is written by lu_swap_pack
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv),
-                                                             nx, n, k0, kb, nb, h->status, whi, wlo, lhi, llo, st));
+                                                             fused_uinv ? static_cast<float*>(h->uinv) : nullptr,
+                                                             nx, n, k0, kb, nb, h->status, nullptr, nullptr, lhi, llo, st));
       if (k0 + kb < n) {
         if (h->use_tc) {
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, kb, nb, uhi, ulo, st));
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, kb, nb, uhi, ulo, whi, wlo, st));
           BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, h->tcws, h->status, st));
           BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, kb, h->tcws, h->status, st));
         } else {
@@ -197,7 +200,8 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
         }
       }
     }
-    BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));
+    if (!fused_uinv)
+      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));
     BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(fac, h->perm, static_cast<float*>(h->linv),
                                                                    static_cast<float*>(h->uinv), h->Fa, h->Fb, nx, n,
                                                                    nb, nullptr, 0, st));
@@ -328,7 +332,8 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
         h->fac = f;
         h->linv = l;
         h->uinv = u;
-        if (ok && !(cfg->flags & BTE_FLAG_SIMT_GEMM) && bte::tc_available()) {
+        if (ok && !(cfg->flags & BTE_FLAG_SIMT_GEMM) && bte::tc_workspace_bytes(o.nx, o.nv, h->nb) > 0 &&
+            bte::tc_available()) {
           unsigned char* w = nullptr;
           ok = chk(dalloc(h, &w, bte::tc_workspace_bytes(o.nx, o.nv, h->nb)));
           h->tcws = w;

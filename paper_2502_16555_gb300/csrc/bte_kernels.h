@@ -43,12 +43,17 @@ int perm_record_ints(int nbmax);
 // Per-point, per-panel records ([point][panel] ...): perm (perm_record_ints each) and inv(L11)
 // (nbmax x nbmax each).
 // li_hi/li_lo (may be NULL): TF32 split of inv(L11) for the tensor-core U12 formation.
+// uinv (may be NULL): per-panel inv(U11) ([point][panel], nbmax x nbmax), written only by the
+// mark-pivoting panel kernel, i.e. when lu_panel_fuses_uinv<T>(n, nbmax) holds.
 template <typename T>
-void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
+void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st);
-// Tensor-core path: displaced-row writes of the panel permutation and the split (P A12)^T operand.
+template <typename T>
+bool lu_panel_fuses_uinv(int n, int nbmax);
+// Tensor-core path: displaced-row writes of the panel permutation, the split (P A12)^T operand
+// (bt_hi/bt_lo) and the split L21 operand (a_hi/a_lo, may be NULL).
 void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,
-                         float* bt_lo, cudaStream_t st);
+                         float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st);
 // inv(U11) of every panel of every point, once the factorisation is complete ([point][panel]).
 template <typename T>
 void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_t st);

@@ -15,6 +15,7 @@
 // columns, which is the same elimination order the factorisation used.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "bte_kernels.h"
@@ -52,8 +53,10 @@ constexpr int kLoadBatch = 8; // independent global loads in flight per thread i
 // (one warp each, lane = column, registers), then row block by row block (downwards for L, upwards
 // for U) X[R, rest] = -inv(D_RR) (D[R, between] X[between, rest]) as two parallel products.
 // All threads of the block; X must not alias D.
+// X = 0, then the inverses of the 16 x 16 diagonal blocks of D into X (lanes 0..15 of a warp one block,
+// 16..31 the next; lane = column, the column in registers). Ends with a barrier.
 template <typename T, bool kLower>
-__device__ void tri_inverse_smem(const T* D, T* X, int nb, int ldl) {
+__device__ void tri_inverse_diag16(const T* D, T* X, int nb, int ldl) {
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
   const int nblk = (nb + 15) / 16;
   for (int idx = tid; idx < nb * nb; idx += bd) X[(idx / nb) * ldl + idx % nb] = T(0);
@@ -96,6 +99,13 @@ __device__ void tri_inverse_smem(const T* D, T* X, int nb, int ldl) {
     }
   }
   __syncthreads();
+}
+
+template <typename T, bool kLower>
+__device__ void tri_inverse_smem(const T* D, T* X, int nb, int ldl) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nblk = (nb + 15) / 16;
+  tri_inverse_diag16<T, kLower>(D, X, nb, ldl);
   // off-diagonal row blocks; the product D[R, between] X[between, rest] is staged in T1, the rows
   // of X below (L) or above (U) the diagonal blocks' area are still zero and serve as scratch
   T* T1 = X;  // write target rows R of X directly after the second product
@@ -105,16 +115,39 @@ __device__ void tri_inverse_smem(const T* D, T* X, int nb, int ldl) {
     const int r0 = 16 * blk, r1 = min(nb, r0 + 16), rb = r1 - r0;
     // columns of X in row block R still to fill: [0, r0) for L, [r1, nb) for U
     const int c_lo = kLower ? 0 : r1, c_hi = kLower ? r0 : nb, ncol = c_hi - c_lo;
-    // acc[r][c] = sum over k between of D[r][k] X[k][c]; stored temporarily in X[r][c]
-    for (int idx = tid; idx < rb * ncol; idx += bd) {
-      const int r = r0 + idx / ncol, c = c_lo + idx % ncol;
-      T acc = T(0);
-      if (kLower) {
-        for (int k = c; k < r0; ++k) acc += D[r * ldl + k] * X[k * ldl + c];
-      } else {
-        for (int k = r1; k <= c; ++k) acc += D[r * ldl + k] * X[k * ldl + c];
+    // acc[r][c] = sum over k between of D[r][k] X[k][c], stored temporarily in X[r][c]. Register
+    // tiles of 4 rows x 2 columns (c and c + half): per k, four broadcast reads of D and two
+    // conflict-free reads of X feed eight FMAs. Entries of X outside its triangle are zero, so the
+    // union of the two columns' k ranges can be used.
+    {
+      const int half = (ncol + 1) / 2, ngrp = (rb + 3) / 4, js = (half + 31) & ~31;
+      for (int t = tid; t < ngrp * js; t += bd) {
+        const int g = t / js, j = t % js;
+        if (j >= half) continue;
+        const int ca = c_lo + j, cb = c_lo + j + half;
+        const bool has_b = cb < c_hi;
+        const int ra = r0 + 4 * g;
+        T acc[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = T(0);
+        const int k_lo = kLower ? ca : r1, k_hi = kLower ? r0 : (has_b ? cb : ca) + 1;
+        for (int k = k_lo; k < k_hi; ++k) {
+          const T xa = X[k * ldl + ca], xb = has_b ? X[k * ldl + cb] : T(0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const T d = (ra + i < r1) ? D[(ra + i) * ldl + k] : T(0);
+            acc[i][0] += d * xa;
+            acc[i][1] += d * xb;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if (ra + i < r1) {
+            X[(ra + i) * ldl + ca] = acc[i][0];
+            if (has_b) X[(ra + i) * ldl + cb] = acc[i][1];
+          }
+        }
       }
-      X[r * ldl + c] = acc;
     }
     __syncthreads();
     // X[R, cols] = -inv(D_RR) acc: each thread one column, the 16 rows in registers
@@ -428,6 +461,99 @@ template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
+// Four consecutive T from a 16-byte aligned address (one or two 16-byte loads).
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T (&o)[4]) {
+  using V = typename Vec16<T>::type;
+  constexpr int VE = Vec16<T>::n;
+#pragma unroll
+  for (int v = 0; v < 4; v += VE) {
+    const V x = *reinterpret_cast<const V*>(p + v);
+    const T* e = reinterpret_cast<const T*>(&x);
+#pragma unroll
+    for (int u = 0; u < VE; ++u) o[v + u] = e[u];
+  }
+}
+
+// acc[r][c] += sum_k A[r][k] B[k][c] for a 4 x 4 tile (rows of A at A + r lda, rows of B at
+// B + k ldb); K, lda, ldb multiples of 4, A and B 16-byte aligned.
+template <typename T>
+__device__ __forceinline__ void tile4_nn(const T* A, int lda, const T* B, int ldb, int K, T (&acc)[4][4]) {
+  for (int k = 0; k < K; k += 4) {
+    T a[4][4], b[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) load4(A + r * lda + k, a[r]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load4(B + (k + q) * ldb, b[q]);
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] += a[r][q] * b[q][c];
+  }
+}
+
+// inv(L) (unit lower, kLower) or inv(U) (upper) of an nb x nb block in shared memory by recursive
+// doubling: the 16 x 16 diagonal blocks first (tri_inverse_diag16), then for w = 16, 32, 64, ... every
+// pair of neighbouring w-blocks [a, b), [b, e) is joined:
+//   lower  X[b:e, a:b] = -X[b:e, b:e] (D[b:e, a:b] X[a:b, a:b])
+//   upper  X[a:b, b:e] = -X[a:b, a:b] (D[a:b, b:e] X[b:e, b:e])
+// each as two 4 x 4-register-tiled products over all pairs of a level at once, with the inner
+// product staged in Tmp (nb * nb / 4 elements at most). Requires nb % 16 == 0, ldl % 4 == 0 and
+// 16-byte aligned D, X, Tmp. X's unused triangle is zero on return. All threads of the block.
+template <typename T, bool kLower>
+__device__ void tri_inverse_rd(const T* D, T* X, T* Tmp, int nb, int ldl) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  tri_inverse_diag16<T, kLower>(D, X, nb, ldl);
+  for (int w = 16; w < nb; w *= 2) {
+    const int npair = (nb + 2 * w - 1) / (2 * w), tw = w / 4, tpp = tw * tw;
+    // phase 1: Tmp_pair = lower: D[b:e, a:b] X[a:b, a:b]  ((e-b) x w);  upper: D[a:b, b:e] X[b:e, b:e]  (w x (e-b))
+    for (int g = tid; g < npair * tpp; g += bd) {
+      const int pr = g / tpp, ti = (g % tpp) / tw, tj = g % tw;
+      const int a0 = 2 * w * pr, b0 = a0 + w, e0 = min(a0 + 2 * w, nb);
+      if (b0 >= nb) continue;
+      const int rows = kLower ? e0 - b0 : w, cols = kLower ? w : e0 - b0;
+      if (4 * ti >= rows || 4 * tj >= cols) continue;
+      T acc[4][4] = {};
+      if (kLower)
+        tile4_nn(D + (b0 + 4 * ti) * ldl + a0, ldl, X + a0 * ldl + a0 + 4 * tj, ldl, w, acc);
+      else
+        tile4_nn(D + (a0 + 4 * ti) * ldl + b0, ldl, X + b0 * ldl + b0 + 4 * tj, ldl, e0 - b0, acc);
+      T* t = Tmp + static_cast<size_t>(pr) * w * w;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) t[(4 * ti + r) * w + 4 * tj + c] = acc[r][c];
+    }
+    __syncthreads();
+    // phase 2: lower X[b:e, a:b] = -X[b:e, b:e] Tmp;  upper X[a:b, b:e] = -X[a:b, a:b] Tmp
+    for (int g = tid; g < npair * tpp; g += bd) {
+      const int pr = g / tpp, ti = (g % tpp) / tw, tj = g % tw;
+      const int a0 = 2 * w * pr, b0 = a0 + w, e0 = min(a0 + 2 * w, nb);
+      if (b0 >= nb) continue;
+      const int rows = kLower ? e0 - b0 : w, cols = kLower ? w : e0 - b0;
+      if (4 * ti >= rows || 4 * tj >= cols) continue;
+      T acc[4][4] = {};
+      const T* t = Tmp + static_cast<size_t>(pr) * w * w;
+      T* out;
+      if (kLower) {
+        tile4_nn(X + (b0 + 4 * ti) * ldl + b0, ldl, t + 4 * tj, w, e0 - b0, acc);
+        out = X + (b0 + 4 * ti) * ldl + a0 + 4 * tj;
+      } else {
+        tile4_nn(X + (a0 + 4 * ti) * ldl + a0, ldl, t + 4 * tj, w, w, acc);
+        out = X + (a0 + 4 * ti) * ldl + b0 + 4 * tj;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out[r * ldl + c] = -acc[r][c];
+    }
+    __syncthreads();
+  }
+}
+
+
 template <typename T>
 __device__ __forceinline__ void vload(const T* p, T* out) {
   using V = typename Vec16<T>::type;
@@ -446,45 +572,63 @@ __device__ __forceinline__ void vstore(T* p, const T* in) {
   *reinterpret_cast<V*>(p) = v;
 }
 
-// Register-resident panel factorisation (same contract as lu_panel_kernel). Thread t holds panel rows
-// t and t + 1024 (RPT rows) of the current W-wide column block in registers. Per block: load it,
-// apply the earlier blocks of this panel left-looking (U block by a W x W unit-lower solve, then the
-// rank-W update of every row below, streaming the earlier L columns), eliminate column by column
-// (two barriers per column: argmax partials, then the pivot/current rows through shared memory),
-// store it, and apply its row swaps to the other panel columns. All global row segments move as
-// 16-byte vectors. Requires n % (16/sizeof(T)) == 0, nb % W == 0 and n - k0 <= 1024 * RPT.
+// Panel factorisation with pivots as marks (same contract as lu_panel_kernel, plus inv(U11); the
+// TF32 split of L21 is left to lu_swap_pack). One CTA of 1024 threads per point; thread t holds
+// physical panel rows t + 1024 q (q < RPT) of the current W-wide column block in registers. Rows do
+// not move while the panel is factored: choosing a pivot marks its row with the column it pivots
+// (pc). Per column block:
+//   load it; apply the earlier blocks left-looking (their pivot rows post the block's entries, the
+//   W x W unit-lower solve goes through the precomputed inverse of that block's diagonal part, the
+//   unmarked rows take the rank-W update streaming their earlier L entries);
+//   eliminate column by column with ONE barrier per column: each warp posts its best unmarked
+//   candidate together with the candidate's row, then every warp reduces the 32 posts itself and
+//   reads the pivot row from the winning post (posts are double-buffered by column parity);
+//   store it and invert the unit-lower part of its own diagonal block for the later blocks.
+// Broadcast operands (pivot rows, U blocks) are read from shared memory as 16-byte vectors.
+// At the end the rows are put in the order of the equivalent swap sequence (only displaced rows
+// move), the panel record and the LAPACK-style pivots are written, and inv(L11) (+ split) and,
+// when uinv is given, inv(U11) are formed from the final diagonal block.
 template <typename T, int W, int RPT>
-__global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, int* __restrict__ piv,
-                                                          int* __restrict__ perm, T* __restrict__ linv,
-                                                          int n, int k0, int nb, int nbmax,
-                                                          unsigned* status, float* __restrict__ ws_hi,
-                                                          float* __restrict__ ws_lo, float* __restrict__ li_hi,
-                                                          float* __restrict__ li_lo) {
-  constexpr int NT = 1024, VE = Vec16<T>::n;
+__global__ void __launch_bounds__(1024, 1) lu_panel_lazy_kernel(T* __restrict__ fac, int* __restrict__ piv,
+                                                               int* __restrict__ perm, T* __restrict__ linv,
+                                                               T* __restrict__ uinv, int n, int k0, int nb,
+                                                               int nbmax, unsigned* status,
+                                                               float* __restrict__ li_hi, float* __restrict__ li_lo) {
+  constexpr int NT = 1024, VE = Vec16<T>::n, NONE = 1 << 30, MAXB = 128 / W;
   extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ T LinvB[MAXB][W][W + 1];             // inverse of the unit-lower part of each block's diagonal block
+  __shared__ T Tb[W][W + 1];                      // the diagonal block of the block just eliminated
+  __shared__ __align__(16) T Raw[W][W];           // block t's pivot rows, current block's columns
+  __shared__ __align__(16) T Ub[2][W][W];         // ... after the unit-lower solve
+  __shared__ T red_v[2][32];
+  __shared__ int red_i[2][32];
+  __shared__ __align__(16) T red_row[2][32][W];
+  __shared__ int pphys[128];
+  __shared__ int s_cnt, s_cnt2;
+
   const int m0 = n - k0;
-  T* SB = reinterpret_cast<T*>(smraw);                       // 2W x nbmax: swap staging
-  int* orig = reinterpret_cast<int*>(SB + 2 * static_cast<size_t>(W) * nbmax);  // m0
-  __shared__ T Ublk[W][W + 1];
-  __shared__ T Lt[W][W + 1];
-  __shared__ T prow[W], orow[W];
-  __shared__ T red_v[32];
-  __shared__ int red_i[32];
-  __shared__ int lp[W], pslot[W], slot_row[2 * W], content[2 * W];
-  __shared__ int s_cnt, s_nslot;
+  int* orig = reinterpret_cast<int*>(smraw);  // logical position -> physical row (panel-relative)
+  int* pos = orig + m0;                       // physical row -> logical position
+  int* dl = pos + m0;                         // displaced logical positions (<= 2 nb)
+  const int ldl = nb + 4;
+  T* triD = reinterpret_cast<T*>(smraw + ((static_cast<size_t>(2 * m0 + 2 * nbmax) * sizeof(int) + 15) & ~size_t(15)));
+  T* triX = triD + static_cast<size_t>(nb) * ldl;
+  T* triT = triX + static_cast<size_t>(nb) * ldl;
 
   const int mat = blockIdx.x;
   T* A = fac + static_cast<size_t>(mat) * n * n;
   int* ip = piv + static_cast<size_t>(mat) * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
-  for (int r = tid; r < m0; r += NT) orig[r] = k0 + r;
+  for (int r = tid; r < m0; r += NT) orig[r] = r, pos[r] = r;
+  int pc[RPT];
+#pragma unroll
+  for (int q = 0; q < RPT; ++q) pc[q] = NONE;
   bool bad_pivot = false;
   T a[RPT][W];
 
-  for (int s0 = 0; s0 < nb; s0 += W) {
-    const int c0 = k0 + s0;
-    // load the column block, every panel row
+  for (int b = 0; b * W < nb; ++b) {
+    const int s0 = b * W, c0 = k0 + s0;
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int r = tid + q * NT;
@@ -493,57 +637,66 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
         for (int v = 0; v < W; v += VE) vload(A + static_cast<size_t>(k0 + r) * n + c0 + v, &a[q][v]);
       }
     }
-    // left-looking: the earlier blocks of this panel
-    for (int t0 = 0; t0 < s0; t0 += W) {
-      const int ct = k0 + t0;
-      if (tid >= t0 && tid < t0 + W) {
+    // left-looking: earlier blocks t of this panel
+    for (int t = 0; t < b; ++t) {
+      const int t0 = t * W;
 #pragma unroll
-        for (int jj = 0; jj < W; ++jj) Ublk[tid - t0][jj] = a[0][jj];
-      }
-      if (tid < W * W) Lt[tid / W][tid % W] = A[static_cast<size_t>(ct + tid / W) * n + ct + tid % W];
-      __syncthreads();
-      if (tid < W) {
-        for (int i = 1; i < W; ++i) {
-          T x = Ublk[i][tid];
-          for (int k = 0; k < i; ++k) x -= Lt[i][k] * Ublk[k][tid];
-          Ublk[i][tid] = x;
+      for (int q = 0; q < RPT; ++q) {
+        if (pc[q] >= t0 && pc[q] < t0 + W) {
+#pragma unroll
+          for (int v = 0; v < W; v += VE) vstore(&Raw[pc[q] - t0][v], &a[q][v]);
         }
       }
       __syncthreads();
-      if (tid >= t0 && tid < t0 + W) {
-#pragma unroll
-        for (int jj = 0; jj < W; ++jj) a[0][jj] = Ublk[tid - t0][jj];
+      T (*U)[W] = Ub[t & 1];
+      if (tid < W * W) {
+        const int i = tid / W, jj = tid % W;
+        T acc = Raw[i][jj];
+        for (int k = 0; k < i; ++k) acc += LinvB[t][i][k] * Raw[k][jj];
+        U[i][jj] = acc;
       }
-      // rows below the block: a[q][:] -= L[r][ct:ct+W] Ublk
+      __syncthreads();
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid + q * NT;
-        if (r >= t0 + W && r < m0) {
-          const T* lr = A + static_cast<size_t>(k0 + r) * n + ct;
+        if (r < m0) {
+          if (pc[q] >= t0 && pc[q] < t0 + W) {
+            const int i = pc[q] - t0;
 #pragma unroll
-          for (int kv = 0; kv < W; kv += VE) {
-            T l[VE];
-            vload(lr + kv, l);
+            for (int v = 0; v < W; v += VE) vload(&U[i][v], &a[q][v]);
+          } else if (pc[q] >= t0 + W) {
+            const T* lr = A + static_cast<size_t>(k0 + r) * n + k0 + t0;
 #pragma unroll
-            for (int u = 0; u < VE; ++u)
+            for (int kv = 0; kv < W; kv += VE) {
+              T l[VE];
+              vload(lr + kv, l);
 #pragma unroll
-              for (int jj = 0; jj < W; ++jj) a[q][jj] -= l[u] * Ublk[kv + u][jj];
+              for (int u = 0; u < VE; ++u) {
+#pragma unroll
+                for (int v = 0; v < W; v += VE) {
+                  T uu[VE];
+                  vload(&U[kv + u][v], uu);
+#pragma unroll
+                  for (int e = 0; e < VE; ++e) a[q][v + e] -= l[u] * uu[e];
+                }
+              }
+            }
           }
         }
       }
-      __syncthreads();
     }
-    // column-by-column elimination of rows s0.. (panel-relative)
+    // column-by-column elimination, one barrier per column
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-      const int cur = s0 + j;
+      const int cur = s0 + j, buf = cur & 1;
       T best = T(-1);
       int bi = 0x7fffffff;
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid + q * NT;
-        if (r >= cur && r < m0) {
-          const T v = tabs(a[q][j]);
+        if (r < m0 && pc[q] == NONE) {
+          T v = tabs(a[q][j]);
+          if (v != v) v = T(INFINITY);  // a NaN candidate wins and is reported as a bad pivot
           if (v > best || (v == best && r < bi)) best = v, bi = r;
         }
       }
@@ -553,53 +706,47 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
       }
-      if (lane == 0) red_v[warp] = best, red_i[warp] = bi;
+      if (lane == 0) red_v[buf][warp] = best, red_i[buf][warp] = bi;
+#pragma unroll
+      for (int q = 0; q < RPT; ++q) {
+        if (tid + q * NT == bi) {
+#pragma unroll
+          for (int v = (j / VE) * VE; v < W; v += VE) vstore(&red_row[buf][warp][v], &a[q][v]);
+        }
+      }
       __syncthreads();
-      best = red_v[lane];
-      bi = red_i[lane];
+      best = red_v[buf][lane];
+      bi = red_i[buf][lane];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const T ov = __shfl_xor_sync(0xffffffffu, best, o);
         const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
       }
-      const int pr = (bi >= cur && bi < m0) ? bi : cur;
+      const T* prow = red_row[buf][(bi % NT) >> 5];
+      T pr[W];
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int r = tid + q * NT;
-        if (r == pr) {
-#pragma unroll
-          for (int jj = 0; jj < W; ++jj) prow[jj] = a[q][jj];
-        }
-        if (r == cur) {
-#pragma unroll
-          for (int jj = 0; jj < W; ++jj) orow[jj] = a[q][jj];
-        }
+      for (int v = (j / VE) * VE; v < W; v += VE) vload(prow + v, &pr[v]);
+      const T pv = pr[j];
+      if (tid == 0) {
+        pphys[cur] = bi;
+        if (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv))) bad_pivot = true;
       }
-      if (tid == 0) lp[j] = pr - s0;
-      __syncthreads();
-      const T pv = prow[j];
-      if (tid == 0 && (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv)))) bad_pivot = true;
       const T inv = (pv != T(0)) ? T(1) / pv : T(0);
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid + q * NT;
-        if (r == cur) {
-#pragma unroll
-          for (int jj = 0; jj < W; ++jj) a[q][jj] = prow[jj];
-        } else if (r == pr) {
-#pragma unroll
-          for (int jj = 0; jj < W; ++jj) a[q][jj] = orow[jj];
-        }
-        if (r > cur && r < m0) {
+        if (r == bi) {
+          pc[q] = cur;
+        } else if (r < m0 && pc[q] == NONE) {
           const T l = a[q][j] * inv;
           a[q][j] = l;
 #pragma unroll
-          for (int jj = j + 1; jj < W; ++jj) a[q][jj] -= l * prow[jj];
+          for (int jj = j + 1; jj < W; ++jj) a[q][jj] -= l * pr[jj];
         }
       }
     }
-    // store the column block
+    // store the block (physical rows)
 #pragma unroll
     for (int q = 0; q < RPT; ++q) {
       const int r = tid + q * NT;
@@ -607,132 +754,123 @@ __global__ void __launch_bounds__(1024) lu_panel_rr_kernel(T* __restrict__ fac, 
 #pragma unroll
         for (int v = 0; v < W; v += VE) vstore(A + static_cast<size_t>(k0 + r) * n + c0 + v, &a[q][v]);
       }
-    }
-    // the block's row permutation as slots (see lu_panel_kernel), applied to the other panel columns
-    if (tid == 0) {
-      int ns = W;
-      for (int k = 0; k < W; ++k) slot_row[k] = c0 + k;
-      for (int j = 0; j < W; ++j) {
-        const int pl = lp[j];
-        int sl = pl;
-        if (pl >= W) {
-          sl = -1;
-          for (int q = W; q < ns; ++q)
-            if (slot_row[q] == c0 + pl) sl = q;
-          if (sl < 0) slot_row[sl = ns++] = c0 + pl;
-        }
-        pslot[j] = sl;
-        ip[c0 + j] = c0 + pl;
-        const int x = c0 + j - k0, y = c0 + pl - k0;
-        const int t = orig[x];
-        orig[x] = orig[y];
-        orig[y] = t;
+      if (pc[q] >= s0 && pc[q] < s0 + W) {
+#pragma unroll
+        for (int jj = 0; jj < W; ++jj) Tb[pc[q] - s0][jj] = a[q][jj];
       }
-      for (int k = 0; k < ns; ++k) content[k] = k;
-      for (int j = 0; j < W; ++j) {
-        const int t = content[j];
-        content[j] = content[pslot[j]];
-        content[pslot[j]] = t;
-      }
-      s_nslot = ns;
     }
     __syncthreads();
-    const int nsl = s_nslot, nleft = s0, noth = nb - W;
-    for (int idx = tid; idx < nsl * noth; idx += NT) {
-      const int k = idx / noth, q = idx % noth;
-      const int col = q < nleft ? k0 + q : c0 + W + (q - nleft);
-      SB[k * noth + q] = A[static_cast<size_t>(slot_row[k]) * n + col];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < nsl * noth; idx += NT) {
-      const int k = idx / noth, q = idx % noth;
-      const int col = q < nleft ? k0 + q : c0 + W + (q - nleft);
-      A[static_cast<size_t>(slot_row[k]) * n + col] = SB[content[k] * noth + q];
+    if (tid < W) {
+      // column c of the inverse of the unit-lower part of Tb, in registers
+      const int c = tid;
+      T x[W];
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        T acc = (r == c) ? T(1) : T(0);
+#pragma unroll
+        for (int k = 0; k < r; ++k) acc -= Tb[r][k] * x[k];
+        x[r] = (r < c) ? T(0) : acc;
+      }
+#pragma unroll
+      for (int r = 0; r < W; ++r) LinvB[b][r][c] = x[r];
+    } else if (tid == 32) {
+      // the swap sequence equivalent to this block's pivots: logical order and LAPACK pivots
+      for (int j = 0; j < W && s0 + j < nb; ++j) {
+        const int cur = s0 + j, p = pphys[cur], y = pos[p], o = orig[cur];
+        ip[k0 + cur] = k0 + y;
+        orig[cur] = p;
+        orig[y] = o;
+        pos[p] = cur;
+        pos[o] = y;
+      }
     }
     __syncthreads();
   }
   if (tid == 0 && bad_pivot) atomicOr(status, kZeroPivot);
 
-  // permutation record for the trailing columns
-  int* pr_rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
-  if (tid == 0) s_cnt = 0;
+  // move displaced rows (panel columns) to their logical positions, staged through the (still
+  // unused) triangular-inverse area: d <= 2 nb rows of nb entries
+  if (tid == 0) s_cnt = 0, s_cnt2 = 0;
   __syncthreads();
-  for (int j = tid; j < nb; j += NT) pr_rec[1 + j] = orig[j];
-  for (int r = nb + tid; r < m0; r += NT) {
-    if (orig[r] != k0 + r) {
-      const int slot = atomicAdd(&s_cnt, 1);
-      pr_rec[1 + nbmax + 2 * slot] = k0 + r;
-      pr_rec[1 + nbmax + 2 * slot + 1] = orig[r];
+  for (int y = tid; y < m0; y += NT)
+    if (orig[y] != y) dl[atomicAdd(&s_cnt, 1)] = y;
+  __syncthreads();
+  const int d = s_cnt, nvr = nb / VE;
+  using V = typename Vec16<T>::type;
+  V* stage = reinterpret_cast<V*>(triD);
+  for (int idx = tid; idx < d * nvr; idx += NT) {
+    const int y = dl[idx / nvr], v = idx % nvr;
+    stage[idx] = *reinterpret_cast<const V*>(A + static_cast<size_t>(k0 + orig[y]) * n + k0 + v * VE);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < d * nvr; idx += NT) {
+    const int y = dl[idx / nvr], v = idx % nvr;
+    *reinterpret_cast<V*>(A + static_cast<size_t>(k0 + y) * n + k0 + v * VE) = stage[idx];
+  }
+  // panel record: origin of the top nb rows, then the displaced rows below them
+  int* rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
+  for (int j = tid; j < nb; j += NT) rec[1 + j] = k0 + orig[j];
+  for (int k = tid; k < d; k += NT) {
+    const int y = dl[k];
+    if (y >= nb) {
+      const int slot = atomicAdd(&s_cnt2, 1);
+      rec[1 + nbmax + 2 * slot] = k0 + y;
+      rec[1 + nbmax + 2 * slot + 1] = k0 + orig[y];
     }
   }
   __syncthreads();
-  if (tid == 0) pr_rec[0] = s_cnt;
+  if (tid == 0) rec[0] = s_cnt2;
 
-}
-
-// After lu_panel_rr: the L21 split for the tensor-core trailing update and inv(L11) (+ its split).
-template <typename T>
-__global__ void __launch_bounds__(1024) lu_panel_tail_kernel(const T* __restrict__ fac, T* __restrict__ linv, int n,
-                                                            int k0, int nb, int nbmax, float* __restrict__ ws_hi,
-                                                            float* __restrict__ ws_lo, float* __restrict__ li_hi,
-                                                            float* __restrict__ li_lo) {
-  constexpr int NT = 1024, VE = Vec16<T>::n;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* LX = reinterpret_cast<T*>(smraw);
-  const int mat = blockIdx.x, tid = threadIdx.x;
-  const T* A = fac + static_cast<size_t>(mat) * n * n;
-  const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
-  // L21 split for the tensor-core trailing update ([point][row][nbmax]), 16-byte vectors
-  if (ws_hi) {
-    const int M = n - k0 - nb, q4 = nb / VE;
-    float* hi = ws_hi + static_cast<size_t>(mat) * (n - nbmax) * nbmax;
-    float* lo = ws_lo + static_cast<size_t>(mat) * (n - nbmax) * nbmax;
-    for (int idx = tid; idx < M * q4; idx += NT) {
-      const int r = idx / q4, k = VE * (idx % q4);
-      T v[VE];
-      vload(A + static_cast<size_t>(k0 + nb + r) * n + k0 + k, v);
-      float h[VE], l[VE];
-#pragma unroll
-      for (int u = 0; u < VE; ++u) split_tf32(static_cast<float>(v[u]), h[u], l[u]);
-      if (VE == 4) {
-        *reinterpret_cast<float4*>(hi + static_cast<size_t>(r) * nbmax + k) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4*>(lo + static_cast<size_t>(r) * nbmax + k) = make_float4(l[0], l[1], l[2], l[3]);
-      } else {
-#pragma unroll
-        for (int u = 0; u < VE; ++u) {
-          hi[static_cast<size_t>(r) * nbmax + k + u] = h[u];
-          lo[static_cast<size_t>(r) * nbmax + k + u] = l[u];
-        }
-      }
-    }
-  }
-
-  // inv(L11) in shared memory (+ its split for the tensor-core U12 formation)
-  const int ldl = nb + 1;
-  T* Ls = LX;
-  T* Xs = LX + static_cast<size_t>(nb) * ldl;
-  for (int idx = tid; idx < nb * nb; idx += NT) Ls[(idx / nb) * ldl + idx % nb] = A[static_cast<size_t>(k0 + idx / nb) * n + k0 + idx % nb];
+  // inv(L11) (+ split) and inv(U11) of the final diagonal block
+  for (int idx = tid; idx < nb * nb; idx += NT)
+    triD[(idx / nb) * ldl + idx % nb] = A[static_cast<size_t>(k0 + idx / nb) * n + k0 + idx % nb];
   __syncthreads();
-  tri_inverse_smem<T, true>(Ls, Xs, nb, ldl);
+  // the 4 x 4 register tiles of the doubling inverse fit the 64-register budget in FP32 only
+  if constexpr (sizeof(T) == 4) {
+    if (nb % 16 == 0) tri_inverse_rd<T, true>(triD, triX, triT, nb, ldl);
+    else tri_inverse_smem<T, true>(triD, triX, nb, ldl);
+  } else {
+    tri_inverse_smem<T, true>(triD, triX, nb, ldl);
+  }
   T* X = linv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
-  for (int idx = tid; idx < nb * nb; idx += NT) X[(idx / nb) * nbmax + idx % nb] = Xs[(idx / nb) * ldl + idx % nb];
+  for (int idx = tid; idx < nb * nb; idx += NT) X[(idx / nb) * nbmax + idx % nb] = triX[(idx / nb) * ldl + idx % nb];
   if (li_hi) {
     for (int idx = tid; idx < nbmax * nbmax; idx += NT) {
       const int r = idx / nbmax, c = idx % nbmax;
       float h = 0.f, l = 0.f;
-      if (r < nb && c < nb) split_tf32(static_cast<float>(Xs[r * ldl + c]), h, l);
+      if (r < nb && c < nb) split_tf32(static_cast<float>(triX[r * ldl + c]), h, l);
       li_hi[static_cast<size_t>(mat) * nbmax * nbmax + idx] = h;
       li_lo[static_cast<size_t>(mat) * nbmax * nbmax + idx] = l;
     }
   }
+  if (uinv) {
+    __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+      if (nb % 16 == 0) tri_inverse_rd<T, false>(triD, triX, triT, nb, ldl);
+      else tri_inverse_smem<T, false>(triD, triX, nb, ldl);
+    } else {
+      tri_inverse_smem<T, false>(triD, triX, nb, ldl);
+    }
+    T* Y = uinv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
+    for (int idx = tid; idx < nb * nb; idx += NT) Y[(idx / nb) * nbmax + idx % nb] = triX[(idx / nb) * ldl + idx % nb];
+  }
 }
 
-
-template <typename T, int W>
-__host__ inline size_t panel_rr_smem_bytes(int m0, int nb, int nbmax) {
-  (void)nb;
-  return 2ull * W * nbmax * sizeof(T) + static_cast<size_t>(m0) * sizeof(int) + 16;
+// Elements of the product staging of tri_inverse_rd for an nb x nb block.
+__host__ __device__ inline int rd_tmp_elems(int nb) {
+  int m = 0;
+  for (int w = 16; w < nb; w *= 2) {
+    const int e = ((nb + 2 * w - 1) / (2 * w)) * w * w;
+    m = e > m ? e : m;
+  }
+  return m;
 }
+
+__host__ inline size_t panel_lazy_smem_bytes(int m0, int nb, int nbmax, size_t tsize) {
+  const size_t ints = ((static_cast<size_t>(2 * m0 + 2 * nbmax) * sizeof(int) + 15) & ~size_t(15));
+  return ints + (2ull * nb * (nb + 4) + rd_tmp_elems(nb)) * tsize;
+}
+
 
 // inv(U11) of every panel of every point, after the factorisation (one CTA per point and panel).
 template <typename T>
@@ -855,7 +993,8 @@ __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, 
 // and write (P A12)^T, split into TF32 head/remainder, as the K-major B operand of the U12 GEMM.
 __global__ void __launch_bounds__(256) lu_swap_pack_kernel(float* __restrict__ fac, const int* __restrict__ perm,
                                                            int n, int k0, int nb, int nbmax,
-                                                           float* __restrict__ bt_hi, float* __restrict__ bt_lo) {
+                                                           float* __restrict__ bt_hi, float* __restrict__ bt_lo,
+                                                           float* __restrict__ a_hi, float* __restrict__ a_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float* top = reinterpret_cast<float*>(smraw);            // original panel rows  nb x ld
   float* Bs = top + static_cast<size_t>(nb) * kTrsmLd;      // permuted panel rows nb x ld
@@ -889,6 +1028,33 @@ __global__ void __launch_bounds__(256) lu_swap_pack_kernel(float* __restrict__ f
     const size_t o = off + static_cast<size_t>(C0 - (k0 + nb) + c) * nbmax + r;
     bt_hi[o] = h;
     bt_lo[o] = l;
+  }
+  // TF32 split of L21 rows [k0 + nb + 64 y, +64) (the A operand of the trailing update), one warp
+  // per row segment of 16-byte vectors
+  const int R0 = blockIdx.y * kTrsmCols, nrow = min(kTrsmCols, n - k0 - nb - R0);
+  if (a_hi && ((n & 3) != 0 || (nb & 3) != 0)) {
+    for (int idx = tid; idx < nrow * nb; idx += bd) {
+      const int r = idx / nb, k = idx % nb;
+      float h, l;
+      split_tf32(A[static_cast<size_t>(k0 + nb + R0 + r) * n + k0 + k], h, l);
+      const size_t o = off + static_cast<size_t>(R0 + r) * nbmax + k;
+      a_hi[o] = h;
+      a_lo[o] = l;
+    }
+  } else if (a_hi) {
+    const int q4 = nb / 4;
+    for (int idx = tid; idx < nrow * q4; idx += bd) {
+      const int r = idx / q4, k = 4 * (idx % q4);
+      const float4 v = *reinterpret_cast<const float4*>(A + static_cast<size_t>(k0 + nb + R0 + r) * n + k0 + k);
+      float h[4], l[4];
+      split_tf32(v.x, h[0], l[0]);
+      split_tf32(v.y, h[1], l[1]);
+      split_tf32(v.z, h[2], l[2]);
+      split_tf32(v.w, h[3], l[3]);
+      const size_t o = off + static_cast<size_t>(R0 + r) * nbmax + k;
+      *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+    }
   }
 }
 
@@ -1037,10 +1203,76 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
   for (int r = tid; r < n; r += bd) xo[r] = accumulate ? xo[r] + static_cast<double>(s[r]) : static_cast<double>(s[r]);
 }
 
+// Sum of four per-lane partials over the warp in six shuffles (a transposing butterfly): lane 0
+// returns row 0's total, lane 8 row 1's, lane 16 row 2's, lane 24 row 3's.
+__device__ __forceinline__ float warp_sum4(float p0, float p1, float p2, float p3, int lane) {
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  float v0 = hi16 ? p2 : p0, v1 = hi16 ? p3 : p1;
+  const float w0 = hi16 ? p0 : p2, w1 = hi16 ? p1 : p3;
+  v0 += __shfl_xor_sync(0xffffffffu, w0, 16);
+  v1 += __shfl_xor_sync(0xffffffffu, w1, 16);
+  float u = hi8 ? v1 : v0;
+  const float x = hi8 ? v0 : v1;
+  u += __shfl_xor_sync(0xffffffffu, x, 8);
+  u += __shfl_xor_sync(0xffffffffu, u, 4);
+  u += __shfl_xor_sync(0xffffffffu, u, 2);
+  u += __shfl_xor_sync(0xffffffffu, u, 1);
+  return u;
+}
+
+// out(r, dot(M[r, 0:128], v)) for rows r in [r0, r1) of a row-major FP32 matrix with leading
+// dimension ld (a multiple of 4, M 16-byte aligned): four rows per warp and pass, one 16-byte load
+// per lane and row, so that a CTA keeps 64 KB of loads in flight. v is in shared memory.
+template <typename Out>
+__device__ __forceinline__ void rows_dot128(const float* __restrict__ M, size_t ld, int r0, int r1, const float* v,
+                                            int warp, int nwarp, int lane, Out out) {
+  const float4 vv = reinterpret_cast<const float4*>(v)[lane];
+  for (int r = r0 + 4 * warp; r < r1; r += 4 * nwarp) {
+    float p[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      p[i] = 0.f;
+      if (r + i < r1) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(M + static_cast<size_t>(r + i) * ld) + lane);
+        p[i] = a.x * vv.x + a.y * vv.y + a.z * vv.z + a.w * vv.w;
+      }
+    }
+    const float t = warp_sum4(p[0], p[1], p[2], p[3], lane);
+    if ((lane & 7) == 0 && r + (lane >> 3) < r1) out(r + (lane >> 3), t);
+  }
+}
+
+// out(r, dot(M[r, 0:kb], v)) for any width: one row per warp, lanes across the columns.
+template <typename T, typename Out>
+__device__ __forceinline__ void rows_dot_any(const T* __restrict__ M, size_t ld, int r0, int r1, int kb, const T* v,
+                                             int warp, int nwarp, int lane, Out out) {
+  for (int r = r0 + warp; r < r1; r += nwarp) {
+    const T* a = M + static_cast<size_t>(r) * ld;
+    T acc = T(0);
+    for (int c = lane; c < kb; c += 32) acc += a[c] * v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out(r, acc);
+  }
+}
+
+template <typename T, typename Out>
+__device__ __forceinline__ void rows_dot(const T* __restrict__ M, size_t ld, int r0, int r1, int kb, const T* v,
+                                         int warp, int nwarp, int lane, Out out) {
+  if constexpr (sizeof(T) == 4) {
+    if (kb == 128 && (ld & 3) == 0) {
+      rows_dot128(M, ld, r0, r1, v, warp, nwarp, lane, out);
+      return;
+    }
+  }
+  rows_dot_any(M, ld, r0, r1, kb, v, warp, nwarp, lane, out);
+}
+
 // x = A^-1 b (or x += A^-1 b) for one point per CTA with the per-panel block inverses: forward,
 // per panel p: permute the right-hand side with the panel's row record, y = inv(L11_p) b_p, then
 // b[below] -= L21_p y; backward, per panel from the last: y = inv(U11_p) b_p, b[above] -= U_p y.
-// Rows are processed one per warp with the lanes across the panel's columns (coalesced).
+// Every product is a batch of row dot products (rows_dot): the stored inverses are zero outside
+// their triangles, so full rows are used. The factors are streamed once per solve.
 template <typename T>
 __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restrict__ fac, const int* __restrict__ perm,
                                                                 const T* __restrict__ linv, const T* __restrict__ uinv,
@@ -1048,8 +1280,8 @@ __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restr
                                                                 int n, int nb, const int* __restrict__ conv,
                                                                 int accumulate) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* s = reinterpret_cast<T*>(smraw);   // n
-  T* y = s + n;                          // nb
+  T* s = reinterpret_cast<T*>(smraw);   // n (rounded up to 4)
+  T* y = s + ((n + 3) & ~3);             // nb
   T* tmp = y + nb;                       // 2 nb
   const int mat = blockIdx.x;
   if (conv && conv[mat]) return;
@@ -1058,6 +1290,8 @@ __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restr
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
   for (int r = tid; r < n; r += bd) s[r] = static_cast<T>(b[static_cast<size_t>(mat) * n + r]);
   __syncthreads();
+  auto set_y = [&](int r, T v) { y[r] = v; };
+  auto sub_s = [&](int r, T v) { s[r] -= v; };
   for (int p = 0; p < npan; ++p) {
     const int k0 = p * nb, kb = min(nb, n - k0);
     const int* rec = perm + (static_cast<size_t>(mat) * npan + p) * perm_stride(nb);
@@ -1069,45 +1303,21 @@ __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restr
     for (int q = tid; q < d; q += bd) s[rec[1 + nb + 2 * q]] = tmp[nb + q];
     __syncthreads();
     const T* X = linv + (static_cast<size_t>(mat) * npan + p) * nb * nb;
-    for (int r = warp; r < kb; r += nwarp) {
-      T acc = T(0);
-      for (int c = lane; c <= r; c += 32) acc += X[r * nb + c] * s[k0 + c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[r] = acc;
-    }
+    rows_dot(X, nb, 0, kb, kb, s + k0, warp, nwarp, lane, set_y);
     __syncthreads();
     for (int j = tid; j < kb; j += bd) s[k0 + j] = y[j];
-    for (int r = k0 + kb + warp; r < n; r += nwarp) {
-      const T* a = A + static_cast<size_t>(r) * n + k0;
-      T acc = T(0);
-      for (int c = lane; c < kb; c += 32) acc += a[c] * y[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) s[r] -= acc;
-    }
+    __syncthreads();
+    rows_dot(A + k0, n, k0 + kb, n, kb, y, warp, nwarp, lane, sub_s);
     __syncthreads();
   }
   for (int p = npan - 1; p >= 0; --p) {
     const int k0 = p * nb, kb = min(nb, n - k0);
     const T* Y = uinv + (static_cast<size_t>(mat) * npan + p) * nb * nb;
-    for (int r = warp; r < kb; r += nwarp) {
-      T acc = T(0);
-      for (int c = r + lane; c < kb; c += 32) acc += Y[r * nb + c] * s[k0 + c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) y[r] = acc;
-    }
+    rows_dot(Y, nb, 0, kb, kb, s + k0, warp, nwarp, lane, set_y);
     __syncthreads();
     for (int j = tid; j < kb; j += bd) s[k0 + j] = y[j];
-    for (int r = warp; r < k0; r += nwarp) {
-      const T* a = A + static_cast<size_t>(r) * n + k0;
-      T acc = T(0);
-      for (int c = lane; c < kb; c += 32) acc += a[c] * y[c];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) s[r] -= acc;
-    }
+    __syncthreads();
+    rows_dot(A + k0, n, 0, k0, kb, y, warp, nwarp, lane, sub_s);
     __syncthreads();
   }
   double* xo = x + static_cast<size_t>(mat) * n;
@@ -1124,53 +1334,69 @@ static int panel_width(int n, int nb) {
   return w < nb ? w : nb;
 }
 
+
 template <typename T, int W, int RPT>
-static void launch_rr(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax, unsigned* status,
-                      float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
+static void launch_lazy(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
+                        unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lu_panel_rr_kernel<T, W, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(lu_panel_lazy_kernel<T, W, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  static bool attr_tail = false;
-  if (!attr_tail) {
-    cudaFuncSetAttribute(lu_panel_tail_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_tail = true;
-  }
-  const size_t smem = panel_rr_smem_bytes<T, W>(n - k0, nb, nbmax);
-  lu_panel_rr_kernel<T, W, RPT><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, status, ws_hi, ws_lo,
-                                                       li_hi, li_lo);
-  const size_t smem_tail = 2ull * nb * (nb + 1) * sizeof(T);
-  lu_panel_tail_kernel<T><<<nx, 1024, smem_tail, st>>>(fac, linv, n, k0, nb, nbmax, ws_hi, ws_lo, li_hi, li_lo);
+  const size_t smem = panel_lazy_smem_bytes(n - k0, nb, nbmax, sizeof(T));
+  (void)ws_hi;
+  (void)ws_lo;
+  lu_panel_lazy_kernel<T, W, RPT><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax, status,
+                                                         li_hi, li_lo);
+}
+
+// Column-block width and rows per thread of the mark-pivoting panel kernel for a panel of m0 rows
+// and width nb (W = 0: the kernel does not apply).
+template <typename T>
+static void lazy_shape(int n, int m0, int nb, int nbmax, int& W, int& rpt) {
+  constexpr int VE = 16 / sizeof(T);
+  constexpr int W2 = sizeof(T) == 4 ? 16 : 8, W4 = sizeof(T) == 4 ? 8 : 4;
+  W = 0, rpt = 0;
+  if (n % VE != 0 || nbmax > 128 || nbmax % VE != 0) return;
+  if (m0 <= 2048 && nb % W2 == 0) W = W2, rpt = 2;
+  else if (m0 <= 4096 && nb % W4 == 0) W = W4, rpt = 4;
 }
 
 template <typename T>
-void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, int nx, int n, int k0, int nb, int nbmax,
+bool lu_panel_fuses_uinv(int n, int nbmax) {
+  for (int k0 = 0; k0 < n; k0 += nbmax) {
+    int W, rpt;
+    lazy_shape<T>(n, n - k0, std::min(nbmax, n - k0), nbmax, W, rpt);
+    if (!W) return false;
+  }
+  return true;
+}
+
+template <typename T>
+void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
   const bool trail = k0 + nb < n;
   float* wh = trail ? ws_hi : nullptr;
   float* lh = trail ? li_hi : nullptr;
-  // register-resident kernel when the shape allows it
-  constexpr int VE = 16 / sizeof(T);
+  int W, rpt;
+  lazy_shape<T>(n, n - k0, nb, nbmax, W, rpt);
   constexpr int W2 = sizeof(T) == 4 ? 16 : 8, W4 = sizeof(T) == 4 ? 8 : 4;
-  if (n % VE == 0 && nbmax <= 128) {
-    if (n - k0 <= 2048 && nb % W2 == 0) {
-      launch_rr<T, W2, 2>(fac, piv, perm, linv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
-      return;
-    }
-    if (n - k0 <= 4096 && nb % W4 == 0) {
-      launch_rr<T, W4, 4>(fac, piv, perm, linv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
-      return;
-    }
+  if (W == W2 && rpt == 2) {
+    launch_lazy<T, W2, 2>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
+    return;
   }
-  const int W = panel_width<T>(n, nbmax);
-  const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, W);
+  if (W == W4 && rpt == 4) {
+    launch_lazy<T, W4, 4>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
+    return;
+  }
+  const int Wf = panel_width<T>(n, nbmax);
+  const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, Wf);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, W, status, wh, ws_lo, lh, li_lo);
+  lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, Wf, status, wh, ws_lo, lh, li_lo);
 }
 
 template <typename T>
@@ -1189,7 +1415,7 @@ void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, 
 }
 
 void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,
-                         float* bt_lo, cudaStream_t st) {
+                         float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st) {
   const int ntrail = n - k0 - nb;
   if (ntrail <= 0) return;
   dim3 grid(nx, (ntrail + kTrsmCols - 1) / kTrsmCols);
@@ -1199,7 +1425,7 @@ void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int
     cudaFuncSetAttribute(lu_swap_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  lu_swap_pack_kernel<<<grid, 256, smem, st>>>(fac, perm, n, k0, nb, nbmax, bt_hi, bt_lo);
+  lu_swap_pack_kernel<<<grid, 256, smem, st>>>(fac, perm, n, k0, nb, nbmax, bt_hi, bt_lo, a_hi, a_lo);
 }
 
 template <typename T>
@@ -1245,7 +1471,7 @@ void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_
 template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
                              double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st) {
-  const size_t smem = (static_cast<size_t>(n) + 3 * nb) * sizeof(T);
+  const size_t smem = (static_cast<size_t>((n + 3) & ~3) + 3 * nb) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_solve_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
@@ -1255,8 +1481,9 @@ void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const
 }
 
 #define BTE_INST(T)                                                                                 \
-  template void launch_lu_panel<T>(T*, int*, int*, T*, int, int, int, int, int, unsigned*, float*,       \
+  template void launch_lu_panel<T>(T*, int*, int*, T*, T*, int, int, int, int, int, unsigned*, float*,   \
                                    float*, float*, float*, cudaStream_t);                           \
+  template bool lu_panel_fuses_uinv<T>(int, int);                                                   \
   template void launch_lu_uinv<T>(const T*, T*, int, int, int, cudaStream_t);                        \
   template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \
                                            double*, int, int, int, const int*, int, cudaStream_t);  \

@@ -39,6 +39,10 @@ constexpr int STAGES = 3;
 constexpr int BOX_BYTES = BM * BK * 4;            // 16 KB (BM == BN)
 constexpr int STAGE_BYTES = 4 * BOX_BYTES;        // A_hi, A_lo, B_hi, B_lo
 constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
+constexpr int CW = 32;                            // C chunk width (columns): one 128-byte swizzle row
+constexpr int CSLOTS = 2;                         // C staging slots
+constexpr int CSLOT_BYTES = BM * CW * 4;          // 16 KB
+constexpr int NCCHUNK = BN / CW;
 constexpr int NTHREADS = 192;
 constexpr long long kWaitCycles = 1ll << 32;     // ~2 s at 2 GHz
 constexpr unsigned kTimeoutBit = 8u;
@@ -50,7 +54,9 @@ constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN 
 
 struct Smem {
   alignas(1024) unsigned char stage[STAGES][STAGE_BYTES];
+  alignas(1024) unsigned char cbuf[CSLOTS][CSLOT_BYTES];  // C chunks, 128-byte swizzled (TMA layout)
   alignas(8) uint64_t full[STAGES];
+  uint64_t cfull[CSLOTS];
   uint64_t empty[STAGES];
   uint64_t tfull[2];
   uint64_t tempty[2];
@@ -107,6 +113,24 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, int 
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(saddr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store3(const CUtensorMap* map, const void* src, int x, int y, int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr(src))
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
@@ -159,9 +183,8 @@ struct TcArgs {
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                   const TcArgs args) {
-  float* __restrict__ fac = args.fac;
-  const int n = args.n, M = args.M, N = args.N, total = args.total;
+                   const __grid_constant__ CUtensorMap mC, const TcArgs args) {
+  const int total = args.total;
   unsigned* status = args.status;
   extern __shared__ unsigned char raw[];
   Smem& s = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
@@ -170,6 +193,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) mbar_init(&s.full[i], 1), mbar_init(&s.empty[i], 1);
     for (int i = 0; i < 2; ++i) mbar_init(&s.tfull[i], 1), mbar_init(&s.tempty[i], 4);
+    for (int i = 0; i < CSLOTS; ++i) mbar_init(&s.cfull[i], 1);
     mbar_init(&s.drain, 1);
     s.abort = 0;
     s.issued = 0;
@@ -262,88 +286,103 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {  // ------------------------------------------------------------------------- epilogue
+    // C moves through two 16 KB shared-memory slots in 128 x 32 chunks: TMA load (mode 0), C -= acc
+    // (or C = acc) by the thread owning the row (its TMEM lane), TMA store. One leader thread waits
+    // on the barriers and issues the bulk copies; the four warps meet at a named barrier, so a
+    // timeout seen by the leader ends every epilogue thread at the same point.
     const int sub = warp & 3;  // TMEM lane quarter this warp may access
-    int acc = 0;
+    const int trow = sub * 32 + lane;
+    const bool leader = warp == 2 && lane == 0;
+    const bool load_c = args.mode == 0;
+    auto cx = [&](int t, int ch) { return args.col0 + ((t % per_point) % args.tiles_n) * BN + CW * ch; };
+    auto cy = [&](int t) { return args.row0 + ((t % per_point) / args.tiles_n) * BM; };
+    auto issue_c = [&](int t, int ch, int slot) {
+      mbar_expect_tx(&s.cfull[slot], CSLOT_BYTES);
+      tma_load3(s.cbuf[slot], &mC, cx(t, ch), cy(t), t / per_point, &s.cfull[slot]);
+    };
+    int c_issued = 0, c_done = 0;  // leader's count of C loads issued and waited for
+    if (leader && load_c)
+      for (int ch = 0; ch < CSLOTS && blockIdx.x < total; ++ch) issue_c(blockIdx.x, ch, ch), ++c_issued;
+    int acc = 0, g = 0;
     uint32_t aph = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    bool stop = false;
+    for (int t = blockIdx.x; t < total && !stop; t += gridDim.x) {
       const int p = t / per_point, r = t % per_point;
-      const int row = (r / args.tiles_n) * BM + sub * 32 + lane;
+      const int row = (r / args.tiles_n) * BM + trow;
       const int col0 = (r % args.tiles_n) * BN;
-      float* crow = fac + static_cast<size_t>(p) * n * n + static_cast<size_t>(args.row0 + row) * n + args.col0;
-      const bool vec = (n & 3) == 0 && (args.col0 & 3) == 0;
-      // mode 0, full tile row: fetch this thread's 128 C values before the accumulator is ready, so
-      // the loads overlap the tile's MMAs
-      const bool pre = args.mode == 0 && vec && row < M && col0 + BN <= N;
-      float4 cv[BN / 4];
-      if (pre) {
-#pragma unroll
-        for (int j = 0; j < BN / 4; ++j) cv[j] = *reinterpret_cast<const float4*>(crow + col0 + 4 * j);
-      }
-      if (!mbar_wait(s, &s.tfull[acc], aph, status)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int ch = 0; ch < BN / 32; ++ch) {
+      if (leader && !mbar_wait(s, &s.tfull[acc], aph, status)) atomicExch(&s.abort, 1);
+      for (int ch = 0; ch < NCCHUNK; ++ch, ++g) {
+        const int slot = g & 1;
+        if (leader && load_c && !*reinterpret_cast<volatile int*>(&s.abort)) {
+          if (mbar_wait(s, &s.cfull[slot], (g >> 1) & 1, status)) ++c_done;
+          else atomicExch(&s.abort, 1);
+        }
+        epi_bar();
+        if (*reinterpret_cast<volatile int*>(&s.abort)) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t v[32];
-        tmem_ld32(tmem + acc * BN + ch * 32 + ((sub * 32) << 16), v);
-        const int c0 = col0 + ch * 32;
-        if (row < M) {
-          float* cp = crow + c0;
-          if (pre) {
+        tmem_ld32(tmem + acc * BN + ch * CW + ((sub * 32) << 16), v);
+        float4* cs = reinterpret_cast<float4*>(s.cbuf[slot] + trow * (CW * 4));
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              float4 x = cv[ch * 8 + j];
-              x.x -= __uint_as_float(v[4 * j]);
-              x.y -= __uint_as_float(v[4 * j + 1]);
-              x.z -= __uint_as_float(v[4 * j + 2]);
-              x.w -= __uint_as_float(v[4 * j + 3]);
-              *reinterpret_cast<float4*>(cp + 4 * j) = x;
-            }
-          } else if (args.mode == 0) {
-            if (vec && c0 + 32 <= N) {
-#pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                float4 x = *reinterpret_cast<float4*>(cp + j);
-                x.x -= __uint_as_float(v[j]);
-                x.y -= __uint_as_float(v[j + 1]);
-                x.z -= __uint_as_float(v[j + 2]);
-                x.w -= __uint_as_float(v[j + 3]);
-                *reinterpret_cast<float4*>(cp + j) = x;
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (c0 + j < N) cp[j] -= __uint_as_float(v[j]);
-            }
+        for (int j = 0; j < CW / 4; ++j) {
+          float4* q = cs + (j ^ (trow & 7));  // 128-byte swizzle: 16-byte chunk index ^ (row % 8)
+          float4 x;
+          if (load_c) {
+            x = *q;
+            x.x -= __uint_as_float(v[4 * j]);
+            x.y -= __uint_as_float(v[4 * j + 1]);
+            x.z -= __uint_as_float(v[4 * j + 2]);
+            x.w -= __uint_as_float(v[4 * j + 3]);
           } else {
-            if (vec && c0 + 32 <= N) {
+            x = make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]), __uint_as_float(v[4 * j + 2]),
+                            __uint_as_float(v[4 * j + 3]));
+          }
+          *q = x;
+        }
+        if (!load_c && row < args.M) {
+          // transposed split of U12: lanes are consecutive rows, so each column's store is coalesced
+          const int c0 = col0 + ch * CW;
+          float* bh = args.bt_hi + static_cast<size_t>(p) * args.rows_b * KTOT + row;
+          float* bl = args.bt_lo + static_cast<size_t>(p) * args.rows_b * KTOT + row;
 #pragma unroll
-              for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<float4*>(cp + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                                                 __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (c0 + j < N) cp[j] = __uint_as_float(v[j]);
-            }
-            // transposed split: lanes are consecutive rows, so each column's store is coalesced
-            float* bh = args.bt_hi + static_cast<size_t>(p) * args.rows_b * KTOT + row;
-            float* bl = args.bt_lo + static_cast<size_t>(p) * args.rows_b * KTOT + row;
-#pragma unroll 4
-            for (int j = 0; j < 32; ++j) {
-              if (c0 + j >= N) break;
-              uint32_t h;
-              const float x = __uint_as_float(v[j]);
-              asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-              bh[static_cast<size_t>(c0 + j) * KTOT] = __uint_as_float(h);
-              bl[static_cast<size_t>(c0 + j) * KTOT] = x - __uint_as_float(h);
-            }
+          for (int j = 0; j < CW; ++j) {
+            if (c0 + j >= args.N) break;
+            uint32_t h;
+            const float x = __uint_as_float(v[j]);
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+            bh[static_cast<size_t>(c0 + j) * KTOT] = __uint_as_float(h);
+            bl[static_cast<size_t>(c0 + j) * KTOT] = x - __uint_as_float(h);
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        epi_bar();
+        if (leader) {
+          tma_store3(&mC, s.cbuf[slot], cx(t, ch), cy(t), p);
+          bulk_wait_read_all();  // the slot is free again
+          if (load_c) {
+            const int t2 = ch + CSLOTS < NCCHUNK ? t : t + gridDim.x;
+            const int ch2 = (ch + CSLOTS) % NCCHUNK;
+            if (t2 < total) issue_c(t2, ch2, slot), ++c_issued;
           }
         }
       }
+      if (stop) break;
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(&s.tempty[acc]);
       if (++acc == 2) acc = 0, aph ^= 1u;
+    }
+    if (leader) {
+      bulk_wait_all();
+      // loads issued but not waited for (only after an abort) must land before the CTA exits
+      for (int q = c_done; q < c_issued; ++q) {
+        const long long t0 = clock64();
+        while (!mbar_try(&s.cfull[q & 1], (q >> 1) & 1) && clock64() - t0 < kWaitCycles) {
+        }
+      }
     }
   }
 
@@ -380,23 +419,40 @@ bool make_map(CUtensorMap* m, float* base, size_t rows) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The per-point matrices as a 3-D tensor [point][row][col] (so tiles are clipped at each point's
+// edge), boxes of 128 rows x 32 columns, 128-byte swizzle: the epilogue's C chunks.
+bool make_cmap(CUtensorMap* m, float* fac, int nx, int n) {
+  auto enc = get_encode();
+  if (!enc || (n & 3) != 0) return false;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(nx)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(n) * 4, static_cast<cuuint64_t>(n) * n * 4};
+  cuuint32_t box[3] = {CW, BM, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fac, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct Maps {
   void* ws = nullptr;
+  float* fac = nullptr;
   int nx = 0, n = 0;
-  CUtensorMap m[6];
+  CUtensorMap m[7];  // A_hi, A_lo, B_hi, B_lo, inv(L11) hi, lo, C
   bool ok = false;
 };
 
-Maps& maps_for(void* ws, int nx, int n) {
+Maps& maps_for(float* fac, void* ws, int nx, int n) {
   static Maps maps;
-  if (!maps.ok || maps.ws != ws || maps.nx != nx || maps.n != n) {
+  if (!maps.ok || maps.ws != ws || maps.fac != fac || maps.nx != nx || maps.n != n) {
     const size_t rows = static_cast<size_t>(nx) * (n - KTOT);
     maps.ok = true;
     for (int part = 0; part < 4; ++part)
       maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), rows);
     for (int part = 4; part < 6; ++part)
       maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KTOT);
+    maps.ok = maps.ok && make_cmap(&maps.m[6], fac, nx, n);
     maps.ws = ws;
+    maps.fac = fac;
     maps.nx = nx;
     maps.n = n;
     cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -417,7 +473,8 @@ int sm_count() {
 
 void launch(const Maps& mp, int ia, int ib, const TcArgs& a, cudaStream_t st) {
   const int grid = a.total < sm_count() ? a.total : sm_count();
-  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1], a);
+  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1], mp.m[6],
+                                                             a);
 }
 
 }  // namespace
@@ -425,7 +482,7 @@ void launch(const Maps& mp, int ia, int ib, const TcArgs& a, cudaStream_t st) {
 // Workspace: four arrays [nx][n - 128][128] floats (A_hi, A_lo, B_hi, B_lo) and two [nx][128][128]
 // (inv(L11) hi, lo).
 size_t tc_workspace_bytes(int nx, int n, int nbmax) {
-  if (nbmax != KTOT || n <= KTOT) return 0;
+  if (nbmax != KTOT || n <= KTOT || (n & 3) != 0) return 0;
   return (4ull * nx * static_cast<size_t>(n - KTOT) * KTOT + 2ull * nx * KTOT * KTOT) * sizeof(float);
 }
 
@@ -448,7 +505,7 @@ bool tc_available() {
 
 void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st) {
   (void)nb;
-  Maps& mp = maps_for(ws, nx, n);
+  Maps& mp = maps_for(fac, ws, nx, n);
   const int base = k0 + KTOT, M = n - base;
   if (M <= 0 || !mp.ok) return;
   TcArgs a{};
@@ -467,7 +524,7 @@ void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* s
 }
 
 void tc_lu_u12(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
-  Maps& mp = maps_for(ws, nx, n);
+  Maps& mp = maps_for(fac, ws, nx, n);
   const int base = k0 + KTOT, N = n - base;
   if (N <= 0 || !mp.ok) return;
   TcArgs a{};

@@ -111,6 +111,8 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
                                 int nt, int nr, int nl) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
+  // a point that has converged keeps its iterate (the solves skip it), so its residual is final
+  if (conv[i]) return;
   const int nv = nt * nr;
   double* xs = sm;             // nv
   double* xS = xs + nv;        // nl*nr
