@@ -278,11 +278,7 @@ def run_ours(args, rank, world):
     e1.record()
     barrier()
     ms_plain = e0.elapsed_time(e1) / args.steps
-    ms = min(ms, ms_plain)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(min(ms, ms_plain), dist)
     value = world * dof / (ms / 1e3)
 
     # ---- plain FP64 on the same GPU, same steps from the same state
@@ -357,6 +353,92 @@ def run_ours(args, rank, world):
     return 0
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest of every rank's value (all-reduce MAX); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(n, rank, world):
+    """Instances of a batched workload handled by one rank: a contiguous, balanced slice (no
+    data-path exchange between ranks)."""
+    lo = (n * rank) // world
+    hi = (n * (rank + 1)) // world
+    return list(range(lo, hi))
+
+
+def run_batched(args, rank, world):
+    """64 uneven discharges (per-instance grids, pressures, amplitudes drawn from a fixed seed)
+    stepped together through one CUDA graph per step, autotuned per shape; instances are sharded
+    across ranks. Mixed precision; with --batched-fp64 also the plain FP64 batch on the same
+    instances (one timed step)."""
+    import torch
+    from paper_2502_16555_gb300 import bte
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    inst = W.batched_instances()
+    mine = [inst[k] for k in shard(len(inst), rank, world)]
+
+    def leg(precision, steps, warmup):
+        sv = [bte.Solver(c, precision=precision) for c in mine]
+        Fs = [s.initial_state() for s in sv]
+        t_setup = time.perf_counter()
+        b = bte.Batch(sv, autotune=True)
+        t_setup = time.perf_counter() - t_setup
+        b.run(Fs, warmup, 0.0)
+        t0 = [warmup * c["dt_s"] for c in mine]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record()
+            b.run(Fs, steps, t0)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist)
+        info = [b.info(i) for i in range(len(sv))]
+        ne = [s.moments(F)[0] for s, F in zip(sv, Fs)]
+        b.close()
+        del sv, Fs
+        torch.cuda.empty_cache()
+        return ms, info, clk.summary(), t_setup, ne
+
+    dof_all = sum(c["nx"] * c["nr"] * c["ntheta"] for c in inst)
+    ms, info, clocks, t_setup, ne_m = leg("mixed", args.steps, args.warmup)
+    out = {
+        "metric": METRIC, "value": dof_all / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
+        "config": {"workload": "batched64_uneven", "instances": len(inst), "dof": dof_all,
+                   "graph": "one CUDA graph launch per step, instances as concurrent branches",
+                   "l2": "working set > L2", "parallelism": f"instances sharded over {world} rank(s)"},
+        "clocks": clocks,
+        "gpu_launches": int(info[0]["launches_per_step"] * args.steps) if info else 0,
+        "autotune": {"setup_s": t_setup,
+                     "tensor_core_instances": sum(i["tensor_cores"] for i in info),
+                     "panel_w8_instances": sum(1 for i in info if i["panel_w"] == 8)},
+    }
+    if args.batched_fp64:
+        ms64, _, _, _, ne_d = leg("fp64", 1, 1)
+        out["fp64"] = {"value": dof_all / (ms64 / 1e3), "ms_per_step": ms64, "unit": UNIT}
+        out["speedup_mixed_over_fp64"] = ms64 / ms
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def measure_peaks():
     """Library GEMM throughput on this GPU (cuBLAS via torch.matmul, 8192^3, best of several): the
     denominators for FP64 and TF32 work that MEASURED_PEAKS.json does not carry."""
@@ -395,6 +477,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64_uneven"],
+                    help="the headline single discharge (default) or the 64 uneven discharges in one graph")
+    ap.add_argument("--batched-fp64", action="store_true", help="batched workload: also time the FP64 batch")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -402,6 +487,8 @@ def main():
         return measure_peaks()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batched64_uneven":
+        return run_batched(args, rank, world)
     return run_ours(args, rank, world)
 
 

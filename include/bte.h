@@ -183,6 +183,51 @@ bte_status bte_profile(bte_handle* h, int enable, double* ms_out, unsigned long 
  * the handle's stream without synchronising it. */
 bte_status bte_init_maxwellian_static(const bte_handle* h, double* F_dev, const double* ne_dev, double Te_eV);
 
+/* ---- Batched stepping of independent discharges ------------------------------------------------
+ * Many discharges with uneven grids (nx, nr, ntheta), pressures and cross sections, stepped
+ * together: every instance is an ordinary handle (its own operators, buffers and precision, all on
+ * the current device); the batch records one CUDA graph whose concurrent branches are the
+ * instances' step sequences of eqs. "bte_semi_implicit" (Section 3.4), framed by a kernel that
+ * writes every instance's uniform field E_i = (V0_i/L_i) sin(2 pi f_i (t_i + dt_i/2)) from a
+ * device-side clock t_i and one that advances the clocks by dt_i. n steps are n launches of that
+ * graph, with no host work between them. The paper steps one discharge; batching is an
+ * interface for running many. */
+typedef struct bte_batch bte_batch;
+
+/* flags for bte_batch_create */
+#define BTE_BATCH_AUTOTUNE 1u  /* per distinct instance shape (nx, nr, ntheta, nl, precision), time
+                                  one short run of every algorithm variant (tensor-core or CUDA-core
+                                  trailing update; panel column-block width) on a scratch Maxwellian
+                                  state and keep the fastest for the instances of that shape */
+
+/* Group `count` (1..4096) distinct handles, created with device buffers and with cross sections
+ * set. Handles stay owned by the caller and must outlive the batch; the autotuner (if asked) sets
+ * their algorithm variants. `stream` is the caller's cudaStream_t: every batched run starts after
+ * the work already enqueued on it. The batch owns its own stream, one branch stream and event per
+ * instance, the field arrays and the graph. */
+bte_status bte_batch_create(int count, bte_handle* const* handles, void* stream, unsigned flags,
+                            bte_batch** out);
+
+/* n_steps steps of every instance i on F_dev[i] (device, [nx_i][ntheta_i][nr_i] FP64, in/out)
+ * from time t0_s[i], with the uniform field of amplitude V0[i] [V] and frequency freq_Hz[i]
+ * (host arrays of count). The graph is recorded on the first call and again whenever the state
+ * pointers differ from the recorded ones. Synchronises the batch's stream at the end, writes every
+ * instance's status into status_out[count] (may be NULL) and returns the first non-OK one. As with
+ * bte_run, an instance whose step fails keeps the last state that stepped cleanly. */
+bte_status bte_batch_run(bte_batch* b, double* const* F_dev, int n_steps, const double* t0_s,
+                         const double* V0, const double* freq_Hz, bte_status* status_out);
+
+/* Variant used by instance i (1 = tensor-core trailing update; panel column-block width, 0 = by
+ * shape) and the kernels launched per batched step (all instances, after the first run). */
+bte_status bte_batch_get_info(const bte_batch* b, int i, int* tensor_cores, int* panel_w,
+                              unsigned long long* launches_per_step);
+
+/* Release the batch (synchronises its stream; the handles are not touched). NULL is accepted. */
+bte_status bte_batch_destroy(bte_batch* b);
+
+/* Message of the last failing batch call ("" if none); NULL: last bte_batch_create error. */
+const char* bte_batch_last_error(const bte_batch* b);
+
 /* Release every buffer of the handle (synchronises its stream first). NULL is accepted. */
 bte_status bte_destroy(bte_handle* h);
 

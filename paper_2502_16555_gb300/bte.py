@@ -31,7 +31,9 @@ OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "U
              "M": 9, "mom_n": 10, "mom_e": 11, "mom_r": 12}
 EXPORTS = ("bte_create", "bte_set_cross_sections", "bte_init_maxwellian", "bte_step", "bte_run",
            "bte_step_host", "bte_moments", "bte_get_operator", "bte_get_info", "bte_profile",
-           "bte_destroy", "bte_last_error", "bte_init_maxwellian_static")
+           "bte_destroy", "bte_last_error", "bte_init_maxwellian_static", "bte_batch_create",
+           "bte_batch_run", "bte_batch_get_info", "bte_batch_destroy", "bte_batch_last_error")
+BATCH_AUTOTUNE = 1
 KERNELS = ("x_to_eigen", "x_apply_q", "x_from_eigen", "v_form", "lu_panel", "lu_swap_trsm", "lu_gemm",
            "lu_solve", "residual", "other")
 
@@ -86,8 +88,14 @@ def load(path: str = LIB_PATH):
     lib.bte_destroy.argtypes = [vp]
     lib.bte_last_error.argtypes = [vp]
     lib.bte_last_error.restype = C.c_char_p
+    lib.bte_batch_create.argtypes = [i, C.POINTER(vp), vp, u, C.POINTER(vp)]
+    lib.bte_batch_run.argtypes = [vp, C.POINTER(vp), i, pd, pd, pd, C.POINTER(C.c_int)]
+    lib.bte_batch_get_info.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]
+    lib.bte_batch_destroy.argtypes = [vp]
+    lib.bte_batch_last_error.argtypes = [vp]
+    lib.bte_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name != "bte_last_error":
+        if name not in ("bte_last_error", "bte_batch_last_error"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -262,3 +270,66 @@ class Solver:
         i = Info()
         self._check(self.lib.bte_get_info(self.h, C.byref(i)))
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+class Batch:
+    """Many Solvers (uneven grids, pressures, cross sections) stepped together through one CUDA
+    graph per step (bte_batch_*). The solvers stay owned by the caller and must outlive the batch."""
+
+    def __init__(self, solvers, autotune: bool = False, stream=None):
+        self.lib = load()
+        import torch
+        self.torch = torch
+        self.solvers = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.solvers[0].device)
+        n = len(self.solvers)
+        hs = (C.c_void_p * n)(*[sv.h for sv in self.solvers])
+        b = C.c_void_p()
+        st = self.lib.bte_batch_create(n, hs, C.c_void_p(stream.cuda_stream), BATCH_AUTOTUNE if autotune else 0,
+                                       C.byref(b))
+        if st != OK:
+            raise BteError(st, self.lib.bte_batch_last_error(None).decode())
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.bte_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, Fs, n_steps: int, t0, V0=None, freq=None, raise_on_error: bool = True):
+        """n_steps steps of every instance; t0, V0, freq: scalars or one value per instance.
+        Returns the per-instance status list."""
+        n = len(self.solvers)
+        if len(Fs) != n:
+            raise ValueError("one state per instance")
+        for sv, F in zip(self.solvers, Fs):
+            sv._f(F)
+
+        def vec(v, key):
+            if v is None:
+                v = [sv.cfg[key] for sv in self.solvers]
+            v = np.broadcast_to(np.asarray(v, dtype=np.float64), (n,)).copy()
+            return v
+        t0v, v0v, fv = vec(t0, None) if t0 is not None else np.zeros(n), vec(V0, "V0"), vec(freq, "freq_Hz")
+        ptrs = (C.c_void_p * n)(*[F.data_ptr() for F in Fs])
+        status = (C.c_int * n)()
+        pd_ = C.POINTER(C.c_double)
+        st = self.lib.bte_batch_run(self.b, ptrs, int(n_steps), t0v.ctypes.data_as(pd_), v0v.ctypes.data_as(pd_),
+                                    fv.ctypes.data_as(pd_), status)
+        if st != OK and raise_on_error:
+            raise BteError(st, self.lib.bte_batch_last_error(self.b).decode())
+        return list(status)
+
+    def info(self, i: int) -> dict:
+        tc, w, lps = C.c_int(), C.c_int(), C.c_ulonglong()
+        st = self.lib.bte_batch_get_info(self.b, int(i), C.byref(tc), C.byref(w), C.byref(lps))
+        if st != OK:
+            raise BteError(st, self.lib.bte_batch_last_error(self.b).decode())
+        return {"tensor_cores": tc.value, "panel_w": w.value, "launches_per_step": lps.value}

@@ -24,6 +24,8 @@ struct bte_handle {
   double tol = 0.0;
   int refine_max = 0;
   bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
+  bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
+  int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)
   size_t bytes = 0;
   std::vector<void*> allocs;
 
@@ -164,7 +166,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
       const int kb = std::min(nb, n - k0);
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nullptr,
                                                               nx, n, k0, kb, nb, h->status, nullptr, nullptr,
-                                                              nullptr, nullptr, st));
+                                                              nullptr, nullptr, h->panel_w, st));
       if (k0 + kb < n) {
         BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
                                                                         n, k0, kb, nb, nullptr, nullptr, st));
@@ -180,14 +182,15 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     float* ulo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 3) : nullptr;
     float* lhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 4) : nullptr;
     float* llo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 5) : nullptr;
-    const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb);
+    const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb, h->panel_w);
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
       const int kb = std::min(nb, n - k0);
       // the L21 split for the tensor cores is written by lu_swap_pack
       BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv),
                                                              fused_uinv ? static_cast<float*>(h->uinv) : nullptr,
-                                                             nx, n, k0, kb, nb, h->status, nullptr, nullptr, lhi, llo, st));
+                                                             nx, n, k0, kb, nb, h->status, nullptr, nullptr, lhi, llo,
+                                                             h->panel_w, st));
       if (k0 + kb < n) {
         if (h->use_tc) {
           BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, kb, nb, uhi, ulo, whi, wlo, st));
@@ -271,6 +274,33 @@ bool valid_cfg(const bte_config* c, std::string& why) {
 }  // namespace
 
 namespace bte {
+bte_status handle_enqueue_step(bte_handle* h, double* F_dev, const double* E_dev, double t, double V0, double freq,
+                               cudaStream_t st) {
+  if (!device_ready(h)) return BTE_ESTATE;
+  cudaStream_t own = h->st;
+  h->st = st;
+  bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t, V0, freq);
+  h->st = own;
+  return s;
+}
+bte_status handle_reset_status(bte_handle* h, cudaStream_t st) {
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+  return BTE_OK;
+}
+bte_status handle_read_status(bte_handle* h) { return read_status(h); }
+bool handle_device_ready(bte_handle* h) { return device_ready(h); }
+bool handle_profiling(const bte_handle* h) { return h->prof; }
+unsigned long long handle_launches(const bte_handle* h) { return h->launches; }
+void handle_add_launches(bte_handle* h, unsigned long long n) { h->launches += n; }
+bool handle_has_tc(const bte_handle* h) { return h->have_tc; }
+void handle_set_variant(bte_handle* h, bool tc, int panel_w) {
+  h->use_tc = tc && h->have_tc;
+  h->panel_w = panel_w;
+}
+void handle_get_variant(const bte_handle* h, bool& tc, int& panel_w) {
+  tc = h->use_tc;
+  panel_w = h->panel_w;
+}
 const HostOps* handle_ops(const bte_handle* h) { return &h->ops; }
 void* handle_stream_ptr(const bte_handle* h) { return static_cast<void*>(h->st); }
 bte_status handle_fail(const bte_handle* h, bte_status s, const std::string& msg) {
@@ -338,6 +368,7 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
           ok = chk(dalloc(h, &w, bte::tc_workspace_bytes(o.nx, o.nv, h->nb)));
           h->tcws = w;
           h->use_tc = ok;
+          h->have_tc = ok;
         }
       }
     }

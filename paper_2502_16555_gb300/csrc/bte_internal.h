@@ -55,5 +55,22 @@ std::vector<double> maxwellian_coeffs(const HostOps& ops, double Te_eV);
 const HostOps* handle_ops(const bte_handle* h);
 void* handle_stream_ptr(const bte_handle* h);
 bte_status handle_fail(const bte_handle* h, bte_status s, const std::string& msg);
+bool handle_device_ready(bte_handle* h);
+bool handle_profiling(const bte_handle* h);
+unsigned long long handle_launches(const bte_handle* h);
+void handle_add_launches(bte_handle* h, unsigned long long n);
+// The step sequence of bte_step (F in place, status word NOT reset) enqueued on stream st (a
+// cudaStream_t) instead of the handle's own stream: used to capture several handles' steps as
+// branches of one CUDA graph.
+bte_status handle_enqueue_step(bte_handle* h, double* F_dev, const double* E_dev, double t, double V0, double freq,
+                               struct CUstream_st* st);
+bte_status handle_reset_status(bte_handle* h, struct CUstream_st* st);
+// Reads the status word back on the handle's stream (synchronising it) and maps it to a status.
+bte_status handle_read_status(bte_handle* h);
+// Algorithm variants the batch autotuner chooses between: the tensor-core trailing update (only
+// if the handle holds its workspace) and the panel kernel's column-block width (0: by shape).
+bool handle_has_tc(const bte_handle* h);
+void handle_set_variant(bte_handle* h, bool tc, int panel_w);
+void handle_get_variant(const bte_handle* h, bool& tc, int& panel_w);
 
 }  // namespace bte

@@ -45,11 +45,13 @@ int perm_record_ints(int nbmax);
 // li_hi/li_lo (may be NULL): TF32 split of inv(L11) for the tensor-core U12 formation.
 // uinv (may be NULL): per-panel inv(U11) ([point][panel], nbmax x nbmax), written only by the
 // mark-pivoting panel kernel, i.e. when lu_panel_fuses_uinv<T>(n, nbmax) holds.
+// w_pref: preferred column-block width of the mark-pivoting kernel (0: chosen by shape).
 template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
-                     unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st);
+                     unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, int w_pref,
+                     cudaStream_t st);
 template <typename T>
-bool lu_panel_fuses_uinv(int n, int nbmax);
+bool lu_panel_fuses_uinv(int n, int nbmax, int w_pref);
 // Tensor-core path: displaced-row writes of the panel permutation, the split (P A12)^T operand
 // (bt_hi/bt_lo) and the split L21 operand (a_hi/a_lo, may be NULL).
 void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,

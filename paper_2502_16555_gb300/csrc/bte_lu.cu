@@ -588,19 +588,21 @@ __device__ __forceinline__ void vstore(T* p, const T* in) {
 // At the end the rows are put in the order of the equivalent swap sequence (only displaced rows
 // move), the panel record and the LAPACK-style pivots are written, and inv(L11) (+ split) and,
 // when uinv is given, inv(U11) are formed from the final diagonal block.
-template <typename T, int W, int RPT>
-__global__ void __launch_bounds__(1024, 1) lu_panel_lazy_kernel(T* __restrict__ fac, int* __restrict__ piv,
+template <typename T, int W, int RPT, int NT>
+__global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fac, int* __restrict__ piv,
                                                                int* __restrict__ perm, T* __restrict__ linv,
                                                                T* __restrict__ uinv, int n, int k0, int nb,
                                                                int nbmax, unsigned* status,
                                                                float* __restrict__ li_hi, float* __restrict__ li_lo) {
-  constexpr int NT = 1024, VE = Vec16<T>::n, NONE = 1 << 30, MAXB = 128 / W;
+  constexpr int VE = Vec16<T>::n, NONE = 1 << 30, MAXB = 128 / W, NW = NT / 32;
+  static_assert(NT % 64 == 0 && NT <= 1024 && W * W <= NT, "block shape");
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ T LinvB[MAXB][W][W + 1];             // inverse of the unit-lower part of each block's diagonal block
   __shared__ T Tb[W][W + 1];                      // the diagonal block of the block just eliminated
   __shared__ __align__(16) T Raw[W][W];           // block t's pivot rows, current block's columns
   __shared__ __align__(16) T Ub[2][W][W];         // ... after the unit-lower solve
-  __shared__ T red_v[2][32];
+  __shared__ T red_v[2][32];                      // candidate magnitude per warp (FP64 path)
+  __shared__ unsigned red_k[2][32];               // candidate key: bits of |v| (FP32 path)
   __shared__ int red_i[2][32];
   __shared__ __align__(16) T red_row[2][32][W];
   __shared__ int pphys[128];
@@ -626,6 +628,13 @@ __global__ void __launch_bounds__(1024, 1) lu_panel_lazy_kernel(T* __restrict__ 
   for (int q = 0; q < RPT; ++q) pc[q] = NONE;
   bool bad_pivot = false;
   T a[RPT][W];
+  // warps without panel rows only take part in the barriers; their posts (and the slots of warps
+  // this block does not have) say "no candidate"
+  const bool active = warp * 32 < m0;
+  for (int i = tid; i < 64; i += NT) {
+    const int w = i & 31;
+    if (w >= NW || w * 32 >= m0) red_v[i >> 5][w] = T(-1), red_k[i >> 5][w] = 0u, red_i[i >> 5][w] = 0x7fffffff;
+  }
 
   for (int b = 0; b * W < nb; ++b) {
     const int s0 = b * W, c0 = k0 + s0;
@@ -656,30 +665,42 @@ __global__ void __launch_bounds__(1024, 1) lu_panel_lazy_kernel(T* __restrict__ 
         U[i][jj] = acc;
       }
       __syncthreads();
+      // pivot rows of block t take their U values; rows below block t (unmarked, or marked by a
+      // later block) take the rank-W update, each U row chunk read once for all of a thread's rows
+      bool upd[RPT];
+      const T* lr[RPT];
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid + q * NT;
-        if (r < m0) {
-          if (pc[q] >= t0 && pc[q] < t0 + W) {
-            const int i = pc[q] - t0;
+        upd[q] = r < m0 && pc[q] >= t0 + W;
+        lr[q] = A + static_cast<size_t>(k0 + (r < m0 ? r : 0)) * n + k0 + t0;
+        if (r < m0 && pc[q] >= t0 && pc[q] < t0 + W) {
+          const int i = pc[q] - t0;
 #pragma unroll
-            for (int v = 0; v < W; v += VE) vload(&U[i][v], &a[q][v]);
-          } else if (pc[q] >= t0 + W) {
-            const T* lr = A + static_cast<size_t>(k0 + r) * n + k0 + t0;
+          for (int v = 0; v < W; v += VE) vload(&U[i][v], &a[q][v]);
+        }
+      }
+      if (active) {
 #pragma unroll
-            for (int kv = 0; kv < W; kv += VE) {
-              T l[VE];
-              vload(lr + kv, l);
+        for (int kv = 0; kv < W; kv += VE) {
+          T l[RPT][VE];
 #pragma unroll
-              for (int u = 0; u < VE; ++u) {
+          for (int q = 0; q < RPT; ++q) {
+            if (upd[q]) vload(lr[q] + kv, l[q]);
+            else
 #pragma unroll
-                for (int v = 0; v < W; v += VE) {
-                  T uu[VE];
-                  vload(&U[kv + u][v], uu);
+              for (int u = 0; u < VE; ++u) l[q][u] = T(0);
+          }
 #pragma unroll
-                  for (int e = 0; e < VE; ++e) a[q][v + e] -= l[u] * uu[e];
-                }
-              }
+          for (int u = 0; u < VE; ++u) {
+#pragma unroll
+            for (int v = 0; v < W; v += VE) {
+              T uu[VE];
+              vload(&U[kv + u][v], uu);
+#pragma unroll
+              for (int q = 0; q < RPT; ++q)
+#pragma unroll
+                for (int e = 0; e < VE; ++e) a[q][v + e] -= l[q][u] * uu[e];
             }
           }
         }
@@ -689,39 +710,75 @@ __global__ void __launch_bounds__(1024, 1) lu_panel_lazy_kernel(T* __restrict__ 
 #pragma unroll
     for (int j = 0; j < W; ++j) {
       const int cur = s0 + j, buf = cur & 1;
-      T best = T(-1);
-      int bi = 0x7fffffff;
+      if (!active) {
+        __syncthreads();
+        continue;
+      }
+      int bi;
+      if constexpr (sizeof(T) == 4) {
+        // argmax as two warp reductions over (bits of |v|, row): the magnitude's bit pattern orders
+        // like the value; NaN counts as infinity, the smallest row wins a tie
+        unsigned key = 0u;
+        int ri = 0x7fffffff;
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int r = tid + q * NT;
-        if (r < m0 && pc[q] == NONE) {
-          T v = tabs(a[q][j]);
-          if (v != v) v = T(INFINITY);  // a NaN candidate wins and is reported as a bad pivot
-          if (v > best || (v == best && r < bi)) best = v, bi = r;
+        for (int q = 0; q < RPT; ++q) {
+          const int r = tid + q * NT;
+          if (r < m0 && pc[q] == NONE) {
+            unsigned k = __float_as_uint(static_cast<float>(a[q][j])) & 0x7fffffffu;
+            if (k > 0x7f800000u) k = 0x7f800000u;
+            if (k > key || ri == 0x7fffffff) key = k, ri = r;
+          }
         }
-      }
+        const unsigned wk = __reduce_max_sync(0xffffffffu, key);
+        const int wi = static_cast<int>(__reduce_min_sync(0xffffffffu, key == wk ? static_cast<unsigned>(ri) : 0x7fffffffu));
+        if (lane == 0) red_k[buf][warp] = wk, red_i[buf][warp] = wi;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
-      }
-      if (lane == 0) red_v[buf][warp] = best, red_i[buf][warp] = bi;
+        for (int q = 0; q < RPT; ++q) {
+          if (tid + q * NT == wi) {
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        if (tid + q * NT == bi) {
-#pragma unroll
-          for (int v = (j / VE) * VE; v < W; v += VE) vstore(&red_row[buf][warp][v], &a[q][v]);
+            for (int v = (j / VE) * VE; v < W; v += VE) vstore(&red_row[buf][warp][v], &a[q][v]);
+          }
         }
-      }
-      __syncthreads();
-      best = red_v[buf][lane];
-      bi = red_i[buf][lane];
+        __syncthreads();
+        const unsigned pk = red_k[buf][lane];
+        const int pi = red_i[buf][lane];
+        const unsigned gk = __reduce_max_sync(0xffffffffu, pk);
+        bi = static_cast<int>(__reduce_min_sync(0xffffffffu, pk == gk ? static_cast<unsigned>(pi) : 0x7fffffffu));
+      } else {
+        T best = T(-1);
+        bi = 0x7fffffff;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, best, o);
-        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+        for (int q = 0; q < RPT; ++q) {
+          const int r = tid + q * NT;
+          if (r < m0 && pc[q] == NONE) {
+            T v = tabs(a[q][j]);
+            if (v != v) v = T(INFINITY);  // a NaN candidate wins and is reported as a bad pivot
+            if (v > best || (v == best && r < bi)) best = v, bi = r;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+        }
+        if (lane == 0) red_v[buf][warp] = best, red_i[buf][warp] = bi;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          if (tid + q * NT == bi) {
+#pragma unroll
+            for (int v = (j / VE) * VE; v < W; v += VE) vstore(&red_row[buf][warp][v], &a[q][v]);
+          }
+        }
+        __syncthreads();
+        best = red_v[buf][lane];
+        bi = red_i[buf][lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+        }
       }
       const T* prow = red_row[buf][(bi % NT) >> 5];
       T pr[W];
@@ -732,7 +789,11 @@ __global__ void __launch_bounds__(1024, 1) lu_panel_lazy_kernel(T* __restrict__ 
         pphys[cur] = bi;
         if (!(tabs(pv) > T(0)) || !isfinite(static_cast<double>(pv))) bad_pivot = true;
       }
-      const T inv = (pv != T(0)) ? T(1) / pv : T(0);
+      T inv = T(0);
+      if (pv != T(0)) {
+        if constexpr (sizeof(T) == 4) inv = __frcp_rn(pv);
+        else inv = __drcp_rn(pv);
+      }
 #pragma unroll
       for (int q = 0; q < RPT; ++q) {
         const int r = tid + q * NT;
@@ -1337,36 +1398,37 @@ static int panel_width(int n, int nb) {
 
 template <typename T, int W, int RPT>
 static void launch_lazy(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
-                        unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
+                        unsigned* status, float* li_hi, float* li_lo, cudaStream_t st) {
+  constexpr int NT = 512;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lu_panel_lazy_kernel<T, W, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(lu_panel_lazy_kernel<T, W, RPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
   const size_t smem = panel_lazy_smem_bytes(n - k0, nb, nbmax, sizeof(T));
-  (void)ws_hi;
-  (void)ws_lo;
-  lu_panel_lazy_kernel<T, W, RPT><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax, status,
-                                                         li_hi, li_lo);
+  lu_panel_lazy_kernel<T, W, RPT, NT><<<nx, NT, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax, status,
+                                                           li_hi, li_lo);
 }
 
-// Column-block width and rows per thread of the mark-pivoting panel kernel for a panel of m0 rows
-// and width nb (W = 0: the kernel does not apply).
+// Column-block width and rows per thread of the mark-pivoting panel kernel (512 threads) for a
+// panel of m0 rows and width nb (W = 0: the kernel does not apply). The W x rows-per-thread block
+// of the panel held in registers stays at 64 values per thread.
+// w_pref selects the narrower block (W4, 8 rows per thread) where both apply; 0 picks by shape.
 template <typename T>
-static void lazy_shape(int n, int m0, int nb, int nbmax, int& W, int& rpt) {
+static void lazy_shape(int n, int m0, int nb, int nbmax, int w_pref, int& W, int& rpt) {
   constexpr int VE = 16 / sizeof(T);
   constexpr int W2 = sizeof(T) == 4 ? 16 : 8, W4 = sizeof(T) == 4 ? 8 : 4;
   W = 0, rpt = 0;
   if (n % VE != 0 || nbmax > 128 || nbmax % VE != 0) return;
-  if (m0 <= 2048 && nb % W2 == 0) W = W2, rpt = 2;
-  else if (m0 <= 4096 && nb % W4 == 0) W = W4, rpt = 4;
+  if (m0 <= 2048 && nb % W2 == 0 && w_pref != W4) W = W2, rpt = 4;
+  else if (m0 <= 4096 && nb % W4 == 0) W = W4, rpt = 8;
 }
 
 template <typename T>
-bool lu_panel_fuses_uinv(int n, int nbmax) {
+bool lu_panel_fuses_uinv(int n, int nbmax, int w_pref) {
   for (int k0 = 0; k0 < n; k0 += nbmax) {
     int W, rpt;
-    lazy_shape<T>(n, n - k0, std::min(nbmax, n - k0), nbmax, W, rpt);
+    lazy_shape<T>(n, n - k0, std::min(nbmax, n - k0), nbmax, w_pref, W, rpt);
     if (!W) return false;
   }
   return true;
@@ -1374,19 +1436,20 @@ bool lu_panel_fuses_uinv(int n, int nbmax) {
 
 template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
-                     unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, cudaStream_t st) {
+                     unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, int w_pref,
+                     cudaStream_t st) {
   const bool trail = k0 + nb < n;
   float* wh = trail ? ws_hi : nullptr;
   float* lh = trail ? li_hi : nullptr;
   int W, rpt;
-  lazy_shape<T>(n, n - k0, nb, nbmax, W, rpt);
+  lazy_shape<T>(n, n - k0, nb, nbmax, w_pref, W, rpt);
   constexpr int W2 = sizeof(T) == 4 ? 16 : 8, W4 = sizeof(T) == 4 ? 8 : 4;
-  if (W == W2 && rpt == 2) {
-    launch_lazy<T, W2, 2>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
+  if (W == W2 && rpt == 4) {
+    launch_lazy<T, W2, 4>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, lh, li_lo, st);
     return;
   }
-  if (W == W4 && rpt == 4) {
-    launch_lazy<T, W4, 4>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, wh, ws_lo, lh, li_lo, st);
+  if (W == W4 && rpt == 8) {
+    launch_lazy<T, W4, 8>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, lh, li_lo, st);
     return;
   }
   const int Wf = panel_width<T>(n, nbmax);
@@ -1482,8 +1545,8 @@ void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const
 
 #define BTE_INST(T)                                                                                 \
   template void launch_lu_panel<T>(T*, int*, int*, T*, T*, int, int, int, int, int, unsigned*, float*,   \
-                                   float*, float*, float*, cudaStream_t);                           \
-  template bool lu_panel_fuses_uinv<T>(int, int);                                                   \
+                                   float*, float*, float*, int, cudaStream_t);                      \
+  template bool lu_panel_fuses_uinv<T>(int, int, int);                                              \
   template void launch_lu_uinv<T>(const T*, T*, int, int, int, cudaStream_t);                        \
   template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \
                                            double*, int, int, int, const int*, int, cudaStream_t);  \

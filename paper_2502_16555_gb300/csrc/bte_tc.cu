@@ -35,12 +35,19 @@ namespace bte {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, KTOT = 128, NCHUNK = KTOT / BK;
-constexpr int STAGES = 3;
+// Operand stages and C staging slots share the 227 KB of shared memory (64 KB and 16 KB each).
+#ifndef BTE_TC_STAGES
+#define BTE_TC_STAGES 2
+#endif
+#ifndef BTE_TC_CSLOTS
+#define BTE_TC_CSLOTS 4
+#endif
+constexpr int STAGES = BTE_TC_STAGES;
 constexpr int BOX_BYTES = BM * BK * 4;            // 16 KB (BM == BN)
 constexpr int STAGE_BYTES = 4 * BOX_BYTES;        // A_hi, A_lo, B_hi, B_lo
 constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
 constexpr int CW = 32;                            // C chunk width (columns): one 128-byte swizzle row
-constexpr int CSLOTS = 2;                         // C staging slots
+constexpr int CSLOTS = BTE_TC_CSLOTS;             // C staging slots
 constexpr int CSLOT_BYTES = BM * CW * 4;          // 16 KB
 constexpr int NCCHUNK = BN / CW;
 constexpr int NTHREADS = 192;
@@ -300,9 +307,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_expect_tx(&s.cfull[slot], CSLOT_BYTES);
       tma_load3(s.cbuf[slot], &mC, cx(t, ch), cy(t), t / per_point, &s.cfull[slot]);
     };
+    // C load number q (the q-th chunk of this CTA) goes to slot q % CSLOTS, phase (q / CSLOTS) & 1
+    auto chunk_at = [&](int q, int& tq, int& chq) {
+      tq = blockIdx.x + (q / NCCHUNK) * gridDim.x;
+      chq = q % NCCHUNK;
+    };
     int c_issued = 0, c_done = 0;  // leader's count of C loads issued and waited for
     if (leader && load_c)
-      for (int ch = 0; ch < CSLOTS && blockIdx.x < total; ++ch) issue_c(blockIdx.x, ch, ch), ++c_issued;
+      for (int q = 0; q < CSLOTS; ++q) {
+        int tq, chq;
+        chunk_at(q, tq, chq);
+        if (tq >= total) break;
+        issue_c(tq, chq, q % CSLOTS);
+        ++c_issued;
+      }
     int acc = 0, g = 0;
     uint32_t aph = 0;
     bool stop = false;
@@ -312,9 +330,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int col0 = (r % args.tiles_n) * BN;
       if (leader && !mbar_wait(s, &s.tfull[acc], aph, status)) atomicExch(&s.abort, 1);
       for (int ch = 0; ch < NCCHUNK; ++ch, ++g) {
-        const int slot = g & 1;
+        const int slot = g % CSLOTS;
         if (leader && load_c && !*reinterpret_cast<volatile int*>(&s.abort)) {
-          if (mbar_wait(s, &s.cfull[slot], (g >> 1) & 1, status)) ++c_done;
+          if (mbar_wait(s, &s.cfull[slot], (g / CSLOTS) & 1, status)) ++c_done;
           else atomicExch(&s.abort, 1);
         }
         epi_bar();
@@ -363,8 +381,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           tma_store3(&mC, s.cbuf[slot], cx(t, ch), cy(t), p);
           bulk_wait_read_all();  // the slot is free again
           if (load_c) {
-            const int t2 = ch + CSLOTS < NCCHUNK ? t : t + gridDim.x;
-            const int ch2 = (ch + CSLOTS) % NCCHUNK;
+            int t2, ch2;
+            chunk_at(g + CSLOTS, t2, ch2);
             if (t2 < total) issue_c(t2, ch2, slot), ++c_issued;
           }
         }
@@ -380,7 +398,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // loads issued but not waited for (only after an abort) must land before the CTA exits
       for (int q = c_done; q < c_issued; ++q) {
         const long long t0 = clock64();
-        while (!mbar_try(&s.cfull[q & 1], (q >> 1) & 1) && clock64() - t0 < kWaitCycles) {
+        while (!mbar_try(&s.cfull[q % CSLOTS], (q / CSLOTS) & 1) && clock64() - t0 < kWaitCycles) {
         }
       }
     }

@@ -1,0 +1,92 @@
+"""Batched stepping of uneven discharges (bte_batch_*) against individually stepped handles and
+against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import bte as O
+from paper_2502_16555_gb300 import workloads as W
+from tests._lib import ensure_built
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def uneven():
+    # three discharges with different grids, pressures and amplitudes; nv = 256, 384, 520
+    a = W.scaled(W.SMALL, nx=9, nr=16, ntheta=16, p_Torr=0.3, V0=120.0)
+    b = W.scaled(W.SMALL, nx=12, nr=24, ntheta=16, p_Torr=1.5, V0=200.0)
+    c = W.scaled(W.SMALL, nx=7, nr=40, ntheta=13, p_Torr=0.8, V0=60.0)
+    return [a, b, c]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_equals_individual_runs(precision):
+    from paper_2502_16555_gb300 import bte
+    cfgs = uneven()
+    sb = [bte.Solver(c, precision) for c in cfgs]
+    si = [bte.Solver(c, precision) for c in cfgs]
+    F0 = [W.random_state(c["nx"], c["ntheta"], c["nr"], seed=40 + k) for k, c in enumerate(cfgs)]
+    t0 = [0.1 / W.RF_FREQ_HZ, 0.3 / W.RF_FREQ_HZ, 0.0]
+    Fb = [torch.from_numpy(f.copy()).cuda() for f in F0]
+    batch = bte.Batch(sb)
+    st = batch.run(Fb, 3, t0)
+    assert st == [bte.OK] * 3
+    assert batch.info(0)["launches_per_step"] > 3 * 20
+    for k, c in enumerate(cfgs):
+        Fi = torch.from_numpy(F0[k].copy()).cuda()
+        si[k].run(Fi, 3, t0[k])
+        assert rel_l2(Fb[k].cpu().numpy(), Fi.cpu().numpy()) <= 1e-12
+    # a second call continues from the device clocks it was given (no recapture)
+    batch.run(Fb, 1, [t + 3 * c["dt_s"] for t, c in zip(t0, cfgs)])
+    for k, c in enumerate(cfgs):
+        Fi = torch.from_numpy(F0[k].copy()).cuda()
+        si[k].run(Fi, 4, t0[k])
+        assert rel_l2(Fb[k].cpu().numpy(), Fi.cpu().numpy()) <= 1e-12
+    batch.close()
+
+
+def test_batch_autotuned_against_oracle():
+    from paper_2502_16555_gb300 import bte
+    cfgs = uneven()[:2]
+    sv = [bte.Solver(c, "mixed") for c in cfgs]
+    batch = bte.Batch(sv, autotune=True)
+    F0 = [W.random_state(c["nx"], c["ntheta"], c["nr"], seed=50 + k) for k, c in enumerate(cfgs)]
+    Fs = [torch.from_numpy(f.copy()).cuda() for f in F0]
+    t0 = 0.17 / W.RF_FREQ_HZ
+    batch.run(Fs, 1, t0)
+    for k, c in enumerate(cfgs):
+        ref = O.Operators(c).step(F0[k], t0)
+        assert rel_l2(Fs[k].cpu().numpy(), ref) <= 1e-9
+        info = batch.info(k)
+        assert info["tensor_cores"] in (0, 1) and info["panel_w"] in (0, 8)
+
+
+def test_batch_recaptures_for_new_states_and_isolates_errors():
+    from paper_2502_16555_gb300 import bte
+    cfgs = uneven()
+    sv = [bte.Solver(c, "fp64") for c in cfgs]
+    batch = bte.Batch(sv)
+    F0 = [W.random_state(c["nx"], c["ntheta"], c["nr"], seed=60 + k) for k, c in enumerate(cfgs)]
+    batch.run([torch.from_numpy(f.copy()).cuda() for f in F0], 1, 0.0)
+    # new tensors (new pointers); instance 1 holds a NaN
+    bad = F0[1].copy()
+    bad[3, 2, 5] = np.nan
+    Fs = [torch.from_numpy(F0[0].copy()).cuda(), torch.from_numpy(bad).cuda(), torch.from_numpy(F0[2].copy()).cuda()]
+    st = batch.run(Fs, 2, 0.0, raise_on_error=False)
+    assert st[0] == bte.OK and st[2] == bte.OK and st[1] == bte.ENONFINITE
+    got = Fs[1].cpu().numpy()
+    assert np.array_equal(np.isnan(got), np.isnan(bad)) and np.array_equal(got[~np.isnan(got)], bad[~np.isnan(bad)])
+    for k in (0, 2):
+        ref = O.run(cfgs[k], steps=2, F0=F0[k], t0=0.0)[0]
+        assert rel_l2(Fs[k].cpu().numpy(), ref) <= 1e-10

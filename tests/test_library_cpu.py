@@ -110,3 +110,23 @@ def test_host_only_handle_refuses_device_work(lib):
     st = lib.bte_step(s.h, None, None, 0.0, 1.0, 1.0)
     assert st == bte.EINVAL
     assert lib.bte_destroy(None) == bte.OK
+
+
+def test_batch_create_validates_before_any_device_work():
+    """bte_batch_create refuses NULL/empty input and handles without device buffers (host-only),
+    without touching a GPU."""
+    import ctypes as C
+    from paper_2502_16555_gb300 import bte
+    lib = bte.load()
+    out = C.c_void_p()
+    assert lib.bte_batch_create(0, None, None, 0, C.byref(out)) == bte.EINVAL
+    cfg = W.scaled(W.SMALL, nx=5, nr=6, ntheta=4)
+    s1 = bte.Solver(cfg, host_only=True)
+    s2 = bte.Solver(cfg, host_only=True)
+    hs = (C.c_void_p * 2)(s1.h, s2.h)
+    assert lib.bte_batch_create(2, hs, None, 0, C.byref(out)) == bte.ESTATE
+    assert b"device buffers" in lib.bte_batch_last_error(None)
+    same = (C.c_void_p * 2)(s1.h, s1.h)
+    assert lib.bte_batch_create(2, same, None, 0, C.byref(out)) in (bte.EINVAL, bte.ESTATE)
+    assert not out.value
+    assert lib.bte_batch_destroy(None) == bte.OK
