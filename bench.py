@@ -439,6 +439,49 @@ def run_batched(args, rank, world):
     return 0
 
 
+def run_adjoint(args, rank, world):
+    """Gradient of the cycle-averaged electron number over one RF cycle (1000 steps, FP64,
+    Nx=64, Nr=32, Ntheta=16) with respect to 8 parameters (four cross-section scales, three
+    threshold shifts, V0) by the adjoint with checkpoints every 50 steps, checked against central
+    differences (h = 1e-6 relative) of the same forward run."""
+    import torch
+    from paper_2502_16555_gb300 import adjoint
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cfg = W.WORKLOADS["adjoint_nx64_nr32_nt16"]
+    steps = cfg["steps"] if args.adjoint_steps <= 0 else args.adjoint_steps
+    m = adjoint.CycleDensity(cfg, steps=steps, checkpoint=50)
+    th = m.theta0()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, saved = m.forward(th)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g = m.gradient(saved)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    fd = []
+    for k in range(th.size):
+        h = 1e-6 * max(1.0, abs(th[k]))
+        up, dn = th.copy(), th.copy()
+        up[k] += h
+        dn[k] -= h
+        fd.append((m.forward(up)[0] - m.forward(dn)[0]) / (2 * h))
+    fd = np.array(fd)
+    rel = np.abs(g - fd) / np.maximum(np.abs(fd), 1e-300)
+    normwise = float(np.abs(g - fd).max() / np.abs(g).max())
+    dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
+    out = {"metric": "adjoint gradient of the cycle-averaged electron number", "workload": "adjoint_nx64_nr32_nt16",
+           "steps": steps, "checkpoint": 50, "J": J, "params": m.names(), "grad_adjoint": g.tolist(),
+           "grad_central_difference": fd.tolist(), "max_rel_deviation": float(rel.max()),
+           "normwise_deviation": normwise,
+           "forward_s": t1 - t0, "adjoint_s": t2 - t1,
+           "forward_dof_updates_per_s": dof * steps / (t1 - t0), "dtype": "f64", "data": "synthetic"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
 def measure_peaks():
     """Library GEMM throughput on this GPU (cuBLAS via torch.matmul, 8192^3, best of several): the
     denominators for FP64 and TF32 work that MEASURED_PEAKS.json does not carry."""
@@ -477,8 +520,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64_uneven"],
-                    help="the headline single discharge (default) or the 64 uneven discharges in one graph")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64_uneven", "adjoint_nx64_nr32_nt16"],
+                    help="the headline single discharge (default), the 64 uneven discharges in one graph, "
+                         "or the adjoint-gradient check")
+    ap.add_argument("--adjoint-steps", type=int, default=0, help="adjoint workload: steps (0 = one RF cycle)")
     ap.add_argument("--batched-fp64", action="store_true", help="batched workload: also time the FP64 batch")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -489,6 +534,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batched64_uneven":
         return run_batched(args, rank, world)
+    if args.workload == "adjoint_nx64_nr32_nt16":
+        return run_adjoint(args, rank, world)
     return run_ours(args, rank, world)
 
 

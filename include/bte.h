@@ -157,7 +157,8 @@ bte_status bte_moments(bte_handle* h, const double* F_dev, double* ne_dev, doubl
 /* Copy one host-assembled operator into a host array of `count` doubles (for inspection/tests):
  * which = 0 x[nx], 1 D_x[nx][nx], 2 mu[ntheta], 3 K_C[nv][nv], 4 K_A[nv][nv], 5 lambda[nr],
  * 6 U[nr][nr], 7 U^-1[nr][nr], 8 Q[ntheta][nr][nx][nx] (inflow column zeroed), 9 M_v[nr][nr],
- * 10 density moment vector [nv], 11 energy moment vector [nv], 12 rate vectors [n_proc][nv].
+ * 10 density moment vector [nv], 11 energy moment vector [nv], 12 rate vectors [n_proc][nv],
+ * 13 Clenshaw-Curtis weights of the collocation points on [0, L] [nx].
  * Returns BTE_EINVAL if count does not match, BTE_ESTATE if the operator is not assembled yet. */
 bte_status bte_get_operator(const bte_handle* h, int which, double* host_out, size_t count);
 
@@ -182,6 +183,37 @@ bte_status bte_profile(bte_handle* h, int enable, double* ms_out, unsigned long 
  * whose work overlaps on the GPU (other streams, or other threads) race on it. Work is enqueued on
  * the handle's stream without synchronising it. */
 bte_status bte_init_maxwellian_static(const bte_handle* h, double* F_dev, const double* ne_dev, double Te_eV);
+
+/* ---- Adjoint of the step ----------------------------------------------------------------------
+ * With a specified field the step of eqs. "bte_semi_implicit" (Section 3.4) is linear in F:
+ * F^{n+1} = S_n F^n, S_n = X V_n X (X: x half step, Algorithm 1; V_n: the per-point solves with
+ * A_i = I - dt (K_C + E_i K_A), eq. "vspace_batched_system"). These entry points give the
+ * transposed map and the parameter sensitivities needed for gradients of functionals of the
+ * trajectory (a discrete adjoint; the paper has no counterpart). FP64 handles only (BTE_ESTATE
+ * otherwise). */
+
+/* lambda <- S_n^T lambda + g_weight * g for the step that starts from F^n = F_dev at time t_s with
+ * the uniform field (V0/L) sin(2 pi freq (t + dt/2)). F_dev, lambda_dev, g_dev: device
+ * [nx][ntheta][nr] FP64 (lambda in/out; g may be NULL). If SC_dev / SA_dev (device nv x nv FP64,
+ * row-major, may be NULL) are given, the step's sensitivity products are added to them:
+ *     SC += sum_i mu_i F*_i^T,    SA += (sin(2 pi freq (t + dt/2)) / L) sum_i mu_i F*_i^T,
+ * mu_i = A_i^-T (X^T lambda)_i the adjoint after the velocity step and F*_i = A_i^-1 (X F^n)_i the
+ * state after it (both at point i, nv entries). The transposed x step uses U^T, the transposed
+ * Q_ij blocks and U^-T (copied to the device on the first call); A_i^T is solved with the same LU
+ * factors (recomputed from F^n). Synchronises the handle's stream. */
+bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_dev, double t_s, double V0,
+                            double freq_Hz, const double* g_dev, double g_weight, double* SC_dev,
+                            double* SA_dev);
+
+/* Gradient of a functional J from the accumulated sensitivities (SC, SA from bte_step_adjoint over
+ * a trajectory, device): grad_out[2 n_proc + 1] =
+ *   [ dJ/dscale_j  (j < n_proc) | dJ/dthreshold_j [per eV] (j < n_proc; 0 without a threshold) |
+ *     dJ/dV0 [per V] ],
+ * dJ/dtheta = dt <dK/dtheta, S> (Frobenius product). dK_C/dscale_j is process j's own K_C at unit
+ * scale; dK_C/dthreshold_j is the central difference of the FP64 assembly with step h_eV; the V0
+ * term uses K_A and SA. Synchronises the handle's stream. */
+bte_status bte_adjoint_gradient(const bte_handle* h, const double* SC_dev, const double* SA_dev, double h_eV,
+                                double* grad_out);
 
 /* ---- Batched stepping of independent discharges ------------------------------------------------
  * Many discharges with uneven grids (nx, nr, ntheta), pressures and cross sections, stepped

@@ -28,11 +28,12 @@ FLAG_SIMT_GEMM = 2
 KINDS = {"elastic": 0, "excitation": 1, "ionization": 2}
 FORMS = {"const": 0, "linear": 1, "log": 2, "table": 3, "nu": 4}
 OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "Uinv": 7, "Q": 8,
-             "M": 9, "mom_n": 10, "mom_e": 11, "mom_r": 12}
+             "M": 9, "mom_n": 10, "mom_e": 11, "mom_r": 12, "ccw": 13}
 EXPORTS = ("bte_create", "bte_set_cross_sections", "bte_init_maxwellian", "bte_step", "bte_run",
            "bte_step_host", "bte_moments", "bte_get_operator", "bte_get_info", "bte_profile",
            "bte_destroy", "bte_last_error", "bte_init_maxwellian_static", "bte_batch_create",
-           "bte_batch_run", "bte_batch_get_info", "bte_batch_destroy", "bte_batch_last_error")
+           "bte_batch_run", "bte_batch_get_info", "bte_batch_destroy", "bte_batch_last_error",
+           "bte_step_adjoint", "bte_adjoint_gradient")
 BATCH_AUTOTUNE = 1
 KERNELS = ("x_to_eigen", "x_apply_q", "x_from_eigen", "v_form", "lu_panel", "lu_swap_trsm", "lu_gemm",
            "lu_solve", "residual", "other")
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
     lib.bte_batch_run.argtypes = [vp, C.POINTER(vp), i, pd, pd, pd, C.POINTER(C.c_int)]
     lib.bte_batch_get_info.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]
     lib.bte_batch_destroy.argtypes = [vp]
+    lib.bte_step_adjoint.argtypes = [vp, vp, vp, d, d, d, vp, d, vp, vp]
+    lib.bte_adjoint_gradient.argtypes = [vp, vp, vp, d, pd]
     lib.bte_batch_last_error.argtypes = [vp]
     lib.bte_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -249,10 +252,31 @@ class Solver:
         sizes = {"x": (self.nx,), "Dx": (self.nx, self.nx), "mu": (self.nt,), "KC": (self.nv, self.nv),
                  "KA": (self.nv, self.nv), "lambda": (self.nr,), "U": (self.nr, self.nr),
                  "Uinv": (self.nr, self.nr), "Q": (self.nt, self.nr, self.nx, self.nx), "M": (self.nr, self.nr),
-                 "mom_n": (self.nv,), "mom_e": (self.nv,), "mom_r": (self.n_proc, self.nv)}
+                 "mom_n": (self.nv,), "mom_e": (self.nv,), "mom_r": (self.n_proc, self.nv), "ccw": (self.nx,)}
         out = np.empty(sizes[name], dtype=np.float64)
         self._check(self.lib.bte_get_operator(self.h, OPERATORS[name], out.ctypes.data_as(C.POINTER(C.c_double)),
                                               out.size))
+        return out
+
+    def step_adjoint(self, F, lam, t: float, g=None, g_weight: float = 0.0, SC=None, SA=None, V0=None, freq=None):
+        """lam <- S_n^T lam + g_weight g for the step from F at time t (bte_step_adjoint); adds the
+        step's sensitivity products to SC / SA (nv x nv float64 CUDA tensors) when given."""
+        V0 = self.cfg["V0"] if V0 is None else V0
+        freq = self.cfg["freq_Hz"] if freq is None else freq
+        for m in (SC, SA):
+            if m is not None and not (m.is_cuda and m.dtype == self.torch.float64 and m.numel() == self.nv * self.nv
+                                      and m.is_contiguous()):
+                raise ValueError("SC/SA must be contiguous float64 CUDA tensors of nv x nv")
+        self._check(self.lib.bte_step_adjoint(self.h, _ptr(self._f(F)), _ptr(self._f(lam)), float(t), float(V0),
+                                              float(freq), _ptr(None if g is None else self._f(g)), float(g_weight),
+                                              _ptr(SC), _ptr(SA)))
+        return lam
+
+    def adjoint_gradient(self, SC, SA, h_eV: float = 1e-4) -> np.ndarray:
+        """[dJ/dscale_j..., dJ/dthreshold_j..., dJ/dV0] from the accumulated sensitivities."""
+        out = np.empty(2 * self.n_proc + 1, dtype=np.float64)
+        self._check(self.lib.bte_adjoint_gradient(self.h, _ptr(SC), _ptr(SA), float(h_eV),
+                                                  out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
     def profile_start(self):

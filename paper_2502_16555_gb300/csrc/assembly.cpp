@@ -354,6 +354,20 @@ std::string assemble_x(const bte_config& cfg, HostOps& o) {
   for (int i = 0; i < nx; ++i) o.x[i] = 0.5 * o.L * (1.0 - std::cos(kPi * i / N));
   o.x[0] = 0.0;
   o.x[N] = o.L;
+  // Clenshaw-Curtis weights for these points on [0, L]: w_i = (L/2) c_i/N (1 - sum_k b_k
+  // cos(2 k theta_i)/(4k^2 - 1)), theta_i = pi i/N, b_k = 1 for k = N/2 and 2 below, c = 1/2 at the
+  // ends and 1 inside (the cosine series of the interpolant integrated term by term)
+  o.ccw.assign(nx, 0.0);
+  for (int i = 0; i <= N; ++i) {
+    const double th = kPi * i / N;
+    double sum = 0.0;
+    for (int k = 1; 2 * k <= N; ++k) {
+      const double bk = (2 * k == N) ? 1.0 : 2.0;
+      sum += bk * std::cos(2.0 * k * th) / (4.0 * k * k - 1.0);
+    }
+    const double ci = (i == 0 || i == N) ? 0.5 : 1.0;
+    o.ccw[i] = 0.5 * o.L * 2.0 * ci / N * (1.0 - sum);
+  }
   o.Dx.assign(nx * nx, 0.0);
   for (int i = 0; i < nx; ++i) {
     const double ci = (i == 0 || i == N) ? 2.0 : 1.0;
@@ -653,6 +667,17 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
   }
   o.have_v = true;
   return "";
+}
+
+std::string assemble_kc_only(const HostOps& o, const std::vector<Process>& procs, std::vector<double>& KC) {
+  HostOps t;
+  t.nx = o.nx, t.nr = o.nr, t.nt = o.nt, t.nl = o.nl, t.nv = o.nv;
+  t.L = o.L, t.vmax = o.vmax, t.n0 = o.n0, t.T0 = o.T0, t.m0 = o.m0, t.dt = o.dt;
+  t.mu = o.mu, t.wmu = o.wmu, t.knots = o.knots, t.M = o.M, t.G = o.G, t.Dv = o.Dv, t.M1 = o.M1;
+  t.TO = o.TO, t.TS = o.TS;
+  std::string e = assemble_v(t, procs);
+  if (e.empty()) KC.swap(t.KC);
+  return e;
 }
 
 std::vector<double> maxwellian_coeffs(const HostOps& o, double Te_eV) {

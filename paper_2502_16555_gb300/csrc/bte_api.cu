@@ -8,57 +8,11 @@
 #include <string>
 #include <vector>
 
-#include "bte_internal.h"
+#include "bte_handle.h"
 #include "bte_kernels.h"
 
 using bte::HostOps;
 
-struct bte_handle {
-  bte_config cfg{};
-  HostOps ops;
-  std::string err;
-  bool host_only = false;
-  cudaStream_t st = nullptr;
-  int precision = BTE_FP64;
-  int nb = 64;            // outer LU panel width
-  double tol = 0.0;
-  int refine_max = 0;
-  bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
-  bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
-  int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)
-  size_t bytes = 0;
-  std::vector<void*> allocs;
-
-  // x-step operators
-  double *U = nullptr, *Uinv = nullptr, *Q = nullptr;
-  // velocity operators
-  double *KC = nullptr, *KA = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
-  double *TO = nullptr, *TS = nullptr;
-  double *mom_n = nullptr, *mom_e = nullptr, *mom_r = nullptr;
-  // work
-  double *Y = nullptr, *Y2 = nullptr, *Fa = nullptr, *Fb = nullptr, *Fw = nullptr, *R = nullptr;
-  double *Fhost_dev = nullptr, *coef = nullptr, *ratio = nullptr;
-  void* fac = nullptr;
-  void* linv = nullptr;
-  void* uinv = nullptr;
-  void* tcws = nullptr;
-  int *piv = nullptr, *perm = nullptr, *conv = nullptr;
-  unsigned* status = nullptr;
-  unsigned* status_host = nullptr;  // pinned
-  int last_sweeps = 0;
-  double last_resid = 0.0;
-  unsigned last_flags = 0;
-  unsigned long long launches = 0;
-  // profiling: events around every launch while enabled
-  struct Rec {
-    int kind;
-    cudaEvent_t a, b;
-  };
-  bool prof = false;
-  std::vector<Rec> recs;
-  std::vector<cudaEvent_t> pool;
-  size_t pool_used = 0;
-};
 
 namespace {
 
@@ -422,6 +376,7 @@ bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* 
   }
   std::string e = bte::assemble_v(h->ops, ps);
   if (!e.empty()) return fail(h, BTE_EINVAL, e);
+  h->procs = ps;
   if (h->host_only) return BTE_OK;
   const HostOps& o = h->ops;
   if (h->mom_r) {
@@ -523,9 +478,10 @@ bte_status bte_get_operator(const bte_handle* hc, int which, double* out, size_t
     case 10: v = &o.mom_n; break;
     case 11: v = &o.mom_e; break;
     case 12: v = &o.mom_r; break;
+    case 13: v = &o.ccw; break;
     default: return fail(h, BTE_EINVAL, "unknown operator id");
   }
-  const bool needs_v = which == 3 || which == 4 || which >= 10;
+  const bool needs_v = which == 3 || which == 4 || (which >= 10 && which <= 12);
   if (needs_v && !o.have_v)
     return fail(h, BTE_ESTATE, "velocity operators not assembled yet");
   if (v->size() != count) return fail(h, BTE_EINVAL, "count does not match the operator size");

@@ -1,0 +1,61 @@
+// The handle behind the C ABI (opaque to callers): operators, device buffers and state. Shared by
+// the translation units that implement entry points (bte_api.cu, bte_adjoint.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "bte_internal.h"
+
+struct bte_handle {
+  bte_config cfg{};
+  bte::HostOps ops;
+  std::string err;
+  bool host_only = false;
+  cudaStream_t st = nullptr;
+  int precision = BTE_FP64;
+  int nb = 64;            // outer LU panel width
+  double tol = 0.0;
+  int refine_max = 0;
+  bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
+  bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
+  int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+
+  // x-step operators
+  double *U = nullptr, *Uinv = nullptr, *Q = nullptr;
+  // velocity operators
+  double *KC = nullptr, *KA = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
+  double *TO = nullptr, *TS = nullptr;
+  double *mom_n = nullptr, *mom_e = nullptr, *mom_r = nullptr;
+  // work
+  double *Y = nullptr, *Y2 = nullptr, *Fa = nullptr, *Fb = nullptr, *Fw = nullptr, *R = nullptr;
+  double *Fhost_dev = nullptr, *coef = nullptr, *ratio = nullptr;
+  void* fac = nullptr;
+  void* linv = nullptr;
+  void* uinv = nullptr;
+  void* tcws = nullptr;
+  int *piv = nullptr, *perm = nullptr, *conv = nullptr;
+  unsigned* status = nullptr;
+  unsigned* status_host = nullptr;  // pinned
+  std::vector<bte::Process> procs;  // the cross sections of the last bte_set_cross_sections
+  // transposed x-step operators for the adjoint (allocated on its first use)
+  double *Ut = nullptr, *Uinvt = nullptr, *Qt = nullptr;
+  int last_sweeps = 0;
+  double last_resid = 0.0;
+  unsigned last_flags = 0;
+  unsigned long long launches = 0;
+  // profiling: events around every launch while enabled
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+};
+

@@ -28,6 +28,7 @@ struct HostOps {
   double L = 0, vmax = 0, n0 = 0, T0 = 0, m0 = 0, dt = 0;
 
   std::vector<double> x, Dx;            // nx, nx*nx
+  std::vector<double> ccw;              // nx Clenshaw-Curtis weights on [0, L]
   std::vector<double> mu, wmu;          // nt Gauss-Legendre nodes (ascending) and weights
   std::vector<double> knots;            // nr + 4
   std::vector<double> M, G, Dv, M1;     // nr*nr radial Galerkin matrices
@@ -48,6 +49,8 @@ struct HostOps {
 std::string assemble_x(const bte_config& cfg, HostOps& ops);
 // Collision and field operators, their projections and the moment vectors.
 std::string assemble_v(HostOps& ops, const std::vector<Process>& procs);
+// K_C of a process list on the grids of o, o untouched (for the parameter derivatives).
+std::string assemble_kc_only(const HostOps& o, const std::vector<Process>& procs, std::vector<double>& KC);
 // Galerkin coefficients of a unit-density Maxwellian at temperature Te (eV).
 std::vector<double> maxwellian_coeffs(const HostOps& ops, double Te_eV);
 

@@ -63,6 +63,9 @@ void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_
 template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
                              double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st);
+// y = A^-T b with the FP64 factors and pivots of the FP64 path (the adjoint of lu_solve).
+void launch_lu_solve_t(const double* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
+                       cudaStream_t st);
 template <typename T>
 void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, int k0, int nb,
                          int nbmax, float* ws_hi, float* ws_lo, cudaStream_t st);

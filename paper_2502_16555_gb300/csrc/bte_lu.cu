@@ -572,6 +572,22 @@ __device__ __forceinline__ void vstore(T* p, const T* in) {
   *reinterpret_cast<V*>(p) = v;
 }
 
+// Elements of the product staging of tri_inverse_rd for an nb x nb block.
+__host__ __device__ inline int rd_tmp_elems(int nb) {
+  int m = 0;
+  for (int w = 16; w < nb; w *= 2) {
+    const int e = ((nb + 2 * w - 1) / (2 * w)) * w * w;
+    m = e > m ? e : m;
+  }
+  return m;
+}
+
+// Elements of the panel kernel's product staging area (after D and X).
+__host__ __device__ inline int lazy_tmp_elems(int nb) {
+  const int a = rd_tmp_elems(nb), b = 16 * (nb + 4);
+  return a > b ? a : b;
+}
+
 // Panel factorisation with pivots as marks (same contract as lu_panel_kernel, plus inv(U11); the
 // TF32 split of L21 is left to lu_swap_pack). One CTA of 1024 threads per point; thread t holds
 // physical panel rows t + 1024 q (q < RPT) of the current W-wide column block in registers. Rows do
@@ -666,7 +682,9 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
       }
       __syncthreads();
       // pivot rows of block t take their U values; rows below block t (unmarked, or marked by a
-      // later block) take the rank-W update, each U row chunk read once for all of a thread's rows
+      // later block) take the rank-W update, each U row chunk read once for all of a thread's rows.
+      // A row's L entries are fetched one 32-byte sector (two 16-byte vectors) at a time.
+      constexpr int KC = 32 / sizeof(T) < W ? 32 / sizeof(T) : W;
       bool upd[RPT];
       const T* lr[RPT];
 #pragma unroll
@@ -682,17 +700,20 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
       }
       if (active) {
 #pragma unroll
-        for (int kv = 0; kv < W; kv += VE) {
-          T l[RPT][VE];
+        for (int kv = 0; kv < W; kv += KC) {
+          T l[RPT][KC];
 #pragma unroll
           for (int q = 0; q < RPT; ++q) {
-            if (upd[q]) vload(lr[q] + kv, l[q]);
-            else
 #pragma unroll
-              for (int u = 0; u < VE; ++u) l[q][u] = T(0);
+            for (int c = 0; c < KC; c += VE) {
+              if (upd[q]) vload(lr[q] + kv + c, &l[q][c]);
+              else
+#pragma unroll
+                for (int u = 0; u < VE; ++u) l[q][c + u] = T(0);
+            }
           }
 #pragma unroll
-          for (int u = 0; u < VE; ++u) {
+          for (int u = 0; u < KC; ++u) {
 #pragma unroll
             for (int v = 0; v < W; v += VE) {
               T uu[VE];
@@ -917,19 +938,13 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
   }
 }
 
-// Elements of the product staging of tri_inverse_rd for an nb x nb block.
-__host__ __device__ inline int rd_tmp_elems(int nb) {
-  int m = 0;
-  for (int w = 16; w < nb; w *= 2) {
-    const int e = ((nb + 2 * w - 1) / (2 * w)) * w * w;
-    m = e > m ? e : m;
-  }
-  return m;
-}
 
+// Dynamic shared memory of the panel kernel: orig/pos/displaced lists, then D and X (nb x (nb+4)
+// each: the diagonal block and the inverse being built) and a product staging area (the
+// doubling inverse's, and 16 rows of X's extension).
 __host__ inline size_t panel_lazy_smem_bytes(int m0, int nb, int nbmax, size_t tsize) {
   const size_t ints = ((static_cast<size_t>(2 * m0 + 2 * nbmax) * sizeof(int) + 15) & ~size_t(15));
-  return ints + (2ull * nb * (nb + 4) + rd_tmp_elems(nb)) * tsize;
+  return ints + (2ull * nb * (nb + 4) + lazy_tmp_elems(nb)) * tsize;
 }
 
 
@@ -1264,42 +1279,150 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
   for (int r = tid; r < n; r += bd) xo[r] = accumulate ? xo[r] + static_cast<double>(s[r]) : static_cast<double>(s[r]);
 }
 
-// Sum of four per-lane partials over the warp in six shuffles (a transposing butterfly): lane 0
-// returns row 0's total, lane 8 row 1's, lane 16 row 2's, lane 24 row 3's.
-__device__ __forceinline__ float warp_sum4(float p0, float p1, float p2, float p3, int lane) {
-  const bool hi16 = lane & 16, hi8 = lane & 8;
-  float v0 = hi16 ? p2 : p0, v1 = hi16 ? p3 : p1;
-  const float w0 = hi16 ? p0 : p2, w1 = hi16 ? p1 : p3;
-  v0 += __shfl_xor_sync(0xffffffffu, w0, 16);
-  v1 += __shfl_xor_sync(0xffffffffu, w1, 16);
-  float u = hi8 ? v1 : v0;
-  const float x = hi8 ? v0 : v1;
-  u += __shfl_xor_sync(0xffffffffu, x, 8);
-  u += __shfl_xor_sync(0xffffffffu, u, 4);
+// y = A^-T c for one point per CTA, with the factors of the FP64 path (LAPACK-style pivots ip,
+// row swaps not applied left of each panel). The forward solve is x = U^-1 E_k ... E_0 c with
+// E_p = (per 32-column block: unit-lower block solve, then the update of all rows below) after the
+// panel's swaps; its transpose runs the other way: U^-T (per 32 block ascending: subtract the
+// column-block dots with the rows above, then the transposed triangular block), then per panel
+// descending and per 32 block descending: subtract the column-block dots with the rows below,
+// solve with the transposed unit-lower block, and finally undo the panel's swaps in reverse.
+__device__ void colblock_dots(const double* A, int n, int j0, int cw, int r0, int r1, const double* s,
+                              double (*red)[33], double* out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double acc = 0.0;
+  if (lane < cw)
+    for (int r = r0 + warp; r < r1; r += nw) acc += A[static_cast<size_t>(r) * n + j0 + lane] * s[r];
+  red[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nw; ++w) t += red[w][lane];
+    if (lane < cw) out[lane] = t;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) lu_solve_t_kernel(const double* __restrict__ fac, const int* __restrict__ piv,
+                                                          const double* __restrict__ b, double* __restrict__ x,
+                                                          int n, int nb) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* s = reinterpret_cast<double*>(smraw);
+  __shared__ double red[32][33];
+  __shared__ double dot[32];
+  __shared__ double dblk[32][33];
+  const int mat = blockIdx.x;
+  const double* A = fac + static_cast<size_t>(mat) * n * n;
+  const int* ip = piv + static_cast<size_t>(mat) * n;
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = tid; r < n; r += bd) s[r] = b[static_cast<size_t>(mat) * n + r];
+  __syncthreads();
+  // z = U^-T c
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int cw = min(32, n - j0);
+    if (j0 > 0) {
+      colblock_dots(A, n, j0, cw, 0, j0, s, red, dot);
+      for (int c = tid; c < cw; c += bd) s[j0 + c] -= dot[c];
+    }
+    for (int idx = tid; idx < cw * cw; idx += bd) {
+      const int r = idx / cw, c = idx % cw;
+      dblk[r][c] = A[static_cast<size_t>(j0 + r) * n + j0 + c];
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double v = lane < cw ? s[j0 + lane] : 0.0;
+      for (int c = 0; c < cw; ++c) {
+        if (lane == c) v /= dblk[c][c];
+        const double zc = __shfl_sync(0xffffffffu, v, c);
+        if (lane > c && lane < cw) v -= dblk[c][lane] * zc;
+      }
+      if (lane < cw) s[j0 + lane] = v;
+    }
+    __syncthreads();
+  }
+  // panels descending: L-blocks transposed, then the swaps undone
+  const int npan = (n + nb - 1) / nb;
+  for (int p = npan - 1; p >= 0; --p) {
+    const int k0 = p * nb, kb = min(nb, n - k0);
+    for (int j0 = k0 + ((kb - 1) / 32) * 32; j0 >= k0; j0 -= 32) {
+      const int cw = min(32, k0 + kb - j0);
+      if (j0 + cw < n) {
+        colblock_dots(A, n, j0, cw, j0 + cw, n, s, red, dot);
+        for (int c = tid; c < cw; c += bd) s[j0 + c] -= dot[c];
+      }
+      for (int idx = tid; idx < cw * cw; idx += bd) {
+        const int r = idx / cw, c = idx % cw;
+        dblk[r][c] = A[static_cast<size_t>(j0 + r) * n + j0 + c];
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double v = lane < cw ? s[j0 + lane] : 0.0;
+        for (int c = cw - 1; c >= 0; --c) {
+          const double zc = __shfl_sync(0xffffffffu, v, c);
+          if (lane < c) v -= dblk[c][lane] * zc;
+        }
+        if (lane < cw) s[j0 + lane] = v;
+      }
+      __syncthreads();
+    }
+    if (tid == 0)
+      for (int j = kb - 1; j >= 0; --j) {
+        const int q = ip[k0 + j];
+        if (q != k0 + j) {
+          const double t = s[k0 + j];
+          s[k0 + j] = s[q];
+          s[q] = t;
+        }
+      }
+    __syncthreads();
+  }
+  for (int r = tid; r < n; r += bd) x[static_cast<size_t>(mat) * n + r] = s[r];
+}
+
+
+// Sum of eight per-lane partials over the warp in nine shuffles (transposing butterfly): lane
+// 4 k returns row k's total (k = 0..7).
+__device__ __forceinline__ float warp_sum8(const float (&p)[8], int lane) {
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  float a[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = h16 ? p[4 + i] : p[i], send = h16 ? p[i] : p[4 + i];
+    a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float b2[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = h8 ? a[2 + i] : a[i], send = h8 ? a[i] : a[2 + i];
+    b2[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float keep = h4 ? b2[1] : b2[0], send = h4 ? b2[0] : b2[1];
+  float u = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   u += __shfl_xor_sync(0xffffffffu, u, 2);
   u += __shfl_xor_sync(0xffffffffu, u, 1);
   return u;
 }
 
 // out(r, dot(M[r, 0:128], v)) for rows r in [r0, r1) of a row-major FP32 matrix with leading
-// dimension ld (a multiple of 4, M 16-byte aligned): four rows per warp and pass, one 16-byte load
-// per lane and row, so that a CTA keeps 64 KB of loads in flight. v is in shared memory.
+// dimension ld (a multiple of 4, M 16-byte aligned): eight rows per warp and pass, one 16-byte
+// streaming load per lane and row, so that a CTA keeps 128 KB of loads in flight. v is in shared
+// memory. The total of row r0 + 8 pass + k sits in lane 4k (bits 4, 3, 2 of the lane = k).
 template <typename Out>
 __device__ __forceinline__ void rows_dot128(const float* __restrict__ M, size_t ld, int r0, int r1, const float* v,
                                             int warp, int nwarp, int lane, Out out) {
   const float4 vv = reinterpret_cast<const float4*>(v)[lane];
-  for (int r = r0 + 4 * warp; r < r1; r += 4 * nwarp) {
-    float p[4];
+  for (int r = r0 + 8 * warp; r < r1; r += 8 * nwarp) {
+    float p[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
       p[i] = 0.f;
       if (r + i < r1) {
         const float4 a = __ldcs(reinterpret_cast<const float4*>(M + static_cast<size_t>(r + i) * ld) + lane);
         p[i] = a.x * vv.x + a.y * vv.y + a.z * vv.z + a.w * vv.w;
       }
     }
-    const float t = warp_sum4(p[0], p[1], p[2], p[3], lane);
-    if ((lane & 7) == 0 && r + (lane >> 3) < r1) out(r + (lane >> 3), t);
+    const float t = warp_sum8(p, lane);
+    const int k = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && r + k < r1) out(r + k, t);
   }
 }
 
@@ -1529,6 +1652,17 @@ void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_
     attr_set = true;
   }
   lu_uinv_kernel<T><<<nx * npan, 256, smem, st>>>(fac, uinv, n, nbmax);
+}
+
+void launch_lu_solve_t(const double* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
+                       cudaStream_t st) {
+  const size_t smem = sizeof(double) * n;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lu_solve_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  lu_solve_t_kernel<<<nx, 1024, smem, st>>>(fac, piv, b, x, n, nb);
 }
 
 template <typename T>

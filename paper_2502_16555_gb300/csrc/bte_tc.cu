@@ -46,9 +46,16 @@ constexpr int STAGES = BTE_TC_STAGES;
 constexpr int BOX_BYTES = BM * BK * 4;            // 16 KB (BM == BN)
 constexpr int STAGE_BYTES = 4 * BOX_BYTES;        // A_hi, A_lo, B_hi, B_lo
 constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
-constexpr int CW = 32;                            // C chunk width (columns): one 128-byte swizzle row
+#ifndef BTE_TC_CW
+#define BTE_TC_CW 32
+#endif
+// C chunk width (columns): 32 = one 128-byte swizzle row, 16 = one 64-byte swizzle row
+constexpr int CW = BTE_TC_CW;
+static_assert(CW == 32 || CW == 16, "C chunk width");
+constexpr int CSWZ_MASK = CW == 32 ? 7 : 3;       // 16-byte chunk index ^= (row >> CSWZ_SHIFT) & mask
+constexpr int CSWZ_SHIFT = CW == 32 ? 0 : 1;
 constexpr int CSLOTS = BTE_TC_CSLOTS;             // C staging slots
-constexpr int CSLOT_BYTES = BM * CW * 4;          // 16 KB
+constexpr int CSLOT_BYTES = BM * CW * 4;          // 16 or 8 KB
 constexpr int NCCHUNK = BN / CW;
 constexpr int NTHREADS = 192;
 constexpr long long kWaitCycles = 1ll << 32;     // ~2 s at 2 GHz
@@ -170,6 +177,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
         "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
         "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -342,11 +358,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t v[32];
-        tmem_ld32(tmem + acc * BN + ch * CW + ((sub * 32) << 16), v);
+        if constexpr (CW == 32) tmem_ld32(tmem + acc * BN + ch * CW + ((sub * 32) << 16), v);
+        else tmem_ld16(tmem + acc * BN + ch * CW + ((sub * 32) << 16), v);
         float4* cs = reinterpret_cast<float4*>(s.cbuf[slot] + trow * (CW * 4));
 #pragma unroll
         for (int j = 0; j < CW / 4; ++j) {
-          float4* q = cs + (j ^ (trow & 7));  // 128-byte swizzle: 16-byte chunk index ^ (row % 8)
+          // TMA swizzle: 16-byte chunk index ^ row bits (128-byte rows: row % 8; 64-byte: (row / 2) % 4)
+          float4* q = cs + (j ^ ((trow >> CSWZ_SHIFT) & CSWZ_MASK));
           float4 x;
           if (load_c) {
             x = *q;
@@ -447,7 +465,7 @@ bool make_cmap(CUtensorMap* m, float* fac, int nx, int n) {
   cuuint32_t box[3] = {CW, BM, 1};
   cuuint32_t es[3] = {1, 1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fac, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CW == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
