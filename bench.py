@@ -38,10 +38,11 @@ TF32_OVER_BF16 = 1.1 / 2.25
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 peak: cuBLAS DGEMM (8192^3) measured on this machine's GB300 with `bench.py --peaks`.
 FP64_PEAK_TFLOPS = 1.10
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernels from
-# one ncu capture of the command in profiles/, scaled from the captured (largest) launch to the
-# average launch by the algorithmic bytes; None once the kernel has changed since the capture.
-TRAFFIC = {}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the first-panel launch (k0 = 0) of
+# the kernels captured with ncu on this workload (the commands are in profiles/); the per-launch
+# figure reported is scaled to the step's average launch by the algorithmic bytes. Remove an entry
+# when its kernel changes.
+TRAFFIC_K0 = {"lu_gemm": 2.391065e9 + 1.829609e9, "lu_panel": 402.5408e6 + 122.445056e6}
 
 
 def load_peaks():
@@ -145,12 +146,30 @@ def algorithmic(cfg, precision, kernel, tc):
     return None, None, None
 
 
-def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc):
+def traffic_per_launch(cfg, kernel, launches_per_step):
+    """Measured DRAM bytes of the k0 = 0 launch scaled to the average launch of the step (both
+    kernels move bytes in proportion to their algorithmic bytes, which shrink with k0)."""
+    if kernel not in TRAFFIC_K0 or not launches_per_step:
+        return None
+    nv = cfg["nr"] * cfg["ntheta"]
+    nb = 128
+    if kernel == "lu_gemm":
+        per = [(nv - k0 - nb) ** 2 for k0 in range(0, nv - nb, nb)]
+    else:
+        per = [nv - k0 for k0 in range(0, nv, nb)]
+    return TRAFFIC_K0[kernel] * (sum(per) / len(per)) / per[0]
+
+
+def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc, sweeps=None):
     amount, unit, bound = algorithmic(cfg, precision, kernel, tc)
     ms, launches = prof.get(kernel, (0.0, 0))
     if amount is None or launches == 0 or ms <= 0:
         return None
-    total = amount * (launches if unit.endswith("/launch") else steps)
+    eff = launches
+    if unit.endswith("/launch") and sweeps is not None:
+        # refinement launches after a point converged return at once: count the ones that worked
+        eff = steps * (1 + sweeps)
+    total = amount * (eff if unit.endswith("/launch") else steps)
     rate = total / (ms / 1e3)
     if bound == "hbm":
         achieved, peak, u = rate / 1e9, peaks["hbm_gbs"], "GB/s"
@@ -165,14 +184,15 @@ def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc):
         achieved, peak, u = rate / 1e12, FP32_SIMT_PEAK_TFLOPS, "TFLOP/s"
         src = "FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
     return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
-            "frac": achieved / peak, "traffic": TRAFFIC.get(kernel), "launches_per_step": launches / steps,
+            "frac": achieved / peak, "traffic": traffic_per_launch(cfg, kernel, launches / steps),
+            "launches_per_step": launches / steps, "working_launches_per_step": eff / steps,
             "ms_per_step": ms / steps, "peak_source": src}
 
 
-def rooflines(cfg, precision, prof, steps, peaks, tc):
+def rooflines(cfg, precision, prof, steps, peaks, tc, sweeps=None):
     out = {}
     for k in prof:
-        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc)
+        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc, sweeps)
         if r:
             out[k] = r
     dom = max(out, key=lambda k: out[k]["ms_per_step"])
@@ -267,6 +287,7 @@ def run_ours(args, rank, world):
         barrier()
         prof = s.profile_stop()
     launches = s.info()["launches"] - launches0
+    sweeps = s.info()["last_refine_sweeps"]
     ms = ev0.elapsed_time(ev1) / args.steps
     # the same timing again without event bracketing of every kernel
     s.run(F, 1, (args.warmup + args.steps) * dt)
@@ -307,6 +328,33 @@ def run_ours(args, rank, world):
                                            "rel_l2_ne": float(torch.linalg.norm(ne_m - ne_d) / torch.linalg.norm(ne_d))}}
         del s64
 
+    # ---- the structure-exploiting velocity solve (block tridiagonal in l), both precisions, from the
+    # same state for the same steps; accuracy against the dense FP64 state after the same steps
+    structured = None
+    if not args.no_structured:
+        structured = {}
+        n_chk = args.warmup + args.steps
+        for prec in ("mixed", "fp64"):
+            ss = bte.Solver(cfg, precision=prec, structured=True)
+            Gs = F0.clone()
+            ss.run(Gs, args.warmup, 0.0)
+            barrier()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record()
+            ss.run(Gs, args.steps, args.warmup * dt)
+            g1.record()
+            barrier()
+            mss = g0.elapsed_time(g1) / args.steps
+            entry = {"value": world * dof / (mss / 1e3), "ms_per_step": mss, "unit": UNIT,
+                     "refine_sweeps": ss.info()["last_refine_sweeps"]}
+            if fp64 is not None:
+                ne_s, _, _ = ss.moments(Gs)
+                entry["rel_l2_f_vs_dense_fp64"] = float(torch.linalg.norm(Gs - G) / torch.linalg.norm(G))
+                entry["rel_l2_ne_vs_dense_fp64"] = float(torch.linalg.norm(ne_s - ne_d) / torch.linalg.norm(ne_d))
+                entry["steps_compared"] = n_chk
+            structured[prec] = entry
+            del ss
+
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -322,7 +370,7 @@ def run_ours(args, rank, world):
         e2e = {"value": world * dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * dof,
                "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"}
 
-    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc)
+    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc, sweeps=sweeps)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -338,6 +386,7 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world}"},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
+        "structured_solve": structured,
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -519,6 +568,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-structured", action="store_true", help="skip the block-tridiagonal solve legs")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64_uneven", "adjoint_nx64_nr32_nt16"],
                     help="the headline single discharge (default), the 64 uneven discharges in one graph, "

@@ -54,6 +54,12 @@ typedef enum {
                                    bte_get_operator works, device entry points return BTE_ESTATE */
 #define BTE_FLAG_SIMT_GEMM 2u   /* BTE_MIXED: do the trailing updates of the factorisation on the CUDA
                                    cores (FP32) instead of the tcgen05 tensor cores (TF32x3) */
+#define BTE_FLAG_STRUCTURED 4u  /* solve the velocity step through its block-tridiagonal structure in l
+                                   (A^-1 f = f + P_O((I - dt B)^-1 - I) P_S f, B = C + E A_v, Section 3.3)
+                                   instead of the dense per-point LU: the same solution with about
+                                   Nv^3 / (5 N_l Nr^3) fewer flops and no dense factors in memory. The
+                                   block elimination runs in FP64 (BTE_FP64) or FP32 with the FP64
+                                   refinement (BTE_MIXED). Requires nr <= 64. */
 
 typedef struct {
   int nx;            /* Chebyshev-Gauss-Lobatto points, >= 3 */
@@ -102,7 +108,8 @@ typedef struct {
   double n0_m3;           /* neutral density */
   double vmax_ms;         /* largest speed [m/s] */
   size_t device_bytes;    /* device memory held by the handle */
-  int last_refine_sweeps; /* sweeps run by the last completed bte_step (needs a synchronised stream) */
+  int last_refine_sweeps; /* correction sweeps per point and step of the last bte_step / bte_run, averaged
+                             over points and steps and rounded up (counted on the device) */
   double last_residual;   /* max over points of max|r|/max|b| after the last step */
   unsigned last_flags;    /* device status bits of the last step (1 zero pivot, 2 non-finite,
                              4 not converged) */

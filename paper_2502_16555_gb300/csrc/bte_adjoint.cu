@@ -110,6 +110,7 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
   if (!F_dev || !lambda_dev) return afail(h, BTE_EINVAL, "F_dev and lambda_dev are required");
   if (h->host_only || !h->ops.have_v) return afail(h, BTE_ESTATE, "needs device buffers and cross sections");
   if (h->precision != BTE_FP64) return afail(h, BTE_ESTATE, "the adjoint is implemented for FP64 handles");
+  if (h->structured) return afail(h, BTE_ESTATE, "the adjoint needs the dense factorisation (no BTE_FLAG_STRUCTURED)");
   bte_status s = ensure_transposed(h);
   if (s != BTE_OK) return s;
   const bte::HostOps& o = h->ops;
@@ -120,7 +121,7 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
   const double Eu = V0 / o.L * std::sin(arg);
   double* fac = static_cast<double*>(h->fac);
   unsigned long long nl = 0;
-  BA_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+  BA_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), st));
   // forward pieces of step n: G = X F^n (Fa), the factors of A_i, F* = A^-1 G (Fb)
   bte::launch_x_to_eigen(F_dev, h->Uinv, h->Y, nx, nt, nr, h->status, st);
   bte::launch_x_apply_q(h->Q, h->Y, h->Y2, nx, nt, nr, st);

@@ -113,7 +113,16 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   BTE_LAUNCH(BTE_K_X_FROM_EIGEN, bte::launch_x_from_eigen(h->Y2, h->U, h->Fa, nx, nt, nr, nullptr, st));
   // velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system")
   const int n = nv, nb = h->nb;
-  if (h->precision == BTE_FP64) {
+  if (h->structured) {
+    if (h->precision == BTE_FP64)
+      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->Fa, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                   h->TO, h->TS, static_cast<double*>(h->xs), nx, nt,
+                                                                   nr, nl, nullptr, 0, h->status, st));
+    else
+      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<float>(h->Fa, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                  h->TO, h->TS, static_cast<float*>(h->xs), nx, nt,
+                                                                  nr, nl, nullptr, 0, h->status, st));
+  } else if (h->precision == BTE_FP64) {
     double* fac = static_cast<double*>(h->fac);
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
     for (int k0 = 0; k0 < n; k0 += nb) {
@@ -169,9 +178,17 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     for (int s = 0; s <= h->refine_max; ++s) {
       BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
                                                       h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, nx,
-                                                      nt, nr, nl, st));
+                                                      nt, nr, nl, h->status, st));
       if (s == h->refine_max) break;
-      if (h->precision == BTE_FP64)
+      if (h->structured && h->precision == BTE_FP64)
+        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->R, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                     h->TO, h->TS, static_cast<double*>(h->xs), nx,
+                                                                     nt, nr, nl, h->conv, 1, nullptr, st));
+      else if (h->structured)
+        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<float>(h->R, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                    h->TO, h->TS, static_cast<float*>(h->xs), nx, nt,
+                                                                    nr, nl, h->conv, 1, nullptr, st));
+      else if (h->precision == BTE_FP64)
         BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(static_cast<double*>(h->fac), h->piv, h->R, h->Fb, nx, n, nb, h->conv, 1, st));
       else
         BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(
@@ -189,11 +206,20 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   return BTE_OK;
 }
 
-bte_status read_status(bte_handle* h) {
-  BTE_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+bte_status read_status(bte_handle* h, int steps = 1) {
+  BTE_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
   BTE_CUDA(h, cudaStreamSynchronize(h->st));
-  const unsigned f = *h->status_host;
+  const unsigned f = h->status_host[0];
   h->last_flags = f;
+  // status word 1 counts the residual evaluations of all points and steps since the reset: per
+  // point and step one more than the correction sweeps
+  if (h->refine_max > 0 && steps > 0) {
+    const double per = static_cast<double>(h->status_host[1]) / (static_cast<double>(h->ops.nx) * steps);
+    h->last_sweeps = static_cast<int>(std::ceil(per - 1.0 - 1e-9));
+    if (h->last_sweeps < 0) h->last_sweeps = 0;
+  } else {
+    h->last_sweeps = 0;
+  }
   if (h->refine_max > 0) {
     std::vector<double> r(h->ops.nx);
     std::vector<int> c(h->ops.nx);
@@ -238,7 +264,7 @@ bte_status handle_enqueue_step(bte_handle* h, double* F_dev, const double* E_dev
   return s;
 }
 bte_status handle_reset_status(bte_handle* h, cudaStream_t st) {
-  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), st));
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), st));
   return BTE_OK;
 }
 bte_status handle_read_status(bte_handle* h) { return read_status(h); }
@@ -275,6 +301,15 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   h->st = static_cast<cudaStream_t>(cfg->stream);
   h->precision = cfg->precision;
   h->nb = cfg->precision == BTE_FP64 ? 64 : 128;
+  h->structured = (cfg->flags & BTE_FLAG_STRUCTURED) != 0;
+  if (h->structured) {
+    const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
+    const size_t ts = cfg->precision == BTE_FP64 ? 8 : 4;
+    if (cfg->nr > 64 || bte::struct_smem_bytes(cfg->nr, nl, ts) > 200 * 1024) {
+      delete h;
+      return fail(nullptr, BTE_EINVAL, "BTE_FLAG_STRUCTURED needs nr <= 64");
+    }
+  }
   h->tol = cfg->refine_tol > 0 ? cfg->refine_tol : (cfg->precision == BTE_FP64 ? 1e-13 : 1e-12);
   h->refine_max = cfg->refine_max >= 0 ? cfg->refine_max : (cfg->precision == BTE_FP64 ? 0 : 4);
   std::string e = bte::assemble_x(*cfg, h->ops);
@@ -301,8 +336,19 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
               chk(dalloc(h, &h->ratio, o.nx)) && chk(dalloc(h, &h->piv, D)) &&
               chk(dalloc(h, &h->perm, static_cast<size_t>(o.nx) * ((o.nv + h->nb - 1) / h->nb) *
                                           bte::perm_record_ints(h->nb))) &&
-              chk(dalloc(h, &h->conv, o.nx)) && chk(dalloc(h, &h->status, 1));
-    if (ok) {
+              chk(dalloc(h, &h->conv, o.nx)) && chk(dalloc(h, &h->status, 2));
+    if (ok && h->structured) {
+      const size_t xsz = static_cast<size_t>(o.nx) * o.nl * o.nr * o.nr;
+      if (h->precision == BTE_FP64) {
+        double* x = nullptr;
+        ok = chk(dalloc(h, &x, xsz));
+        h->xs = x;
+      } else {
+        float* x = nullptr;
+        ok = chk(dalloc(h, &x, xsz));
+        h->xs = x;
+      }
+    } else if (ok) {
       const size_t npan = (o.nv + h->nb - 1) / h->nb;
       const size_t blk = static_cast<size_t>(o.nx) * npan * h->nb * h->nb;
       if (h->precision == BTE_FP64) {
@@ -327,13 +373,13 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
       }
     }
     if (ok) {
-      cudaError_t ce = cudaMallocHost(reinterpret_cast<void**>(&h->status_host), sizeof(unsigned));
+      cudaError_t ce = cudaMallocHost(reinterpret_cast<void**>(&h->status_host), 2 * sizeof(unsigned));
       if (ce != cudaSuccess) ok = false, s = cuda_fail(h, ce, "cudaMallocHost");
     }
     if (ok) ok = chk(upload(h, h->U, o.U)) && chk(upload(h, h->Uinv, o.Uinv)) && chk(upload(h, h->Q, o.Q)) &&
                  chk(upload(h, h->TO, o.TO)) && chk(upload(h, h->TS, o.TS));
     if (ok) {
-      cudaError_t ce = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
+      cudaError_t ce = cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
       if (ce != cudaSuccess) ok = false, s = cuda_fail(h, ce, "initialising device buffers");
     }
@@ -414,10 +460,9 @@ bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev) return fail(h, BTE_EINVAL, "F_dev is NULL");
   if (!device_ready(h)) return BTE_ESTATE;
-  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
   bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t_s, V0, freq_Hz);
   if (s != BTE_OK) return s;
-  h->last_sweeps = h->refine_max;
   return read_status(h);
 }
 
@@ -425,13 +470,12 @@ bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || n_steps < 0) return fail(h, BTE_EINVAL, "bad arguments");
   if (!device_ready(h)) return BTE_ESTATE;
-  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
   for (int i = 0; i < n_steps; ++i) {
     bte_status s = enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * h->ops.dt, V0, freq_Hz);
     if (s != BTE_OK) return s;
   }
-  h->last_sweeps = h->refine_max;
-  return read_status(h);
+  return read_status(h, n_steps);
 }
 
 bte_status bte_step_host(bte_handle* h, double* F_host, double t_s, double V0, double freq_Hz) {
@@ -440,7 +484,7 @@ bte_status bte_step_host(bte_handle* h, double* F_host, double t_s, double V0, d
   if (!device_ready(h)) return BTE_ESTATE;
   const size_t bytes = sizeof(double) * h->ops.nx * h->ops.nv;
   BTE_CUDA(h, cudaMemcpyAsync(h->Fhost_dev, F_host, bytes, cudaMemcpyHostToDevice, h->st));
-  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st));
+  BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
   bte_status s = enqueue_step(h, h->Fhost_dev, h->Fhost_dev, nullptr, t_s, V0, freq_Hz);
   if (s != BTE_OK) return s;
   BTE_CUDA(h, cudaMemcpyAsync(F_host, h->Fhost_dev, bytes, cudaMemcpyDeviceToHost, h->st));

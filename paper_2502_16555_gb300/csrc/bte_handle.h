@@ -19,6 +19,8 @@ struct bte_handle {
   int nb = 64;            // outer LU panel width
   double tol = 0.0;
   int refine_max = 0;
+  bool structured = false;  // block-tridiagonal velocity solve instead of the dense LU
+  void* xs = nullptr;       // its per-point scratch (nx * nl * nr * nr values)
   bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
   bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
   int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)

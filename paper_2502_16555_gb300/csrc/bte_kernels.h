@@ -63,6 +63,16 @@ void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_
 template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
                              double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st);
+// ---- structure-exploiting velocity solve (block tridiagonal in l): Fout = A_i^-1 Fin per point
+// (Fout += when accumulate); T is the arithmetic of the block elimination; Xscratch holds
+// nx * nl * nr * nr values of T.
+size_t struct_smem_bytes(int nr, int nl, size_t tsize);
+template <typename T>
+void launch_vsolve_struct(const double* Fin, double* Fout, const double* E, double E_uniform, double dt,
+                          const double* Cs, const double* Alo, const double* Aup, const double* TO, const double* TS,
+                          T* Xscratch, int nx, int nt, int nr, int nl, const int* conv, int accumulate,
+                          unsigned* status, cudaStream_t st);
+
 // y = A^-T b with the FP64 factors and pivots of the FP64 path (the adjoint of lu_solve).
 void launch_lu_solve_t(const double* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
                        cudaStream_t st);
@@ -82,7 +92,7 @@ void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, i
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
                      const double* Cs, const double* Alo, const double* Aup, const double* TO,
                      const double* TS, double* r, double* ratio, int* conv, double tol, int nx,
-                     int nt, int nr, int nl, cudaStream_t st);
+                     int nt, int nr, int nl, unsigned* status, cudaStream_t st);
 void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st);
 
 // ---- misc

@@ -34,7 +34,11 @@
 namespace bte {
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 32, KTOT = 128, NCHUNK = KTOT / BK;
+#ifndef BTE_TC_BN
+#define BTE_TC_BN 128
+#endif
+constexpr int BM = 128, BN = BTE_TC_BN, BK = 32, KTOT = 128, NCHUNK = KTOT / BK;
+static_assert(BN == 128 || BN == 256, "tile width");
 // Operand stages and C staging slots share the 227 KB of shared memory (64 KB and 16 KB each).
 #ifndef BTE_TC_STAGES
 #define BTE_TC_STAGES 2
@@ -43,8 +47,9 @@ constexpr int BM = 128, BN = 128, BK = 32, KTOT = 128, NCHUNK = KTOT / BK;
 #define BTE_TC_CSLOTS 4
 #endif
 constexpr int STAGES = BTE_TC_STAGES;
-constexpr int BOX_BYTES = BM * BK * 4;            // 16 KB (BM == BN)
-constexpr int STAGE_BYTES = 4 * BOX_BYTES;        // A_hi, A_lo, B_hi, B_lo
+constexpr int A_BOX = BM * BK * 4;                // 16 KB
+constexpr int B_BOX = BN * BK * 4;                // 16 or 32 KB
+constexpr int STAGE_BYTES = 2 * A_BOX + 2 * B_BOX;  // A_hi, A_lo, B_hi, B_lo
 constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
 #ifndef BTE_TC_CW
 #define BTE_TC_CW 32
@@ -248,9 +253,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           mbar_expect_tx(&s.full[st], STAGE_BYTES);
           unsigned char* d = s.stage[st];
           tma_load(d, &mAhi, c * BK, ya, &s.full[st]);
-          tma_load(d + BOX_BYTES, &mAlo, c * BK, ya, &s.full[st]);
-          tma_load(d + 2 * BOX_BYTES, &mBhi, c * BK, yb, &s.full[st]);
-          tma_load(d + 3 * BOX_BYTES, &mBlo, c * BK, yb, &s.full[st]);
+          tma_load(d + A_BOX, &mAlo, c * BK, ya, &s.full[st]);
+          tma_load(d + 2 * A_BOX, &mBhi, c * BK, yb, &s.full[st]);
+          tma_load(d + 2 * A_BOX + B_BOX, &mBlo, c * BK, yb, &s.full[st]);
           s.issued += 1;
           if (++st == STAGES) st = 0, ph ^= 1u;
         }
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ++consumed;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = saddr(s.stage[st]);
-          const uint32_t a1 = a0 + BOX_BYTES, b0 = a0 + 2 * BOX_BYTES, b1 = a0 + 3 * BOX_BYTES;
+          const uint32_t a1 = a0 + A_BOX, b0 = a0 + 2 * A_BOX, b1 = b0 + B_BOX;
 #pragma unroll
           for (int k = 0; k < BK / 8; ++k) {
             const uint32_t off = k * 32;  // 8 tf32 = 32 bytes inside the 128-byte swizzle row
@@ -443,12 +448,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, float* base, size_t rows) {
+bool make_map(CUtensorMap* m, float* base, size_t rows, int box_rows) {
   auto enc = get_encode();
   if (!enc) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(KTOT), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(KTOT) * 4};
-  cuuint32_t box[2] = {BK, BM};
+  cuuint32_t box[2] = {BK, static_cast<cuuint32_t>(box_rows)};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -482,10 +487,11 @@ Maps& maps_for(float* fac, void* ws, int nx, int n) {
   if (!maps.ok || maps.ws != ws || maps.fac != fac || maps.nx != nx || maps.n != n) {
     const size_t rows = static_cast<size_t>(nx) * (n - KTOT);
     maps.ok = true;
+    // A operands (L21 split, inv(L11) split) in boxes of BM rows, B operands in boxes of BN rows
     for (int part = 0; part < 4; ++part)
-      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), rows);
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), rows, part < 2 ? BM : BN);
     for (int part = 4; part < 6; ++part)
-      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KTOT);
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KTOT, BM);
     maps.ok = maps.ok && make_cmap(&maps.m[6], fac, nx, n);
     maps.ws = ws;
     maps.fac = fac;
@@ -551,7 +557,8 @@ void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* s
   a.col0 = base;
   a.M = M;
   a.N = M;
-  a.tiles_m = a.tiles_n = (M + BM - 1) / BM;
+  a.tiles_m = (M + BM - 1) / BM;
+  a.tiles_n = (M + BN - 1) / BN;
   a.total = nx * a.tiles_m * a.tiles_n;
   a.rows_a = a.rows_b = n - KTOT;
   a.mode = 0;

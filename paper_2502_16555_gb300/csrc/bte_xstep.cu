@@ -108,7 +108,7 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
                                 const double* __restrict__ Aup, const double* __restrict__ TO,
                                 const double* __restrict__ TS, double* __restrict__ R,
                                 double* __restrict__ ratio, int* __restrict__ conv, double tol,
-                                int nt, int nr, int nl) {
+                                int nt, int nr, int nl, unsigned* __restrict__ status) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
   // a point that has converged keeps its iterate (the solves skip it), so its residual is final
@@ -164,6 +164,7 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
     const double q = mb > 0.0 ? mr / mb : (mr > 0.0 ? INFINITY : 0.0);
     ratio[i] = q;
     conv[i] = (q <= tol) ? 1 : 0;
+    atomicAdd(status + 1, 1u);  // residual evaluations (refinement accounting)
   }
 }
 
@@ -267,7 +268,7 @@ template void launch_v_form<float>(const double*, const double*, const double*, 
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
                      const double* Cs, const double* Alo, const double* Aup, const double* TO,
                      const double* TS, double* r, double* ratio, int* conv, double tol, int nx,
-                     int nt, int nr, int nl, cudaStream_t st) {
+                     int nt, int nr, int nl, unsigned* status, cudaStream_t st) {
   const size_t smem = sizeof(double) * (static_cast<size_t>(nt) * nr + 2 * nl * nr);
   static bool attr_set = false;
   if (!attr_set) {
@@ -275,7 +276,7 @@ void launch_residual(const double* x, const double* b, const double* E, double E
     attr_set = true;
   }
   residual_kernel<<<nx, 256, smem, st>>>(x, b, E, E_uniform, dt, Cs, Alo, Aup, TO, TS, r, ratio,
-                                         conv, tol, nt, nr, nl);
+                                         conv, tol, nt, nr, nl, status);
 }
 
 void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st) {

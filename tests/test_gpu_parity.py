@@ -207,3 +207,50 @@ def test_moments_of_maxwellian_match_oracle():
     assert np.allclose(mean.cpu().numpy()[inner], mean_r[inner], rtol=1e-12)
     assert np.allclose(rates.cpu().numpy()[:, inner], rates_r[:, inner], rtol=1e-11)
     assert np.all(mean.cpu().numpy()[~inner] == 0)
+
+
+# ------------------------------------------------------------------ structure-exploiting v-solve
+
+@pytest.mark.parametrize("name", ["small", "nl_lt_ntheta", "odd_ntheta", "tiny", "ragged"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_structured_solve_one_step(name, precision):
+    """BTE_FLAG_STRUCTURED (block-tridiagonal elimination in l) gives the same step as the oracle."""
+    cfg = dict(CASES[name])
+    cfg["V0"] = 300.0
+    ops = O.Operators(cfg)
+    F0 = W.random_state(ops.nx, ops.nt, ops.nr, seed=17)
+    t = 0.23 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t)
+    s = solver(cfg, precision, structured=True)
+    F = to_dev(F0)
+    s.step(F, t)
+    assert rel_l2(F.cpu().numpy(), ref) <= (1e-10 if precision == "fp64" else 1e-9)
+
+
+def test_structured_small_workload_full_run_and_medium_step():
+    cfg = W.SMALL
+    F_ref, _, ops = O.run(cfg)
+    s = solver(cfg, "fp64", structured=True)
+    F = s.initial_state()
+    s.run(F, cfg["steps"], 0.0)
+    assert rel_l2(F.cpu().numpy(), F_ref) <= 1e-10
+    cfg = W.MEDIUM
+    ops = O.Operators(cfg)
+    F0 = ops.initial_state()
+    t = 0.25 / W.RF_FREQ_HZ - 0.5 * cfg["dt_s"]
+    ref = ops.step(F0, t)
+    for precision in ("fp64", "mixed"):
+        s = solver(cfg, precision, structured=True)
+        F = to_dev(F0)
+        s.step(F, t)
+        assert rel_l2(F.cpu().numpy(), ref) <= (1e-10 if precision == "fp64" else 1e-9), precision
+
+
+def test_structured_matches_dense_path_on_field_array():
+    cfg = W.scaled(W.SMALL, nx=12, nr=16, ntheta=8)
+    F0 = W.random_state(12, 8, 16, seed=19)
+    E = to_dev(W.random_field(12, seed=5, e0=8e3))
+    a, b = to_dev(F0), to_dev(F0)
+    solver(cfg, "fp64").step(a, 0.0, E=E)
+    solver(cfg, "fp64", structured=True).step(b, 0.0, E=E)
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) <= 1e-11

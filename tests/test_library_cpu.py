@@ -130,3 +130,19 @@ def test_batch_create_validates_before_any_device_work():
     assert lib.bte_batch_create(2, same, None, 0, C.byref(out)) in (bte.EINVAL, bte.ESTATE)
     assert not out.value
     assert lib.bte_batch_destroy(None) == bte.OK
+
+
+def test_structured_flag_validates_nr_without_device_work():
+    import ctypes as C
+    from paper_2502_16555_gb300 import bte
+    lib = bte.load()
+    c = bte.Config()
+    cfg = W.scaled(W.SMALL, nx=5, nr=80, ntheta=4)
+    c.nx, c.nr, c.ntheta, c.nl = cfg["nx"], cfg["nr"], cfg["ntheta"], 0
+    c.L_m, c.vmax_eV, c.p_Torr = cfg["L_m"], cfg["vmax_eV"], cfg["p_Torr"]
+    c.T0_K, c.m0_amu, c.dt_s = cfg["T0_K"], cfg["m0_amu"], cfg["dt_s"]
+    c.precision, c.refine_tol, c.refine_max, c.stream = bte.FP64, 0.0, -1, None
+    c.flags = bte.FLAG_STRUCTURED
+    h = C.c_void_p()
+    assert lib.bte_create(C.byref(c), C.byref(h)) == bte.EINVAL
+    assert b"nr <= 64" in lib.bte_last_error(None)
