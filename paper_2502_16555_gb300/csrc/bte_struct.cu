@@ -10,9 +10,12 @@
 // (in-block growth 1.0 and pivots >= 0.2 on the workloads' field range), and the FP64 refinement
 // that follows (Algorithm 2 residual) removes what rounding leaves.
 //
-// One CTA of 256 threads per point; four Nr x Nr tiles in shared memory (S^-1, the previous
-// X = S^-1 U, the current X, a coupling block), the right-hand sides and intermediate vectors;
-// the X_q of the forward sweep go to a per-point global scratch for the back substitution.
+// One CTA of 256 threads per point, a 16 x 16 thread grid over the Nr x Nr blocks (Nr <= 64):
+// thread (ty, tx) owns the elements (ty + 16 a, tx + 16 b), a, b < 4, of the block being inverted and
+// keeps them in registers for the whole Gauss-Jordan sweep; only the pivot row and column go
+// through shared memory. Inverses are stored transposed, couplings transposed where they are the
+// left factor, so every shared-memory read is a broadcast or conflict-free. The X_q of the
+// forward sweep go to a per-point global scratch for the back substitution.
 #include <cuda_runtime.h>
 
 #include "bte_kernels.h"
@@ -21,77 +24,79 @@ namespace bte {
 namespace {
 
 constexpr int kST = 256;  // threads per CTA
+constexpr int kG = 4;     // elements per thread and dimension (Nr <= 16 kG)
 
-// C = alpha * A B (+ C if accumulate) for n x n row-major tiles in shared memory (ld = n), 4 x 4
-// register tiles over the 256 threads (edges masked).
-template <typename T, typename TA>
-__device__ void tile_gemm(const TA* A, const T* B, T* C, int n, T alpha, bool accumulate) {
-  const int tn = (n + 3) / 4;
-  for (int tt = threadIdx.x; tt < tn * tn; tt += kST) {
-    const int ti = tt / tn, tj = tt % tn;
-    T acc[4][4] = {};
-    for (int k = 0; k < n; ++k) {
-      T a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = 4 * ti + r < n ? static_cast<T>(A[(4 * ti + r) * n + k]) : T(0);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = 4 * tj + c < n ? B[k * n + 4 * tj + c] : T(0);
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (4 * ti + r < n && 4 * tj + c < n) {
-          T& o = C[(4 * ti + r) * n + 4 * tj + c];
-          o = accumulate ? o + alpha * acc[r][c] : alpha * acc[r][c];
-        }
-      }
-  }
-}
-
-// In-place inverse of the n x n tile S by Gauss-Jordan elimination without pivoting. The threads
-// form a 16 x 16 grid over the tile (element (i, j) belongs to thread (i % 16, j % 16)). Per step k
-// every element reads the pivot row and column of step k from a copy (double-buffered by step
-// parity), and the threads owning row k + 1 and column k + 1 write those copies for the next
-// step as they update them, so one barrier per step suffices.
+// acc(a, b) += sum_k AT[k][ty + 16 a] B[k][tx + 16 b] over k < n: AT is the left factor stored
+// transposed (AT[k][i] = A[i][k]), both n x n with leading dimension n in shared memory.
 template <typename T>
-__device__ void gauss_jordan_inverse(T* S, int n, T* prow2, T* pcol2) {
+__device__ __forceinline__ void grid_gemm(const T* AT, const T* B, int n, T (&acc)[kG][kG]) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-  for (int j = threadIdx.x; j < n; j += kST) prow2[j] = S[j], pcol2[j] = S[j * n];
-  __syncthreads();
   for (int k = 0; k < n; ++k) {
-    const T* prow = prow2 + (k & 1) * n;
-    const T* pcol = pcol2 + (k & 1) * n;
-    T* nrow = prow2 + ((k + 1) & 1) * n;
-    T* ncol = pcol2 + ((k + 1) & 1) * n;
-    const T p = T(1) / prow[k];
-    for (int i = ty; i < n; i += 16) {
-      const T fi = pcol[i] * p;
-      for (int j = tx; j < n; j += 16) {
-        T v;
-        if (i == k) v = (j == k) ? p : prow[j] * p;
-        else if (j == k) v = -fi;
-        else v = S[i * n + j] - fi * prow[j];
-        S[i * n + j] = v;
-        if (i == k + 1) nrow[j] = v;
-        if (j == k + 1) ncol[i] = v;
-      }
+    T a[kG], b[kG];
+#pragma unroll
+    for (int u = 0; u < kG; ++u) {
+      a[u] = ty + 16 * u < n ? AT[k * n + ty + 16 * u] : T(0);
+      b[u] = tx + 16 * u < n ? B[k * n + tx + 16 * u] : T(0);
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kG; ++u)
+#pragma unroll
+      for (int v = 0; v < kG; ++v) acc[u][v] += a[u] * b[v];
   }
 }
 
-// y[w] (+)= alpha * sum_k M[w][k] x[k], n x n tile M, one warp-stride thread per output row.
+// out[i] = alpha * sum_k MT[k][i] x[k] for i < n (MT the matrix stored transposed): thread i,
+// consecutive threads read consecutive addresses.
 template <typename T>
-__device__ void tile_gemv(const T* M, const T* x, T* y, int n, T alpha, bool accumulate) {
+__device__ __forceinline__ void gemv_t(const T* MT, const T* x, T* out, int n, T alpha) {
   for (int i = threadIdx.x; i < n; i += kST) {
     T acc = T(0);
-    for (int k = 0; k < n; ++k) acc += M[i * n + k] * x[k];
-    y[i] = accumulate ? y[i] + alpha * acc : alpha * acc;
+    for (int k = 0; k < n; ++k) acc += MT[k * n + i] * x[k];
+    out[i] = alpha * acc;
+  }
+}
+
+// In-place inverse of the block held in registers (s[a][b] = S[ty + 16 a][tx + 16 b]) by
+// Gauss-Jordan elimination without pivoting. Step k reads the pivot row and column from a copy
+// written in step k - 1 by the owners of row/column k (double-buffered by parity): one barrier
+// per step.
+template <typename T>
+__device__ void grid_gauss_jordan(T (&s)[kG][kG], int n, T* prow2, T* pcol2) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < kG; ++a)
+#pragma unroll
+    for (int b = 0; b < kG; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i == 0 && j < n) prow2[j] = s[a][b];
+      if (j == 0 && i < n) pcol2[i] = s[a][b];
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const T* prow = prow2 + (k & 1) * 64;
+    const T* pcol = pcol2 + (k & 1) * 64;
+    T* nrow = prow2 + ((k + 1) & 1) * 64;
+    T* ncol = pcol2 + ((k + 1) & 1) * 64;
+    const T p = T(1) / prow[k];
+    T pr[kG], fc[kG];
+#pragma unroll
+    for (int u = 0; u < kG; ++u) {
+      pr[u] = tx + 16 * u < n ? prow[tx + 16 * u] : T(0);
+      fc[u] = ty + 16 * u < n ? pcol[ty + 16 * u] * p : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < kG; ++a)
+#pragma unroll
+      for (int b = 0; b < kG; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        T v = s[a][b] - fc[a] * pr[b];
+        if (i == k) v = pr[b] * p;
+        if (j == k) v = (i == k) ? p : -fc[a];
+        s[a][b] = v;
+        if (i == k + 1 && j < n) nrow[j] = v;
+        if (j == k + 1 && i < n) ncol[i] = v;
+      }
+    __syncthreads();
   }
 }
 
@@ -104,21 +109,22 @@ __global__ void __launch_bounds__(kST) vsolve_struct_kernel(const double* __rest
                                                             int nr, int nl, const int* __restrict__ conv, int accumulate,
                                                             unsigned* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int i = blockIdx.x;
-  if (conv && conv[i]) return;
+  const int pt = blockIdx.x;
+  if (conv && conv[pt]) return;
   const int n = nr, nn = nr * nr, nv = nt * nr;
-  T* Sinv = reinterpret_cast<T*>(smraw);
-  T* Xp = Sinv + nn;        // previous X = S^-1 U
-  T* Xc = Xp + nn;          // current X
-  T* Ab = Xc + nn;          // coupling block
-  T* y = Ab + nn;           // nl x nr: P_S f
-  T* wq = y + nl * nr;      // nl x nr: S_q^-1 w_q
-  T* tmp = wq + nl * nr;    // nr
-  T* prow = tmp + nr;       // 2 nr (double-buffered pivot rows)
-  T* pcol = prow + 2 * nr;  // 2 nr
-  const double* f = Fin + static_cast<size_t>(i) * nv;
-  const T eE = static_cast<T>(dt * (E ? E[i] : E_uniform));
-  T* X = Xg + static_cast<size_t>(i) * nl * nn;
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* SinvT = reinterpret_cast<T*>(smraw);  // S_q^-1, transposed
+  T* Xp = SinvT + nn;                      // X_{q-1} = S_{q-1}^-1 U_{q-1}, row-major
+  T* Xc = Xp + nn;                         // X_q
+  T* Ab = Xc + nn;                         // As_lo[q] transposed, then As_up[q] row-major
+  T* y = Ab + nn;                          // nl x nr: P_S f, then w_q
+  T* wq = y + nl * nr;                     // nl x nr: S_q^-1 w_q, then z
+  T* tmp = wq + nl * nr;                   // nr
+  T* prow2 = tmp + nr;                     // 2 x 64 pivot rows
+  T* pcol2 = prow2 + 128;                  // 2 x 64 pivot columns
+  const double* f = Fin + static_cast<size_t>(pt) * nv;
+  const T eE = static_cast<T>(dt * (E ? E[pt] : E_uniform));
+  T* X = Xg + static_cast<size_t>(pt) * nl * nn;
 
   // y = T_S f (per radial index)
   for (int e = threadIdx.x; e < nl * nr; e += kST) {
@@ -129,58 +135,86 @@ __global__ void __launch_bounds__(kST) vsolve_struct_kernel(const double* __rest
   }
   __syncthreads();
   for (int q = 0; q < nl; ++q) {
-    // S_q = I - dt Cs_q - L_q X_{q-1} = I - dt Cs_q + dt E As_lo[q] X_{q-1};  w_q = y_q + dt E As_lo[q] wq_{q-1}
+    // S_q = I - dt Cs_q + dt E As_lo[q] X_{q-1} in registers;  w_q = y_q + dt E As_lo[q] wq_{q-1}
+    T s[kG][kG];
     const double* C = Cs + static_cast<size_t>(q) * nn;
-    for (int e = threadIdx.x; e < nn; e += kST) Sinv[e] = (e / n == e % n ? T(1) : T(0)) - static_cast<T>(dt * C[e]);
-    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < kG; ++a)
+#pragma unroll
+      for (int b = 0; b < kG; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        s[a][b] = (i < n && j < n) ? (i == j ? T(1) : T(0)) - static_cast<T>(dt * C[i * n + j]) : T(0);
+      }
     if (q > 0) {
       const double* Al = Alo + static_cast<size_t>(q) * nn;
-      for (int e = threadIdx.x; e < nn; e += kST) Ab[e] = static_cast<T>(Al[e]);
+      for (int e = threadIdx.x; e < nn; e += kST) Ab[(e % n) * n + e / n] = static_cast<T>(Al[e]);
       __syncthreads();
-      tile_gemm<T, T>(Ab, Xp, Sinv, n, eE, true);
-      tile_gemv<T>(Ab, wq + (q - 1) * nr, tmp, n, eE, false);
-      __syncthreads();
-      for (int k = threadIdx.x; k < nr; k += kST) y[q * nr + k] += tmp[k];  // y_q now holds w_q
-      __syncthreads();
+      T acc[kG][kG] = {};
+      grid_gemm<T>(Ab, Xp, n, acc);
+#pragma unroll
+      for (int a = 0; a < kG; ++a)
+#pragma unroll
+        for (int b = 0; b < kG; ++b) s[a][b] += eE * acc[a][b];
+      gemv_t<T>(Ab, wq + (q - 1) * nr, tmp, n, eE);
+      for (int k = threadIdx.x; k < nr; k += kST) y[q * nr + k] += tmp[k];  // same thread wrote tmp[k]
     }
-    gauss_jordan_inverse<T>(Sinv, n, prow, pcol);
-    // wq_q = S_q^-1 w_q;  X_q = S_q^-1 U_q = -dt E S_q^-1 As_up[q]
-    tile_gemv<T>(Sinv, y + q * nr, wq + q * nr, n, T(1), false);
+    grid_gauss_jordan<T>(s, n, prow2, pcol2);
+#pragma unroll
+    for (int a = 0; a < kG; ++a)
+#pragma unroll
+      for (int b = 0; b < kG; ++b) {
+        const int i = ty + 16 * a, j = tx + 16 * b;
+        if (i < n && j < n) SinvT[j * n + i] = s[a][b];
+      }
     if (q + 1 < nl) {
       const double* Au = Aup + static_cast<size_t>(q) * nn;
       for (int e = threadIdx.x; e < nn; e += kST) Ab[e] = static_cast<T>(Au[e]);
-      __syncthreads();
-      tile_gemm<T, T>(Sinv, Ab, Xc, n, -eE, false);
-      __syncthreads();
-      for (int e = threadIdx.x; e < nn; e += kST) X[static_cast<size_t>(q) * nn + e] = Xc[e];
+    }
+    __syncthreads();
+    // wq_q = S_q^-1 w_q;  X_q = S_q^-1 U_q = -dt E S_q^-1 As_up[q]
+    gemv_t<T>(SinvT, y + q * nr, wq + q * nr, n, T(1));
+    if (q + 1 < nl) {
+      T acc[kG][kG] = {};
+      grid_gemm<T>(SinvT, Ab, n, acc);
+#pragma unroll
+      for (int a = 0; a < kG; ++a)
+#pragma unroll
+        for (int b = 0; b < kG; ++b) {
+          const int i = ty + 16 * a, j = tx + 16 * b;
+          if (i < n && j < n) {
+            const T v = -eE * acc[a][b];
+            Xc[i * n + j] = v;
+            X[static_cast<size_t>(q) * nn + i * n + j] = v;
+          }
+        }
       T* t = Xp;
       Xp = Xc;
       Xc = t;
     }
     __syncthreads();
   }
-  // back substitution: z_{L-1} = wq_{L-1}; z_q = wq_q - X_q z_{q+1}  (z overwrites wq)
+  // back substitution: z_{L-1} = wq_{L-1}; z_q = wq_q - X_q z_{q+1}, a warp per row, lanes across k
   for (int q = nl - 2; q >= 0; --q) {
     const T* Xq = X + static_cast<size_t>(q) * nn;
-    for (int e = threadIdx.x; e < nn; e += kST) Xc[e] = Xq[e];  // coalesced staging
-    __syncthreads();
-    for (int r = threadIdx.x; r < nr; r += kST) {
+    for (int r = warp; r < nr; r += kST / 32) {
       T acc = T(0);
-      for (int k = 0; k < nr; ++k) acc += Xc[r * nr + k] * wq[(q + 1) * nr + k];
-      wq[q * nr + r] -= acc;
+      for (int k = lane; k < nr; k += 32) acc += Xq[r * nr + k] * wq[(q + 1) * nr + k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) wq[q * nr + r] -= acc;
     }
     __syncthreads();
   }
-  // restore y = P_S f (it held w_q) and form f* = f + T_O (z - y)
+  // z - y with y = P_S f again (y held w_q), then f* = f + T_O (z - y)
   for (int e = threadIdx.x; e < nl * nr; e += kST) {
     const int l = e / nr, k = e % nr;
     double s = 0.0;
     for (int a = 0; a < nt; ++a) s += TS[l * nt + a] * f[a * nr + k];
-    y[e] = wq[e] - static_cast<T>(s);  // z - y
+    y[e] = wq[e] - static_cast<T>(s);
   }
   __syncthreads();
   bool bad = false;
-  double* out = Fout + static_cast<size_t>(i) * nv;
+  double* out = Fout + static_cast<size_t>(pt) * nv;
   for (int e = threadIdx.x; e < nv; e += kST) {
     const int a = e / nr, k = e % nr;
     double s = 0.0;
@@ -195,7 +229,7 @@ __global__ void __launch_bounds__(kST) vsolve_struct_kernel(const double* __rest
 }  // namespace
 
 size_t struct_smem_bytes(int nr, int nl, size_t tsize) {
-  return (4ull * nr * nr + 2ull * nl * nr + 5ull * nr) * tsize;
+  return (4ull * nr * nr + 2ull * nl * nr + nr + 4ull * 64) * tsize;
 }
 
 template <typename T>
