@@ -146,7 +146,9 @@ __device__ __forceinline__ void tma_store3(const CUtensorMap* map, const void* s
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all_but_last() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -401,12 +403,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         epi_bar();
         if (leader) {
+          // store this chunk; wait only until the previous chunk's store has read its slot, then
+          // refill that slot (the store just issued overlaps the next chunk)
           tma_store3(&mC, s.cbuf[slot], cx(t, ch), cy(t), p);
-          bulk_wait_read_all();  // the slot is free again
-          if (load_c) {
+          bulk_wait_read_all_but_last();
+          if (load_c && g >= 1) {
             int t2, ch2;
-            chunk_at(g + CSLOTS, t2, ch2);
-            if (t2 < total) issue_c(t2, ch2, slot), ++c_issued;
+            chunk_at(g - 1 + CSLOTS, t2, ch2);
+            if (t2 < total) issue_c(t2, ch2, (g - 1) % CSLOTS), ++c_issued;
           }
         }
       }
