@@ -60,6 +60,10 @@ typedef enum {
                                    Nv^3 / (5 N_l Nr^3) fewer flops and no dense factors in memory. The
                                    block elimination runs in FP64 (BTE_FP64) or FP32 with the FP64
                                    refinement (BTE_MIXED). Requires nr <= 64. */
+#define BTE_FLAG_TC_SINGLE 8u   /* BTE_MIXED on the tensor cores: apply each 128-column panel to the
+                                   trailing matrix on its own (K = 128) instead of two panels at a time
+                                   (K = 256, half the trailing-matrix traffic); same factors up to
+                                   rounding order */
 
 typedef struct {
   int nx;            /* Chebyshev-Gauss-Lobatto points, >= 3 */

@@ -139,29 +139,63 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st));
   } else {
     float* fac = static_cast<float*>(h->fac);
-    float* whi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 0) : nullptr;
-    float* wlo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 1) : nullptr;
-    float* uhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 2) : nullptr;
-    float* ulo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 3) : nullptr;
-    float* lhi = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 4) : nullptr;
-    float* llo = h->use_tc ? bte::tc_ws_part(h->tcws, nx, n, 5) : nullptr;
     const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb, h->panel_w);
+    float* linv = static_cast<float*>(h->linv);
+    float* uinv = fused_uinv ? static_cast<float*>(h->uinv) : nullptr;
     BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
-    for (int k0 = 0; k0 < n; k0 += nb) {
-      const int kb = std::min(nb, n - k0);
-      // the L21 split for the tensor cores is written by lu_swap_pack
-      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, static_cast<float*>(h->linv),
-                                                             fused_uinv ? static_cast<float*>(h->uinv) : nullptr,
-                                                             nx, n, k0, kb, nb, h->status, nullptr, nullptr, lhi, llo,
-                                                             h->panel_w, st));
-      if (k0 + kb < n) {
-        if (h->use_tc) {
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, kb, nb, uhi, ulo, whi, wlo, st));
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, h->tcws, h->status, st));
-          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, kb, h->tcws, h->status, st));
-        } else {
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, static_cast<float*>(h->linv),
-                                                                         nx, n, k0, kb, nb, nullptr, nullptr, st));
+    if (h->use_tc) {
+      // workspace parts (tc_ws_part): 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11)
+      // split, 8-9 the two-panel block's inv(L11) split (6-7, U12^T, stay inside the tc_lu_* calls)
+      float* ws[10];
+      for (int p = 0; p < 10; ++p) ws[p] = bte::tc_ws_part(h->tcws, nx, n, p);
+      const int ks = bte::kTcKs;
+      auto panel = [&](int k0, int kb) {
+        // the L21 split for the tensor cores is written by lu_swap_pack
+        BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
+                                                               h->status, nullptr, nullptr, ws[4], ws[5],
+                                                               h->panel_w, st));
+      };
+      // the panel at k0 applied to the next ncols columns (U12, then A22 -= L21 U12)
+      auto single = [&](int k0, int ncols) {
+        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, nb, nb, ncols, ks, ws[2],
+                                                                ws[3], ws[0], ws[1], st));
+        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, ncols, h->tcws, h->status, st));
+        BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, ncols, h->tcws, h->status, st));
+      };
+      if (!h->tc_pair) {
+        for (int k0 = 0; k0 < n; k0 += nb) {
+          const int kb = std::min(nb, n - k0);
+          panel(k0, kb);
+          if (k0 + kb < n) single(k0, n - k0 - kb);
+        }
+      } else {
+        // panels in pairs: the first panel updates only the second panel's columns; once the
+        // second panel is factored, both update the rest together (K = 256), which reads and
+        // writes the trailing matrix once per pair instead of once per panel
+        for (int k0 = 0; k0 < n; k0 += 2 * nb) {
+          const int kb1 = std::min(nb, n - k0);
+          panel(k0, kb1);
+          if (k0 + kb1 == n) break;
+          const int kb2 = std::min(nb, n - k0 - nb);
+          single(k0, kb2);
+          panel(k0 + nb, kb2);
+          if (k0 + nb + kb2 == n) break;
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_pair_linv(fac, h->perm, linv, nx, n, k0, ws[8], ws[9], st));
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack_pair(fac, h->perm, nx, n, k0, ks, ws[2], ws[3],
+                                                                       ws[0], ws[1], st));
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12_pair(fac, nx, n, k0, h->tcws, h->status, st));
+          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st));
+        }
+      }
+    } else {
+      for (int k0 = 0; k0 < n; k0 += nb) {
+        const int kb = std::min(nb, n - k0);
+        BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
+                                                               h->status, nullptr, nullptr, nullptr, nullptr,
+                                                               h->panel_w, st));
+        if (k0 + kb < n) {
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, linv, nx, n, k0, kb, nb,
+                                                                         nullptr, nullptr, st));
           BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
         }
       }
@@ -302,6 +336,7 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   h->precision = cfg->precision;
   h->nb = cfg->precision == BTE_FP64 ? 64 : 128;
   h->structured = (cfg->flags & BTE_FLAG_STRUCTURED) != 0;
+  h->tc_pair = (cfg->flags & BTE_FLAG_TC_SINGLE) == 0;
   if (h->structured) {
     const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
     const size_t ts = cfg->precision == BTE_FP64 ? 8 : 4;

@@ -24,6 +24,7 @@ struct bte_handle {
   bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
   bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
   int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)
+  bool tc_pair = true;    // tensor-core updates two panels at a time (K = 256)
   size_t bytes = 0;
   std::vector<void*> allocs;
 

@@ -14,14 +14,20 @@ enum StatusBits : unsigned {
   kTimeout = 8u,     // a bounded device-side wait expired (tensor-core pipeline)
 };
 
-// tensor-core (tcgen05) trailing update of the FP32 LU; workspace of tc_workspace_bytes()
+// tensor-core (tcgen05) trailing updates of the FP32 LU; workspace of tc_workspace_bytes(), parts
+// 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11) split, 6-7 U12^T split, 8-9 a
+// two-panel block's inv(L11) split (layout in bte_tc.cu)
 bool tc_available();
 size_t tc_workspace_bytes(int nx, int n, int nbmax);
-float* tc_ws_part(void* ws, int nx, int n, int part);  // 0 A_hi, 1 A_lo, 2 B_hi, 3 B_lo
-void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st);
-// U12 = inv(L11) (P A12) on the tensor cores, written into the matrix and (transposed, split) into
-// the B operand of the following trailing update.
-void tc_lu_u12(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
+float* tc_ws_part(void* ws, int nx, int n, int part);
+constexpr int kTcKs = 256;  // K capacity (row length) of the operand parts
+// One 128-wide panel at k0: U12 = inv(L11) (P A12) for the first ncols trailing columns (written
+// into the matrix and, transposed and split, into parts 6-7), then A22 -= L21 U12 on those columns.
+void tc_lu_u12(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st);
+void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st);
+// The two panels at k0 and k0 + 128 together (K = 256) on every column right of k0 + 256.
+void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
+void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
 
 // ---- x half step (Algorithm 1): eigen-basis transform, Q_ij apply, back transform
 void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
@@ -52,10 +58,22 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int 
                      cudaStream_t st);
 template <typename T>
 bool lu_panel_fuses_uinv(int n, int nbmax, int w_pref);
-// Tensor-core path: displaced-row writes of the panel permutation, the split (P A12)^T operand
-// (bt_hi/bt_lo) and the split L21 operand (a_hi/a_lo, may be NULL).
-void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,
-                         float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st);
+// Tensor-core path: for the first ncols columns right of the panel, the displaced-row writes of the
+// panel permutation and the split (P A12)^T operand (bt_hi/bt_lo); for every row below the panel,
+// the split L21 operand (a_hi/a_lo). Operand rows are ks floats long.
+void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, int ncols,
+                         int ks, float* bt_hi, float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st);
+// The same for the two 128-wide panels at k0 and k0 + 128 taken together, on the columns and rows
+// right of and below k0 + 256: both permutations applied in order, (P A12)^T over 256 rows of K, and
+// the L21 operand [P_2 L21_1, L21_2] with the second panel's permutation applied to the first
+// panel's columns (they stay unpermuted in the matrix, as the solve expects).
+void launch_lu_swap_pack_pair(float* fac, const int* perm, int nx, int n, int k0, int ks, float* bt_hi,
+                              float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st);
+// inv(L11) of the 256 x 256 two-panel block [L_1 0; (P_2 L21_1)_top L_2] from the two panels'
+// inverses: [inv(L_1) 0; -inv(L_2) (P_2 L21_1)_top inv(L_1)  inv(L_2)], TF32-split into o_hi/o_lo
+// ([point][256][256]).
+void launch_lu_pair_linv(const float* fac, const int* perm, const float* linv, int nx, int n, int k0,
+                         float* o_hi, float* o_lo, cudaStream_t st);
 // inv(U11) of every panel of every point, once the factorisation is complete ([point][panel]).
 template <typename T>
 void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_t st);

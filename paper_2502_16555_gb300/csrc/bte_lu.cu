@@ -1065,10 +1065,12 @@ __global__ void __launch_bounds__(256) lu_swap_trsm_kernel(T* __restrict__ fac, 
   }
 }
 
-// Tensor-core path: apply the panel's row permutation to the trailing columns (displaced rows only)
-// and write (P A12)^T, split into TF32 head/remainder, as the K-major B operand of the U12 GEMM.
+// Tensor-core path: apply the panel's row permutation to the first ncols trailing columns
+// (displaced rows only) and write (P A12)^T, split into TF32 head/remainder, as the K-major B
+// operand of the U12 product; split L21 (every row below the panel) into the A operand of the
+// trailing update. Operand rows hold ks floats (K = nbmax of them used here).
 __global__ void __launch_bounds__(256) lu_swap_pack_kernel(float* __restrict__ fac, const int* __restrict__ perm,
-                                                           int n, int k0, int nb, int nbmax,
+                                                           int n, int k0, int nb, int nbmax, int ncols, int ks,
                                                            float* __restrict__ bt_hi, float* __restrict__ bt_lo,
                                                            float* __restrict__ a_hi, float* __restrict__ a_lo) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1076,61 +1078,311 @@ __global__ void __launch_bounds__(256) lu_swap_pack_kernel(float* __restrict__ f
   float* Bs = top + static_cast<size_t>(nb) * kTrsmLd;      // permuted panel rows nb x ld
   const int mat = blockIdx.x;
   const int C0 = k0 + nb + blockIdx.y * kTrsmCols;
-  const int ncol = min(kTrsmCols, n - C0);
+  const int ncol = min(kTrsmCols, k0 + nb + ncols - C0);
   float* A = fac + static_cast<size_t>(mat) * n * n;
   const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
   const int* rec = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(nbmax);
   const int tid = threadIdx.x, bd = blockDim.x;
-  for (int idx = tid; idx < nb * kTrsmCols; idx += bd) {
-    const int r = idx / kTrsmCols, c = idx % kTrsmCols;
-    top[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(k0 + r) * n + C0 + c] : 0.f;
-    const int o = rec[1 + r];
-    Bs[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(o) * n + C0 + c] : 0.f;
+  const size_t off = static_cast<size_t>(mat) * (n - nbmax) * ks;
+  if (ncol > 0) {
+    for (int idx = tid; idx < nb * kTrsmCols; idx += bd) {
+      const int r = idx / kTrsmCols, c = idx % kTrsmCols;
+      top[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(k0 + r) * n + C0 + c] : 0.f;
+      const int o = rec[1 + r];
+      Bs[r * kTrsmLd + c] = c < ncol ? A[static_cast<size_t>(o) * n + C0 + c] : 0.f;
+    }
+    __syncthreads();
+    const int d = rec[0];
+    for (int idx = tid; idx < d * kTrsmCols; idx += bd) {
+      const int q = idx / kTrsmCols, c = idx % kTrsmCols;
+      if (c >= ncol) continue;
+      const int dst = rec[1 + nbmax + 2 * q], src = rec[1 + nbmax + 2 * q + 1];
+      A[static_cast<size_t>(dst) * n + C0 + c] = top[(src - k0) * kTrsmLd + c];
+    }
+    for (int idx = tid; idx < kTrsmCols * nbmax; idx += bd) {
+      const int c = idx / nbmax, r = idx % nbmax;
+      if (c >= ncol) continue;
+      float h = 0.f, l = 0.f;
+      if (r < nb) split_tf32(Bs[r * kTrsmLd + c], h, l);
+      const size_t o = off + static_cast<size_t>(C0 - (k0 + nb) + c) * ks + r;
+      bt_hi[o] = h;
+      bt_lo[o] = l;
+    }
   }
-  __syncthreads();
-  const int d = rec[0];
-  for (int idx = tid; idx < d * kTrsmCols; idx += bd) {
-    const int q = idx / kTrsmCols, c = idx % kTrsmCols;
-    if (c >= ncol) continue;
-    const int dst = rec[1 + nbmax + 2 * q], src = rec[1 + nbmax + 2 * q + 1];
-    A[static_cast<size_t>(dst) * n + C0 + c] = top[(src - k0) * kTrsmLd + c];
-  }
-  const size_t off = static_cast<size_t>(mat) * (n - nbmax) * nbmax;
-  for (int idx = tid; idx < kTrsmCols * nbmax; idx += bd) {
-    const int c = idx / nbmax, r = idx % nbmax;
-    if (c >= ncol) continue;
-    float h = 0.f, l = 0.f;
-    if (r < nb) split_tf32(Bs[r * kTrsmLd + c], h, l);
-    const size_t o = off + static_cast<size_t>(C0 - (k0 + nb) + c) * nbmax + r;
-    bt_hi[o] = h;
-    bt_lo[o] = l;
-  }
-  // TF32 split of L21 rows [k0 + nb + 64 y, +64) (the A operand of the trailing update), one warp
-  // per row segment of 16-byte vectors
+  // TF32 split of L21 rows [k0 + nb + 64 y, +64) (the A operand of the trailing update)
   const int R0 = blockIdx.y * kTrsmCols, nrow = min(kTrsmCols, n - k0 - nb - R0);
-  if (a_hi && ((n & 3) != 0 || (nb & 3) != 0)) {
+  if (!a_hi || nrow <= 0) return;
+  if ((n & 3) != 0 || (nb & 3) != 0) {
     for (int idx = tid; idx < nrow * nb; idx += bd) {
       const int r = idx / nb, k = idx % nb;
       float h, l;
       split_tf32(A[static_cast<size_t>(k0 + nb + R0 + r) * n + k0 + k], h, l);
-      const size_t o = off + static_cast<size_t>(R0 + r) * nbmax + k;
+      const size_t o = off + static_cast<size_t>(R0 + r) * ks + k;
       a_hi[o] = h;
       a_lo[o] = l;
     }
-  } else if (a_hi) {
+  } else {
     const int q4 = nb / 4;
     for (int idx = tid; idx < nrow * q4; idx += bd) {
       const int r = idx / q4, k = 4 * (idx % q4);
       const float4 v = *reinterpret_cast<const float4*>(A + static_cast<size_t>(k0 + nb + R0 + r) * n + k0 + k);
-      float h[4], l[4];
-      split_tf32(v.x, h[0], l[0]);
-      split_tf32(v.y, h[1], l[1]);
-      split_tf32(v.z, h[2], l[2]);
-      split_tf32(v.w, h[3], l[3]);
-      const size_t o = off + static_cast<size_t>(R0 + r) * nbmax + k;
-      *reinterpret_cast<float4*>(a_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(a_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+      float4 h, l;
+      split_tf32(v.x, h.x, l.x);
+      split_tf32(v.y, h.y, l.y);
+      split_tf32(v.z, h.z, l.z);
+      split_tf32(v.w, h.w, l.w);
+      const size_t o = off + static_cast<size_t>(R0 + r) * ks + k;
+      *reinterpret_cast<float4*>(a_hi + o) = h;
+      *reinterpret_cast<float4*>(a_lo + o) = l;
     }
+  }
+}
+
+// The two 128-wide panels at k0 (P_1, L_1, L21_1) and k0 + 128 (P_2, L_2, L21_2) as one 256-wide
+// step, for the columns right of and the rows below base = k0 + 256. Blocks y < ncb take 32 columns
+// each:
+//   A <- P_2 P_1 A on those columns (displaced rows only; the pivot rows go to the B operand);
+//   (P A12)^T split over the 256 panel rows (B operand of the block's U12 product);
+// blocks y >= ncb take 32 rows each of the A operand of the trailing update, [P_2 L21_1, L21_2]
+// split, row i of P_2 L21_1 being the matrix row that P_2 moved to i. Both panels are full (128
+// columns); n % 4 == 0, so every row segment here is whole 16-byte vectors.
+constexpr int kPairP = 128, kPairCols = 32, kPairLd = kPairCols + 1;
+__global__ void __launch_bounds__(256) lu_swap_pack_pair_kernel(float* __restrict__ fac, const int* __restrict__ perm,
+                                                                int n, int k0, int ks, int ncb,
+                                                                float* __restrict__ bt_hi, float* __restrict__ bt_lo,
+                                                                float* __restrict__ a_hi, float* __restrict__ a_lo) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* piv = reinterpret_cast<float*>(smraw);  // rows of P A over the pair's 256 panel rows, 256 x ld
+  int* srow = reinterpret_cast<int*>(piv + 2 * kPairP * kPairLd);  // pivot rows, 2 x 128
+  int* spair = srow + 2 * kPairP;                                   // displaced (dst, src), 2 x 2 x 128
+  const int mat = blockIdx.x, tid = threadIdx.x;
+  const int base = k0 + 2 * kPairP, M = n - base;
+  float* A = fac + static_cast<size_t>(mat) * n * n;
+  const int npan = (n + kPairP - 1) / kPairP, pan = k0 / kPairP;
+  const int* rec1 = perm + (static_cast<size_t>(mat) * npan + pan) * perm_stride(kPairP);
+  const int* rec2 = rec1 + perm_stride(kPairP);
+  const size_t off = static_cast<size_t>(mat) * (n - kPairP) * ks;
+  const int d1 = rec1[0], d2 = rec2[0];
+  if (static_cast<int>(blockIdx.y) < ncb) {
+    const int C0 = base + blockIdx.y * kPairCols;
+    const int ncol = min(kPairCols, n - C0);
+    for (int q = tid; q < 2 * kPairP; q += 256) {
+      const int* rec = q < kPairP ? rec1 : rec2;
+      const int r = q % kPairP;
+      srow[q] = rec[1 + r];
+      spair[2 * q] = rec[1 + kPairP + 2 * r];
+      spair[2 * q + 1] = rec[1 + kPairP + 2 * r + 1];
+    }
+    __syncthreads();
+    const int r8 = tid / 8, c4 = 4 * (tid % 8);  // 8 threads per row, one float4 each
+    const bool cok = c4 < ncol;
+    for (int half = 0; half < 2; ++half) {
+      // pivot rows into shared memory (all 128 loads of the half in flight together)
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = r8 + 32 * u;
+        v[u] = cok ? *reinterpret_cast<const float4*>(A + static_cast<size_t>(srow[half * kPairP + r]) * n + C0 + c4)
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float* d = piv + (half * kPairP + r8 + 32 * u) * kPairLd + c4;
+        d[0] = v[u].x, d[1] = v[u].y, d[2] = v[u].z, d[3] = v[u].w;
+      }
+      // every pivot row is read before a displaced row overwrites its old place
+      __syncthreads();
+      const int d = half ? d2 : d1;
+      const int* pr = spair + half * 2 * kPairP;
+      float4 w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = r8 + 32 * u;
+        w[u] = q < d && cok ? *reinterpret_cast<const float4*>(A + static_cast<size_t>(pr[2 * q + 1]) * n + C0 + c4)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = r8 + 32 * u;
+        if (q < d && cok) *reinterpret_cast<float4*>(A + static_cast<size_t>(pr[2 * q]) * n + C0 + c4) = w[u];
+      }
+      // the second permutation reads rows the first one wrote (global writes of this block are
+      // visible to it after the barrier)
+      __syncthreads();
+    }
+    // (P A12)^T split: column c of the block is operand row C0 - base + c, K = the 256 panel rows
+#pragma unroll 4
+    for (int idx = tid; idx < kPairCols * 2 * kPairP; idx += 256) {
+      const int c = idx / (2 * kPairP), r = idx % (2 * kPairP);
+      if (c >= ncol) continue;
+      float h, l;
+      split_tf32(piv[r * kPairLd + c], h, l);
+      const size_t o = off + static_cast<size_t>(C0 - base + c) * ks + r;
+      bt_hi[o] = h;
+      bt_lo[o] = l;
+    }
+    return;
+  }
+  // ---- L21 operand rows [base + R0, +32)
+  int* rowsrc = srow;
+  const int R0 = (blockIdx.y - ncb) * kPairCols, nrow = min(kPairCols, M - R0);
+  if (tid < kPairCols) rowsrc[tid] = base + R0 + tid;
+  __syncthreads();
+  for (int q = tid; q < d2; q += 256) {
+    const int dst = rec2[1 + kPairP + 2 * q] - (base + R0);
+    if (dst >= 0 && dst < nrow) rowsrc[dst] = rec2[1 + kPairP + 2 * q + 1];
+  }
+  __syncthreads();
+  // 32 rows x 64 float4: 8 per thread, loads first
+  float4 v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int f = tid + 256 * u, r = f / 64, k = 4 * (f % 64);
+    const int src = k < kPairP ? rowsrc[r] : base + R0 + r;
+    v[u] = r < nrow ? *reinterpret_cast<const float4*>(A + static_cast<size_t>(src) * n + k0 + k)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int f = tid + 256 * u, r = f / 64, k = 4 * (f % 64);
+    if (r >= nrow) continue;
+    float4 h, l;
+    split_tf32(v[u].x, h.x, l.x);
+    split_tf32(v[u].y, h.y, l.y);
+    split_tf32(v[u].z, h.z, l.z);
+    split_tf32(v[u].w, h.w, l.w);
+    const size_t o = off + static_cast<size_t>(R0 + r) * ks + k;
+    *reinterpret_cast<float4*>(a_hi + o) = h;
+    *reinterpret_cast<float4*>(a_lo + o) = l;
+  }
+}
+
+// inv(L11) of the two-panel block at k0 (see launch_lu_pair_linv), one 32-column slice per block:
+//   T = Lp inv(L_1)   (Lp = rows P_2 moved to the top of panel 2, first panel's columns),
+//   X = -inv(L_2) T,
+// both products over the nonzero (lower-triangular) part of the inverses only; 4 x 4 outputs per
+// thread. The slice of the diagonal blocks and of the zero block is written alongside.
+__global__ void __launch_bounds__(256) lu_pair_linv_kernel(const float* __restrict__ fac, const int* __restrict__ perm,
+                                                           const float* __restrict__ linv, int n, int k0,
+                                                           float* __restrict__ o_hi, float* __restrict__ o_lo) {
+  constexpr int P = kPairP, LD = P + 4, S = 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* Mt = reinterpret_cast<float*>(smraw);  // Lp^T, then inv(L_2)^T   [k][i], P x LD
+  float* Ia = Mt + P * LD;                      // inv(L_1)[:, slice]       [k][j], P x S
+  float* Ts = Ia + P * S;                       // T[:, slice]              [i][j], P x S
+  int* srow = reinterpret_cast<int*>(Ts + P * S);
+  const int mat = blockIdx.x, j0 = blockIdx.y * S, tid = threadIdx.x;
+  const float* A = fac + static_cast<size_t>(mat) * n * n;
+  const int npan = (n + P - 1) / P, pan = k0 / P;
+  const int* rec2 = perm + (static_cast<size_t>(mat) * npan + pan + 1) * perm_stride(P);
+  const float* La = linv + (static_cast<size_t>(mat) * npan + pan) * P * P;
+  const float* Lb = La + P * P;
+  if (tid < P) srow[tid] = rec2[1 + tid];
+  __syncthreads();
+  // a P x P matrix into Mt transposed: thread i % 128 takes row i in 16-byte pieces; all 16 loads
+  // of a thread are issued before its shared-memory stores
+  auto load_t = [&](auto row_ptr) {
+    float4 v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int f = tid + 256 * u, i = f % P, k = 4 * (f / P);
+      v[u] = *reinterpret_cast<const float4*>(row_ptr(i) + k);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int f = tid + 256 * u, i = f % P, k = 4 * (f / P);
+      Mt[k * LD + i] = v[u].x;
+      Mt[(k + 1) * LD + i] = v[u].y;
+      Mt[(k + 2) * LD + i] = v[u].z;
+      Mt[(k + 3) * LD + i] = v[u].w;
+    }
+  };
+  load_t([&](int i) { return A + static_cast<size_t>(srow[i]) * n + k0; });
+  {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = tid + 256 * u, k = f / (S / 4), j = 4 * (f % (S / 4));
+      v[u] = *reinterpret_cast<const float4*>(La + k * P + j0 + j);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int f = tid + 256 * u, k = f / (S / 4), j = 4 * (f % (S / 4));
+      float* d = Ia + k * S + j;
+      // inv(L_1) is lower triangular: only k >= column is kept
+      d[0] = k >= j0 + j ? v[u].x : 0.f;
+      d[1] = k >= j0 + j + 1 ? v[u].y : 0.f;
+      d[2] = k >= j0 + j + 2 ? v[u].z : 0.f;
+      d[3] = k >= j0 + j + 3 ? v[u].w : 0.f;
+    }
+  }
+  __syncthreads();
+  const int ti = tid / 8, tj = tid % 8;  // rows 4 ti .. +3, slice columns 4 tj .. +3
+  float acc[4][4] = {};
+  for (int k = j0 + 4 * tj; k < P; ++k) {  // inv(L_1)[k][j] = 0 for k < j
+    const float4 a = *reinterpret_cast<const float4*>(Mt + k * LD + 4 * ti);
+    const float4 b = *reinterpret_cast<const float4*>(Ia + k * S + 4 * tj);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    *reinterpret_cast<float4*>(Ts + (4 * ti + r) * S + 4 * tj) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+  __syncthreads();
+  load_t([&](int i) { return Lb + static_cast<size_t>(i) * P; });
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
+  for (int k = 0; k <= 4 * ti + 3; ++k) {  // inv(L_2)[i][k] = 0 for k > i
+    const float4 a = *reinterpret_cast<const float4*>(Mt + k * LD + 4 * ti);
+    const float4 b = *reinterpret_cast<const float4*>(Ts + k * S + 4 * tj);
+    const float av[4] = {k <= 4 * ti ? a.x : 0.f, k <= 4 * ti + 1 ? a.y : 0.f, k <= 4 * ti + 2 ? a.z : 0.f, a.w};
+    const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+  }
+  constexpr int W = 2 * P;
+  float* oh = o_hi + static_cast<size_t>(mat) * W * W;
+  float* ol = o_lo + static_cast<size_t>(mat) * W * W;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    float4 h, l;
+    split_tf32(-acc[r][0], h.x, l.x);
+    split_tf32(-acc[r][1], h.y, l.y);
+    split_tf32(-acc[r][2], h.z, l.z);
+    split_tf32(-acc[r][3], h.w, l.w);
+    const size_t o = static_cast<size_t>(P + 4 * ti + r) * W + j0 + 4 * tj;
+    *reinterpret_cast<float4*>(oh + o) = h;
+    *reinterpret_cast<float4*>(ol + o) = l;
+  }
+  // diagonal blocks (lower triangles of the panel inverses) and the zero block, this slice:
+  // 128 rows x 8 float4 per block
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int f = tid + 256 * u, i = f / (S / 4), j = j0 + 4 * (f % (S / 4));
+    const float4 a = *reinterpret_cast<const float4*>(La + i * P + j);
+    const float4 b = *reinterpret_cast<const float4*>(Lb + i * P + j);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    float ha[4], la[4], hb[4], lb[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      split_tf32(j + e <= i ? av[e] : 0.f, ha[e], la[e]);
+      split_tf32(j + e <= i ? bv[e] : 0.f, hb[e], lb[e]);
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(oh + static_cast<size_t>(i) * W + j) = make_float4(ha[0], ha[1], ha[2], ha[3]);
+    *reinterpret_cast<float4*>(ol + static_cast<size_t>(i) * W + j) = make_float4(la[0], la[1], la[2], la[3]);
+    *reinterpret_cast<float4*>(oh + static_cast<size_t>(i) * W + P + j) = z;
+    *reinterpret_cast<float4*>(ol + static_cast<size_t>(i) * W + P + j) = z;
+    *reinterpret_cast<float4*>(oh + static_cast<size_t>(P + i) * W + P + j) = make_float4(hb[0], hb[1], hb[2], hb[3]);
+    *reinterpret_cast<float4*>(ol + static_cast<size_t>(P + i) * W + P + j) = make_float4(lb[0], lb[1], lb[2], lb[3]);
   }
 }
 
@@ -1600,18 +1852,42 @@ void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, 
   lu_swap_trsm_kernel<T><<<grid, 256, smem, st>>>(fac, perm, linv, n, k0, nb, nbmax, ws_hi, ws_lo);
 }
 
-void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, float* bt_hi,
-                         float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st) {
+void launch_lu_swap_pack(float* fac, const int* perm, int nx, int n, int k0, int nb, int nbmax, int ncols,
+                         int ks, float* bt_hi, float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st) {
   const int ntrail = n - k0 - nb;
-  if (ntrail <= 0) return;
-  dim3 grid(nx, (ntrail + kTrsmCols - 1) / kTrsmCols);
+  ncols = std::min(ncols, ntrail);
+  if (ntrail <= 0 || ncols <= 0) return;
+  const int by = (std::max(ncols, a_hi ? ntrail : 0) + kTrsmCols - 1) / kTrsmCols;
+  dim3 grid(nx, by);
   const size_t smem = 2ull * nb * kTrsmLd * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_swap_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  lu_swap_pack_kernel<<<grid, 256, smem, st>>>(fac, perm, n, k0, nb, nbmax, bt_hi, bt_lo, a_hi, a_lo);
+  lu_swap_pack_kernel<<<grid, 256, smem, st>>>(fac, perm, n, k0, nb, nbmax, ncols, ks, bt_hi, bt_lo, a_hi, a_lo);
+}
+
+void launch_lu_swap_pack_pair(float* fac, const int* perm, int nx, int n, int k0, int ks, float* bt_hi,
+                              float* bt_lo, float* a_hi, float* a_lo, cudaStream_t st) {
+  const int M = n - k0 - 2 * kPairP;
+  if (M <= 0) return;
+  const int ncb = (M + kPairCols - 1) / kPairCols;
+  dim3 grid(nx, 2 * ncb);
+  const size_t smem = 2ull * kPairP * kPairLd * sizeof(float) + 6ull * kPairP * sizeof(int);
+  lu_swap_pack_pair_kernel<<<grid, 256, smem, st>>>(fac, perm, n, k0, ks, ncb, bt_hi, bt_lo, a_hi, a_lo);
+}
+
+void launch_lu_pair_linv(const float* fac, const int* perm, const float* linv, int nx, int n, int k0,
+                         float* o_hi, float* o_lo, cudaStream_t st) {
+  constexpr int P = kPairP;
+  const size_t smem = (static_cast<size_t>(P) * (P + 4) + 2ull * P * 32) * sizeof(float) + P * sizeof(int);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(lu_pair_linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  lu_pair_linv_kernel<<<dim3(nx, P / 32), 256, smem, st>>>(fac, perm, linv, n, k0, o_hi, o_lo);
 }
 
 template <typename T>

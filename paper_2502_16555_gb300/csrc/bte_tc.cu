@@ -37,7 +37,9 @@ namespace {
 #ifndef BTE_TC_BN
 #define BTE_TC_BN 128
 #endif
-constexpr int BM = 128, BN = BTE_TC_BN, BK = 32, KTOT = 128, NCHUNK = KTOT / BK;
+// KP: panel width (K of one panel's update); KS: K capacity of the operand workspace, the depth of
+// the two-panel update
+constexpr int BM = 128, BN = BTE_TC_BN, BK = 32, KP = 128, KS = 2 * KP;
 static_assert(BN == 128 || BN == 256, "tile width");
 // Operand stages and C staging slots share the 227 KB of shared memory (64 KB and 16 KB each).
 #ifndef BTE_TC_STAGES
@@ -204,6 +206,8 @@ struct TcArgs {
   int M, N;          // extent of C
   int tiles_m, tiles_n, total;
   int rows_a, rows_b;  // rows per point of the A and B operand arrays
+  int nchunk;        // K / 32: 4 for one panel's update, 8 for a two-panel update
+  int nchunk_m0;     // K / 32 for the first row tile (the two-panel inv(L11) is zero right of 128)
   int mode;          // 0: C -= A B^T;  1: C = A B^T and (bt_hi, bt_lo)[point][col][row] = split(C)
   float* bt_hi;
   float* bt_lo;
@@ -249,8 +253,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int p = t / per_point, r = t % per_point;
         const int ya = p * args.rows_a + (r / args.tiles_n) * BM;
         const int yb = p * args.rows_b + (r % args.tiles_n) * BN;
+        const int nch = r < args.tiles_n ? args.nchunk_m0 : args.nchunk;
         bool ok = true;
-        for (int c = 0; c < NCHUNK; ++c) {
+        for (int c = 0; c < nch; ++c) {
           if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status)) { ok = false; break; }
           mbar_expect_tx(&s.full[st], STAGE_BYTES);
           unsigned char* d = s.stage[st];
@@ -279,8 +284,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(s, &s.tempty[acc], aph ^ 1u, status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d = tmem + acc * BN;
+        const int nch = t % per_point < args.tiles_n ? args.nchunk_m0 : args.nchunk;
         bool ok = true;
-        for (int c = 0; c < NCHUNK; ++c) {
+        for (int c = 0; c < nch; ++c) {
           if (!mbar_wait(s, &s.full[st], ph, status)) { ok = false; break; }
           ++consumed;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -316,7 +322,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {  // ------------------------------------------------------------------------- epilogue
-    // C moves through two 16 KB shared-memory slots in 128 x 32 chunks: TMA load (mode 0), C -= acc
+    // C moves through CSLOTS 16 KB shared-memory slots in 128 x 32 chunks: TMA load (mode 0), C -= acc
     // (or C = acc) by the thread owning the row (its TMEM lane), TMA store. One leader thread waits
     // on the barriers and issues the bulk copies; the four warps meet at a named barrier, so a
     // timeout seen by the leader ends every epilogue thread at the same point.
@@ -388,16 +394,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!load_c && row < args.M) {
           // transposed split of U12: lanes are consecutive rows, so each column's store is coalesced
           const int c0 = col0 + ch * CW;
-          float* bh = args.bt_hi + static_cast<size_t>(p) * args.rows_b * KTOT + row;
-          float* bl = args.bt_lo + static_cast<size_t>(p) * args.rows_b * KTOT + row;
+          float* bh = args.bt_hi + static_cast<size_t>(p) * args.rows_b * KS + row;
+          float* bl = args.bt_lo + static_cast<size_t>(p) * args.rows_b * KS + row;
 #pragma unroll
           for (int j = 0; j < CW; ++j) {
             if (c0 + j >= args.N) break;
             uint32_t h;
             const float x = __uint_as_float(v[j]);
             asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-            bh[static_cast<size_t>(c0 + j) * KTOT] = __uint_as_float(h);
-            bl[static_cast<size_t>(c0 + j) * KTOT] = x - __uint_as_float(h);
+            bh[static_cast<size_t>(c0 + j) * KS] = __uint_as_float(h);
+            bl[static_cast<size_t>(c0 + j) * KS] = x - __uint_as_float(h);
           }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -452,11 +458,12 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, float* base, size_t rows, int box_rows) {
+// 2-D K-major operand array of `rows` rows of `kext` floats, boxes of box_rows x 32, 128-byte swizzle
+bool make_map(CUtensorMap* m, float* base, size_t rows, int box_rows, int kext) {
   auto enc = get_encode();
   if (!enc) return false;
-  cuuint64_t dims[2] = {static_cast<cuuint64_t>(KTOT), static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {static_cast<cuuint64_t>(KTOT) * 4};
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(kext), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(kext) * 4};
   cuuint32_t box[2] = {BK, static_cast<cuuint32_t>(box_rows)};
   cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -478,25 +485,30 @@ bool make_cmap(CUtensorMap* m, float* fac, int nx, int n) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// tensor maps of the workspace parts (tc_ws_part numbering) and of the matrices (C)
+enum { kMapC = 10 };
 struct Maps {
   void* ws = nullptr;
   float* fac = nullptr;
   int nx = 0, n = 0;
-  CUtensorMap m[7];  // A_hi, A_lo, B_hi, B_lo, inv(L11) hi, lo, C
+  CUtensorMap m[11];
   bool ok = false;
 };
 
 Maps& maps_for(float* fac, void* ws, int nx, int n) {
   static Maps maps;
   if (!maps.ok || maps.ws != ws || maps.fac != fac || maps.nx != nx || maps.n != n) {
-    const size_t rows = static_cast<size_t>(nx) * (n - KTOT);
+    const size_t rows = static_cast<size_t>(nx) * (n - KP);
     maps.ok = true;
-    // A operands (L21 split, inv(L11) split) in boxes of BM rows, B operands in boxes of BN rows
-    for (int part = 0; part < 4; ++part)
-      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), rows, part < 2 ? BM : BN);
-    for (int part = 4; part < 6; ++part)
-      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KTOT, BM);
-    maps.ok = maps.ok && make_cmap(&maps.m[6], fac, nx, n);
+    // L21 split (A of the updates, boxes of BM rows); (P A12)^T and U12^T splits (B, boxes of BN rows)
+    for (int part : {0, 1, 2, 3, 6, 7})
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), rows, part < 2 ? BM : BN, KS);
+    // inv(L11) of one panel and of a two-panel block (A of the U12 products)
+    for (int part : {4, 5})
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KP, BM, KP);
+    for (int part : {8, 9})
+      maps.ok = maps.ok && make_map(&maps.m[part], tc_ws_part(ws, nx, n, part), static_cast<size_t>(nx) * KS, BM, KS);
+    maps.ok = maps.ok && make_cmap(&maps.m[kMapC], fac, nx, n);
     maps.ws = ws;
     maps.fac = fac;
     maps.nx = nx;
@@ -519,24 +531,78 @@ int sm_count() {
 
 void launch(const Maps& mp, int ia, int ib, const TcArgs& a, cudaStream_t st) {
   const int grid = a.total < sm_count() ? a.total : sm_count();
-  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1], mp.m[6],
-                                                             a);
+  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1],
+                                                             mp.m[kMapC], a);
+}
+
+// C -= A B^T over the block of C at (row0, col0) of every point: A = L21 split (parts 0, 1), B =
+// U12^T split (parts 6, 7), depth nchunk * 32
+void gemm(Maps& mp, float* fac, int nx, int n, int row0, int col0, int M, int N, int nchunk, unsigned* status,
+          cudaStream_t st) {
+  if (M <= 0 || N <= 0 || !mp.ok) return;
+  TcArgs a{};
+  a.fac = fac;
+  a.n = n;
+  a.row0 = row0;
+  a.col0 = col0;
+  a.M = M;
+  a.N = N;
+  a.tiles_m = (M + BM - 1) / BM;
+  a.tiles_n = (N + BN - 1) / BN;
+  a.total = nx * a.tiles_m * a.tiles_n;
+  a.rows_a = a.rows_b = n - KP;
+  a.nchunk = a.nchunk_m0 = nchunk;
+  a.mode = 0;
+  a.status = status;
+  launch(mp, 0, 6, a, st);
+}
+
+// U12 = inv(L11) (P A12) for the M = 128 or 256 panel rows at row0 and the N columns at col0; A =
+// the inverse split (parts 4, 5 or 8, 9), B = (P A12)^T split (parts 2, 3); U12 goes into the matrix
+// and, transposed and split, into parts 6, 7
+void u12(Maps& mp, float* fac, void* ws, int nx, int n, int row0, int col0, int M, int N, unsigned* status,
+         cudaStream_t st) {
+  if (N <= 0 || !mp.ok) return;
+  TcArgs a{};
+  a.fac = fac;
+  a.n = n;
+  a.row0 = row0;
+  a.col0 = col0;
+  a.M = M;
+  a.N = N;
+  a.tiles_m = M / BM;
+  a.tiles_n = (N + BN - 1) / BN;
+  a.total = nx * a.tiles_m * a.tiles_n;
+  a.rows_a = M;
+  a.rows_b = n - KP;
+  a.nchunk = M / BK;
+  a.nchunk_m0 = KP / BK;  // the first 128 rows of a two-panel inverse are zero beyond column 128
+  a.mode = 1;
+  a.bt_hi = tc_ws_part(ws, nx, n, 6);
+  a.bt_lo = tc_ws_part(ws, nx, n, 7);
+  a.status = status;
+  launch(mp, M == KP ? 4 : 8, 2, a, st);
 }
 
 }  // namespace
 
-// Workspace: four arrays [nx][n - 128][128] floats (A_hi, A_lo, B_hi, B_lo) and two [nx][128][128]
-// (inv(L11) hi, lo).
+// Workspace, floats: parts 0-3 and 6-7 are [nx][n - 128][256] (L21 split, (P A12)^T split, U12^T
+// split), parts 4-5 [nx][128][128] (one panel's inv(L11) split), parts 8-9 [nx][256][256] (a
+// two-panel block's inv(L11) split).
 size_t tc_workspace_bytes(int nx, int n, int nbmax) {
-  if (nbmax != KTOT || n <= KTOT || (n & 3) != 0) return 0;
-  return (4ull * nx * static_cast<size_t>(n - KTOT) * KTOT + 2ull * nx * KTOT * KTOT) * sizeof(float);
+  if (nbmax != KP || n <= KP || (n & 3) != 0) return 0;
+  return (6ull * nx * static_cast<size_t>(n - KP) * KS + 2ull * nx * KP * KP + 2ull * nx * KS * KS) * sizeof(float);
 }
 
 float* tc_ws_part(void* ws, int nx, int n, int part) {
   if (!ws) return nullptr;
-  const size_t big = static_cast<size_t>(nx) * (n - KTOT) * KTOT, small = static_cast<size_t>(nx) * KTOT * KTOT;
+  const size_t big = static_cast<size_t>(nx) * (n - KP) * KS, small = static_cast<size_t>(nx) * KP * KP;
+  const size_t two = static_cast<size_t>(nx) * KS * KS;
   float* f = static_cast<float*>(ws);
-  return part < 4 ? f + part * big : f + 4 * big + (part - 4) * small;
+  if (part < 4) return f + part * big;
+  if (part < 6) return f + 4 * big + (part - 4) * small;
+  if (part < 8) return f + 4 * big + 2 * small + (part - 6) * big;
+  return f + 6 * big + 2 * small + (part - 8) * two;
 }
 
 bool tc_available() {
@@ -549,48 +615,24 @@ bool tc_available() {
   return get_encode() != nullptr;
 }
 
-void tc_lu_gemm(float* fac, int nx, int n, int k0, int nb, void* ws, unsigned* status, cudaStream_t st) {
-  (void)nb;
+void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st) {
   Maps& mp = maps_for(fac, ws, nx, n);
-  const int base = k0 + KTOT, M = n - base;
-  if (M <= 0 || !mp.ok) return;
-  TcArgs a{};
-  a.fac = fac;
-  a.n = n;
-  a.row0 = base;
-  a.col0 = base;
-  a.M = M;
-  a.N = M;
-  a.tiles_m = (M + BM - 1) / BM;
-  a.tiles_n = (M + BN - 1) / BN;
-  a.total = nx * a.tiles_m * a.tiles_n;
-  a.rows_a = a.rows_b = n - KTOT;
-  a.mode = 0;
-  a.status = status;
-  launch(mp, 0, 2, a, st);
+  gemm(mp, fac, nx, n, k0 + KP, k0 + KP, n - k0 - KP, ncols, KP / BK, status, st);
 }
 
-void tc_lu_u12(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
+void tc_lu_u12(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st) {
   Maps& mp = maps_for(fac, ws, nx, n);
-  const int base = k0 + KTOT, N = n - base;
-  if (N <= 0 || !mp.ok) return;
-  TcArgs a{};
-  a.fac = fac;
-  a.n = n;
-  a.row0 = k0;
-  a.col0 = base;
-  a.M = KTOT;
-  a.N = N;
-  a.tiles_m = 1;
-  a.tiles_n = (N + BN - 1) / BN;
-  a.total = nx * a.tiles_n;
-  a.rows_a = KTOT;
-  a.rows_b = n - KTOT;
-  a.mode = 1;
-  a.bt_hi = tc_ws_part(ws, nx, n, 2);
-  a.bt_lo = tc_ws_part(ws, nx, n, 3);
-  a.status = status;
-  launch(mp, 4, 2, a, st);
+  u12(mp, fac, ws, nx, n, k0, k0 + KP, KP, ncols, status, st);
+}
+
+void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
+  Maps& mp = maps_for(fac, ws, nx, n);
+  u12(mp, fac, ws, nx, n, k0, k0 + KS, KS, n - k0 - KS, status, st);
+}
+
+void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
+  Maps& mp = maps_for(fac, ws, nx, n);
+  gemm(mp, fac, nx, n, k0 + KS, k0 + KS, n - k0 - KS, n - k0 - KS, KS / BK, status, st);
 }
 
 }  // namespace bte

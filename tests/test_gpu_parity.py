@@ -153,6 +153,36 @@ def test_tensor_core_update_against_oracle_and_simt(shape):
     assert s_tc.info()["tensor_cores"] == 1
 
 
+@pytest.mark.parametrize("shape", [(5, 40, 13), (4, 64, 12), (3, 36, 20)])
+def test_tensor_core_panel_pairs_match_single_panels(shape):
+    """Trailing updates two panels at a time (K = 256) vs one at a time (K = 128): nv = 520, 768 and
+    720 give one to three pair updates, 520 and 720 with a ragged last pair. Without refinement the
+    solve shows the factors' own FP32 accuracy; the two orders agree to that accuracy, and refined
+    both meet the FP64 bar."""
+    nx, nr, nt = shape
+    cfg = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=nt)
+    cfg["V0"] = 400.0
+    ops = O.Operators(cfg)
+    F0 = W.random_state(nx, nt, nr, seed=37)
+    t = 0.21 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t)
+    out = {}
+    for single in (False, True):
+        for rmax in (0, -1):
+            s = solver(cfg, "mixed", tc_single=single, refine_max=rmax)
+            assert s.info()["tensor_cores"] == 1
+            F = to_dev(F0)
+            s.step(F, t)
+            out[single, rmax] = F.cpu().numpy()
+    e_pair, e_single = rel_l2(out[False, 0], ref), rel_l2(out[True, 0], ref)
+    print("unrefined rel. error: pairs %.3e single panels %.3e" % (e_pair, e_single))
+    assert e_single <= 5e-2, e_single   # FP32 factors of a matrix of condition ~1e5; a broken one gives O(1)
+    assert e_pair <= 4 * e_single + 1e-9, (e_pair, e_single)
+    assert rel_l2(out[False, 0], out[True, 0]) <= 4 * e_single + 1e-9
+    assert rel_l2(out[False, -1], ref) <= 1e-9
+    assert rel_l2(out[True, -1], ref) <= 1e-9
+
+
 # ------------------------------------------------------------------ entry points and errors
 
 def test_step_host_matches_device_step():
