@@ -52,7 +52,6 @@ constexpr int STAGES = BTE_TC_STAGES;
 constexpr int A_BOX = BM * BK * 4;                // 16 KB
 constexpr int B_BOX = BN * BK * 4;                // 16 or 32 KB
 constexpr int STAGE_BYTES = 2 * A_BOX + 2 * B_BOX;  // A_hi, A_lo, B_hi, B_lo
-constexpr int TMEM_COLS = 2 * BN;                 // two accumulators
 #ifndef BTE_TC_CW
 #define BTE_TC_CW 32
 #endif
@@ -63,15 +62,13 @@ constexpr int CSWZ_MASK = CW == 32 ? 7 : 3;       // 16-byte chunk index ^= (row
 constexpr int CSWZ_SHIFT = CW == 32 ? 0 : 1;
 constexpr int CSLOTS = BTE_TC_CSLOTS;             // C staging slots
 constexpr int CSLOT_BYTES = BM * CW * 4;          // 16 or 8 KB
-constexpr int NCCHUNK = BN / CW;
 constexpr int NTHREADS = 192;
 constexpr long long kWaitCycles = 1ll << 32;     // ~2 s at 2 GHz
 constexpr unsigned kTimeoutBit = 8u;
 
-// instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9, 10-12 = 2),
-// both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// instruction descriptor, kind::tf32 (formed per tile shape in the kernel): D = F32 (bits 4-5 = 1),
+// A = B = TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28
 
 struct Smem {
   alignas(1024) unsigned char stage[STAGES][STAGE_BYTES];
@@ -113,10 +110,21 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
+// the same with cluster-scope acquire (arrivals from the other CTA of a pair)
+__device__ __forceinline__ bool mbar_try_cl(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait: false if the phase did not complete in time or the CTA is aborting.
-__device__ bool mbar_wait(Smem& s, uint64_t* b, uint32_t parity, unsigned* status) {
+__device__ bool mbar_wait(Smem& s, uint64_t* b, uint32_t parity, unsigned* status, bool cl = false) {
   const long long t0 = clock64();
-  while (!mbar_try(b, parity)) {
+  while (!(cl ? mbar_try_cl(b, parity) : mbar_try(b, parity))) {
     if (*reinterpret_cast<volatile int*>(&s.abort)) return false;
     if (clock64() - t0 > kWaitCycles) {
       atomicExch(&s.abort, 1);
@@ -165,17 +173,72 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   return d;
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-      ::"r"(tmem_d), "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+// D (+)= A B^T. CG = 1: one CTA, M = 128. CG = 2: the CTA pair of a cluster, M = 256 (each CTA
+// holds 128 rows of A and half of the N rows of B at the same shared-memory offsets, and receives
+// its 128 rows of D in its own tensor memory); issued by the even CTA only.
+template <int CG>
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  if constexpr (CG == 1)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
-               : "memory");
+// arrive on `bar` once the MMAs issued so far have completed: in this CTA (CG = 1), or at the same
+// offset in both CTAs of the pair (CG = 2)
+template <int CG>
+__device__ __forceinline__ void mma_commit_all(uint64_t* bar) {
+  if constexpr (CG == 1)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+  else
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            saddr(bar)),
+        "h"(static_cast<uint16_t>(3))
+        : "memory");
 }
+
+// arrive on `bar` of this CTA only
+template <int CG>
+__device__ __forceinline__ void mma_commit_own(uint64_t* bar) {
+  if constexpr (CG == 1)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+// shared::cluster address of the object at p's offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr(p)), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+
+// tile load into this CTA's shared memory whose completion is counted on the pair leader's barrier
+__device__ __forceinline__ void tma_load_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t cluster_bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(saddr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(cluster_bar)
+      : "memory");
+}
+
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -214,19 +277,32 @@ struct TcArgs {
   unsigned* status;
 };
 
+// CG = 1: one CTA per 128 x BN output tile. CG = 2: a cluster of two CTAs per 256 x 256 tile (each
+// CTA stages 128 rows of A and 128 of the 256 rows of B, the even CTA issues M = 256, N = 256 MMAs
+// over both CTAs' stages, each CTA's epilogue takes its 128 rows): twice the MMA work per staged
+// byte of the one-CTA tile.
+template <int CG>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
                    const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
                    const __grid_constant__ CUtensorMap mC, const TcArgs args) {
+  static_assert(CG == 1 || (CG == 2 && BN == 128), "a CTA pair stages 128 rows of B per CTA");
+  constexpr int TN = CG * BN, TM = CG * BM;  // output tile of the CTA (pair)
+  constexpr int NCC = TN / CW;               // C chunks per CTA and tile
+  constexpr uint32_t TCOLS = 2 * TN;         // two accumulators
+  constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                             ((uint32_t)(TM >> 4) << 24);
   const int total = args.total;
   unsigned* status = args.status;
   extern __shared__ unsigned char raw[];
   Smem& s = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rank = CG == 2 ? static_cast<int>(blockIdx.x & 1) : 0;  // CTA within the pair
+  const int cid = blockIdx.x / CG, ncl = gridDim.x / CG;            // tile scheduler unit
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) mbar_init(&s.full[i], 1), mbar_init(&s.empty[i], 1);
-    for (int i = 0; i < 2; ++i) mbar_init(&s.tfull[i], 1), mbar_init(&s.tempty[i], 4);
+    for (int i = 0; i < 2; ++i) mbar_init(&s.tfull[i], 1), mbar_init(&s.tempty[i], 4 * CG);
     for (int i = 0; i < CSLOTS; ++i) mbar_init(&s.cfull[i], 1);
     mbar_init(&s.drain, 1);
     s.abort = 0;
@@ -235,12 +311,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem_base)),
-                 "r"(TMEM_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (CG == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem_base)),
+                   "r"(TCOLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&s.tmem_base)),
+                   "r"(TCOLS));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  if constexpr (CG == 2) cluster_sync();  // both CTAs' barriers exist before any cross-CTA signal
+  else __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s.tmem_base;
   const int per_point = args.tiles_m * args.tiles_n;
@@ -249,45 +332,62 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {  // ---------------------------------------------------------------- producer
       int st = 0;
       uint32_t ph = 0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+      for (int t = cid; t < total; t += ncl) {
         const int p = t / per_point, r = t % per_point;
-        const int ya = p * args.rows_a + (r / args.tiles_n) * BM;
-        const int yb = p * args.rows_b + (r % args.tiles_n) * BN;
+        const int ya = p * args.rows_a + (r / args.tiles_n) * TM + rank * BM;
+        const int yb = p * args.rows_b + (r % args.tiles_n) * TN + rank * BN;
         const int nch = r < args.tiles_n ? args.nchunk_m0 : args.nchunk;
         bool ok = true;
         for (int c = 0; c < nch; ++c) {
-          if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status)) { ok = false; break; }
-          mbar_expect_tx(&s.full[st], STAGE_BYTES);
+          if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status, CG == 2)) { ok = false; break; }
           unsigned char* d = s.stage[st];
-          tma_load(d, &mAhi, c * BK, ya, &s.full[st]);
-          tma_load(d + A_BOX, &mAlo, c * BK, ya, &s.full[st]);
-          tma_load(d + 2 * A_BOX, &mBhi, c * BK, yb, &s.full[st]);
-          tma_load(d + 2 * A_BOX + B_BOX, &mBlo, c * BK, yb, &s.full[st]);
+          if constexpr (CG == 1) {
+            mbar_expect_tx(&s.full[st], STAGE_BYTES);
+            tma_load(d, &mAhi, c * BK, ya, &s.full[st]);
+            tma_load(d + A_BOX, &mAlo, c * BK, ya, &s.full[st]);
+            tma_load(d + 2 * A_BOX, &mBhi, c * BK, yb, &s.full[st]);
+            tma_load(d + 2 * A_BOX + B_BOX, &mBlo, c * BK, yb, &s.full[st]);
+          } else {
+            // both CTAs' bytes complete on the even CTA's barrier, which expects them all
+            if (rank == 0) mbar_expect_tx(&s.full[st], 2 * STAGE_BYTES);
+            const uint32_t bar = cluster_addr(&s.full[st], 0);
+            tma_load_pair(d, &mAhi, c * BK, ya, bar);
+            tma_load_pair(d + A_BOX, &mAlo, c * BK, ya, bar);
+            tma_load_pair(d + 2 * A_BOX, &mBhi, c * BK, yb, bar);
+            tma_load_pair(d + 2 * A_BOX + B_BOX, &mBlo, c * BK, yb, bar);
+          }
           s.issued += 1;
           if (++st == STAGES) st = 0, ph ^= 1u;
         }
         if (!ok) break;
       }
       // producer tail: every stage handed out must have been released by its MMAs
-      if (!*reinterpret_cast<volatile int*>(&s.abort))
+      if (!*reinterpret_cast<volatile int*>(&s.abort)) {
         for (int i = 0; i < STAGES; ++i) {
-          if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status)) break;
+          if (!mbar_wait(s, &s.empty[st], ph ^ 1u, status, CG == 2)) break;
           if (++st == STAGES) st = 0, ph ^= 1u;
         }
+      } else if (CG == 2) {
+        // after an abort this CTA cannot see its own loads complete (they count on the other
+        // CTA's barrier): give any still in flight time to land before the CTA exits
+        const long long t0 = clock64();
+        while (clock64() - t0 < (1ll << 21)) {
+        }
+      }
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0 && rank == 0) {  // ------------------------------------------------ MMA issuer
       int st = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       int consumed = 0;
-      for (int t = blockIdx.x; t < total; t += gridDim.x) {
-        if (!mbar_wait(s, &s.tempty[acc], aph ^ 1u, status)) break;
+      for (int t = cid; t < total; t += ncl) {
+        if (!mbar_wait(s, &s.tempty[acc], aph ^ 1u, status, CG == 2)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + acc * BN;
+        const uint32_t d = tmem + acc * TN;
         const int nch = t % per_point < args.tiles_n ? args.nchunk_m0 : args.nchunk;
         bool ok = true;
         for (int c = 0; c < nch; ++c) {
-          if (!mbar_wait(s, &s.full[st], ph, status)) { ok = false; break; }
+          if (!mbar_wait(s, &s.full[st], ph, status, CG == 2)) { ok = false; break; }
           ++consumed;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = saddr(s.stage[st]);
@@ -295,15 +395,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int k = 0; k < BK / 8; ++k) {
             const uint32_t off = k * 32;  // 8 tf32 = 32 bytes inside the 128-byte swizzle row
-            mma_tf32(d, sdesc(a1 + off), sdesc(b0 + off), (c | k) ? 1u : 0u);  // a_lo b_hi
-            mma_tf32(d, sdesc(a0 + off), sdesc(b1 + off), 1u);                 // a_hi b_lo
-            mma_tf32(d, sdesc(a0 + off), sdesc(b0 + off), 1u);                 // a_hi b_hi
+            mma_tf32<CG>(d, sdesc(a1 + off), sdesc(b0 + off), IDESC, (c | k) ? 1u : 0u);  // a_lo b_hi
+            mma_tf32<CG>(d, sdesc(a0 + off), sdesc(b1 + off), IDESC, 1u);                 // a_hi b_lo
+            mma_tf32<CG>(d, sdesc(a0 + off), sdesc(b0 + off), IDESC, 1u);                 // a_hi b_hi
           }
-          mma_commit(&s.empty[st]);
+          mma_commit_all<CG>(&s.empty[st]);
           if (++st == STAGES) st = 0, ph ^= 1u;
         }
         if (!ok) break;
-        mma_commit(&s.tfull[acc]);
+        mma_commit_all<CG>(&s.tfull[acc]);
         if (++acc == 2) acc = 0, aph ^= 1u;
       }
       // drain: loads issued but not consumed must land before the CTA exits
@@ -316,7 +416,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       // every MMA issued by this thread has retired once the drain barrier completes
-      mma_commit(&s.drain);
+      mma_commit_own<CG>(&s.drain);
       const long long t0 = clock64();
       while (!mbar_try(&s.drain, 0) && clock64() - t0 < kWaitCycles) {
       }
@@ -330,16 +430,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int trow = sub * 32 + lane;
     const bool leader = warp == 2 && lane == 0;
     const bool load_c = args.mode == 0;
-    auto cx = [&](int t, int ch) { return args.col0 + ((t % per_point) % args.tiles_n) * BN + CW * ch; };
-    auto cy = [&](int t) { return args.row0 + ((t % per_point) / args.tiles_n) * BM; };
+    auto cx = [&](int t, int ch) { return args.col0 + ((t % per_point) % args.tiles_n) * TN + CW * ch; };
+    auto cy = [&](int t) { return args.row0 + ((t % per_point) / args.tiles_n) * TM + rank * BM; };
     auto issue_c = [&](int t, int ch, int slot) {
       mbar_expect_tx(&s.cfull[slot], CSLOT_BYTES);
       tma_load3(s.cbuf[slot], &mC, cx(t, ch), cy(t), t / per_point, &s.cfull[slot]);
     };
     // C load number q (the q-th chunk of this CTA) goes to slot q % CSLOTS, phase (q / CSLOTS) & 1
     auto chunk_at = [&](int q, int& tq, int& chq) {
-      tq = blockIdx.x + (q / NCCHUNK) * gridDim.x;
-      chq = q % NCCHUNK;
+      tq = cid + (q / NCC) * ncl;
+      chq = q % NCC;
     };
     int c_issued = 0, c_done = 0;  // leader's count of C loads issued and waited for
     if (leader && load_c)
@@ -353,12 +453,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int acc = 0, g = 0;
     uint32_t aph = 0;
     bool stop = false;
-    for (int t = blockIdx.x; t < total && !stop; t += gridDim.x) {
+    for (int t = cid; t < total && !stop; t += ncl) {
       const int p = t / per_point, r = t % per_point;
-      const int row = (r / args.tiles_n) * BM + trow;
-      const int col0 = (r % args.tiles_n) * BN;
-      if (leader && !mbar_wait(s, &s.tfull[acc], aph, status)) atomicExch(&s.abort, 1);
-      for (int ch = 0; ch < NCCHUNK; ++ch, ++g) {
+      const int row = (r / args.tiles_n) * TM + rank * BM + trow;
+      const int col0 = (r % args.tiles_n) * TN;
+      if (leader && !mbar_wait(s, &s.tfull[acc], aph, status, CG == 2)) atomicExch(&s.abort, 1);
+      for (int ch = 0; ch < NCC; ++ch, ++g) {
         const int slot = g % CSLOTS;
         if (leader && load_c && !*reinterpret_cast<volatile int*>(&s.abort)) {
           if (mbar_wait(s, &s.cfull[slot], (g / CSLOTS) & 1, status)) ++c_done;
@@ -371,8 +471,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         uint32_t v[32];
-        if constexpr (CW == 32) tmem_ld32(tmem + acc * BN + ch * CW + ((sub * 32) << 16), v);
-        else tmem_ld16(tmem + acc * BN + ch * CW + ((sub * 32) << 16), v);
+        if constexpr (CW == 32) tmem_ld32(tmem + acc * TN + ch * CW + ((sub * 32) << 16), v);
+        else tmem_ld16(tmem + acc * TN + ch * CW + ((sub * 32) << 16), v);
         float4* cs = reinterpret_cast<float4*>(s.cbuf[slot] + trow * (CW * 4));
 #pragma unroll
         for (int j = 0; j < CW / 4; ++j) {
@@ -423,7 +523,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (stop) break;
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&s.tempty[acc]);
+      if (lane == 0) {
+        // the accumulator is free again (for a pair: counted on the even CTA, whose MMAs write it)
+        if constexpr (CG == 1) mbar_arrive(&s.tempty[acc]);
+        else mbar_arrive_remote(cluster_addr(&s.tempty[acc], 0));
+      }
       if (++acc == 2) acc = 0, aph ^= 1u;
     }
     if (leader) {
@@ -437,11 +541,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   }
 
+  __syncwarp();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
+  // a pair's MMAs write both CTAs' tensor memory and signal both CTAs' barriers: neither CTA frees
+  // its tensor memory or exits before the other is done
+  if constexpr (CG == 2) cluster_sync();
+  else __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    if constexpr (CG == 1)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
   }
 }
 
@@ -513,7 +624,9 @@ Maps& maps_for(float* fac, void* ws, int nx, int n) {
     maps.fac = fac;
     maps.nx = nx;
     maps.n = n;
-    cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tc_gemm_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(sizeof(Smem) + 1024));
+    cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(sizeof(Smem) + 1024));
   }
   return maps;
@@ -531,8 +644,48 @@ int sm_count() {
 
 void launch(const Maps& mp, int ia, int ib, const TcArgs& a, cudaStream_t st) {
   const int grid = a.total < sm_count() ? a.total : sm_count();
-  tc_gemm_kernel<<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1],
-                                                             mp.m[kMapC], a);
+  tc_gemm_kernel<1><<<grid, NTHREADS, sizeof(Smem) + 1024, st>>>(mp.m[ia], mp.m[ia + 1], mp.m[ib], mp.m[ib + 1],
+                                                                mp.m[kMapC], a);
+}
+
+cudaLaunchConfig_t pair_config(int clusters, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t c{};
+  c.gridDim = dim3(2 * clusters);
+  c.blockDim = dim3(NTHREADS);
+  c.dynamicSmemBytes = sizeof(Smem) + 1024;
+  c.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  c.attrs = attr;
+  c.numAttrs = 1;
+  return c;
+}
+
+// CTA pairs that can be resident at once (0: the pair kernel is not available)
+int pair_clusters() {
+  static int n = -1;
+  if (n < 0) {
+    n = 0;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t c = pair_config(sm_count() / 2, nullptr, attr);
+    int k = 0;
+    if (cudaFuncSetAttribute(tc_gemm_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(sizeof(Smem) + 1024)) == cudaSuccess &&
+        cudaOccupancyMaxActiveClusters(&k, tc_gemm_kernel<2>, &c) == cudaSuccess)
+      n = k;
+    cudaGetLastError();
+  }
+  return n;
+}
+
+// C -= A B^T over 256 x 256 tiles, one CTA pair per tile (mode 0 only)
+void launch_pair(const Maps& mp, const TcArgs& a, cudaStream_t st) {
+  const int clusters = a.total < pair_clusters() ? a.total : pair_clusters();
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t c = pair_config(clusters, st, attr);
+  cudaLaunchKernelEx(&c, tc_gemm_kernel<2>, mp.m[0], mp.m[1], mp.m[6], mp.m[7], mp.m[kMapC], a);
 }
 
 // C -= A B^T over the block of C at (row0, col0) of every point: A = L21 split (parts 0, 1), B =
@@ -611,7 +764,7 @@ bool tc_available() {
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&p, dev) != cudaSuccess) return false;
   if (p.major != 10) return false;
   cudaFuncAttributes a;
-  if (cudaFuncGetAttributes(&a, tc_gemm_kernel) != cudaSuccess) return false;
+  if (cudaFuncGetAttributes(&a, tc_gemm_kernel<1>) != cudaSuccess) return false;
   return get_encode() != nullptr;
 }
 
@@ -632,7 +785,24 @@ void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* statu
 
 void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
   Maps& mp = maps_for(fac, ws, nx, n);
-  gemm(mp, fac, nx, n, k0 + KS, k0 + KS, n - k0 - KS, n - k0 - KS, KS / BK, status, st);
+  const int M = n - k0 - KS;
+  if (M <= 0 || !mp.ok) return;
+  if (pair_clusters() < 1) {
+    gemm(mp, fac, nx, n, k0 + KS, k0 + KS, M, M, KS / BK, status, st);
+    return;
+  }
+  TcArgs a{};
+  a.fac = fac;
+  a.n = n;
+  a.row0 = a.col0 = k0 + KS;
+  a.M = a.N = M;
+  a.tiles_m = a.tiles_n = (M + 2 * BM - 1) / (2 * BM);
+  a.total = nx * a.tiles_m * a.tiles_n;
+  a.rows_a = a.rows_b = n - KP;
+  a.nchunk = a.nchunk_m0 = KS / BK;
+  a.mode = 0;
+  a.status = status;
+  launch_pair(mp, a, st);
 }
 
 }  // namespace bte
