@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 1.10
 # the kernels captured with ncu on this workload (the commands are in profiles/); the per-launch
 # figure reported is scaled to the step's average launch by the algorithmic bytes. Remove an entry
 # when its kernel changes.
-TRAFFIC_K0 = {"lu_gemm": 2.391065e9 + 1.829609e9, "lu_panel": 402.5408e6 + 122.445056e6}
+TRAFFIC_K0 = {"lu_panel": 402.5408e6 + 122.445056e6}
 
 
 def load_peaks():
@@ -113,12 +113,29 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------------- work model
 
-def algorithmic(cfg, precision, kernel, tc):
+def tc_pairs(nv):
+    """The tensor-core factorisation in panel pairs: (k0, width of the second panel, trailing
+    columns right of the pair) per pair, as the library orders it."""
+    out = []
+    for k0 in range(0, nv, 256):
+        if k0 + min(128, nv - k0) >= nv:
+            break
+        kb2 = min(128, nv - k0 - 128)
+        out.append((k0, kb2, max(0, nv - k0 - 256)))
+    return out
+
+
+def algorithmic(cfg, precision, kernel, tc, pair=True):
     """(amount, unit, bound) of the algorithmic work of one step for a kernel class (per-step sums
     over its launches; per unit):
       lu_panel     read + write of every outer panel once: 2 * 4 B * (Nv - k0) * 128 per point;
-      lu_gemm      trailing updates, 2 M^2 128 flop per point and panel (M = Nv - k0 - 128);
-      lu_swap_trsm U12 = inv(L11) P A12, 2 * 128 * M * 128 flop per point and panel;
+      lu_gemm      trailing updates, 2 M^2 128 flop per point and panel (M = Nv - k0 - 128); on the
+                   tensor cores in panel pairs: 2 M1 kb2 128 for the first panel's update of the
+                   second panel's columns (M1 = Nv - k0 - 128) plus 2 M2^2 256 for the pair's update
+                   (M2 = Nv - k0 - 256);
+      lu_swap_trsm U12 = inv(L11) P A12, 2 * 128 * M * 128 flop per point and panel; in pairs
+                   2 * 128 * kb2 * 128 plus 2 * 3 * 128^2 * M2 (the nonzero blocks of the pair's
+                   inv(L11)) plus 2 * 128^3 for that inverse's off-diagonal block;
       lu_solve     one read of the FP32 factors per solve launch (4 B * Nv^2 per point);
       x_apply_q    the FP64 Q stream (8 B Nv Nx^2) plus Y in/out, per half step;
       v_form       write of the per-point matrices plus the K_C/K_A read;
@@ -132,8 +149,14 @@ def algorithmic(cfg, precision, kernel, tc):
     if kernel == "lu_panel":
         return sum(2.0 * esz * (nv - k0) * kb for k0, kb in panels) * nx, "byte", "hbm"
     if kernel == "lu_gemm":
+        if tc and pair:
+            return sum(2.0 * (nv - k0 - 128) * kb2 * 128 + 2.0 * m2 ** 2 * 256
+                       for k0, kb2, m2 in tc_pairs(nv)) * nx, "flop", "tensor"
         return sum(2.0 * (nv - k0 - kb) ** 2 * kb for k0, kb in panels) * nx, "flop", "tensor" if tc else "alu"
     if kernel == "lu_swap_trsm":
+        if tc and pair:
+            return sum(2.0 * 128 * kb2 * 128 + (2.0 * 3 * 128 ** 2 * m2 + 2.0 * 128 ** 3 if m2 else 0.0)
+                       for k0, kb2, m2 in tc_pairs(nv)) * nx, "flop", "tensor"
         return sum(2.0 * kb * (nv - k0 - kb) * kb for k0, kb in panels) * nx, "flop", "tensor" if tc else "alu"
     if kernel == "lu_solve":
         return float(esz) * nx * nv * nv, "byte/launch", "hbm"
@@ -154,7 +177,14 @@ def traffic_per_launch(cfg, kernel, launches_per_step):
     nv = cfg["nr"] * cfg["ntheta"]
     nb = 128
     if kernel == "lu_gemm":
-        per = [(nv - k0 - nb) ** 2 for k0 in range(0, nv - nb, nb)]
+        # the k0 = 0 pair launch (C read and written once: 2 M2^2 words) scales the pair launches by
+        # M2^2 and the single-panel-column launches by their M1 x kb2 block
+        per = []
+        for k0, kb2, m2 in tc_pairs(nv):
+            per.append((nv - k0 - 128) * kb2)
+            if m2:
+                per.append(m2 ** 2)
+        return TRAFFIC_K0[kernel] * (sum(per) / len(per)) / (nv - 256) ** 2
     else:
         per = [nv - k0 for k0 in range(0, nv, nb)]
     return TRAFFIC_K0[kernel] * (sum(per) / len(per)) / per[0]
@@ -266,6 +296,10 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
 
     cfg = W.WORKLOADS[WORKLOAD]
+    if args.nx:
+        # fewer collocation points of the same velocity grid: the small case that profiler
+        # captures use (not a bench line)
+        cfg = W.scaled(cfg, nx=args.nx)
     dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
     dt = cfg["dt_s"]
     peaks = load_peaks()
@@ -575,6 +609,8 @@ def main():
                          "or the adjoint-gradient check")
     ap.add_argument("--adjoint-steps", type=int, default=0, help="adjoint workload: steps (0 = one RF cycle)")
     ap.add_argument("--batched-fp64", action="store_true", help="batched workload: also time the FP64 batch")
+    ap.add_argument("--nx", type=int, default=0,
+                    help="profiling only: run the default workload with this many x points instead of 128")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
