@@ -42,7 +42,7 @@ FP64_PEAK_TFLOPS = 1.10
 # the kernels captured with ncu on this workload (the commands are in profiles/); the per-launch
 # figure reported is scaled to the step's average launch by the algorithmic bytes. Remove an entry
 # when its kernel changes.
-TRAFFIC_K0 = {"lu_panel": 402.5408e6 + 122.445056e6}
+TRAFFIC_K0 = {"lu_gemm": 2.584127e9 + 1.590629e9, "lu_panel": 402.5408e6 + 122.445056e6}
 
 
 def load_peaks():
