@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 from paper_2502_16555_gb300 import workloads as W  # noqa: E402
 
 WORKLOAD = "medium_nx128_nr64_nt32"
+LARGEST = "largest_nx256_nr128_nt32"   # the largest single discharge: a parity and timing case
 METRIC = "DOF-updates/s per bte_step (mixed vs plain FP64, same GPU) at rel-L2 <=1e-6 vs FP64"
 UNIT = "DOF-updates/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -190,7 +191,7 @@ def traffic_per_launch(cfg, kernel, launches_per_step):
     return TRAFFIC_K0[kernel] * (sum(per) / len(per)) / per[0]
 
 
-def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc, sweeps=None):
+def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc, sweeps=None, measured=True):
     amount, unit, bound = algorithmic(cfg, precision, kernel, tc)
     ms, launches = prof.get(kernel, (0.0, 0))
     if amount is None or launches == 0 or ms <= 0:
@@ -214,15 +215,16 @@ def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc, sweeps=None):
         achieved, peak, u = rate / 1e12, FP32_SIMT_PEAK_TFLOPS, "TFLOP/s"
         src = "FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
     return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
-            "frac": achieved / peak, "traffic": traffic_per_launch(cfg, kernel, launches / steps),
+            "frac": achieved / peak,
+            "traffic": traffic_per_launch(cfg, kernel, launches / steps) if measured else None,
             "launches_per_step": launches / steps, "working_launches_per_step": eff / steps,
             "ms_per_step": ms / steps, "peak_source": src}
 
 
-def rooflines(cfg, precision, prof, steps, peaks, tc, sweeps=None):
+def rooflines(cfg, precision, prof, steps, peaks, tc, sweeps=None, measured=True):
     out = {}
     for k in prof:
-        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc, sweeps)
+        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc, sweeps, measured)
         if r:
             out[k] = r
     dom = max(out, key=lambda k: out[k]["ms_per_step"])
@@ -231,7 +233,7 @@ def rooflines(cfg, precision, prof, steps, peaks, tc, sweeps=None):
 
 # ---------------------------------------------------------------------------------- CPU oracle leg
 
-def oracle_sample(cfg, budget_s=20.0):
+def oracle_sample(cfg, budget_s=20.0, name=WORKLOAD):
     """Time the oracle (as it stands) on the host: one full x half step plus the velocity solve of a
     bounded subset of points; the per-step time is 2 t_x + (Nx/k) t_v(k)."""
     from oracle import bte as O
@@ -251,7 +253,7 @@ def oracle_sample(cfg, budget_s=20.0):
     dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
     cores = len(os.sched_getaffinity(0))
     return {"value": dof / step_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{WORKLOAD}: 1 full x half step ({tx:.2f} s) + dense v-solves of {k}/{cfg['nx']} points "
+            "sample": f"{name}: 1 full x half step ({tx:.2f} s) + dense v-solves of {k}/{cfg['nx']} points "
                       f"({tv:.2f} s), extrapolated to one step = {step_s:.2f} s; numpy/LAPACK on {cores} host threads"}
 
 
@@ -295,7 +297,8 @@ def run_ours(args, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
-    cfg = W.WORKLOADS[WORKLOAD]
+    name = args.workload if args.workload in (WORKLOAD, LARGEST) else WORKLOAD
+    cfg = W.WORKLOADS[name]
     if args.nx:
         # fewer collocation points of the same velocity grid: the small case that profiler
         # captures use (not a bench line)
@@ -365,7 +368,7 @@ def run_ours(args, rank, world):
     # ---- the structure-exploiting velocity solve (block tridiagonal in l), both precisions, from the
     # same state for the same steps; accuracy against the dense FP64 state after the same steps
     structured = None
-    if not args.no_structured:
+    if not args.no_structured and cfg["nr"] <= 64:
         structured = {}
         n_chk = args.warmup + args.steps
         for prec in ("mixed", "fp64"):
@@ -404,7 +407,9 @@ def run_ours(args, rank, world):
         e2e = {"value": world * dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * dof,
                "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"}
 
-    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc, sweeps=sweeps)
+    # the measured DRAM traffic was captured on the default workload only
+    measured = name == WORKLOAD and not args.nx
+    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc, sweeps=sweeps, measured=measured)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -414,9 +419,10 @@ def run_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "tf32x3+f64" if prof["lu_gemm"][1] and tc else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": cfg["nx"], "nr": cfg["nr"], "ntheta": cfg["ntheta"],
+        "config": {"workload": name, "nx": cfg["nx"], "nr": cfg["nr"], "ntheta": cfg["ntheta"],
                    "nv": cfg["nr"] * cfg["ntheta"], "dof": dof, "precision": "mixed",
-                   "l2": "working set > L2: 2.1 GB of per-point FP32 factors streamed every step",
+                   "l2": "working set > L2: %.1f GB of per-point FP32 factors streamed every step"
+                         % (4.0 * cfg["nx"] * (cfg["nr"] * cfg["ntheta"]) ** 2 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "fp64": fp64,
         "speedup_mixed_over_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
@@ -429,7 +435,7 @@ def run_ours(args, rank, world):
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
     }
     if world == 1 and not args.no_cpu:
-        out["cpu_baseline"] = oracle_sample(cfg)
+        out["cpu_baseline"] = oracle_sample(cfg, name=name)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -604,9 +610,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-structured", action="store_true", help="skip the block-tridiagonal solve legs")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batched64_uneven", "adjoint_nx64_nr32_nt16"],
-                    help="the headline single discharge (default), the 64 uneven discharges in one graph, "
-                         "or the adjoint-gradient check")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, LARGEST, "batched64_uneven", "adjoint_nx64_nr32_nt16"],
+                    help="the headline single discharge (default), the largest single discharge (Nv = 4096; "
+                         "use a few steps: its FP64 leg takes seconds per step), the 64 uneven discharges "
+                         "in one graph, or the adjoint-gradient check")
     ap.add_argument("--adjoint-steps", type=int, default=0, help="adjoint workload: steps (0 = one RF cycle)")
     ap.add_argument("--batched-fp64", action="store_true", help="batched workload: also time the FP64 batch")
     ap.add_argument("--nx", type=int, default=0,

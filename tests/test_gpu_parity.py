@@ -129,6 +129,46 @@ def test_medium_workload_one_step(precision):
     assert rel_l2(ne.cpu().numpy(), ne_r) <= (1e-10 if precision == "fp64" else 1e-8)
 
 
+def v_result_at(ops, F, j):
+    """The velocity-step result f*[j] at an interior point j recovered from F = S_x f* (the second
+    x half step): per ordinate a and eigen-index i the half step solves
+    (I + dt/2 lam_i mu_a D_x) y = Y* on every row but the inflow row, so Y*[j] =
+    Y'[j] + dt/2 mu_a lam (D_x[j] Y') with Y' the eigen-coefficients of F; f*[j] = Y*[j] U^T."""
+    out = np.empty((ops.nt, ops.nr))
+    for a in range(ops.nt):
+        Yp = F[:, a, :] @ ops.Uinv.T
+        out[a] = (Yp[j] + 0.5 * ops.dt * ops.mu[a] * ops.lam * (ops.Dx[j] @ Yp)) @ ops.U.T
+    return out
+
+
+def test_largest_workload_one_step_sampled_points():
+    """Nx=256, Nr=128, Ntheta=32 (Nv = 4096), the mixed path as the bench runs it, one step at the
+    field maximum. The oracle cannot afford all 256 dense 4096 x 4096 solves in a test, so at five
+    interior points the velocity-step result is recovered from the GPU's output through the forward
+    x operator and compared with the oracle's own x half step and dense solve at that point; the
+    whole state is compared with the FP64 GPU path."""
+    cfg = W.WORKLOADS["largest_nx256_nr128_nt32"]
+    ops = O.Operators(cfg)
+    F0 = ops.initial_state()
+    t = 0.25 / W.RF_FREQ_HZ - 0.5 * cfg["dt_s"]
+    E = ops.field(t + 0.5 * cfg["dt_s"])
+    G = ops.x_halfstep(F0)
+    s = solver(cfg, "mixed")
+    assert s.info()["tensor_cores"] == 1
+    F = to_dev(F0)
+    s.step(F, t)
+    Fm = F.cpu().numpy()
+    del s, F
+    for j in (1, 64, 127, 200, 254):
+        ref = np.linalg.solve(ops.v_matrix(E[j]), G[j].reshape(-1)).reshape(ops.nt, ops.nr)
+        err = rel_l2(v_result_at(ops, Fm, j), ref)
+        assert err <= 1e-8, (j, err)
+    s64 = solver(cfg, "fp64")
+    F = to_dev(F0)
+    s64.step(F, t)
+    assert rel_l2(Fm, F.cpu().numpy()) <= 1e-9
+
+
 # ------------------------------------------------------------------ tensor-core trailing update
 
 @pytest.mark.parametrize("shape", [(4, 32, 8), (6, 24, 16), (5, 40, 13)])
