@@ -60,6 +60,38 @@ __global__ void x_apply_q_kernel(const double* __restrict__ Q, const double* __r
   }
 }
 
+// The same for even nx: each warp takes 4 rows at a time in 16-byte loads, so a lane has 8 loads in
+// flight per pass (nx = 128) and the Q stream keeps the memory system busy.
+__global__ void x_apply_q2_kernel(const double* __restrict__ Q, const double* __restrict__ Y,
+                                  double* __restrict__ Y2, int nx) {
+  extern __shared__ double ys[];
+  const size_t b = blockIdx.x;
+  const double* y = Y + b * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) ys[i] = y[i];
+  __syncthreads();
+  const int h = nx >> 1;  // 16-byte pairs per row
+  const double2* Qb = reinterpret_cast<const double2*>(Q + b * nx * nx);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r0 = 4 * warp; r0 < nx; r0 += 4 * nw) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+    for (int c = lane; c < h; c += 32) {
+      double2 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        q[u] = r0 + u < nx ? __ldg(Qb + static_cast<size_t>(r0 + u) * h + c) : make_double2(0.0, 0.0);
+      const double y0 = ys[2 * c], y1 = ys[2 * c + 1];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] = fma(q[u].y, y1, fma(q[u].x, y0, s[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+    if (lane < 4 && r0 + lane < nx) Y2[b * nx + r0 + lane] = lane == 0 ? s[0] : lane == 1 ? s[1] : lane == 2 ? s[2] : s[3];
+  }
+}
+
 // F[x][a][k] = sum_i U[k][i] Y2[a][i][x]; flags non-finite results.
 __global__ void x_from_eigen_kernel(const double* __restrict__ Y2, const double* __restrict__ U,
                                     double* __restrict__ F, int nx, int nt, int nr,
@@ -244,7 +276,10 @@ void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, i
 
 void launch_x_apply_q(const double* Q, const double* Y, double* Y2, int nx, int nt, int nr,
                       cudaStream_t st) {
-  x_apply_q_kernel<<<nt * nr, 256, sizeof(double) * nx, st>>>(Q, Y, Y2, nx);
+  if ((nx & 1) == 0)
+    x_apply_q2_kernel<<<nt * nr, 256, sizeof(double) * nx, st>>>(Q, Y, Y2, nx);
+  else
+    x_apply_q_kernel<<<nt * nr, 256, sizeof(double) * nx, st>>>(Q, Y, Y2, nx);
 }
 
 void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, int nt, int nr,
