@@ -226,6 +226,63 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
 bte_status bte_adjoint_gradient(const bte_handle* h, const double* SC_dev, const double* SA_dev, double h_eV,
                                 double* grad_out);
 
+/* ---- Self-consistent field, ions, fully-implicit electrons (Section 2.3, Section 3.4) ----------
+ * n_i is the ion number density [m^-3] at the nx collocation points (device, FP64); F the electron
+ * state as for bte_step. None of these entry points changes bte_step; they allocate their device
+ * operators (the nx x nx field and ion matrices) on first use and bte_step_implicit its work
+ * vectors ((restart + 10) x nx x Nv doubles) on first use or when the restart grows. */
+
+/* Ion transport coefficients as n0 times the mobility [1/(V m s)] and n0 times the diffusion
+ * coefficient [1/(m s)] (the parameter table of Section 4; defaults 4.65e21 and 2.07e20). mu >= 0,
+ * D > 0, else BTE_EINVAL. */
+bte_status bte_set_ion_transport(bte_handle* h, double n0_mu_i, double n0_D_i);
+
+/* E_dev[nx] = L (n_i - u^T F) + V0 sin(2 pi f t) E_1 (eqs. "hybrid_discrete_c", "voltage_bc"): the
+ * field of Gauss's law d^2V/dx^2 = -(e/eps0)(n_i - n_e) on the collocation points with
+ * V(0, t) = V0 sin(2 pi f t), V(L) = 0, E = -D_x V. ni_dev may be NULL (no ions). Enqueued on the
+ * handle's stream (no synchronisation). */
+bte_status bte_field(bte_handle* h, const double* F_dev, const double* ni_dev, double t_s, double V0,
+                     double freq_Hz, double* E_dev);
+
+/* The ion step of eq. "fluid_step": n_i <- n_i^{n+1} solving
+ * (n^{n+1} - n^n)/dt + D_x J(n^{n+1}) = n0 k_i n_e (F^n), J = mu_i E^n n - D_i D_x n, with E^n the
+ * field of (n_i^n, F^n) at t_s and the wall fluxes of eq. "fl_ion_bc" (outflow only) as the first
+ * and last rows. ni_dev is updated in place only on success (BTE_ESINGULAR leaves it). Synchronises
+ * the handle's stream. */
+bte_status bte_ion_step(bte_handle* h, double* ni_dev, const double* F_dev, double t_s, double V0,
+                        double freq_Hz);
+
+/* One semi-implicit electron step with the self-consistent field (eqs. "bte_semi_implicit" with
+ * "bte_semi_implicit_efield"): after the first x half step E^{1/2} = L (n_i - u^T F^{n+1/2}) plus
+ * the electrode field at t_s + dt/2; then the per-point solves with that field, refinement and the
+ * second x half step as in bte_step. ni_dev is required (zeros for no ions); E_out_dev (may be NULL)
+ * receives E^{1/2}. Same error contract as bte_step. Synchronises the handle's stream. */
+bte_status bte_step_sc(bte_handle* h, double* F_dev, const double* ni_dev, double t_s, double V0, double freq_Hz,
+                       double* E_out_dev);
+
+/* Options and report of bte_step_implicit (zero fields take the defaults). */
+typedef struct {
+  double newton_rtol;  /* stop when |R(F)| <= newton_rtol |F^n| (default 1e-10) */
+  int newton_max;      /* Newton iterations (default 8) */
+  int gmres_restart;   /* GMRES basis size per Newton iteration, <= 200 (default 30) */
+  double gmres_rtol;   /* inner tolerance relative to |R| (default 1e-3) */
+  int newton_iters;    /* out: Newton iterations taken */
+  int gmres_iters;     /* out: GMRES iterations, all Newton iterations together */
+  double residual;     /* out: final |R| / |F^n| */
+} bte_implicit_opts;
+
+/* One fully-implicit electron step (eqs. "bte_fully_implicit"): F <- the root of
+ * R(F) = F - F^n + dt [A_x F D_x^T - P_O C P_S F - P_O A_v P_S (E(F) . F)], E(F) the field of
+ * (n_i, u^T F) at t_s + dt, with the zero-inflow rows R = F. Newton with backtracking from the
+ * semi-implicit self-consistent step's result; each Newton system by GMRES on the Jacobian action
+ * of eq. "1dbte_jac_action", right-preconditioned by the semi-implicit step's linear map at the
+ * iterate's field (its per-point factors formed once per Newton iteration). ni_dev is required;
+ * opts may be NULL.
+ * BTE_ENOCONV if Newton stops above newton_rtol; F is written only on success. Synchronises the
+ * handle's stream. */
+bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev, double t_s, double V0,
+                             double freq_Hz, bte_implicit_opts* opts);
+
 /* ---- Batched stepping of independent discharges ------------------------------------------------
  * Many discharges with uneven grids (nx, nr, ntheta), pressures and cross sections, stepped
  * together: every instance is an ordinary handle (its own operators, buffers and precision, all on

@@ -35,7 +35,8 @@ EXPORTS = ("bte_create", "bte_set_cross_sections", "bte_init_maxwellian", "bte_s
            "bte_step_host", "bte_moments", "bte_get_operator", "bte_get_info", "bte_profile",
            "bte_destroy", "bte_last_error", "bte_init_maxwellian_static", "bte_batch_create",
            "bte_batch_run", "bte_batch_get_info", "bte_batch_destroy", "bte_batch_last_error",
-           "bte_step_adjoint", "bte_adjoint_gradient")
+           "bte_step_adjoint", "bte_adjoint_gradient", "bte_set_ion_transport", "bte_field",
+           "bte_ion_step", "bte_step_sc", "bte_step_implicit")
 BATCH_AUTOTUNE = 1
 KERNELS = ("x_to_eigen", "x_apply_q", "x_from_eigen", "v_form", "lu_panel", "lu_swap_trsm", "lu_gemm",
            "lu_solve", "residual", "other")
@@ -53,6 +54,12 @@ class Process(C.Structure):
     _fields_ = [("kind", C.c_int), ("form", C.c_int), ("threshold_eV", C.c_double),
                 ("scale", C.c_double), ("sigma0", C.c_double), ("n_tab", C.c_int),
                 ("eps_eV", C.POINTER(C.c_double)), ("sigma_m2", C.POINTER(C.c_double))]
+
+
+class ImplicitOpts(C.Structure):
+    _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("gmres_restart", C.c_int),
+                ("gmres_rtol", C.c_double), ("newton_iters", C.c_int), ("gmres_iters", C.c_int),
+                ("residual", C.c_double)]
 
 
 class Info(C.Structure):
@@ -97,6 +104,11 @@ def load(path: str = LIB_PATH):
     lib.bte_batch_destroy.argtypes = [vp]
     lib.bte_step_adjoint.argtypes = [vp, vp, vp, d, d, d, vp, d, vp, vp]
     lib.bte_adjoint_gradient.argtypes = [vp, vp, vp, d, pd]
+    lib.bte_set_ion_transport.argtypes = [vp, d, d]
+    lib.bte_field.argtypes = [vp, vp, vp, d, d, d, vp]
+    lib.bte_ion_step.argtypes = [vp, vp, vp, d, d, d]
+    lib.bte_step_sc.argtypes = [vp, vp, vp, d, d, d, vp]
+    lib.bte_step_implicit.argtypes = [vp, vp, vp, d, d, d, C.POINTER(ImplicitOpts)]
     lib.bte_batch_last_error.argtypes = [vp]
     lib.bte_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -225,6 +237,50 @@ class Solver:
             raise ValueError("E must be a float64 CUDA tensor with nx entries")
         self._check(self.lib.bte_step(self.h, _ptr(self._f(F)), _ptr(E), float(t), float(V0), float(freq)))
         return F
+
+    # ---- self-consistent field, ions, fully-implicit electrons
+    def _nx_vec(self, v, name):
+        if v is not None and not (v.is_cuda and v.dtype == self.torch.float64 and v.numel() == self.nx
+                                  and v.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor with nx entries")
+        return v
+
+    def set_ion_transport(self, n0_mu_i: float, n0_D_i: float):
+        self._check(self.lib.bte_set_ion_transport(self.h, float(n0_mu_i), float(n0_D_i)))
+
+    def field(self, F, ni, t: float, V0=None, freq=None):
+        """E = L (n_i - u^T F) + V(0, t) E_1 at the collocation points (a new CUDA tensor)."""
+        V0 = self.cfg["V0"] if V0 is None else V0
+        freq = self.cfg["freq_Hz"] if freq is None else freq
+        E = self.torch.empty(self.nx, dtype=self.torch.float64, device=self.device)
+        self._check(self.lib.bte_field(self.h, _ptr(self._f(F)), _ptr(self._nx_vec(ni, "ni")), float(t),
+                                       float(V0), float(freq), _ptr(E)))
+        return E
+
+    def ion_step(self, ni, F, t: float, V0=None, freq=None):
+        V0 = self.cfg["V0"] if V0 is None else V0
+        freq = self.cfg["freq_Hz"] if freq is None else freq
+        self._check(self.lib.bte_ion_step(self.h, _ptr(self._nx_vec(ni, "ni")), _ptr(self._f(F)), float(t),
+                                          float(V0), float(freq)))
+        return ni
+
+    def step_sc(self, F, ni, t: float, V0=None, freq=None, E_out=None):
+        V0 = self.cfg["V0"] if V0 is None else V0
+        freq = self.cfg["freq_Hz"] if freq is None else freq
+        self._check(self.lib.bte_step_sc(self.h, _ptr(self._f(F)), _ptr(self._nx_vec(ni, "ni")), float(t),
+                                         float(V0), float(freq), _ptr(self._nx_vec(E_out, "E_out"))))
+        return F
+
+    def step_implicit(self, F, ni, t: float, V0=None, freq=None, newton_rtol=0.0, newton_max=0,
+                      gmres_restart=0, gmres_rtol=0.0):
+        """One fully-implicit step; returns (newton_iters, gmres_iters, relative residual)."""
+        V0 = self.cfg["V0"] if V0 is None else V0
+        freq = self.cfg["freq_Hz"] if freq is None else freq
+        o = ImplicitOpts(newton_rtol=newton_rtol, newton_max=newton_max, gmres_restart=gmres_restart,
+                         gmres_rtol=gmres_rtol)
+        self._check(self.lib.bte_step_implicit(self.h, _ptr(self._f(F)), _ptr(self._nx_vec(ni, "ni")), float(t),
+                                               float(V0), float(freq), C.byref(o)))
+        return o.newton_iters, o.gmres_iters, o.residual
 
     def run(self, F, n_steps: int, t: float, V0=None, freq=None):
         V0 = self.cfg["V0"] if V0 is None else V0

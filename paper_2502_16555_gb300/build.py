@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libbte.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["assembly.cpp", "bte_api.cu", "bte_xstep.cu", "bte_lu.cu", "bte_tc.cu", "bte_noalloc.cu", "bte_batch.cu", "bte_adjoint.cu", "bte_struct.cu"]
+SOURCES = ["assembly.cpp", "bte_api.cu", "bte_xstep.cu", "bte_lu.cu", "bte_tc.cu", "bte_noalloc.cu", "bte_batch.cu", "bte_adjoint.cu", "bte_struct.cu", "bte_hybrid.cu"]
 
 
 def nvcc():

@@ -680,6 +680,35 @@ std::string assemble_kc_only(const HostOps& o, const std::vector<Process>& procs
   return e;
 }
 
+std::string assemble_field(const HostOps& o, std::vector<double>& Lop, std::vector<double>& E1) {
+  const int nx = o.nx;
+  // Dirichlet Laplacian: D_x D_x with the wall rows replaced by V itself
+  std::vector<double> A(static_cast<size_t>(nx) * nx, 0.0), Ainv(static_cast<size_t>(nx) * nx);
+  for (int i = 1; i + 1 < nx; ++i)
+    for (int j = 0; j < nx; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < nx; ++k) s += o.Dx[i * nx + k] * o.Dx[k * nx + j];
+      A[i * nx + j] = s;
+    }
+  A[0] = 1.0;
+  A[static_cast<size_t>(nx) * nx - 1] = 1.0;
+  if (!invert(A, nx, Ainv.data())) return "the Dirichlet Laplacian is singular";
+  // V = Ainv b with b = -(e/eps0) rho inside and the wall voltages on rows 0, nx-1: Lop takes the
+  // interior columns of Ainv scaled by -e/eps0, E1 its column 0; then E = -D_x V
+  const double c = -kE / kEps0;
+  Lop.assign(static_cast<size_t>(nx) * nx, 0.0);
+  E1.assign(nx, 0.0);
+  for (int i = 0; i < nx; ++i) {
+    for (int j = 0; j < nx; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < nx; ++k) s += o.Dx[i * nx + k] * Ainv[k * nx + j];
+      if (j == 0) E1[i] = -s;
+      else if (j + 1 < nx) Lop[i * nx + j] = -c * s;
+    }
+  }
+  return "";
+}
+
 std::vector<double> maxwellian_coeffs(const HostOps& o, double Te_eV) {
   const int nr = o.nr;
   Spline sp(nr, o.vmax);

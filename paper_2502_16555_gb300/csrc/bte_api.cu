@@ -100,9 +100,119 @@ bool device_ready(bte_handle* h) {
   return true;
 }
 
+// Velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system"): out_i = A_i^-1 in_i at
+// every point, A_i = I - dt (K_C + E_i K_A) with E_i = E_dev[i] (or Eu when E_dev is NULL). With
+// factor the per-point matrices are formed and factored first; without it the factors of the last
+// factoring call are reused (dense path; the structured solve has no factors and always runs).
+bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const double* E_dev, double Eu,
+                          bool factor) {
+  const HostOps& o = h->ops;
+  const int nx = o.nx, nt = o.nt, nr = o.nr, nv = o.nv, nl = o.nl;
+  cudaStream_t st = h->st;
+  const int n = nv, nb = h->nb;
+  if (h->structured) {
+    if (h->precision == BTE_FP64)
+      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(in, out, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                   h->TO, h->TS, static_cast<double*>(h->xs), nx, nt,
+                                                                   nr, nl, nullptr, 0, h->status, st));
+    else
+      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<float>(in, out, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                  h->TO, h->TS, static_cast<float*>(h->xs), nx, nt,
+                                                                  nr, nl, nullptr, 0, h->status, st));
+  } else if (h->precision == BTE_FP64) {
+    double* fac = static_cast<double*>(h->fac);
+    if (factor) {
+      BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
+      for (int k0 = 0; k0 < n; k0 += nb) {
+        const int kb = std::min(nb, n - k0);
+        BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nullptr,
+                                                                nx, n, k0, kb, nb, h->status, nullptr, nullptr,
+                                                                nullptr, nullptr, h->panel_w, st));
+        if (k0 + kb < n) {
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
+                                                                          n, k0, kb, nb, nullptr, nullptr, st));
+          BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<double>(fac, nx, n, k0, kb, st));
+        }
+      }
+    }
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(fac, h->piv, in, out, nx, n, nb, nullptr, 0, st));
+  } else {
+    float* fac = static_cast<float*>(h->fac);
+    const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb, h->panel_w);
+    float* linv = static_cast<float*>(h->linv);
+    float* uinv = fused_uinv ? static_cast<float*>(h->uinv) : nullptr;
+    if (factor) {
+      BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
+      if (h->use_tc) {
+        // workspace parts (tc_ws_part): 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11)
+        // split, 8-9 the two-panel block's inv(L11) split (6-7, U12^T, stay inside the tc_lu_* calls)
+        float* ws[10];
+        for (int p = 0; p < 10; ++p) ws[p] = bte::tc_ws_part(h->tcws, nx, n, p);
+        const int ks = bte::kTcKs;
+        auto panel = [&](int k0, int kb) {
+          // the L21 split for the tensor cores is written by lu_swap_pack
+          BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
+                                                                 h->status, nullptr, nullptr, ws[4], ws[5],
+                                                                 h->panel_w, st));
+        };
+        // the panel at k0 applied to the next ncols columns (U12, then A22 -= L21 U12)
+        auto single = [&](int k0, int ncols) {
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, nb, nb, ncols, ks, ws[2],
+                                                                  ws[3], ws[0], ws[1], st));
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, ncols, h->tcws, h->status, st));
+          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, ncols, h->tcws, h->status, st));
+        };
+        if (!h->tc_pair) {
+          for (int k0 = 0; k0 < n; k0 += nb) {
+            const int kb = std::min(nb, n - k0);
+            panel(k0, kb);
+            if (k0 + kb < n) single(k0, n - k0 - kb);
+          }
+        } else {
+          // panels in pairs: the first panel updates only the second panel's columns; once the
+          // second panel is factored, both update the rest together (K = 256), which reads and
+          // writes the trailing matrix once per pair instead of once per panel
+          for (int k0 = 0; k0 < n; k0 += 2 * nb) {
+            const int kb1 = std::min(nb, n - k0);
+            panel(k0, kb1);
+            if (k0 + kb1 == n) break;
+            const int kb2 = std::min(nb, n - k0 - nb);
+            single(k0, kb2);
+            panel(k0 + nb, kb2);
+            if (k0 + nb + kb2 == n) break;
+            BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_pair_linv(fac, h->perm, linv, nx, n, k0, ws[8], ws[9], st));
+            BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack_pair(fac, h->perm, nx, n, k0, ks, ws[2], ws[3],
+                                                                         ws[0], ws[1], st));
+            BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12_pair(fac, nx, n, k0, h->tcws, h->status, st));
+            BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st));
+          }
+        }
+      } else {
+        for (int k0 = 0; k0 < n; k0 += nb) {
+          const int kb = std::min(nb, n - k0);
+          BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
+                                                                 h->status, nullptr, nullptr, nullptr, nullptr,
+                                                                 h->panel_w, st));
+          if (k0 + kb < n) {
+            BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, linv, nx, n, k0, kb, nb,
+                                                                           nullptr, nullptr, st));
+            BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
+          }
+        }
+      }
+      if (!fused_uinv)
+        BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));
+    }
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(fac, h->perm, static_cast<float*>(h->linv),
+                                                                   static_cast<float*>(h->uinv), in, out, nx, n,
+                                                                   nb, nullptr, 0, st));
+  }
+  return BTE_OK;
+}
+
 // One semi-implicit step of F_in into F_out (F_out is written only if the status word stays 0).
 bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const double* E_dev,
-                        double t, double V0, double freq) {
+                        double t, double V0, double freq, const double* ni_dev = nullptr) {
   const HostOps& o = h->ops;
   const int nx = o.nx, nt = o.nt, nr = o.nr, nv = o.nv, nl = o.nl;
   const double Eu = V0 / o.L * std::sin(2.0 * bte::kPi * freq * (t + 0.5 * o.dt));
@@ -111,100 +221,18 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   BTE_LAUNCH(BTE_K_X_TO_EIGEN, bte::launch_x_to_eigen(F_in, h->Uinv, h->Y, nx, nt, nr, h->status, st));
   BTE_LAUNCH(BTE_K_X_APPLY_Q, bte::launch_x_apply_q(h->Q, h->Y, h->Y2, nx, nt, nr, st));
   BTE_LAUNCH(BTE_K_X_FROM_EIGEN, bte::launch_x_from_eigen(h->Y2, h->U, h->Fa, nx, nt, nr, nullptr, st));
+  // self-consistent field (eq. "bte_semi_implicit_efield"): E^{1/2} from the ions and the electrons
+  // after the first x half step
+  if (ni_dev) {
+    const bte_status fs = bte::enqueue_field(h, h->Fa, ni_dev, t + 0.5 * o.dt, V0, freq, h->Esc);
+    if (fs != BTE_OK) return fs;
+    E_dev = h->Esc;
+  }
   // velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system")
   const int n = nv, nb = h->nb;
-  if (h->structured) {
-    if (h->precision == BTE_FP64)
-      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->Fa, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
-                                                                   h->TO, h->TS, static_cast<double*>(h->xs), nx, nt,
-                                                                   nr, nl, nullptr, 0, h->status, st));
-    else
-      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<float>(h->Fa, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
-                                                                  h->TO, h->TS, static_cast<float*>(h->xs), nx, nt,
-                                                                  nr, nl, nullptr, 0, h->status, st));
-  } else if (h->precision == BTE_FP64) {
-    double* fac = static_cast<double*>(h->fac);
-    BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
-    for (int k0 = 0; k0 < n; k0 += nb) {
-      const int kb = std::min(nb, n - k0);
-      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nullptr,
-                                                              nx, n, k0, kb, nb, h->status, nullptr, nullptr,
-                                                              nullptr, nullptr, h->panel_w, st));
-      if (k0 + kb < n) {
-        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<double>(fac, h->perm, static_cast<double*>(h->linv), nx,
-                                                                        n, k0, kb, nb, nullptr, nullptr, st));
-        BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<double>(fac, nx, n, k0, kb, st));
-      }
-    }
-    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st));
-  } else {
-    float* fac = static_cast<float*>(h->fac);
-    const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb, h->panel_w);
-    float* linv = static_cast<float*>(h->linv);
-    float* uinv = fused_uinv ? static_cast<float*>(h->uinv) : nullptr;
-    BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
-    if (h->use_tc) {
-      // workspace parts (tc_ws_part): 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11)
-      // split, 8-9 the two-panel block's inv(L11) split (6-7, U12^T, stay inside the tc_lu_* calls)
-      float* ws[10];
-      for (int p = 0; p < 10; ++p) ws[p] = bte::tc_ws_part(h->tcws, nx, n, p);
-      const int ks = bte::kTcKs;
-      auto panel = [&](int k0, int kb) {
-        // the L21 split for the tensor cores is written by lu_swap_pack
-        BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
-                                                               h->status, nullptr, nullptr, ws[4], ws[5],
-                                                               h->panel_w, st));
-      };
-      // the panel at k0 applied to the next ncols columns (U12, then A22 -= L21 U12)
-      auto single = [&](int k0, int ncols) {
-        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, nb, nb, ncols, ks, ws[2],
-                                                                ws[3], ws[0], ws[1], st));
-        BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, ncols, h->tcws, h->status, st));
-        BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, ncols, h->tcws, h->status, st));
-      };
-      if (!h->tc_pair) {
-        for (int k0 = 0; k0 < n; k0 += nb) {
-          const int kb = std::min(nb, n - k0);
-          panel(k0, kb);
-          if (k0 + kb < n) single(k0, n - k0 - kb);
-        }
-      } else {
-        // panels in pairs: the first panel updates only the second panel's columns; once the
-        // second panel is factored, both update the rest together (K = 256), which reads and
-        // writes the trailing matrix once per pair instead of once per panel
-        for (int k0 = 0; k0 < n; k0 += 2 * nb) {
-          const int kb1 = std::min(nb, n - k0);
-          panel(k0, kb1);
-          if (k0 + kb1 == n) break;
-          const int kb2 = std::min(nb, n - k0 - nb);
-          single(k0, kb2);
-          panel(k0 + nb, kb2);
-          if (k0 + nb + kb2 == n) break;
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_pair_linv(fac, h->perm, linv, nx, n, k0, ws[8], ws[9], st));
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack_pair(fac, h->perm, nx, n, k0, ks, ws[2], ws[3],
-                                                                       ws[0], ws[1], st));
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12_pair(fac, nx, n, k0, h->tcws, h->status, st));
-          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st));
-        }
-      }
-    } else {
-      for (int k0 = 0; k0 < n; k0 += nb) {
-        const int kb = std::min(nb, n - k0);
-        BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
-                                                               h->status, nullptr, nullptr, nullptr, nullptr,
-                                                               h->panel_w, st));
-        if (k0 + kb < n) {
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_trsm<float>(fac, h->perm, linv, nx, n, k0, kb, nb,
-                                                                         nullptr, nullptr, st));
-          BTE_LAUNCH(BTE_K_LU_GEMM, bte::launch_lu_gemm_simt<float>(fac, nx, n, k0, kb, st));
-        }
-      }
-    }
-    if (!fused_uinv)
-      BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));
-    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(fac, h->perm, static_cast<float*>(h->linv),
-                                                                   static_cast<float*>(h->uinv), h->Fa, h->Fb, nx, n,
-                                                                   nb, nullptr, 0, st));
+  {
+    const bte_status vs = enqueue_vsolve(h, h->Fa, h->Fb, E_dev, Eu, true);
+    if (vs != BTE_OK) return vs;
   }
   // FP64 iterative refinement: residual through Algorithm 2, correction through the factors
   if (h->refine_max > 0) {
@@ -296,6 +324,22 @@ bte_status handle_enqueue_step(bte_handle* h, double* F_dev, const double* E_dev
   bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t, V0, freq);
   h->st = own;
   return s;
+}
+bte_status handle_enqueue_sc_step(bte_handle* h, double* F_dev, const double* ni_dev, double t, double V0,
+                                  double freq) {
+  return enqueue_step(h, F_dev, F_dev, nullptr, t, V0, freq, ni_dev);
+}
+bte_status handle_enqueue_xhalf(bte_handle* h, const double* in, double* out) {
+  const HostOps& o = h->ops;
+  cudaStream_t st = h->st;
+  BTE_LAUNCH(BTE_K_X_TO_EIGEN, bte::launch_x_to_eigen(in, h->Uinv, h->Y, o.nx, o.nt, o.nr, nullptr, st));
+  BTE_LAUNCH(BTE_K_X_APPLY_Q, bte::launch_x_apply_q(h->Q, h->Y, h->Y2, o.nx, o.nt, o.nr, st));
+  BTE_LAUNCH(BTE_K_X_FROM_EIGEN, bte::launch_x_from_eigen(h->Y2, h->U, out, o.nx, o.nt, o.nr, h->status, st));
+  BTE_CUDA(h, cudaGetLastError());
+  return BTE_OK;
+}
+bte_status handle_enqueue_vsolve(bte_handle* h, const double* in, double* out, const double* E_dev, bool factor) {
+  return enqueue_vsolve(h, in, out, E_dev, 0.0, factor);
 }
 bte_status handle_reset_status(bte_handle* h, cudaStream_t st) {
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), st));
@@ -625,6 +669,7 @@ bte_status bte_destroy(bte_handle* h) {
     for (void* p : h->allocs) cudaFree(p);
     if (h->mom_r) cudaFree(h->mom_r);
     if (h->status_host) cudaFreeHost(h->status_host);
+    if (h->dsum_host) cudaFreeHost(h->dsum_host);
   }
   delete h;
   return BTE_OK;

@@ -47,6 +47,15 @@ struct bte_handle {
   std::vector<bte::Process> procs;  // the cross sections of the last bte_set_cross_sections
   // transposed x-step operators for the adjoint (allocated on its first use)
   double *Ut = nullptr, *Uinvt = nullptr, *Qt = nullptr;
+  // self-consistent field, ions and the fully-implicit step (allocated on their first use)
+  bool hybrid = false;
+  double n0_mu_i = 4.65e21, n0_D_i = 2.07e20;   // n0 times ion mobility and diffusion
+  double *Lop = nullptr, *E1 = nullptr, *Dxd = nullptr, *mud = nullptr, *lamd = nullptr, *rion = nullptr;
+  double *Esc = nullptr, *Ek = nullptr, *ned = nullptr, *ionA = nullptr, *ionb = nullptr;
+  int gm = 0;                                   // GMRES basis size allocated
+  double *Fk = nullptr, *Fn = nullptr, *Rv = nullptr, *Zx = nullptr, *VX = nullptr, *KAF = nullptr;
+  double *El = nullptr, *Wv = nullptr, *Pz = nullptr, *Vb = nullptr, *part = nullptr, *dsum = nullptr;
+  double* dsum_host = nullptr;                  // pinned
   int last_sweeps = 0;
   double last_resid = 0.0;
   unsigned last_flags = 0;

@@ -14,6 +14,7 @@ constexpr double kMe = 9.1093837015e-31;
 constexpr double kKB = 1.380649e-23;
 constexpr double kAmu = 1.66053906660e-27;
 constexpr double kTorr = 101325.0 / 760.0;
+constexpr double kEps0 = 8.8541878128e-12;  // vacuum permittivity, CODATA 2018
 constexpr double kPi = 3.14159265358979323846;
 
 struct Process {
@@ -51,6 +52,10 @@ std::string assemble_x(const bte_config& cfg, HostOps& ops);
 std::string assemble_v(HostOps& ops, const std::vector<Process>& procs);
 // K_C of a process list on the grids of o, o untouched (for the parameter derivatives).
 std::string assemble_kc_only(const HostOps& o, const std::vector<Process>& procs, std::vector<double>& KC);
+// Electrostatics of Section 2.3 (eq. "hybrid_cnt_c" with the electrode voltages of eq.
+// "voltage_bc") on the collocation points: d^2V/dx^2 = -(e/eps0) rho inside, V(0) = V_left,
+// V(L) = 0, E = -D_x V. Linear in (rho, V_left): E = Lop rho + V_left E1 (Lop nx*nx, E1 nx).
+std::string assemble_field(const HostOps& ops, std::vector<double>& Lop, std::vector<double>& E1);
 // Galerkin coefficients of a unit-density Maxwellian at temperature Te (eV).
 std::vector<double> maxwellian_coeffs(const HostOps& ops, double Te_eV);
 
@@ -68,6 +73,18 @@ void handle_add_launches(bte_handle* h, unsigned long long n);
 bte_status handle_enqueue_step(bte_handle* h, double* F_dev, const double* E_dev, double t, double V0, double freq,
                                struct CUstream_st* st);
 bte_status handle_reset_status(bte_handle* h, struct CUstream_st* st);
+// The step of bte_step with the field recomputed after the first x half step from the ion density
+// ni_dev and the electrons (eq. "bte_semi_implicit_efield"), on the handle's stream.
+bte_status handle_enqueue_sc_step(bte_handle* h, double* F_dev, const double* ni_dev, double t, double V0,
+                                  double freq);
+// One x half step (Algorithm 1) of in into out, and the per-point velocity solve of in into out with
+// the field E_dev (factor: form and factor first; else reuse the last factors, no refinement).
+bte_status handle_enqueue_xhalf(bte_handle* h, const double* in, double* out);
+bte_status handle_enqueue_vsolve(bte_handle* h, const double* in, double* out, const double* E_dev, bool factor);
+// The field of eq. "hybrid_discrete_c" (bte_hybrid.cu): E = L (ni - u^T F) + V0 sin(2 pi f t) E_1
+// into E_dev on the handle's stream (ni_dev NULL: no ions; V0 = 0: no electrode voltage).
+bte_status enqueue_field(bte_handle* h, const double* F_dev, const double* ni_dev, double t, double V0,
+                         double freq, double* E_dev);
 // Reads the status word back on the handle's stream (synchronising it) and maps it to a status.
 bte_status handle_read_status(bte_handle* h);
 // Algorithm variants the batch autotuner chooses between: the tensor-core trailing update (only

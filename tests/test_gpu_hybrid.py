@@ -1,0 +1,165 @@
+"""GPU parity of the self-consistent parts against oracle/hybrid.py: the field of Gauss's law, the
+ion step (eq. "fluid_step"), the semi-implicit step with the field recomputed from the electrons,
+and the fully-implicit step (Newton-GMRES on the GPU against Newton with the dense Jacobian in the
+oracle), in both precisions where the path has two."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bte as O
+from oracle import hybrid as H
+from paper_2502_16555_gb300 import workloads as W
+from tests._lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def solver(cfg, precision="fp64", **kw):
+    from paper_2502_16555_gb300 import bte
+    return bte.Solver(cfg, precision=precision, **kw)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def tiny(nx=9, nr=8, nt=6, **kw):
+    cfg = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=nt)
+    cfg.update(kw)
+    return cfg
+
+
+def ions(ops, peak=1.1e15, shift=2e13):
+    xi = 2.0 * ops.x / ops.L - 1.0
+    return peak * (1.0 - xi * xi) + shift
+
+
+SHAPES = [(9, 8, 6), (13, 10, 5), (24, 12, 8)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_field_matches_oracle(shape):
+    cfg = tiny(*shape)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = ops.initial_state() * (1.0 + 0.2 * W.random_state(ops.nx, ops.nt, ops.nr, seed=3) / 1e15)
+    ni = ions(ops)
+    t = 0.31 / cfg["freq_Hz"]
+    ref = h.field(ni, F, t)
+    s = solver(cfg)
+    E = s.field(dev(F), dev(ni), t).cpu().numpy()
+    assert np.max(np.abs(E - ref)) <= 1e-10 * np.max(np.abs(ref))
+    E0 = s.field(dev(F), None, t).cpu().numpy()   # no ions
+    ref0 = h.field(np.zeros(ops.nx), F, t)
+    assert np.max(np.abs(E0 - ref0)) <= 1e-10 * np.max(np.abs(ref0))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_ion_step_matches_oracle(shape):
+    cfg = tiny(*shape)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = ops.initial_state()
+    ni = ions(ops)
+    t = 0.13 / cfg["freq_Hz"]
+    ref = h.ion_step(ni, F, t)
+    s = solver(cfg)
+    n = dev(ni)
+    s.ion_step(n, dev(F), t)
+    assert rel(n.cpu().numpy(), ref) <= 1e-10
+
+
+def test_ion_step_with_other_transport_coefficients():
+    cfg = tiny(13, 10, 5)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops, n0_mu_i=2.0e21, n0_d_i=5.0e20)
+    F = ops.initial_state()
+    ni = ions(ops, 0.8e15)
+    ref = h.ion_step(ni, F, 0.6 / cfg["freq_Hz"])
+    s = solver(cfg)
+    s.set_ion_transport(2.0e21, 5.0e20)
+    n = dev(ni)
+    s.ion_step(n, dev(F), 0.6 / cfg["freq_Hz"])
+    assert rel(n.cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_self_consistent_step_matches_oracle(shape, precision):
+    cfg = tiny(*shape)
+    cfg["V0"] = 300.0
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = W.random_state(ops.nx, ops.nt, ops.nr, seed=7)
+    ni = ions(ops)
+    t = 0.42 / cfg["freq_Hz"]
+    ref, Eref = h.sc_step(F, ni, t)
+    s = solver(cfg, precision)
+    Fd = dev(F)
+    E = torch.empty(ops.nx, dtype=torch.float64, device="cuda")
+    s.step_sc(Fd, dev(ni), t, E_out=E)
+    assert np.max(np.abs(E.cpu().numpy() - Eref)) <= 1e-10 * np.max(np.abs(Eref))
+    assert rel(Fd.cpu().numpy(), ref) <= (1e-10 if precision == "fp64" else 1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(9, 8, 6), (11, 10, 5)])
+def test_implicit_step_matches_oracle_root(shape, precision):
+    """The GPU's Newton-GMRES root against the oracle's Newton root (dense Jacobian)."""
+    cfg = tiny(*shape)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = ops.initial_state() * (1.0 + 0.1 * W.random_state(ops.nx, ops.nt, ops.nr, seed=4) / 1e15)
+    ni = ions(ops)
+    t = 0.27 / cfg["freq_Hz"]
+    ref, _ = h.implicit_step(F, ni, t)
+    s = solver(cfg, precision)
+    Fd = dev(F)
+    newton, gmres, res = s.step_implicit(Fd, dev(ni), t, newton_rtol=1e-12)
+    assert res <= 1e-12 and 1 <= newton <= 8 and gmres >= 1, (newton, gmres, res)
+    assert rel(Fd.cpu().numpy(), ref) <= 1e-9
+
+
+def test_hybrid_sequence_ions_then_electrons():
+    """Five operator-split steps (ions with the lagged state, then the self-consistent electron
+    step), FP64, against the same sequence in the oracle."""
+    cfg = tiny(11, 10, 6)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = ops.initial_state()
+    ni = ions(ops)
+    s = solver(cfg)
+    Fd, nd = dev(F), dev(ni)
+    for n in range(5):
+        t = n * ops.dt
+        ni = h.ion_step(ni, F, t)
+        F, _ = h.sc_step(F, ni, t)
+        s.ion_step(nd, Fd, t)
+        s.step_sc(Fd, nd, t)
+    assert rel(nd.cpu().numpy(), ni) <= 1e-10
+    assert rel(Fd.cpu().numpy(), F) <= 1e-10
+
+
+def test_implicit_step_medium_workload_converges():
+    """Nx=128, Nv=2048 (mixed): Newton-GMRES converges in a few iterations and stays within the
+    schemes' O(dt^2) distance of the semi-implicit step from the same state."""
+    cfg = W.MEDIUM
+    s = solver(cfg, "mixed")
+    F = s.initial_state()
+    ops_x = O.cheb_points(cfg["nx"], cfg["L_m"])
+    ni = dev(1.05e15 * (1.0 - (2.0 * ops_x / cfg["L_m"] - 1.0) ** 2) + 1e13)
+    t = 0.25 / cfg["freq_Hz"]
+    Fs = F.clone()
+    s.step_sc(Fs, ni, t)
+    newton, gmres, res = s.step_implicit(F, ni, t)
+    assert res <= 1e-10 and newton <= 6, (newton, gmres, res)
+    assert float(torch.linalg.norm(F - Fs) / torch.linalg.norm(Fs)) <= 1e-2
