@@ -104,6 +104,10 @@ class Hybrid:
         A[-1, -1] += max(0.0, self.mu_i * E[-1])
         rhs[0] = 0.0
         rhs[-1] = 0.0
+        # the flux rows are ~1e-9 of the interior rows (1/dt) in scale: equilibrate them (same
+        # solution) so the wall values are not left to the rounding of a badly scaled system
+        for w in (0, -1):
+            A[w, :] *= (1.0 / dt) / np.max(np.abs(A[w, :]))
         return np.linalg.solve(A, rhs)
 
     # ---- electrons, semi-implicit with the electrostatics update
