@@ -88,6 +88,23 @@ __global__ void ion_assemble_kernel(const double* __restrict__ Dx, const double*
     a[j] = v;
   }
   if (threadIdx.x == 0) b[i] = wall ? 0.0 : ni[i] / dt + src[i];
+  if (wall) {
+    // the flux rows are ~1e-9 of the interior rows (1/dt) in scale: equilibrate them (same
+    // solution) so the wall values are not left to the rounding of a badly scaled system
+    __shared__ double red[32];
+    __syncthreads();
+    double mx = 0.0;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) mx = fmax(mx, fabs(a[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) red[0] = fmax(red[0], red[w]);
+    }
+    __syncthreads();
+    const double sc = red[0] > 0.0 ? (1.0 / dt) / red[0] : 1.0;
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) a[j] *= sc;
+  }
 }
 
 // x = A^-1 b by Gaussian elimination with partial pivoting, one CTA, A and b in global memory
