@@ -264,8 +264,11 @@ bte_status bte_step_sc(bte_handle* h, double* F_dev, const double* ni_dev, doubl
 typedef struct {
   double newton_rtol;  /* stop when |R(F)| <= newton_rtol |F^n| (default 1e-10) */
   int newton_max;      /* Newton iterations (default 8) */
-  int gmres_restart;   /* GMRES basis size per Newton iteration, <= 200 (default 30) */
+  int gmres_restart;   /* GMRES basis size, <= 200 (default 40) */
   double gmres_rtol;   /* inner tolerance relative to |R| (default 1e-3) */
+  int gmres_max;       /* GMRES iterations per Newton iteration, restarts included (default 400) */
+  int precond;         /* 0: the per-point solves at the iterate's field, then one full x step
+                          (default); 1: the semi-implicit step's map (x half step, solves, x half step) */
   int newton_iters;    /* out: Newton iterations taken */
   int gmres_iters;     /* out: GMRES iterations, all Newton iterations together */
   double residual;     /* out: final |R| / |F^n| */
@@ -274,9 +277,10 @@ typedef struct {
 /* One fully-implicit electron step (eqs. "bte_fully_implicit"): F <- the root of
  * R(F) = F - F^n + dt [A_x F D_x^T - P_O C P_S F - P_O A_v P_S (E(F) . F)], E(F) the field of
  * (n_i, u^T F) at t_s + dt, with the zero-inflow rows R = F. Newton with backtracking from the
- * semi-implicit self-consistent step's result; each Newton system by GMRES on the Jacobian action
- * of eq. "1dbte_jac_action", right-preconditioned by the semi-implicit step's linear map at the
- * iterate's field (its per-point factors formed once per Newton iteration). ni_dev is required;
+ * semi-implicit self-consistent step's result; each Newton system by restarted GMRES on the
+ * Jacobian action of eq. "1dbte_jac_action", right-preconditioned by the split operator at the
+ * iterate's field (opts->precond; the per-point factors formed once per Newton iteration; the
+ * full-step x operators are assembled on the first call with precond 0). ni_dev is required;
  * opts may be NULL.
  * BTE_ENOCONV if Newton stops above newton_rtol; F is written only on success. Synchronises the
  * handle's stream. */

@@ -58,8 +58,8 @@ class Process(C.Structure):
 
 class ImplicitOpts(C.Structure):
     _fields_ = [("newton_rtol", C.c_double), ("newton_max", C.c_int), ("gmres_restart", C.c_int),
-                ("gmres_rtol", C.c_double), ("newton_iters", C.c_int), ("gmres_iters", C.c_int),
-                ("residual", C.c_double)]
+                ("gmres_rtol", C.c_double), ("gmres_max", C.c_int), ("precond", C.c_int),
+                ("newton_iters", C.c_int), ("gmres_iters", C.c_int), ("residual", C.c_double)]
 
 
 class Info(C.Structure):
@@ -272,12 +272,12 @@ class Solver:
         return F
 
     def step_implicit(self, F, ni, t: float, V0=None, freq=None, newton_rtol=0.0, newton_max=0,
-                      gmres_restart=0, gmres_rtol=0.0):
+                      gmres_restart=0, gmres_rtol=0.0, gmres_max=0, precond=0):
         """One fully-implicit step; returns (newton_iters, gmres_iters, relative residual)."""
         V0 = self.cfg["V0"] if V0 is None else V0
         freq = self.cfg["freq_Hz"] if freq is None else freq
         o = ImplicitOpts(newton_rtol=newton_rtol, newton_max=newton_max, gmres_restart=gmres_restart,
-                         gmres_rtol=gmres_rtol)
+                         gmres_rtol=gmres_rtol, gmres_max=gmres_max, precond=precond)
         self._check(self.lib.bte_step_implicit(self.h, _ptr(self._f(F)), _ptr(self._nx_vec(ni, "ni")), float(t),
                                                float(V0), float(freq), C.byref(o)))
         return o.newton_iters, o.gmres_iters, o.residual

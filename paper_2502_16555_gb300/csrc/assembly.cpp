@@ -466,23 +466,28 @@ std::string assemble_x(const bte_config& cfg, HostOps& o) {
 
   // Q_ij = (I + dt/2 lam_i mu_a D_x)^-1 with the inflow row replaced by the identity row; the
   // inflow column of Q is zeroed, which applies the zero right-hand side of that row.
-  o.Q.assign(static_cast<size_t>(nt) * nr * nx * nx, 0.0);
+  if (!assemble_q(o, 0.5 * o.dt, o.Q)) return "an x half-step operator is singular";
+  return "";
+}
+
+bool assemble_q(const HostOps& o, double tau, std::vector<double>& Q) {
+  const int nx = o.nx, nr = o.nr, nt = o.nt;
+  Q.assign(static_cast<size_t>(nt) * nr * nx * nx, 0.0);
   bool ok = true;
 #pragma omp parallel for schedule(dynamic) reduction(&& : ok)
   for (int ai = 0; ai < nt * nr; ++ai) {
     const int a = ai / nr, i = ai % nr;
     const int row = o.mu[a] >= 0.0 ? 0 : nx - 1;
-    const double c = 0.5 * o.dt * o.lam[i] * o.mu[a];
+    const double c = tau * o.lam[i] * o.mu[a];
     std::vector<double> B(nx * nx);
     for (int p = 0; p < nx; ++p)
       for (int q = 0; q < nx; ++q) B[p * nx + q] = (p == q ? 1.0 : 0.0) + c * o.Dx[p * nx + q];
     for (int q = 0; q < nx; ++q) B[row * nx + q] = (q == row) ? 1.0 : 0.0;
-    double* Qa = o.Q.data() + static_cast<size_t>(ai) * nx * nx;
+    double* Qa = Q.data() + static_cast<size_t>(ai) * nx * nx;
     ok = invert(B, nx, Qa) && ok;
     for (int p = 0; p < nx; ++p) Qa[p * nx + row] = 0.0;
   }
-  if (!ok) return "an x half-step operator is singular";
-  return "";
+  return ok;
 }
 
 // ------------------------------------------------------------------------ velocity-side assembly

@@ -378,12 +378,18 @@ bte_status hybrid_setup(bte_handle* h) {
 }
 
 // Work vectors of the fully-implicit step for a GMRES basis of m + 1 vectors.
-bte_status implicit_setup(bte_handle* h, int m) {
+bte_status implicit_setup(bte_handle* h, int m, bool full_q) {
+  bte_status s = BTE_OK;
+  if (full_q && !h->Qfull) {
+    // Q_ij for a full step, (I + dt lam_i mu_a D_x)^-1 with the inflow rows
+    std::vector<double> Q;
+    if (!assemble_q(h->ops, h->ops.dt, Q)) return hfail(h, BTE_EINVAL, "a full-step x operator is singular");
+    if ((s = hupload(h, &h->Qfull, Q)) != BTE_OK) return s;
+  }
   if (h->gm >= m) return BTE_OK;
   const size_t D = static_cast<size_t>(h->ops.nx) * h->ops.nv;
-  bte_status s = BTE_OK;
   if (!h->Fk) {
-    for (double** p : {&h->Fk, &h->Fn, &h->Rv, &h->Zx, &h->VX, &h->KAF, &h->Wv, &h->Pz})
+    for (double** p : {&h->Fk, &h->Fn, &h->Rv, &h->Zx, &h->VX, &h->KAF, &h->Wv, &h->Pz, &h->Dl})
       if (s == BTE_OK) s = halloc(h, p, D);
     if (s == BTE_OK) s = halloc(h, &h->El, h->ops.nx);
   }
@@ -508,18 +514,21 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
   if (!F_dev || !ni_dev) return hfail(h, BTE_EINVAL, "F_dev and ni_dev must not be NULL");
   if (!bte::handle_device_ready(h)) return BTE_ESTATE;
   double rtol = 1e-10, grtol = 1e-3;
-  int newton_max = 8, m = 30;
+  int newton_max = 8, m = 40, gmax = 400, precond = 0;
   if (opts) {
     if (opts->newton_rtol > 0) rtol = opts->newton_rtol;
     if (opts->gmres_rtol > 0) grtol = opts->gmres_rtol;
     if (opts->newton_max > 0) newton_max = opts->newton_max;
     if (opts->gmres_restart > 0) m = opts->gmres_restart;
+    if (opts->gmres_max > 0) gmax = opts->gmres_max;
+    precond = opts->precond;
     opts->newton_iters = opts->gmres_iters = 0;
     opts->residual = 0.0;
   }
   if (m > 200) return hfail(h, BTE_EINVAL, "gmres_restart must be <= 200");
+  if (precond != 0 && precond != 1) return hfail(h, BTE_EINVAL, "precond must be 0 or 1");
   bte_status s = bte::hybrid_setup(h);
-  if (s == BTE_OK) s = bte::implicit_setup(h, m);
+  if (s == BTE_OK) s = bte::implicit_setup(h, m, precond == 0);
   if (s != BTE_OK) return s;
   const bte::HostOps& o = h->ops;
   const int nx = o.nx, nt = o.nt, nr = o.nr;
@@ -555,12 +564,26 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
     launches += 2;
     return r;
   };
-  // the semi-implicit step's linear map at the frozen field Ek: x half step, solves with the
-  // factors of this Newton iteration, x half step
+  // the preconditioner at the frozen field Ek, from the split step's pieces with the factors of
+  // this Newton iteration. precond 0: the per-point solves, then one full x step (exact when either
+  // part vanishes, also for the stiffest x modes); 1: the semi-implicit step's map (x half step,
+  // solves, x half step), whose x part is (I + dt/2 A_x)^-2, far from (I + dt A_x)^-1 for x modes
+  // with dt |A_x| >> 1
   auto pinv = [&](const double* in, double* out) -> bte_status {
-    bte_status r = bte::handle_enqueue_xhalf(h, in, h->Wv);
-    if (r == BTE_OK) r = bte::handle_enqueue_vsolve(h, h->Wv, h->VX, h->Ek, false);
-    if (r == BTE_OK) r = bte::handle_enqueue_xhalf(h, h->VX, out);
+    bte_status r = BTE_OK;
+    if (precond == 0) {
+      r = bte::handle_enqueue_vsolve(h, in, h->VX, h->Ek, false);
+      if (r == BTE_OK) {
+        bte::launch_x_to_eigen(h->VX, h->Uinv, h->Y, nx, nt, nr, nullptr, st);
+        bte::launch_x_apply_q(h->Qfull, h->Y, h->Y2, nx, nt, nr, st);
+        bte::launch_x_from_eigen(h->Y2, h->U, out, nx, nt, nr, nullptr, st);
+        launches += 3;
+      }
+    } else {
+      r = bte::handle_enqueue_xhalf(h, in, h->Wv);
+      if (r == BTE_OK) r = bte::handle_enqueue_vsolve(h, h->Wv, h->VX, h->Ek, false);
+      if (r == BTE_OK) r = bte::handle_enqueue_xhalf(h, h->VX, out);
+    }
     return r;
   };
   // Jacobian action at F_k (eq. "1dbte_jac_action" with the inflow rows as identity)
@@ -586,61 +609,83 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
     BH_CUDA(h, cudaMemcpyAsync(h->Ek, h->Esc, nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if ((s = bte::handle_enqueue_vsolve(h, h->Rv, h->Pz, h->Ek, true)) != BTE_OK) return s;
     bte::enqueue_vapply(h, h->Fk, nullptr, 0.0, h->KAF);
-    // GMRES on J delta = -R, right-preconditioned, one cycle of at most m vectors
-    BH_CUDA(h, cudaMemcpyAsync(h->Vb, h->Rv, D * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, -1.0 / rn, nullptr, D, 0, nullptr, 0.0, D);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = rn;
-    int k = 0;
-    for (int j = 0; j < m; ++j) {
-      double* Vj = h->Vb + static_cast<size_t>(j) * D;
-      double* Vn = h->Vb + static_cast<size_t>(j + 1) * D;
-      if ((s = pinv(Vj, h->Pz)) != BTE_OK) return s;
-      jac(h->Pz, Vn);
-      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-        if ((s = bte::host_dots(h, h->Vb, D, j + 1, Vn, hv)) != BTE_OK) return s;
-        for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] += hv[i];
-        multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0, h->Vb, D, j + 1, h->dsum, -1.0, D);
-        launches += 3;
+    // restarted GMRES on J delta = -R, right-preconditioned: delta accumulates in Dl; every cycle
+    // solves J P^-1 y = r for the current residual r = -R - J delta
+    BH_CUDA(h, cudaMemsetAsync(h->Dl, 0, D * sizeof(double), st));
+    int inner = 0;
+    double rc = rn;  // |r| of the current cycle
+    for (int cyc = 0; inner < gmax; ++cyc) {
+      if (cyc > 0) {
+        jac(h->Dl, h->Vb);  // r = -R - J delta
+        multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, -1.0, nullptr, D, 0, nullptr, 0.0, D);
+        axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, -1.0, h->Rv, D);
+        if ((s = norm(h->Vb, rc)) != BTE_OK) return s;
+        if (rc <= grtol * rn) break;
+        multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, 1.0 / rc, nullptr, D, 0, nullptr, 0.0, D);
+      } else {
+        BH_CUDA(h, cudaMemcpyAsync(h->Vb, h->Rv, D * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, -1.0 / rn, nullptr, D, 0, nullptr, 0.0, D);
       }
-      double hn = 0.0;
-      if ((s = norm(Vn, hn)) != BTE_OK) return s;
-      H[static_cast<size_t>(j + 1) * m + j] = hn;
-      if (hn > 0.0) multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0 / hn, nullptr, D, 0, nullptr, 0.0, D);
-      for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
-        const double a = H[static_cast<size_t>(i) * m + j], b = H[static_cast<size_t>(i + 1) * m + j];
-        H[static_cast<size_t>(i) * m + j] = cs[i] * a + sn[i] * b;
-        H[static_cast<size_t>(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      std::fill(H.begin(), H.end(), 0.0);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = rc;
+      int k = 0;
+      bool done = false;
+      for (int j = 0; j < m && inner < gmax; ++j, ++inner) {
+        double* Vj = h->Vb + static_cast<size_t>(j) * D;
+        double* Vn = h->Vb + static_cast<size_t>(j + 1) * D;
+        if ((s = pinv(Vj, h->Pz)) != BTE_OK) return s;
+        jac(h->Pz, Vn);
+        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+          if ((s = bte::host_dots(h, h->Vb, D, j + 1, Vn, hv)) != BTE_OK) return s;
+          for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] += hv[i];
+          multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0, h->Vb, D, j + 1, h->dsum, -1.0, D);
+          launches += 3;
+        }
+        double hn = 0.0;
+        if ((s = norm(Vn, hn)) != BTE_OK) return s;
+        H[static_cast<size_t>(j + 1) * m + j] = hn;
+        if (hn > 0.0) multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0 / hn, nullptr, D, 0, nullptr, 0.0, D);
+        for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
+          const double a = H[static_cast<size_t>(i) * m + j], b = H[static_cast<size_t>(i + 1) * m + j];
+          H[static_cast<size_t>(i) * m + j] = cs[i] * a + sn[i] * b;
+          H[static_cast<size_t>(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = H[static_cast<size_t>(j) * m + j], b = H[static_cast<size_t>(j + 1) * m + j];
+        const double r = std::hypot(a, b);
+        cs[j] = r > 0.0 ? a / r : 1.0;
+        sn[j] = r > 0.0 ? b / r : 0.0;
+        H[static_cast<size_t>(j) * m + j] = r;
+        H[static_cast<size_t>(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k = j + 1;
+        if (std::fabs(g[j + 1]) <= grtol * rn || hn == 0.0) {
+          done = true;
+          ++inner;
+          break;
+        }
       }
-      const double a = H[static_cast<size_t>(j) * m + j], b = H[static_cast<size_t>(j + 1) * m + j];
-      const double r = std::hypot(a, b);
-      cs[j] = r > 0.0 ? a / r : 1.0;
-      sn[j] = r > 0.0 ? b / r : 0.0;
-      H[static_cast<size_t>(j) * m + j] = r;
-      H[static_cast<size_t>(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      k = j + 1;
-      if (std::fabs(g[j + 1]) <= grtol * rn || hn == 0.0) break;
+      for (int i = k - 1; i >= 0; --i) {  // H y = g, upper triangular
+        double v = g[i];
+        for (int q = i + 1; q < k; ++q) v -= H[static_cast<size_t>(i) * m + q] * y[q];
+        y[i] = v / H[static_cast<size_t>(i) * m + i];
+      }
+      // delta += P^-1 (V y)
+      std::copy(y.begin(), y.begin() + k, h->dsum_host);
+      BH_CUDA(h, cudaMemcpyAsync(h->dsum, h->dsum_host, k * sizeof(double), cudaMemcpyHostToDevice, st));
+      multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Zx, 0.0, h->Vb, D, k, h->dsum, 1.0, D);
+      if ((s = pinv(h->Zx, h->Pz)) != BTE_OK) return s;
+      axpy_kernel<<<vg, 256, 0, st>>>(h->Dl, 1.0, h->Pz, D);
+      if (done) break;
     }
-    for (int i = k - 1; i >= 0; --i) {  // H y = g, upper triangular
-      double v = g[i];
-      for (int q = i + 1; q < k; ++q) v -= H[static_cast<size_t>(i) * m + q] * y[q];
-      y[i] = v / H[static_cast<size_t>(i) * m + i];
-    }
-    gm_total += k;
-    // delta = P^-1 (V y)
-    std::copy(y.begin(), y.begin() + k, h->dsum_host);
-    BH_CUDA(h, cudaMemcpyAsync(h->dsum, h->dsum_host, k * sizeof(double), cudaMemcpyHostToDevice, st));
-    multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Zx, 0.0, h->Vb, D, k, h->dsum, 1.0, D);
-    if ((s = pinv(h->Zx, h->Pz)) != BTE_OK) return s;
+    gm_total += inner;
     // backtracking on |R|
     double lam = 1.0, rt = 0.0;
     bool acc = false;
     for (int ls = 0; ls < 8 && !acc; ++ls) {
       BH_CUDA(h, cudaMemcpyAsync(h->Wv, h->Fk, D * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      axpy_kernel<<<vg, 256, 0, st>>>(h->Wv, lam, h->Pz, D);
+      axpy_kernel<<<vg, 256, 0, st>>>(h->Wv, lam, h->Dl, D);
       residual(h->Wv, h->Rv);
       if ((s = norm(h->Rv, rt)) != BTE_OK) return s;
       if (rt <= (1.0 - 1e-4 * lam) * rn) acc = true;

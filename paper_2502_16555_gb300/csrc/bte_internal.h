@@ -48,6 +48,9 @@ struct HostOps {
 
 // Grids, radial matrices, eigen-decomposition and Q_ij. Returns "" on success, else a message.
 std::string assemble_x(const bte_config& cfg, HostOps& ops);
+// Q_ij = (I + tau lam_i mu_a D_x)^-1 with the inflow rows of Algorithm 1 (tau = dt/2 for the half
+// steps). False if one of them is singular.
+bool assemble_q(const HostOps& ops, double tau, std::vector<double>& Q);
 // Collision and field operators, their projections and the moment vectors.
 std::string assemble_v(HostOps& ops, const std::vector<Process>& procs);
 // K_C of a process list on the grids of o, o untouched (for the parameter derivatives).
