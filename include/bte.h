@@ -265,7 +265,7 @@ typedef struct {
   double newton_rtol;  /* stop when |R(F)| <= newton_rtol |F^n| (default 1e-10) */
   int newton_max;      /* Newton iterations (default 8) */
   int gmres_restart;   /* GMRES basis size, <= 200 (default 40) */
-  double gmres_rtol;   /* inner tolerance relative to |R| (default 1e-3) */
+  double gmres_rtol;   /* inner tolerance relative to |R| (default 1e-2) */
   int gmres_max;       /* GMRES iterations per Newton iteration, restarts included (default 400) */
   int precond;         /* 0: the per-point solves at the iterate's field, then one full x step
                           (default); 1: the semi-implicit step's map (x half step, solves, x half step) */

@@ -513,7 +513,7 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
   if (!h) return hfail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || !ni_dev) return hfail(h, BTE_EINVAL, "F_dev and ni_dev must not be NULL");
   if (!bte::handle_device_ready(h)) return BTE_ESTATE;
-  double rtol = 1e-10, grtol = 1e-3;
+  double rtol = 1e-10, grtol = 1e-2;
   int newton_max = 8, m = 40, gmax = 400, precond = 0;
   if (opts) {
     if (opts->newton_rtol > 0) rtol = opts->newton_rtol;

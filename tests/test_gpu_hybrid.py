@@ -131,6 +131,27 @@ def test_implicit_step_matches_oracle_root(shape, precision):
     assert rel(Fd.cpu().numpy(), ref) <= 1e-9
 
 
+def test_implicit_step_preconditioners_reach_the_same_root():
+    """The default preconditioner (solves, then one full x step) and the semi-implicit step's map
+    both lead Newton to the oracle's root; the default needs fewer GMRES iterations."""
+    cfg = tiny(9, 8, 6)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = ops.initial_state()
+    ni = ions(ops)
+    t = 0.11 / cfg["freq_Hz"]
+    ref, _ = h.implicit_step(F, ni, t)
+    its = []
+    for pc in (0, 1):
+        s = solver(cfg)
+        Fd = dev(F)
+        newton, gmres, res = s.step_implicit(Fd, dev(ni), t, newton_rtol=1e-12, precond=pc, gmres_max=2000)
+        assert res <= 1e-12
+        assert rel(Fd.cpu().numpy(), ref) <= 1e-9
+        its.append(gmres)
+    assert its[0] <= its[1], its
+
+
 def test_hybrid_sequence_ions_then_electrons():
     """Five operator-split steps (ions with the lagged state, then the self-consistent electron
     step), FP64, against the same sequence in the oracle."""
