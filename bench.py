@@ -528,6 +528,81 @@ def run_batched(args, rank, world):
     return 0
 
 
+HYBRID = "hybrid_nx128_nr64_nt32"
+
+
+def run_hybrid(args, rank, world):
+    """The self-consistent parts on the medium workload (mixed precision, ion density of the same
+    parabolic shape as the electrons, 1.05e15 m^-3 peak): the ion step (eq. "fluid_step"), the
+    semi-implicit step with the field recomputed from the electrons, and the fully-implicit step
+    (Newton-GMRES) at the same dt and at 4 dt (the paper's comparison of the two schemes runs the
+    fully-implicit one at a 4x larger step). Each leg starts from the same state; times are CUDA
+    events around `steps` steps after `warmup` steps."""
+    import torch
+    from paper_2502_16555_gb300 import bte
+    from oracle import bte as O
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank != 0:
+        return 0
+    cfg = W.WORKLOADS[WORKLOAD]
+    dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
+    x = O.cheb_points(cfg["nx"], cfg["L_m"])
+    ni0 = torch.from_numpy(1.05e15 * (1.0 - (2.0 * x / cfg["L_m"] - 1.0) ** 2) + 1e13).cuda()
+    t0 = 0.25 / cfg["freq_Hz"]
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = [fn(i) for i in range(n)]
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n, out
+
+    s = bte.Solver(cfg, precision="mixed")
+    F0 = s.initial_state()
+    out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "data": "synthetic", "dtype": "tf32x3+f64",
+           "config": {"workload": HYBRID, "nx": cfg["nx"], "nr": cfg["nr"], "ntheta": cfg["ntheta"],
+                      "dof": dof, "precision": "mixed", "ions": "parabolic, peak 1.05e15 m^-3"}}
+    # ions
+    ni = ni0.clone()
+    for i in range(args.warmup):
+        s.ion_step(ni, F0, t0)
+    ms_ion, _ = timed(lambda i: s.ion_step(ni, F0, t0 + i * cfg["dt_s"]), args.steps)
+    out["ion_step"] = {"ms_per_step": ms_ion, "nx": cfg["nx"]}
+    # semi-implicit, self-consistent field
+    F = F0.clone()
+    for i in range(args.warmup):
+        s.step_sc(F, ni0, t0 + i * cfg["dt_s"])
+    F = F0.clone()
+    ms_sc, _ = timed(lambda i: s.step_sc(F, ni0, t0 + i * cfg["dt_s"]), args.steps)
+    out["semi_implicit_sc"] = {"ms_per_step": ms_sc, "value": dof / (ms_sc / 1e3), "dt_s": cfg["dt_s"]}
+    # fully implicit at dt and at 4 dt
+    for tag, k in (("fully_implicit", 1), ("fully_implicit_4dt", 4)):
+        c = dict(cfg)
+        c["dt_s"] = k * cfg["dt_s"]
+        si = s if k == 1 else bte.Solver(c, precision="mixed")
+        Fi = F0.clone()
+        for i in range(max(1, args.warmup)):
+            si.step_implicit(Fi, ni0, t0 + i * c["dt_s"])
+        Fi = F0.clone()
+        ms, stats = timed(lambda i: si.step_implicit(Fi, ni0, t0 + i * c["dt_s"]), args.steps)
+        newton = sum(st[0] for st in stats) / len(stats)
+        gmres = sum(st[1] for st in stats) / len(stats)
+        out[tag] = {"ms_per_step": ms, "value": dof / (ms / 1e3), "dt_s": c["dt_s"],
+                    "newton_per_step": newton, "gmres_per_step": gmres,
+                    "max_relative_residual": max(st[2] for st in stats)}
+    # cost per simulated time, semi-implicit over fully-implicit at 4 dt (> 1: the implicit wins)
+    out["semi_over_fully_4dt_per_simulated_time"] = (ms_sc / cfg["dt_s"]) / (
+        out["fully_implicit_4dt"]["ms_per_step"] / (4 * cfg["dt_s"]))
+    out["value"] = out["semi_implicit_sc"]["value"]
+    out["ms_per_step"] = ms_sc
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_adjoint(args, rank, world):
     """Gradient of the cycle-averaged electron number over one RF cycle (1000 steps, FP64,
     Nx=64, Nr=32, Ntheta=16) with respect to 8 parameters (four cross-section scales, three
@@ -611,7 +686,7 @@ def main():
     ap.add_argument("--no-structured", action="store_true", help="skip the block-tridiagonal solve legs")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, LARGEST, "batched64_uneven", "adjoint_nx64_nr32_nt16"],
+                    choices=[WORKLOAD, LARGEST, "batched64_uneven", "adjoint_nx64_nr32_nt16", HYBRID],
                     help="the headline single discharge (default), the largest single discharge (Nv = 4096; "
                          "use a few steps: its FP64 leg takes seconds per step), the 64 uneven discharges "
                          "in one graph, or the adjoint-gradient check")
@@ -630,6 +705,8 @@ def main():
         return run_batched(args, rank, world)
     if args.workload == "adjoint_nx64_nr32_nt16":
         return run_adjoint(args, rank, world)
+    if args.workload == HYBRID:
+        return run_hybrid(args, rank, world)
     return run_ours(args, rank, world)
 
 
