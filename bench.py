@@ -166,6 +166,8 @@ def algorithmic(cfg, precision, kernel, tc, pair=True):
         return float(esz) * nx * nv * nv, "byte/launch", "hbm"
     if kernel == "x_apply_q":
         return 2 * (8.0 * nv * nx * nx + 16.0 * nv * nx), "byte", "hbm"
+    if kernel == "x_apply_q_flops":
+        return 2 * (2.0 * nv * nx * nx), "flop", "alu"
     if kernel == "v_form":
         return float(esz) * nx * nv * nv + 16.0 * nv * nv, "byte", "hbm"
     if kernel == "residual":
@@ -413,21 +415,26 @@ def run_ours(args, rank, world):
     # the measured DRAM traffic was captured on the default workload only
     measured = name == WORKLOAD and not args.nx
     rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc, sweeps=sweeps, measured=measured)
-    # the panel against its binding roofline: its FP32 flops need longer at the SIMT peak than its
-    # bytes at the HBM peak, so the arithmetic bound is the one it is measured against
-    if "lu_panel" in prof and prof["lu_panel"][1]:
-        fl, _, _ = algorithmic(cfg, "mixed", "lu_panel_flops", tc)
-        by, _, _ = algorithmic(cfg, "mixed", "lu_panel", tc)
-        t_alu, t_hbm = fl / (FP32_SIMT_PEAK_TFLOPS * 1e12), by / (peaks["hbm_gbs"] * 1e9)
-        ms_p = prof["lu_panel"][0] / args.steps
-        if t_alu > t_hbm:
-            hbm = rf_all["lu_panel"]
-            rf_all["lu_panel"] = dict(hbm, bound="alu", achieved=fl / (ms_p / 1e3) / 1e12, peak=FP32_SIMT_PEAK_TFLOPS,
-                                      unit="TFLOP/s", frac=fl / (ms_p / 1e3) / 1e12 / FP32_SIMT_PEAK_TFLOPS,
-                                      peak_source="FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
-                                      hbm_frac=hbm["frac"], floor_ms={"alu": t_alu * 1e3, "hbm": t_hbm * 1e3})
-            if rf_dom["kernel"] == "lu_panel":
-                rf_dom = rf_all["lu_panel"]
+    # kernels with a flop and a byte floor are measured against the binding one: the panel's FP32
+    # flops (SIMT peak) and the Q apply's FP64 flops (FP64 peak) take longer than their bytes
+    for kern, fkey, fpeak, fsrc in (
+            ("lu_panel", "lu_panel_flops", FP32_SIMT_PEAK_TFLOPS,
+             "FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"),
+            ("x_apply_q", "x_apply_q_flops", FP64_PEAK_TFLOPS, "FP64 DGEMM measured on this GB300 (bench.py --peaks)")):
+        if kern not in prof or not prof[kern][1] or kern not in rf_all:
+            continue
+        fl, _, _ = algorithmic(cfg, "mixed", fkey, tc)
+        by, _, _ = algorithmic(cfg, "mixed", kern, tc)
+        t_alu, t_hbm = fl / (fpeak * 1e12), by / (peaks["hbm_gbs"] * 1e9)
+        if t_alu <= t_hbm:
+            continue
+        ms_k = prof[kern][0] / args.steps
+        hbm = rf_all[kern]
+        rate = fl / (ms_k / 1e3) / 1e12
+        rf_all[kern] = dict(hbm, bound="alu", achieved=rate, peak=fpeak, unit="TFLOP/s", frac=rate / fpeak,
+                            peak_source=fsrc, hbm_frac=hbm["frac"], floor_ms={"alu": t_alu * 1e3, "hbm": t_hbm * 1e3})
+        if rf_dom["kernel"] == kern:
+            rf_dom = rf_all[kern]
     if rank != 0:
         if dist:
             dist.destroy_process_group()
