@@ -1257,21 +1257,22 @@ __global__ void __launch_bounds__(256) lu_swap_pack_pair_kernel(float* __restric
   }
 }
 
-// inv(L11) of the two-panel block at k0 (see launch_lu_pair_linv), one 32-column slice per block:
+// inv(L11) of the two-panel block at k0 (see launch_lu_pair_linv), one CTA per point:
 //   T = Lp inv(L_1)   (Lp = rows P_2 moved to the top of panel 2, first panel's columns),
 //   X = -inv(L_2) T,
-// both products over the nonzero (lower-triangular) part of the inverses only; 4 x 4 outputs per
-// thread. The slice of the diagonal blocks and of the zero block is written alongside.
+// both products over the nonzero (lower-triangular) part of the inverses only; 8 x 8 outputs per
+// thread (16 x 16 threads), operands from shared memory. The diagonal blocks and the zero block are
+// written alongside.
 __global__ void __launch_bounds__(256) lu_pair_linv_kernel(const float* __restrict__ fac, const int* __restrict__ perm,
                                                            const float* __restrict__ linv, int n, int k0,
                                                            float* __restrict__ o_hi, float* __restrict__ o_lo) {
-  constexpr int P = kPairP, LD = P + 4, S = 32;
+  constexpr int P = kPairP, LD = P + 4;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float* Mt = reinterpret_cast<float*>(smraw);  // Lp^T, then inv(L_2)^T   [k][i], P x LD
-  float* Ia = Mt + P * LD;                      // inv(L_1)[:, slice]       [k][j], P x S
-  float* Ts = Ia + P * S;                       // T[:, slice]              [i][j], P x S
-  int* srow = reinterpret_cast<int*>(Ts + P * S);
-  const int mat = blockIdx.x, j0 = blockIdx.y * S, tid = threadIdx.x;
+  float* Mt = reinterpret_cast<float*>(smraw);  // Lp^T, then inv(L_2)^T   [k][i]
+  float* Ia = Mt + P * LD;                      // inv(L_1), upper part 0  [k][j]
+  float* Ts = Ia + P * LD;                      // T                       [k][j]
+  int* srow = reinterpret_cast<int*>(Ts + P * LD);
+  const int mat = blockIdx.x, tid = threadIdx.x;
   const float* A = fac + static_cast<size_t>(mat) * n * n;
   const int npan = (n + P - 1) / P, pan = k0 / P;
   const int* rec2 = perm + (static_cast<size_t>(mat) * npan + pan + 1) * perm_stride(P);
@@ -1299,74 +1300,89 @@ __global__ void __launch_bounds__(256) lu_pair_linv_kernel(const float* __restri
   };
   load_t([&](int i) { return A + static_cast<size_t>(srow[i]) * n + k0; });
   {
-    float4 v[4];
+    float4 v[16];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = tid + 256 * u, k = f / (S / 4), j = 4 * (f % (S / 4));
-      v[u] = *reinterpret_cast<const float4*>(La + k * P + j0 + j);
+    for (int u = 0; u < 16; ++u) {
+      const int f = tid + 256 * u, k = f / (P / 4), j = 4 * (f % (P / 4));
+      v[u] = *reinterpret_cast<const float4*>(La + k * P + j);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int f = tid + 256 * u, k = f / (S / 4), j = 4 * (f % (S / 4));
-      float* d = Ia + k * S + j;
-      // inv(L_1) is lower triangular: only k >= column is kept
-      d[0] = k >= j0 + j ? v[u].x : 0.f;
-      d[1] = k >= j0 + j + 1 ? v[u].y : 0.f;
-      d[2] = k >= j0 + j + 2 ? v[u].z : 0.f;
-      d[3] = k >= j0 + j + 3 ? v[u].w : 0.f;
+    for (int u = 0; u < 16; ++u) {
+      const int f = tid + 256 * u, k = f / (P / 4), j = 4 * (f % (P / 4));
+      // inv(L_1) is lower triangular: entries above the diagonal are zero
+      *reinterpret_cast<float4*>(Ia + k * LD + j) =
+          make_float4(k >= j ? v[u].x : 0.f, k >= j + 1 ? v[u].y : 0.f, k >= j + 2 ? v[u].z : 0.f,
+                      k >= j + 3 ? v[u].w : 0.f);
     }
   }
   __syncthreads();
-  const int ti = tid / 8, tj = tid % 8;  // rows 4 ti .. +3, slice columns 4 tj .. +3
-  float acc[4][4] = {};
-  for (int k = j0 + 4 * tj; k < P; ++k) {  // inv(L_1)[k][j] = 0 for k < j
-    const float4 a = *reinterpret_cast<const float4*>(Mt + k * LD + 4 * ti);
-    const float4 b = *reinterpret_cast<const float4*>(Ia + k * S + 4 * tj);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+  const int ti = tid / 16, tj = tid % 16;  // rows 8 ti .. +7, columns 8 tj .. +7
+  float acc[8][8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  for (int k = 8 * tj; k < P; ++k) {  // inv(L_1)[k][j] = 0 for k < j
+    const float4 a0 = *reinterpret_cast<const float4*>(Mt + k * LD + 8 * ti);
+    const float4 a1 = *reinterpret_cast<const float4*>(Mt + k * LD + 8 * ti + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Ia + k * LD + 8 * tj);
+    const float4 b1 = *reinterpret_cast<const float4*>(Ia + k * LD + 8 * tj + 4);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
-    *reinterpret_cast<float4*>(Ts + (4 * ti + r) * S + 4 * tj) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+  for (int r = 0; r < 8; ++r) {
+    float* d = Ts + (8 * ti + r) * LD + 8 * tj;
+    *reinterpret_cast<float4*>(d) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    *reinterpret_cast<float4*>(d + 4) = make_float4(acc[r][4], acc[r][5], acc[r][6], acc[r][7]);
+  }
   __syncthreads();
   load_t([&](int i) { return Lb + static_cast<size_t>(i) * P; });
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-  for (int k = 0; k <= 4 * ti + 3; ++k) {  // inv(L_2)[i][k] = 0 for k > i
-    const float4 a = *reinterpret_cast<const float4*>(Mt + k * LD + 4 * ti);
-    const float4 b = *reinterpret_cast<const float4*>(Ts + k * S + 4 * tj);
-    const float av[4] = {k <= 4 * ti ? a.x : 0.f, k <= 4 * ti + 1 ? a.y : 0.f, k <= 4 * ti + 2 ? a.z : 0.f, a.w};
-    const float bv[4] = {b.x, b.y, b.z, b.w};
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+  for (int k = 0; k <= 8 * ti + 7; ++k) {  // inv(L_2)[i][k] = 0 for k > i
+    const float4 a0 = *reinterpret_cast<const float4*>(Mt + k * LD + 8 * ti);
+    const float4 a1 = *reinterpret_cast<const float4*>(Mt + k * LD + 8 * ti + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(Ts + k * LD + 8 * tj);
+    const float4 b1 = *reinterpret_cast<const float4*>(Ts + k * LD + 8 * tj + 4);
+    const float ar[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    float av[8];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < 8; ++r) av[r] = k <= 8 * ti + r ? ar[r] : 0.f;
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
   }
   constexpr int W = 2 * P;
   float* oh = o_hi + static_cast<size_t>(mat) * W * W;
   float* ol = o_lo + static_cast<size_t>(mat) * W * W;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    float4 h, l;
-    split_tf32(-acc[r][0], h.x, l.x);
-    split_tf32(-acc[r][1], h.y, l.y);
-    split_tf32(-acc[r][2], h.z, l.z);
-    split_tf32(-acc[r][3], h.w, l.w);
-    const size_t o = static_cast<size_t>(P + 4 * ti + r) * W + j0 + 4 * tj;
-    *reinterpret_cast<float4*>(oh + o) = h;
-    *reinterpret_cast<float4*>(ol + o) = l;
-  }
-  // diagonal blocks (lower triangles of the panel inverses) and the zero block, this slice:
-  // 128 rows x 8 float4 per block
+  for (int r = 0; r < 8; ++r) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int f = tid + 256 * u, i = f / (S / 4), j = j0 + 4 * (f % (S / 4));
+    for (int h = 0; h < 2; ++h) {
+      float4 hi, lo;
+      split_tf32(-acc[r][4 * h], hi.x, lo.x);
+      split_tf32(-acc[r][4 * h + 1], hi.y, lo.y);
+      split_tf32(-acc[r][4 * h + 2], hi.z, lo.z);
+      split_tf32(-acc[r][4 * h + 3], hi.w, lo.w);
+      const size_t o = static_cast<size_t>(P + 8 * ti + r) * W + 8 * tj + 4 * h;
+      *reinterpret_cast<float4*>(oh + o) = hi;
+      *reinterpret_cast<float4*>(ol + o) = lo;
+    }
+  }
+  // diagonal blocks (lower triangles of the panel inverses) and the zero block: 128 rows x 32 float4
+#pragma unroll 4
+  for (int u = 0; u < 16; ++u) {
+    const int f = tid + 256 * u, i = f / (P / 4), j = 4 * (f % (P / 4));
     const float4 a = *reinterpret_cast<const float4*>(La + i * P + j);
     const float4 b = *reinterpret_cast<const float4*>(Lb + i * P + j);
     const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
@@ -1881,13 +1897,13 @@ void launch_lu_swap_pack_pair(float* fac, const int* perm, int nx, int n, int k0
 void launch_lu_pair_linv(const float* fac, const int* perm, const float* linv, int nx, int n, int k0,
                          float* o_hi, float* o_lo, cudaStream_t st) {
   constexpr int P = kPairP;
-  const size_t smem = (static_cast<size_t>(P) * (P + 4) + 2ull * P * 32) * sizeof(float) + P * sizeof(int);
+  const size_t smem = 3ull * P * (P + 4) * sizeof(float) + P * sizeof(int);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lu_pair_linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(lu_pair_linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  lu_pair_linv_kernel<<<dim3(nx, P / 32), 256, smem, st>>>(fac, perm, linv, n, k0, o_hi, o_lo);
+  lu_pair_linv_kernel<<<nx, 256, smem, st>>>(fac, perm, linv, n, k0, o_hi, o_lo);
 }
 
 template <typename T>

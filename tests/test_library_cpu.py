@@ -146,3 +146,25 @@ def test_structured_flag_validates_nr_without_device_work():
     h = C.c_void_p()
     assert lib.bte_create(C.byref(c), C.byref(h)) == bte.EINVAL
     assert b"nr <= 64" in lib.bte_last_error(None)
+
+
+def test_self_consistent_entry_points_validate_without_device_work(lib):
+    """The field, ion and implicit entry points reject NULL arguments and bad ion coefficients,
+    and refuse a host-only handle (no device buffers), before any device work."""
+    import ctypes as C
+    from paper_2502_16555_gb300 import bte
+    s = _solver(W.scaled(W.SMALL, nx=5, nr=6, ntheta=4))
+    p = C.c_void_p(1)
+    assert lib.bte_set_ion_transport(s.h, -1.0, 1.0) == bte.EINVAL
+    assert lib.bte_set_ion_transport(s.h, 1.0, 0.0) == bte.EINVAL
+    assert lib.bte_set_ion_transport(s.h, 4.65e21, 2.07e20) == bte.OK
+    assert lib.bte_field(s.h, None, None, 0.0, 1.0, 1.0, p) == bte.EINVAL
+    assert lib.bte_field(s.h, p, None, 0.0, 1.0, 1.0, p) == bte.ESTATE
+    assert lib.bte_ion_step(s.h, None, p, 0.0, 1.0, 1.0) == bte.EINVAL
+    assert lib.bte_ion_step(s.h, p, p, 0.0, 1.0, 1.0) == bte.ESTATE
+    assert lib.bte_step_sc(s.h, p, None, 0.0, 1.0, 1.0, None) == bte.EINVAL
+    assert lib.bte_step_sc(s.h, p, p, 0.0, 1.0, 1.0, None) == bte.ESTATE
+    o = bte.ImplicitOpts()
+    assert lib.bte_step_implicit(s.h, p, None, 0.0, 1.0, 1.0, C.byref(o)) == bte.EINVAL
+    assert lib.bte_step_implicit(s.h, p, p, 0.0, 1.0, 1.0, C.byref(o)) == bte.ESTATE
+    assert lib.bte_step_implicit(None, p, p, 0.0, 1.0, 1.0, None) == bte.EINVAL
