@@ -637,6 +637,92 @@ def run_hybrid(args, rank, world):
     return 0
 
 
+HYBRID_TABLE = "hybrid_table_nt16_nl3"
+# The rows of the paper's table comparing the two electron schemes in the hybrid model
+# (Section 5.3, Table "performance_hybrid"): (Nr, Nx) at Ntheta = 16 ordinates and N_l = 3
+# harmonics, semi-implicit at dt f = 5e-5, fully-implicit at dt f = 2e-4; the paper's step
+# times on one A100 (seconds, whole hybrid step with the ions), context only.
+TABLE_ROWS = [(64, 100, 3.53e-2, 6.52e-2), (128, 100, 3.61e-2, 6.55e-2), (256, 100, 3.71e-2, 6.68e-2),
+              (128, 200, 3.93e-2, 2.52e-1)]
+
+
+def run_hybrid_table(args, rank, world):
+    """The whole hybrid step (ion step, then the electron step) on the paper's table rows, both
+    electron schemes, from the workload's initial state (Maxwellian at 2 eV, n_e peak 1e15 m^-3)
+    with parabolic ions (peak 1.05e15 m^-3), argon at 1 Torr with the three analytic processes,
+    V0 = 100 V. Times are CUDA events around `steps` consecutive steps after `warmup` steps; the
+    fully-implicit leg records its Newton and GMRES counts and whether each step converged."""
+    import ctypes as C
+    import torch
+    from paper_2502_16555_gb300 import bte
+    from oracle import bte as O
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank != 0:
+        return 0
+    f = W.RF_FREQ_HZ
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = [fn(i) for i in range(n)]
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n, out
+
+    rows = []
+    for nr, nx, paper_semi, paper_fully in TABLE_ROWS:
+        row = {"nr": nr, "ntheta": 16, "nl": 3, "nx": nx, "dof": nx * nr * 16,
+               "paper_a100_s": {"semi_implicit": paper_semi, "fully_implicit": paper_fully,
+                                "speedup": 4 * paper_semi / paper_fully}}
+        x = O.cheb_points(nx, W.GAP_M)
+        ni0 = torch.from_numpy(1.05e15 * (1.0 - (2.0 * x / W.GAP_M - 1.0) ** 2) + 1e13).cuda()
+        for tag, dtf in (("semi_implicit", 5e-5), ("fully_implicit", 2e-4)):
+            cfg = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=16, nl=3, p_Torr=1.0, V0=100.0, dt_s=dtf / f)
+            s = bte.Solver(cfg, precision="mixed")
+            F, ni = s.initial_state(), ni0.clone()
+            t0 = 0.25 / f
+            opts = bte.ImplicitOpts(newton_max=12, gmres_max=1000)
+
+            def step(i, s=s, F=F, ni=ni, cfg=cfg, tag=tag, opts=opts):
+                t = t0 + i * cfg["dt_s"]
+                s.ion_step(ni, F, t)
+                if tag == "semi_implicit":
+                    s.step_sc(F, ni, t)
+                    return (bte.OK, 0, 0, 0.0)
+                st = s.lib.bte_step_implicit(s.h, bte._ptr(F), bte._ptr(ni), t, float(cfg["V0"]),
+                                             float(cfg["freq_Hz"]), C.byref(opts))
+                return (st, opts.newton_iters, opts.gmres_iters, opts.residual)
+
+            for i in range(args.warmup):
+                step(i)
+            n = args.steps if tag == "semi_implicit" else max(1, min(args.steps, 3))
+            ms, stats = timed(lambda i: step(args.warmup + i), n)
+            leg = {"ms_per_step": ms, "dt_f": dtf, "steps": n}
+            if tag == "fully_implicit":
+                leg.update({"converged_steps": sum(1 for st in stats if st[0] == bte.OK),
+                            "newton_per_step": sum(st[1] for st in stats) / n,
+                            "gmres_per_step": sum(st[2] for st in stats) / n,
+                            "relative_residuals": [st[3] for st in stats]})
+            row[tag] = leg
+            del s, F, ni
+            torch.cuda.empty_cache()
+        # overall runtime for the same simulated time, semi-implicit over fully-implicit
+        row["speedup"] = 4 * row["semi_implicit"]["ms_per_step"] / row["fully_implicit"]["ms_per_step"]
+        row["semi_implicit_vs_paper"] = paper_semi * 1e3 / row["semi_implicit"]["ms_per_step"]
+        row["fully_implicit_vs_paper"] = paper_fully * 1e3 / row["fully_implicit"]["ms_per_step"]
+        rows.append(row)
+    out = {"metric": "hybrid step time, semi-implicit vs fully-implicit electrons (ions included)",
+           "unit": "ms/step", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "data": "synthetic", "dtype": "tf32x3+f64",
+           "config": {"workload": HYBRID_TABLE, "precision": "mixed", "p_Torr": 1.0, "V0": 100.0,
+                      "ions": "parabolic, peak 1.05e15 m^-3"},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def run_adjoint(args, rank, world):
     """Gradient of the cycle-averaged electron number over one RF cycle (1000 steps, FP64,
     Nx=64, Nr=32, Ntheta=16) with respect to 8 parameters (four cross-section scales, three
@@ -720,10 +806,11 @@ def main():
     ap.add_argument("--no-structured", action="store_true", help="skip the block-tridiagonal solve legs")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, LARGEST, "batched64_uneven", "adjoint_nx64_nr32_nt16", HYBRID],
+                    choices=[WORKLOAD, LARGEST, "batched64_uneven", "adjoint_nx64_nr32_nt16", HYBRID, HYBRID_TABLE],
                     help="the headline single discharge (default), the largest single discharge (Nv = 4096; "
                          "use a few steps: its FP64 leg takes seconds per step), the 64 uneven discharges "
-                         "in one graph, or the adjoint-gradient check")
+                         "in one graph, the adjoint-gradient check, the self-consistent parts on the medium grid, "
+                         "or the paper's semi- vs fully-implicit table rows")
     ap.add_argument("--adjoint-steps", type=int, default=0, help="adjoint workload: steps (0 = one RF cycle)")
     ap.add_argument("--batched-fp64", action="store_true", help="batched workload: also time the FP64 batch")
     ap.add_argument("--nx", type=int, default=0,
@@ -741,6 +828,8 @@ def main():
         return run_adjoint(args, rank, world)
     if args.workload == HYBRID:
         return run_hybrid(args, rank, world)
+    if args.workload == HYBRID_TABLE:
+        return run_hybrid_table(args, rank, world)
     return run_ours(args, rank, world)
 
 

@@ -36,7 +36,8 @@ typedef enum {
   BTE_OK = 0,
   BTE_EINVAL = 1,      /* bad argument (NULL, size, nl > ntheta, unknown enum ...) */
   BTE_ENOMEM = 2,      /* device or host allocation failed */
-  BTE_ECUDA = 3,       /* a CUDA runtime call failed (message in bte_last_error) */
+  BTE_ECUDA = 3,       /* a CUDA runtime call or launch failed, or a CUDA error was already pending when
+                          the call began (message in bte_last_error; a pending error is cleared) */
   BTE_ESINGULAR = 4,   /* a zero or non-finite pivot in some per-point factorisation */
   BTE_ENOCONV = 5,     /* iterative refinement did not reach refine_tol within refine_max sweeps */
   BTE_ENONFINITE = 6,  /* the input or the result of a step holds NaN/Inf */
@@ -64,6 +65,12 @@ typedef enum {
                                    trailing matrix on its own (K = 128) instead of two panels at a time
                                    (K = 256, half the trailing-matrix traffic); same factors up to
                                    rounding order */
+#define BTE_FLAG_FULL_V 16u     /* with nl < ntheta, factor the full Nv x Nv matrix A_i per point. By
+                                   default such a handle factors the reduced matrix I - dt B_i of order
+                                   nl * nr (B = C + E A_v in the harmonic basis, Section 3.3) and solves
+                                   through A^-1 f = f + P_O((I - dt B)^-1 - I) P_S f: the same solution,
+                                   (nv / (nl nr))^3 fewer factorisation flops and (nv / (nl nr))^2 less
+                                   factor memory. bte_step_adjoint needs the full factors. */
 
 typedef struct {
   int nx;            /* Chebyshev-Gauss-Lobatto points, >= 3 */
@@ -119,6 +126,8 @@ typedef struct {
                              4 not converged) */
   unsigned long long launches; /* kernels launched by this handle so far */
   int tensor_cores;       /* 1 if the trailing updates run on tcgen05 (TF32x3) */
+  int solve_n;            /* order of the per-point factorisation: nv, or nl * nr for the reduced
+                             system (nl < ntheta without BTE_FLAG_FULL_V); 0 with BTE_FLAG_STRUCTURED */
 } bte_info;
 
 /* Kernel classes reported by bte_profile (index into its output arrays). */
@@ -131,6 +140,8 @@ enum {
 /* Create a handle: validates cfg, assembles the grids and the x-step operators on the host (the
  * velocity operators need bte_set_cross_sections), and allocates its device buffers with cudaMalloc.
  * Ownership: the handle owns every buffer it allocates; free with bte_destroy.
+ * Limits (BTE_EINVAL beyond them, set by the kernels' shared-memory plans): nx in [3, 4096],
+ * nr in [4, 880], ntheta >= 2, 1 <= nl <= ntheta, nr * ntheta <= 7936.
  * Section 3.4 (discretisation) and Algorithm 1 (precomputed Q_ij). */
 bte_status bte_create(const bte_config* cfg, bte_handle** out);
 

@@ -111,6 +111,8 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
   if (h->host_only || !h->ops.have_v) return afail(h, BTE_ESTATE, "needs device buffers and cross sections");
   if (h->precision != BTE_FP64) return afail(h, BTE_ESTATE, "the adjoint is implemented for FP64 handles");
   if (h->structured) return afail(h, BTE_ESTATE, "the adjoint needs the dense factorisation (no BTE_FLAG_STRUCTURED)");
+  if (h->reduced)
+    return afail(h, BTE_ESTATE, "the adjoint needs the full Nv x Nv factors (BTE_FLAG_FULL_V when nl < ntheta)");
   bte_status s = ensure_transposed(h);
   if (s != BTE_OK) return s;
   const bte::HostOps& o = h->ops;

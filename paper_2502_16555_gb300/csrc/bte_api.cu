@@ -34,6 +34,12 @@ bte_status cuda_fail(bte_handle* h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
   } while (0)
 
+#define BTE_TRY(x)               \
+  do {                           \
+    const bte_status r_ = (x);   \
+    if (r_ != BTE_OK) return r_; \
+  } while (0)
+
 template <typename T>
 bte_status dalloc(bte_handle* h, T** p, size_t count) {
   void* q = nullptr;
@@ -82,22 +88,74 @@ struct Launch {
     }
   }
 };
-#define BTE_LAUNCH(kind, call) \
-  do {                         \
-    Launch l_(h, kind);        \
-    call;                      \
+// A launch whose configuration the runtime rejects (grid, block, shared memory, cluster shape)
+// fails the call at once, naming the launcher; execution errors surface at the next sync.
+bte_status launch_fail(bte_handle* h, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  std::string w(what);
+  const size_t paren = w.find('(');
+  return fail(h, BTE_ECUDA, "launch rejected in " + w.substr(0, paren) + ": " + cudaGetErrorString(e));
+}
+#define BTE_LAUNCH(kind, call)                                    \
+  do {                                                            \
+    {                                                             \
+      Launch l_(h, kind);                                         \
+      call;                                                       \
+    }                                                             \
+    const cudaError_t le_ = cudaPeekAtLastError();                \
+    if (le_ != cudaSuccess) return launch_fail(h, le_, #call);    \
   } while (0)
 
-bool device_ready(bte_handle* h) {
-  if (h->host_only) {
-    h->err = "handle was created with BTE_FLAG_HOST_ONLY";
-    return false;
+bte_status device_status(bte_handle* h) {
+  if (h->host_only) return fail(h, BTE_ESTATE, "handle was created with BTE_FLAG_HOST_ONLY");
+  if (!h->ops.have_v) return fail(h, BTE_ESTATE, "bte_set_cross_sections has not been called");
+  // a launch error left behind by earlier work in the process (ours or the caller's) is reported
+  // here, not against the first launch of this call
+  const cudaError_t pend = cudaGetLastError();
+  if (pend != cudaSuccess)
+    return fail(h, BTE_ECUDA, std::string("a CUDA error was pending before this call: ") + cudaGetErrorString(pend));
+  return BTE_OK;
+}
+
+// out_i (+)= A_i^-1 in_i through the factors of the last factoring call (dense paths), at the
+// points with conv[i] == 0 (conv NULL: every point). With the reduced system (nl < ntheta) the
+// factors are those of G_i = I - dt B_i and A_i^-1 f = f + P_O (G_i^-1 - I) P_S f (Section 3.3).
+bte_status enqueue_lu_solve(bte_handle* h, const double* in, double* out, const int* conv, int accumulate) {
+  const HostOps& o = h->ops;
+  const int nx = o.nx, n = h->nlu, nb = h->nb;
+  cudaStream_t st = h->st;
+  const double* src = in;
+  double* dst = out;
+  int acc = accumulate;
+  if (h->reduced) {
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_reduce_project(in, h->TS, h->yred, conv, nx, o.nt, o.nr, o.nl, st));
+    src = h->yred;
+    dst = h->zred;
+    acc = 0;
   }
-  if (!h->ops.have_v) {
-    h->err = "bte_set_cross_sections has not been called";
-    return false;
-  }
-  return true;
+  if (h->precision == BTE_FP64)
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(static_cast<double*>(h->fac), h->piv, src, dst, nx, n, nb,
+                                                            conv, acc, st));
+  else
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(static_cast<float*>(h->fac), h->perm,
+                                                                   static_cast<float*>(h->linv),
+                                                                   static_cast<float*>(h->uinv), src, dst, nx, n, nb,
+                                                                   conv, acc, st));
+  if (h->reduced)
+    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_reduce_lift(in, h->yred, h->zred, h->TO, out, conv, accumulate, nx, o.nt,
+                                                       o.nr, o.nl, st));
+  return BTE_OK;
+}
+
+// The per-point matrices the dense paths factor: A_i = I - dt (K_C + E_i K_A), or G_i = I - dt B_i
+// (order nl * nr) for the reduced system.
+template <typename T>
+void form_v(bte_handle* h, const double* E_dev, double Eu, T* fac) {
+  const HostOps& o = h->ops;
+  if (h->reduced)
+    bte::launch_v_form_reduced<T>(h->Cs, h->Alo, h->Aup, E_dev, Eu, o.dt, fac, o.nx, o.nr, o.nl, h->st);
+  else
+    bte::launch_v_form<T>(h->KC, h->KA, E_dev, Eu, o.dt, fac, o.nx, o.nv, h->st);
 }
 
 // Velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system"): out_i = A_i^-1 in_i at
@@ -107,9 +165,9 @@ bool device_ready(bte_handle* h) {
 bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const double* E_dev, double Eu,
                           bool factor) {
   const HostOps& o = h->ops;
-  const int nx = o.nx, nt = o.nt, nr = o.nr, nv = o.nv, nl = o.nl;
+  const int nx = o.nx, nt = o.nt, nr = o.nr, nl = o.nl;
   cudaStream_t st = h->st;
-  const int n = nv, nb = h->nb;
+  const int n = h->nlu, nb = h->nb;
   if (h->structured) {
     if (h->precision == BTE_FP64)
       BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(in, out, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
@@ -122,7 +180,7 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
   } else if (h->precision == BTE_FP64) {
     double* fac = static_cast<double*>(h->fac);
     if (factor) {
-      BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<double>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
+      BTE_LAUNCH(BTE_K_V_FORM, form_v<double>(h, E_dev, Eu, fac));
       for (int k0 = 0; k0 < n; k0 += nb) {
         const int kb = std::min(nb, n - k0);
         BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<double>(fac, h->piv, h->perm, static_cast<double*>(h->linv), nullptr,
@@ -135,14 +193,13 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
         }
       }
     }
-    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(fac, h->piv, in, out, nx, n, nb, nullptr, 0, st));
   } else {
     float* fac = static_cast<float*>(h->fac);
     const bool fused_uinv = bte::lu_panel_fuses_uinv<float>(n, nb, h->panel_w);
     float* linv = static_cast<float*>(h->linv);
     float* uinv = fused_uinv ? static_cast<float*>(h->uinv) : nullptr;
     if (factor) {
-      BTE_LAUNCH(BTE_K_V_FORM, bte::launch_v_form<float>(h->KC, h->KA, E_dev, Eu, o.dt, fac, nx, nv, st));
+      BTE_LAUNCH(BTE_K_V_FORM, form_v<float>(h, E_dev, Eu, fac));
       if (h->use_tc) {
         // workspace parts (tc_ws_part): 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11)
         // split, 8-9 the two-panel block's inv(L11) split (6-7, U12^T, stay inside the tc_lu_* calls)
@@ -154,6 +211,7 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
           BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
                                                                  h->status, nullptr, nullptr, ws[4], ws[5],
                                                                  h->panel_w, st));
+          return BTE_OK;
         };
         // the panel at k0 applied to the next ncols columns (U12, then A22 -= L21 U12)
         auto single = [&](int k0, int ncols) {
@@ -161,12 +219,13 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
                                                                   ws[3], ws[0], ws[1], st));
           BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, ncols, h->tcws, h->status, st));
           BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, ncols, h->tcws, h->status, st));
+          return BTE_OK;
         };
         if (!h->tc_pair) {
           for (int k0 = 0; k0 < n; k0 += nb) {
             const int kb = std::min(nb, n - k0);
-            panel(k0, kb);
-            if (k0 + kb < n) single(k0, n - k0 - kb);
+            BTE_TRY(panel(k0, kb));
+            if (k0 + kb < n) BTE_TRY(single(k0, n - k0 - kb));
           }
         } else {
           // panels in pairs: the first panel updates only the second panel's columns; once the
@@ -174,11 +233,11 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
           // writes the trailing matrix once per pair instead of once per panel
           for (int k0 = 0; k0 < n; k0 += 2 * nb) {
             const int kb1 = std::min(nb, n - k0);
-            panel(k0, kb1);
+            BTE_TRY(panel(k0, kb1));
             if (k0 + kb1 == n) break;
             const int kb2 = std::min(nb, n - k0 - nb);
-            single(k0, kb2);
-            panel(k0 + nb, kb2);
+            BTE_TRY(single(k0, kb2));
+            BTE_TRY(panel(k0 + nb, kb2));
             if (k0 + nb + kb2 == n) break;
             BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_pair_linv(fac, h->perm, linv, nx, n, k0, ws[8], ws[9], st));
             BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack_pair(fac, h->perm, nx, n, k0, ks, ws[2], ws[3],
@@ -203,10 +262,8 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
       if (!fused_uinv)
         BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_uinv<float>(fac, static_cast<float*>(h->uinv), nx, n, nb, st));
     }
-    BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(fac, h->perm, static_cast<float*>(h->linv),
-                                                                   static_cast<float*>(h->uinv), in, out, nx, n,
-                                                                   nb, nullptr, 0, st));
   }
+  if (!h->structured) BTE_TRY(enqueue_lu_solve(h, in, out, nullptr, 0));
   return BTE_OK;
 }
 
@@ -229,7 +286,6 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     E_dev = h->Esc;
   }
   // velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system")
-  const int n = nv, nb = h->nb;
   {
     const bte_status vs = enqueue_vsolve(h, h->Fa, h->Fb, E_dev, Eu, true);
     if (vs != BTE_OK) return vs;
@@ -250,12 +306,8 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
         BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<float>(h->R, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
                                                                     h->TO, h->TS, static_cast<float*>(h->xs), nx, nt,
                                                                     nr, nl, h->conv, 1, nullptr, st));
-      else if (h->precision == BTE_FP64)
-        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(static_cast<double*>(h->fac), h->piv, h->R, h->Fb, nx, n, nb, h->conv, 1, st));
       else
-        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(
-                                       static_cast<float*>(h->fac), h->perm, static_cast<float*>(h->linv),
-                                       static_cast<float*>(h->uinv), h->R, h->Fb, nx, n, nb, h->conv, 1, st));
+        BTE_TRY(enqueue_lu_solve(h, h->R, h->Fb, h->conv, 1));
     }
     BTE_LAUNCH(BTE_K_OTHER, bte::launch_check_conv(h->conv, nx, h->status, st));
   }
@@ -308,8 +360,13 @@ bool valid_cfg(const bte_config* c, std::string& why) {
       !(c->dt_s > 0))
     return why = "L_m, vmax_eV, p_Torr, T0_K, m0_amu and dt_s must be positive", false;
   if (c->precision != BTE_FP64 && c->precision != BTE_MIXED) return why = "unknown precision", false;
+  // what the kernels' shared-memory plans hold (opt-in sizes): the eigen-basis transforms stage
+  // nr x 33 doubles (nr <= 880); the FP64 panel of a tall first panel stages about 28 bytes per
+  // row (nv <= 7936); the structured residual and operator applies stage nv + 2 nl nr <= 3 nv
+  // doubles, within 220 KB under that bound
   const double nv = static_cast<double>(c->nr) * c->ntheta;
-  if (nv > 16384 || c->nx > 4096) return why = "grid too large (nr*ntheta <= 16384, nx <= 4096)", false;
+  if (c->nr > bte::kMaxNr) return why = "nr must be <= 880", false;
+  if (nv > bte::kMaxNv || c->nx > 4096) return why = "grid too large (nr*ntheta <= 7936, nx <= 4096)", false;
   return true;
 }
 
@@ -318,7 +375,7 @@ bool valid_cfg(const bte_config* c, std::string& why) {
 namespace bte {
 bte_status handle_enqueue_step(bte_handle* h, double* F_dev, const double* E_dev, double t, double V0, double freq,
                                cudaStream_t st) {
-  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_TRY(device_status(h));
   cudaStream_t own = h->st;
   h->st = st;
   bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t, V0, freq);
@@ -346,7 +403,7 @@ bte_status handle_reset_status(bte_handle* h, cudaStream_t st) {
   return BTE_OK;
 }
 bte_status handle_read_status(bte_handle* h) { return read_status(h); }
-bool handle_device_ready(bte_handle* h) { return device_ready(h); }
+bte_status handle_device_status(bte_handle* h) { return device_status(h); }
 bool handle_profiling(const bte_handle* h) { return h->prof; }
 unsigned long long handle_launches(const bte_handle* h) { return h->launches; }
 void handle_add_launches(bte_handle* h, unsigned long long n) { h->launches += n; }
@@ -381,6 +438,11 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   h->nb = cfg->precision == BTE_FP64 ? 64 : 128;
   h->structured = (cfg->flags & BTE_FLAG_STRUCTURED) != 0;
   h->tc_pair = (cfg->flags & BTE_FLAG_TC_SINGLE) == 0;
+  {
+    const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
+    h->reduced = !h->structured && nl < cfg->ntheta && (cfg->flags & BTE_FLAG_FULL_V) == 0;
+    h->nlu = h->reduced ? nl * cfg->nr : cfg->nr * cfg->ntheta;
+  }
   if (h->structured) {
     const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
     const size_t ts = cfg->precision == BTE_FP64 ? 8 : 4;
@@ -399,11 +461,15 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   if (!h->host_only) {
     const HostOps& o = h->ops;
     const size_t D = static_cast<size_t>(o.nx) * o.nv;
-    const size_t nn = static_cast<size_t>(o.nv) * o.nv;
+    const size_t nn = static_cast<size_t>(h->nlu) * h->nlu;
+    // the dense K_C, K_A (nv x nv) serve only the full-matrix form and the adjoint
+    const bool dense_k = !h->reduced && !h->structured;
     bte_status s;
     auto chk = [&](bte_status r) { s = r; return r == BTE_OK; };
     bool ok = chk(dalloc(h, &h->U, o.U.size())) && chk(dalloc(h, &h->Uinv, o.Uinv.size())) &&
-              chk(dalloc(h, &h->Q, o.Q.size())) && chk(dalloc(h, &h->KC, nn)) && chk(dalloc(h, &h->KA, nn)) &&
+              chk(dalloc(h, &h->Q, o.Q.size())) &&
+              (!dense_k || (chk(dalloc(h, &h->KC, static_cast<size_t>(o.nv) * o.nv)) &&
+                            chk(dalloc(h, &h->KA, static_cast<size_t>(o.nv) * o.nv)))) &&
               chk(dalloc(h, &h->Cs, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Alo, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Aup, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
@@ -413,7 +479,7 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
               chk(dalloc(h, &h->Fb, D)) && chk(dalloc(h, &h->Fw, D)) && chk(dalloc(h, &h->R, D)) &&
               chk(dalloc(h, &h->Fhost_dev, D)) && chk(dalloc(h, &h->coef, o.nr)) &&
               chk(dalloc(h, &h->ratio, o.nx)) && chk(dalloc(h, &h->piv, D)) &&
-              chk(dalloc(h, &h->perm, static_cast<size_t>(o.nx) * ((o.nv + h->nb - 1) / h->nb) *
+              chk(dalloc(h, &h->perm, static_cast<size_t>(o.nx) * ((h->nlu + h->nb - 1) / h->nb) *
                                           bte::perm_record_ints(h->nb))) &&
               chk(dalloc(h, &h->conv, o.nx)) && chk(dalloc(h, &h->status, 2));
     if (ok && h->structured) {
@@ -428,23 +494,26 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
         h->xs = x;
       }
     } else if (ok) {
-      const size_t npan = (o.nv + h->nb - 1) / h->nb;
+      if (h->reduced)
+        ok = chk(dalloc(h, &h->yred, static_cast<size_t>(o.nx) * h->nlu)) &&
+             chk(dalloc(h, &h->zred, static_cast<size_t>(o.nx) * h->nlu));
+      const size_t npan = (h->nlu + h->nb - 1) / h->nb;
       const size_t blk = static_cast<size_t>(o.nx) * npan * h->nb * h->nb;
       if (h->precision == BTE_FP64) {
         double *f = nullptr, *l = nullptr;
-        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, blk));
+        ok = ok && chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, blk));
         h->fac = f;
         h->linv = l;
       } else {
         float *f = nullptr, *l = nullptr, *u = nullptr;
-        ok = chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, blk)) && chk(dalloc(h, &u, blk));
+        ok = ok && chk(dalloc(h, &f, nn * o.nx)) && chk(dalloc(h, &l, blk)) && chk(dalloc(h, &u, blk));
         h->fac = f;
         h->linv = l;
         h->uinv = u;
-        if (ok && !(cfg->flags & BTE_FLAG_SIMT_GEMM) && bte::tc_workspace_bytes(o.nx, o.nv, h->nb) > 0 &&
+        if (ok && !(cfg->flags & BTE_FLAG_SIMT_GEMM) && bte::tc_workspace_bytes(o.nx, h->nlu, h->nb) > 0 &&
             bte::tc_available()) {
           unsigned char* w = nullptr;
-          ok = chk(dalloc(h, &w, bte::tc_workspace_bytes(o.nx, o.nv, h->nb)));
+          ok = chk(dalloc(h, &w, bte::tc_workspace_bytes(o.nx, h->nlu, h->nb)));
           h->tcws = w;
           h->use_tc = ok;
           h->have_tc = ok;
@@ -512,7 +581,7 @@ bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* 
     BTE_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->mom_r), sizeof(double) * o.mom_r.size()));
   }
   bte_status s;
-  if ((s = upload(h, h->KC, o.KC)) != BTE_OK || (s = upload(h, h->KA, o.KA)) != BTE_OK ||
+  if ((h->KC && (s = upload(h, h->KC, o.KC)) != BTE_OK) || (h->KA && (s = upload(h, h->KA, o.KA)) != BTE_OK) ||
       (s = upload(h, h->Cs, o.Cs)) != BTE_OK || (s = upload(h, h->Alo, o.As_lo)) != BTE_OK ||
       (s = upload(h, h->Aup, o.As_up)) != BTE_OK || (s = upload(h, h->mom_n, o.mom_n)) != BTE_OK ||
       (s = upload(h, h->mom_e, o.mom_e)) != BTE_OK || (o.n_proc > 0 && (s = upload(h, h->mom_r, o.mom_r)) != BTE_OK))
@@ -538,7 +607,7 @@ bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_
                     double freq_Hz) {
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev) return fail(h, BTE_EINVAL, "F_dev is NULL");
-  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_TRY(device_status(h));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
   bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t_s, V0, freq_Hz);
   if (s != BTE_OK) return s;
@@ -548,7 +617,7 @@ bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_
 bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double V0, double freq_Hz) {
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || n_steps < 0) return fail(h, BTE_EINVAL, "bad arguments");
-  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_TRY(device_status(h));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
   for (int i = 0; i < n_steps; ++i) {
     bte_status s = enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * h->ops.dt, V0, freq_Hz);
@@ -560,7 +629,7 @@ bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double
 bte_status bte_step_host(bte_handle* h, double* F_host, double t_s, double V0, double freq_Hz) {
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_host) return fail(h, BTE_EINVAL, "F_host is NULL");
-  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_TRY(device_status(h));
   const size_t bytes = sizeof(double) * h->ops.nx * h->ops.nv;
   BTE_CUDA(h, cudaMemcpyAsync(h->Fhost_dev, F_host, bytes, cudaMemcpyHostToDevice, h->st));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
@@ -574,7 +643,7 @@ bte_status bte_moments(bte_handle* h, const double* F_dev, double* ne_dev, doubl
                        double* rates_dev) {
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev) return fail(h, BTE_EINVAL, "F_dev is NULL");
-  if (!device_ready(h)) return BTE_ESTATE;
+  BTE_TRY(device_status(h));
   bte::launch_moments(F_dev, h->mom_n, h->mom_e, h->mom_r, rates_dev ? h->ops.n_proc : 0, ne_dev,
                       mean_eV_dev, rates_dev, h->ops.nx, h->ops.nv, h->st);
   BTE_CUDA(h, cudaGetLastError());
@@ -630,6 +699,7 @@ bte_status bte_get_info(const bte_handle* hc, bte_info* info) {
   info->last_flags = hc->last_flags;
   info->launches = hc->launches;
   info->tensor_cores = hc->use_tc ? 1 : 0;
+  info->solve_n = hc->structured ? 0 : hc->nlu;
   return BTE_OK;
 }
 

@@ -200,7 +200,7 @@ bte_status bte_batch_create(int count, bte_handle* const* handles, void* stream,
   if (count < 1 || count > 4096 || !handles) return bfail(nullptr, BTE_EINVAL, "count must be in [1, 4096]");
   for (int i = 0; i < count; ++i) {
     if (!handles[i]) return bfail(nullptr, BTE_EINVAL, "a handle is NULL");
-    if (!bte::handle_device_ready(handles[i]))
+    if (bte::handle_device_status(handles[i]) != BTE_OK)
       return bfail(nullptr, BTE_ESTATE, "every handle needs device buffers and cross sections");
     if (bte::handle_profiling(handles[i])) return bfail(nullptr, BTE_ESTATE, "a handle is recording a profile");
     for (int j = 0; j < i; ++j)

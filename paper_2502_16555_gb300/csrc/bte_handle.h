@@ -21,6 +21,9 @@ struct bte_handle {
   int refine_max = 0;
   bool structured = false;  // block-tridiagonal velocity solve instead of the dense LU
   void* xs = nullptr;       // its per-point scratch (nx * nl * nr * nr values)
+  bool reduced = false;     // dense LU of I - dt B_i (order nl * nr) instead of A_i (order nv)
+  int nlu = 0;              // order of the per-point factorisation (nv, or nl * nr when reduced)
+  double *yred = nullptr, *zred = nullptr;  // P_S f and the reduced solution (nx * nlu each)
   bool use_tc = false;    // tcgen05 trailing update (FP32 storage only)
   bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
   int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)

@@ -170,6 +170,65 @@ __global__ void dense_solve_kernel(double* __restrict__ A, double* __restrict__ 
   }
 }
 
+// The same elimination with A and b staged in shared memory (n <= kSmemSolve): one CTA, the
+// pivot column scanned by warp 0, rows exchanged and updated in shared memory.
+constexpr int kSmemSolve = 150;
+__global__ void dense_solve_smem_kernel(const double* __restrict__ Ag, const double* __restrict__ bg, int n,
+                                        double* __restrict__ x, unsigned* status) {
+  extern __shared__ double sm[];
+  const int ld = n + 1;          // padded rows; column n holds b
+  double* A = sm;
+  __shared__ int piv;
+  __shared__ double red[32];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  for (int idx = tid; idx < n * n; idx += nt) A[(idx / n) * ld + idx % n] = Ag[idx];
+  for (int i = tid; i < n; i += nt) A[i * ld + n] = bg[i];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = fabs(A[i * ld + k]);
+        if (v > best) best = v, bi = i;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) best = ov, bi = oi;
+      }
+      if (lane == 0) {
+        piv = bi;
+        if (!(best > 0.0) || !isfinite(best)) atomicOr(status, bte::kZeroPivot);
+      }
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k)
+      for (int j = k + tid; j <= n; j += nt) {
+        const double t = A[k * ld + j];
+        A[k * ld + j] = A[p * ld + j];
+        A[p * ld + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[k * ld + k];
+    const int m = n - k - 1;
+    for (int idx = tid; idx < m * (m + 1); idx += nt) {
+      const int i = k + 1 + idx / (m + 1), j = k + 1 + idx % (m + 1);  // j == n: right-hand side
+      A[i * ld + j] -= A[i * ld + k] * inv * A[k * ld + j];
+    }
+    __syncthreads();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = 0.0;
+    for (int j = i + 1 + tid; j < n; j += nt) s = fma(A[i * ld + j], A[j * ld + n], s);
+    s = block_sum(s, red);
+    if (tid == 0) A[i * ld + n] = (A[i * ld + n] - s) / A[i * ld + i];
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) x[i] = A[i * ld + n];
+}
+
 // Y2[a][i][:] = lam_i mu_a D_x Y[a][i][:] (the x-advection operator in the eigen basis of
 // M_v^-1 G_v), one CTA per (ordinate, eigen-index), a warp per row.
 __global__ void x_dx_kernel(const double* __restrict__ Dx, const double* __restrict__ lam,
@@ -463,7 +522,10 @@ bte_status bte_field(bte_handle* h, const double* F_dev, const double* ni_dev, d
                      double freq_Hz, double* E_dev) {
   if (!h) return hfail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || !E_dev) return hfail(h, BTE_EINVAL, "F_dev and E_dev must not be NULL");
-  if (!bte::handle_device_ready(h)) return BTE_ESTATE;
+  {
+    const bte_status ds = bte::handle_device_status(h);
+    if (ds != BTE_OK) return ds;
+  }
   bte_status s = bte::hybrid_setup(h);
   if (s != BTE_OK) return s;
   return bte::enqueue_field(h, F_dev, ni_dev, t_s, V0, freq_Hz, E_dev);
@@ -473,7 +535,10 @@ bte_status bte_ion_step(bte_handle* h, double* ni_dev, const double* F_dev, doub
                         double freq_Hz) {
   if (!h) return hfail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!ni_dev || !F_dev) return hfail(h, BTE_EINVAL, "ni_dev and F_dev must not be NULL");
-  if (!bte::handle_device_ready(h)) return BTE_ESTATE;
+  {
+    const bte_status ds = bte::handle_device_status(h);
+    if (ds != BTE_OK) return ds;
+  }
   bte_status s = bte::hybrid_setup(h);
   if (s != BTE_OK) return s;
   const bte::HostOps& o = h->ops;
@@ -486,7 +551,17 @@ bte_status bte_ion_step(bte_handle* h, double* ni_dev, const double* F_dev, doub
   scale_kernel<<<(o.nx + 255) / 256, 256, 0, st>>>(h->ned, o.n0, o.nx);
   ion_assemble_kernel<<<o.nx, 256, 0, st>>>(h->Dxd, h->Esc, ni_dev, h->ned, h->n0_mu_i / o.n0, h->n0_D_i / o.n0,
                                            o.dt, o.nx, h->ionA, h->ionb);
-  dense_solve_kernel<<<1, 1024, 0, st>>>(h->ionA, h->ionb, o.nx, h->ned, h->status);
+  if (o.nx <= kSmemSolve) {
+    const size_t smem = sizeof(double) * o.nx * (o.nx + 1);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(dense_solve_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
+    dense_solve_smem_kernel<<<1, 1024, smem, st>>>(h->ionA, h->ionb, o.nx, h->ned, h->status);
+  } else {
+    dense_solve_kernel<<<1, 1024, 0, st>>>(h->ionA, h->ionb, o.nx, h->ned, h->status);
+  }
   bte::launch_commit(h->ned, ni_dev, o.nx, h->status, st);
   bte::handle_add_launches(h, 5);
   BH_CUDA(h, cudaGetLastError());
@@ -497,7 +572,10 @@ bte_status bte_step_sc(bte_handle* h, double* F_dev, const double* ni_dev, doubl
                        double* E_out_dev) {
   if (!h) return hfail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || !ni_dev) return hfail(h, BTE_EINVAL, "F_dev and ni_dev must not be NULL");
-  if (!bte::handle_device_ready(h)) return BTE_ESTATE;
+  {
+    const bte_status ds = bte::handle_device_status(h);
+    if (ds != BTE_OK) return ds;
+  }
   bte_status s = bte::hybrid_setup(h);
   if (s != BTE_OK) return s;
   BH_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
@@ -512,7 +590,10 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
                              double freq_Hz, bte_implicit_opts* opts) {
   if (!h) return hfail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || !ni_dev) return hfail(h, BTE_EINVAL, "F_dev and ni_dev must not be NULL");
-  if (!bte::handle_device_ready(h)) return BTE_ESTATE;
+  {
+    const bte_status ds = bte::handle_device_status(h);
+    if (ds != BTE_OK) return ds;
+  }
   double rtol = 1e-10, grtol = 1e-2;
   int newton_max = 8, m = 40, gmax = 400, precond = 0;
   if (opts) {

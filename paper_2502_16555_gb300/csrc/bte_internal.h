@@ -15,6 +15,8 @@ constexpr double kKB = 1.380649e-23;
 constexpr double kAmu = 1.66053906660e-27;
 constexpr double kTorr = 101325.0 / 760.0;
 constexpr double kEps0 = 8.8541878128e-12;  // vacuum permittivity, CODATA 2018
+constexpr int kMaxNr = 880;    // B-splines: the eigen-basis transforms stage nr x 33 doubles
+constexpr int kMaxNv = 7936;   // nr * ntheta: the FP64 panel of a tall first panel
 constexpr double kPi = 3.14159265358979323846;
 
 struct Process {
@@ -66,7 +68,7 @@ std::vector<double> maxwellian_coeffs(const HostOps& ops, double Te_eV);
 const HostOps* handle_ops(const bte_handle* h);
 void* handle_stream_ptr(const bte_handle* h);
 bte_status handle_fail(const bte_handle* h, bte_status s, const std::string& msg);
-bool handle_device_ready(bte_handle* h);
+bte_status handle_device_status(bte_handle* h);  // BTE_OK, or why the handle cannot run device work
 bool handle_profiling(const bte_handle* h);
 unsigned long long handle_launches(const bte_handle* h);
 void handle_add_launches(bte_handle* h, unsigned long long n);

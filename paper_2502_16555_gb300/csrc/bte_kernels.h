@@ -91,6 +91,18 @@ void launch_vsolve_struct(const double* Fin, double* Fout, const double* E, doub
                           T* Xscratch, int nx, int nt, int nr, int nl, const int* conv, int accumulate,
                           unsigned* status, cudaStream_t st);
 
+// The reduced dense system of the same identity when N_l < N_theta (m = N_l Nr): G_i = I - dt B_i
+// formed densely as G[nx][m][m] (T the storage of the factorisation), y = P_S f and
+// out (+)= f + P_O (z - y) around the solve z = G_i^-1 y; Yr, Zr hold nx * m doubles; points with
+// conv[i] != 0 are skipped (conv may be NULL).
+template <typename T>
+void launch_v_form_reduced(const double* Cs, const double* Alo, const double* Aup, const double* E, double E_uniform,
+                           double dt, T* G, int nx, int nr, int nl, cudaStream_t st);
+void launch_reduce_project(const double* F, const double* TS, double* Yr, const int* conv, int nx, int nt, int nr,
+                           int nl, cudaStream_t st);
+void launch_reduce_lift(const double* F, const double* Yr, const double* Zr, const double* TO, double* out,
+                        const int* conv, int accumulate, int nx, int nt, int nr, int nl, cudaStream_t st);
+
 // y = A^-T b with the FP64 factors and pivots of the FP64 path (the adjoint of lu_solve).
 void launch_lu_solve_t(const double* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
                        cudaStream_t st);

@@ -226,7 +226,91 @@ __global__ void __launch_bounds__(kST) vsolve_struct_kernel(const double* __rest
   if (bad && status) atomicOr(status, kNonFinite);
 }
 
+// ---- the reduced dense system (N_l < N_theta): the same identity with I - dt B_i factored as a
+// dense m x m matrix, m = N_l Nr, by the LU kernels of the full system. Row and column (l, k) of
+// B_i sit at l Nr + k: block (l, l) = Cs_l, block (l, l - 1) = E_i As_lo[l], block (l, l + 1) =
+// E_i As_up[l], zero elsewhere.
+
+// G_i = I - dt B_i, one CTA per row (point i, row (l, p)); columns in blocks of Nr.
+template <typename T>
+__global__ void v_form_reduced_kernel(const double* __restrict__ Cs, const double* __restrict__ Alo,
+                                      const double* __restrict__ Aup, const double* __restrict__ E,
+                                      double E_uniform, double dt, T* __restrict__ G, int nr, int nl) {
+  const int m = nl * nr;
+  const size_t rowg = blockIdx.x;  // i * m + row
+  const int i = static_cast<int>(rowg / m), row = static_cast<int>(rowg % m);
+  const int l = row / nr, p = row % nr;
+  const double Ei = E ? E[i] : E_uniform;
+  const size_t off = (static_cast<size_t>(l) * nr + p) * nr;
+  T* out = G + rowg * m;
+  for (int lc = 0; lc < nl; ++lc) {
+    const double* src = lc == l ? Cs : lc == l - 1 ? Alo : lc == l + 1 ? Aup : nullptr;
+    const double w = lc == l ? 1.0 : Ei;
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+      const double b = src ? w * __ldg(src + off + k) : 0.0;
+      out[lc * nr + k] = static_cast<T>((lc == l && k == p ? 1.0 : 0.0) - dt * b);
+    }
+  }
+}
+
+// y_i = P_S f_i: y[l][k] = sum_a T_S[l][a] f[a][k], skipping converged points.
+__global__ void reduce_project_kernel(const double* __restrict__ F, const double* __restrict__ TS,
+                                      double* __restrict__ Yr, const int* __restrict__ conv, int nt, int nr,
+                                      int nl) {
+  const int i = blockIdx.x;
+  if (conv && conv[i]) return;
+  const int m = nl * nr;
+  const double* f = F + static_cast<size_t>(i) * nt * nr;
+  for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+    const int l = idx / nr, k = idx % nr;
+    double s = 0.0;
+    for (int a = 0; a < nt; ++a) s = fma(__ldg(TS + l * nt + a), f[a * nr + k], s);
+    Yr[static_cast<size_t>(i) * m + idx] = s;
+  }
+}
+
+// out_i (+)= f_i + P_O (z_i - y_i): out[a][k] = f[a][k] + sum_l T_O[a][l] (z[l][k] - y[l][k]),
+// skipping converged points.
+__global__ void reduce_lift_kernel(const double* __restrict__ F, const double* __restrict__ Yr,
+                                   const double* __restrict__ Zr, const double* __restrict__ TO,
+                                   double* __restrict__ out, const int* __restrict__ conv, int accumulate, int nt,
+                                   int nr, int nl) {
+  const int i = blockIdx.x;
+  if (conv && conv[i]) return;
+  const int m = nl * nr, nv = nt * nr;
+  const size_t base = static_cast<size_t>(i) * nv;
+  const double* y = Yr + static_cast<size_t>(i) * m;
+  const double* z = Zr + static_cast<size_t>(i) * m;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const int a = v / nr, k = v % nr;
+    double s = F[base + v];
+    for (int l = 0; l < nl; ++l) s = fma(__ldg(TO + a * nl + l), z[l * nr + k] - y[l * nr + k], s);
+    out[base + v] = accumulate ? out[base + v] + s : s;
+  }
+}
+
 }  // namespace
+
+template <typename T>
+void launch_v_form_reduced(const double* Cs, const double* Alo, const double* Aup, const double* E, double E_uniform,
+                           double dt, T* G, int nx, int nr, int nl, cudaStream_t st) {
+  const unsigned rows = static_cast<unsigned>(nx) * nl * nr;
+  v_form_reduced_kernel<T><<<rows, nr >= 128 ? 128 : 64, 0, st>>>(Cs, Alo, Aup, E, E_uniform, dt, G, nr, nl);
+}
+template void launch_v_form_reduced<float>(const double*, const double*, const double*, const double*, double, double,
+                                           float*, int, int, int, cudaStream_t);
+template void launch_v_form_reduced<double>(const double*, const double*, const double*, const double*, double,
+                                            double, double*, int, int, int, cudaStream_t);
+
+void launch_reduce_project(const double* F, const double* TS, double* Yr, const int* conv, int nx, int nt, int nr,
+                           int nl, cudaStream_t st) {
+  reduce_project_kernel<<<nx, 256, 0, st>>>(F, TS, Yr, conv, nt, nr, nl);
+}
+
+void launch_reduce_lift(const double* F, const double* Yr, const double* Zr, const double* TO, double* out,
+                        const int* conv, int accumulate, int nx, int nt, int nr, int nl, cudaStream_t st) {
+  reduce_lift_kernel<<<nx, 256, 0, st>>>(F, Yr, Zr, TO, out, conv, accumulate, nt, nr, nl);
+}
 
 size_t struct_smem_bytes(int nr, int nl, size_t tsize) {
   return (4ull * nr * nr + 2ull * nl * nr + nr + 4ull * 64) * tsize;

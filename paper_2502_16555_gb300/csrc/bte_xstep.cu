@@ -267,8 +267,19 @@ int grid_for(size_t n, int block) {
 
 }  // namespace
 
+// Both transforms stage nr x (kXT + 1) doubles: past 48 KB (nr > 186) they need the opt-in
+// shared-memory size, which bte_create keeps them within (nr <= kMaxNr).
+static void set_x_transform_smem() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(x_to_eigen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaFuncSetAttribute(x_from_eigen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  done = true;
+}
+
 void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
                        unsigned* status, cudaStream_t st) {
+  set_x_transform_smem();
   dim3 grid(nt, (nx + kXT - 1) / kXT);
   const size_t smem = sizeof(double) * kXT * (nr + 1);
   x_to_eigen_kernel<<<grid, 256, smem, st>>>(F, Uinv, Y, nx, nt, nr, status);
@@ -284,6 +295,7 @@ void launch_x_apply_q(const double* Q, const double* Y, double* Y2, int nx, int 
 
 void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, int nt, int nr,
                          unsigned* status, cudaStream_t st) {
+  set_x_transform_smem();
   dim3 grid(nt, (nx + kXT - 1) / kXT);
   const size_t smem = sizeof(double) * nr * (kXT + 1);
   x_from_eigen_kernel<<<grid, 256, smem, st>>>(Y2, U, F, nx, nt, nr, status);

@@ -78,6 +78,23 @@ def test_ion_step_matches_oracle(shape):
     assert rel(n.cpu().numpy(), ref) <= 1e-10
 
 
+@pytest.mark.parametrize("nx", [150, 151, 200])
+def test_ion_step_both_elimination_paths(nx):
+    """Up to 150 points the ion system is eliminated in shared memory, above that in global
+    memory: both sides of the switch, and a larger grid, against the oracle."""
+    cfg = tiny(nx, 6, 4)
+    ops = O.Operators(cfg)
+    h = H.Hybrid(ops)
+    F = ops.initial_state()
+    ni = ions(ops)
+    t = 0.13 / cfg["freq_Hz"]
+    ref = h.ion_step(ni, F, t)
+    s = solver(cfg)
+    n = dev(ni)
+    s.ion_step(n, dev(F), t)
+    assert rel(n.cpu().numpy(), ref) <= 1e-10
+
+
 def test_ion_step_with_other_transport_coefficients():
     cfg = tiny(13, 10, 5)
     ops = O.Operators(cfg)

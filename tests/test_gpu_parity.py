@@ -44,6 +44,8 @@ CASES = {
     "nl_lt_ntheta": W.scaled(W.SMALL, nx=11, nr=16, ntheta=8, nl=3),
     "odd_ntheta": W.scaled(W.SMALL, nx=7, nr=9, ntheta=5),
     "tiny": W.scaled(W.SMALL, nx=3, nr=4, ntheta=2),
+    # nr > 186: the eigen-basis transforms stage more than 48 KB of shared memory per CTA
+    "many_bsplines": W.scaled(W.SMALL, nx=5, nr=256, ntheta=2),
 }
 
 
@@ -324,3 +326,74 @@ def test_structured_matches_dense_path_on_field_array():
     solver(cfg, "fp64").step(a, 0.0, E=E)
     solver(cfg, "fp64", structured=True).step(b, 0.0, E=E)
     assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) <= 1e-11
+
+
+# ------------------------------------------------------------------ reduced system (nl < ntheta)
+
+REDUCED = {
+    # m = nl * nr = 48: one panel, no tensor cores
+    "one_panel": W.scaled(W.SMALL, nx=11, nr=16, ntheta=8, nl=3),
+    # m = 288 over three panels (ragged last), nv = 768: the tensor-core factorisation of G_i
+    "three_panels": W.scaled(W.SMALL, nx=6, nr=96, ntheta=8, nl=3),
+    # nl = ntheta - 1
+    "nl_near_ntheta": W.scaled(W.SMALL, nx=5, nr=24, ntheta=6, nl=5),
+}
+
+
+@pytest.mark.parametrize("name", list(REDUCED))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reduced_system_one_step(name, precision):
+    """With nl < ntheta the default factors G_i = I - dt B_i (order nl nr) and lifts the solution back
+    through P_O; one step with a per-point field against the oracle's dense Nv x Nv solves, and
+    against the same handle kind factoring the full matrix (BTE_FLAG_FULL_V)."""
+    cfg = dict(REDUCED[name])
+    ops = O.Operators(cfg)
+    F0 = W.random_state(ops.nx, ops.nt, ops.nr, seed=23)
+    E = W.random_field(ops.nx, seed=6, e0=8e3)
+    ref = ops.step(F0, 0.0, E=E)
+    s = solver(cfg, precision)
+    assert s.info()["solve_n"] == cfg["nl"] * cfg["nr"]
+    F = to_dev(F0)
+    s.step(F, 0.0, E=to_dev(E))
+    tol = 1e-10 if precision == "fp64" else 1e-9
+    assert rel_l2(F.cpu().numpy(), ref) <= tol
+    full = solver(cfg, precision, full_v=True)
+    assert full.info()["solve_n"] == ops.nv
+    G = to_dev(F0)
+    full.step(G, 0.0, E=to_dev(E))
+    assert rel_l2(F.cpu().numpy(), G.cpu().numpy()) <= tol
+
+
+def test_reduced_system_run_and_self_consistent_step():
+    """Ten steps of the uniform-field step and one step with the field of Gauss's law, reduced
+    system against the oracle (FP64 and mixed)."""
+    from oracle import hybrid as H
+    cfg = W.scaled(W.SMALL, nx=9, nr=40, ntheta=8, nl=3)
+    ops = O.Operators(cfg)
+    F0 = ops.initial_state()
+    F_ref = F0.copy()
+    for k in range(10):
+        F_ref = ops.step(F_ref, k * ops.dt)
+    hy = H.Hybrid(ops)
+    xi = 2.0 * ops.x / ops.L - 1.0
+    ni = 1.1e15 * (1.0 - xi * xi) + 2e13
+    sc_ref, _ = hy.sc_step(F0, ni, 0.3 / cfg["freq_Hz"])
+    for precision in ("fp64", "mixed"):
+        s = solver(cfg, precision)
+        F = to_dev(F0)
+        s.run(F, 10, 0.0)
+        tol = 1e-10 if precision == "fp64" else 1e-9
+        assert rel_l2(F.cpu().numpy(), F_ref) <= tol, precision
+        F = to_dev(F0)
+        s.step_sc(F, to_dev(ni), 0.3 / cfg["freq_Hz"])
+        assert rel_l2(F.cpu().numpy(), sc_ref) <= tol, precision
+
+
+def test_reduced_system_refuses_the_adjoint():
+    from paper_2502_16555_gb300 import bte
+    cfg = W.scaled(W.SMALL, nx=5, nr=8, ntheta=4, nl=2)
+    s = solver(cfg, "fp64")
+    F = s.initial_state()
+    lam = torch.zeros_like(F)
+    st = s.lib.bte_step_adjoint(s.h, bte._ptr(F), bte._ptr(lam), 0.0, 100.0, 13.56e6, None, 0.0, None, None)
+    assert st == bte.ESTATE

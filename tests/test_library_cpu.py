@@ -83,7 +83,8 @@ def test_host_assembly_matches_oracle(name, cfg):
 
 def test_create_rejects_bad_configs(lib):
     from paper_2502_16555_gb300 import bte
-    bad = [dict(nx=2), dict(nr=3), dict(ntheta=1), dict(nl=9, ntheta=8), dict(dt_s=0.0), dict(p_Torr=-1.0)]
+    bad = [dict(nx=2), dict(nr=3), dict(ntheta=1), dict(nl=9, ntheta=8), dict(dt_s=0.0), dict(p_Torr=-1.0),
+           dict(nx=4097), dict(nr=881, ntheta=2), dict(nr=128, ntheta=64)]
     for kw in bad:
         cfg = W.scaled(W.SMALL, **{k: v for k, v in kw.items() if k != "nl"})
         if "nl" in kw:
@@ -91,6 +92,25 @@ def test_create_rejects_bad_configs(lib):
         with pytest.raises(bte.BteError) as e:
             bte.Solver(cfg, host_only=True)
         assert e.value.status == bte.EINVAL, kw
+
+
+def test_create_accepts_the_largest_grids(lib):
+    """The limits themselves are accepted: nr = 880 and nr * ntheta = 7936."""
+    from paper_2502_16555_gb300 import bte
+    for kw in (dict(nx=3, nr=880, ntheta=2), dict(nx=3, nr=124, ntheta=64)):
+        s = bte.Solver(W.scaled(W.SMALL, **kw), host_only=True)
+        assert s.info()["nr"] == kw["nr"]
+
+
+def test_factorisation_order_follows_the_harmonic_count(lib):
+    """nl < ntheta factors the reduced matrix of order nl * nr unless BTE_FLAG_FULL_V; nl = ntheta
+    factors A_i (order nv); the structured solve holds no factors."""
+    from paper_2502_16555_gb300 import bte
+    cfg = W.scaled(W.SMALL, nx=5, nr=12, ntheta=8, nl=3)
+    assert bte.Solver(cfg, host_only=True).info()["solve_n"] == 36
+    assert bte.Solver(cfg, host_only=True, full_v=True).info()["solve_n"] == 96
+    assert bte.Solver(cfg, host_only=True, structured=True).info()["solve_n"] == 0
+    assert bte.Solver(W.scaled(W.SMALL, nx=5, nr=12, ntheta=8), host_only=True).info()["solve_n"] == 96
 
 
 def test_bad_process_lists(lib):
