@@ -275,7 +275,7 @@ bte_status bte_step_sc(bte_handle* h, double* F_dev, const double* ni_dev, doubl
 typedef struct {
   double newton_rtol;  /* stop when |R(F)| <= newton_rtol |F^n| (default 1e-10) */
   int newton_max;      /* Newton iterations (default 8) */
-  int gmres_restart;   /* GMRES basis size, <= 200 (default 40) */
+  int gmres_restart;   /* GMRES basis size, <= 200 (default 100) */
   double gmres_rtol;   /* inner tolerance relative to |R| (default 1e-2) */
   int gmres_max;       /* GMRES iterations per Newton iteration, restarts included (default 400) */
   int precond;         /* 0: the per-point solves at the iterate's field, then one full x step

@@ -333,13 +333,15 @@ __global__ void multi_dot_kernel(const double* __restrict__ V, size_t ld, int k,
   }
 }
 
-// out[j] = sum over blocks of partial[blk][j] (one thread per j, fixed order: reproducible)
+// out[j] = sum over blocks of partial[blk][j]: one CTA per j, strided partial sums then a tree
+// (a fixed order, so the result is reproducible)
 __global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk, int k, double* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= k) return;
+  __shared__ double red[32];
+  const int j = blockIdx.x;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += partial[static_cast<size_t>(b) * k + j];
-  out[j] = s;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[static_cast<size_t>(b) * k + j];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[j] = s;
 }
 
 // w = a w + sg sum_{j<k} c_j V_j   (c in device memory)
@@ -481,7 +483,7 @@ void enqueue_vapply(bte_handle* h, const double* X, const double* E, double c, d
 bte_status host_dots(bte_handle* h, const double* V, size_t ld, int k, const double* w, std::vector<double>& out) {
   const size_t D = static_cast<size_t>(h->ops.nx) * h->ops.nv;
   multi_dot_kernel<<<kDotGrid, kDotBlock, 0, h->st>>>(V, ld, k, w, D, h->part);
-  sum_partials_kernel<<<(k + 127) / 128, 128, 0, h->st>>>(h->part, kDotGrid, k, h->dsum);
+  sum_partials_kernel<<<k, 128, 0, h->st>>>(h->part, kDotGrid, k, h->dsum);
   BH_CUDA(h, cudaMemcpyAsync(h->dsum_host, h->dsum, k * sizeof(double), cudaMemcpyDeviceToHost, h->st));
   BH_CUDA(h, cudaStreamSynchronize(h->st));
   out.assign(h->dsum_host, h->dsum_host + k);
@@ -595,7 +597,7 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
     if (ds != BTE_OK) return ds;
   }
   double rtol = 1e-10, grtol = 1e-2;
-  int newton_max = 8, m = 40, gmax = 400, precond = 0;
+  int newton_max = 8, m = 100, gmax = 400, precond = 0;
   if (opts) {
     if (opts->newton_rtol > 0) rtol = opts->newton_rtol;
     if (opts->gmres_rtol > 0) grtol = opts->gmres_rtol;

@@ -10,27 +10,31 @@ namespace bte {
 namespace {
 
 constexpr int kXT = 32;  // x points per CTA in the eigen-basis transforms
+constexpr int kIC = 64;  // eigen (to) or B-spline (from) indices per CTA: a third grid dimension
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
-// Y[a][i][x] = sum_k Uinv[i][k] F[x][a][k]  (the U^-1 contraction of Algorithm 1). Flags
-// non-finite inputs, which is where a NaN handed in by the caller is first seen.
+// Y[a][i][x] = sum_k Uinv[i][k] F[x][a][k]  (the U^-1 contraction of Algorithm 1) for the kXT
+// points and kIC eigen indices of this CTA: a warp shares i (the Uinv row is a broadcast) and its
+// lanes run over x. Flags non-finite inputs (blockIdx.z == 0 only), which is where a NaN handed in
+// by the caller is first seen.
 __global__ void x_to_eigen_kernel(const double* __restrict__ F, const double* __restrict__ Uinv,
                                   double* __restrict__ Y, int nx, int nt, int nr,
                                   unsigned* status) {
   extern __shared__ double sm[];
-  const int a = blockIdx.x, x0 = blockIdx.y * kXT;
-  const int nxt = min(kXT, nx - x0);
+  const int a = blockIdx.x, x0 = blockIdx.y * kXT, i0 = blockIdx.z * kIC;
+  const int nxt = min(kXT, nx - x0), nit = min(kIC, nr - i0);
   const int ld = nr + 1;  // padded row
+  const bool check = status && blockIdx.z == 0;
   for (int idx = threadIdx.x; idx < nxt * nr; idx += blockDim.x) {
     const int xx = idx / nr, k = idx % nr;
     const double v = F[(static_cast<size_t>(x0 + xx) * nt + a) * nr + k];
-    if (status && !finite(v)) atomicOr(status, kNonFinite);
+    if (check && !finite(v)) atomicOr(status, kNonFinite);
     sm[xx * ld + k] = v;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nr * kXT; idx += blockDim.x) {
-    const int i = idx / kXT, xx = idx % kXT;
+  for (int idx = threadIdx.x; idx < nit * kXT; idx += blockDim.x) {
+    const int i = i0 + idx / kXT, xx = idx % kXT;
     if (xx >= nxt) continue;
     const double* u = Uinv + static_cast<size_t>(i) * nr;
     double s = 0.0;
@@ -92,21 +96,24 @@ __global__ void x_apply_q2_kernel(const double* __restrict__ Q, const double* __
   }
 }
 
-// F[x][a][k] = sum_i U[k][i] Y2[a][i][x]; flags non-finite results.
+// F[x][a][k] = sum_i U[k][i] Y2[a][i][x] for the kXT points and kIC B-spline indices of this CTA:
+// a warp shares k (the U row is a broadcast) and its lanes run over x (consecutive shared-memory
+// words); flags non-finite results.
 __global__ void x_from_eigen_kernel(const double* __restrict__ Y2, const double* __restrict__ U,
                                     double* __restrict__ F, int nx, int nt, int nr,
                                     unsigned* status) {
   extern __shared__ double sm[];
-  const int a = blockIdx.x, x0 = blockIdx.y * kXT;
-  const int nxt = min(kXT, nx - x0);
+  const int a = blockIdx.x, x0 = blockIdx.y * kXT, k0 = blockIdx.z * kIC;
+  const int nxt = min(kXT, nx - x0), nkt = min(kIC, nr - k0);
   for (int idx = threadIdx.x; idx < nr * kXT; idx += blockDim.x) {
     const int i = idx / kXT, xx = idx % kXT;
     sm[i * (kXT + 1) + xx] = xx < nxt ? Y2[(static_cast<size_t>(a) * nr + i) * nx + x0 + xx] : 0.0;
   }
   __syncthreads();
   bool bad = false;
-  for (int idx = threadIdx.x; idx < nxt * nr; idx += blockDim.x) {
-    const int xx = idx / nr, k = idx % nr;
+  for (int idx = threadIdx.x; idx < nkt * kXT; idx += blockDim.x) {
+    const int k = k0 + idx / kXT, xx = idx % kXT;
+    if (xx >= nxt) continue;
     const double* u = U + static_cast<size_t>(k) * nr;
     double s = 0.0;
     for (int i = 0; i < nr; ++i) s = fma(__ldg(u + i), sm[i * (kXT + 1) + xx], s);
@@ -280,7 +287,7 @@ static void set_x_transform_smem() {
 void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
                        unsigned* status, cudaStream_t st) {
   set_x_transform_smem();
-  dim3 grid(nt, (nx + kXT - 1) / kXT);
+  dim3 grid(nt, (nx + kXT - 1) / kXT, (nr + kIC - 1) / kIC);
   const size_t smem = sizeof(double) * kXT * (nr + 1);
   x_to_eigen_kernel<<<grid, 256, smem, st>>>(F, Uinv, Y, nx, nt, nr, status);
 }
@@ -296,7 +303,7 @@ void launch_x_apply_q(const double* Q, const double* Y, double* Y2, int nx, int 
 void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, int nt, int nr,
                          unsigned* status, cudaStream_t st) {
   set_x_transform_smem();
-  dim3 grid(nt, (nx + kXT - 1) / kXT);
+  dim3 grid(nt, (nx + kXT - 1) / kXT, (nr + kIC - 1) / kIC);
   const size_t smem = sizeof(double) * nr * (kXT + 1);
   x_from_eigen_kernel<<<grid, 256, smem, st>>>(Y2, U, F, nx, nt, nr, status);
 }
