@@ -241,7 +241,7 @@ bte_status bte_adjoint_gradient(const bte_handle* h, const double* SC_dev, const
  * n_i is the ion number density [m^-3] at the nx collocation points (device, FP64); F the electron
  * state as for bte_step. None of these entry points changes bte_step; they allocate their device
  * operators (the nx x nx field and ion matrices) on first use and bte_step_implicit its work
- * vectors ((restart + 10) x nx x Nv doubles) on first use or when the restart grows. */
+ * vectors ((2 restart + 10) x nx x Nv doubles) on first use or when the restart grows. */
 
 /* Ion transport coefficients as n0 times the mobility [1/(V m s)] and n0 times the diffusion
  * coefficient [1/(m s)] (the parameter table of Section 4; defaults 4.65e21 and 2.07e20). mu >= 0,
@@ -288,11 +288,13 @@ typedef struct {
 /* One fully-implicit electron step (eqs. "bte_fully_implicit"): F <- the root of
  * R(F) = F - F^n + dt [A_x F D_x^T - P_O C P_S F - P_O A_v P_S (E(F) . F)], E(F) the field of
  * (n_i, u^T F) at t_s + dt, with the zero-inflow rows R = F. Newton with backtracking from the
- * semi-implicit self-consistent step's result; each Newton system by restarted GMRES on the
+ * semi-implicit self-consistent step's result; each Newton system by restarted flexible GMRES
+ * (the preconditioned basis is stored, so its FP32 solves need not act linearly) on the
  * Jacobian action of eq. "1dbte_jac_action", right-preconditioned by the split operator at the
  * iterate's field (opts->precond; the per-point factors formed once per Newton iteration; the
- * full-step x operators are assembled on the first call with precond 0). ni_dev is required;
- * opts may be NULL.
+ * full-step x operators are assembled on the first call with precond 0). A line search that
+ * finds no sufficient decrease retries its Newton iteration with a 100x smaller GMRES tolerance,
+ * at most twice. ni_dev is required; opts may be NULL.
  * BTE_ENOCONV if Newton stops above newton_rtol; F is written only on success. Synchronises the
  * handle's stream. */
 bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev, double t_s, double V0,

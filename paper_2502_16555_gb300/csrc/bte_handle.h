@@ -58,6 +58,7 @@ struct bte_handle {
   int gm = 0;                                   // GMRES basis size allocated
   double *Fk = nullptr, *Fn = nullptr, *Rv = nullptr, *Zx = nullptr, *VX = nullptr, *KAF = nullptr;
   double *El = nullptr, *Wv = nullptr, *Pz = nullptr, *Vb = nullptr, *part = nullptr, *dsum = nullptr;
+  double* Zb = nullptr;                         // preconditioned basis Z_j = P^-1 V_j (flexible GMRES)
   double *Dl = nullptr, *Qfull = nullptr;       // Newton direction; full-step Q_ij of the preconditioner
   double* dsum_host = nullptr;                  // pinned
   int last_sweeps = 0;

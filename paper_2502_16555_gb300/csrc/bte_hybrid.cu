@@ -8,12 +8,14 @@
 //                outflow-only wall fluxes as the first and last rows, solved by one CTA (GEPP);
 //   sc step      the semi-implicit step with E^{1/2} recomputed after the first x half step;
 //   implicit     Newton with backtracking on R(F) = F - F^n + dt [A_x F D_x^T - P_O (C + E(F) A_v) P_S F]
-//                (inflow rows R = F), each Newton system by restarted GMRES on the Jacobian action
-//                J X = X + dt [A_x X D_x^T - P_O (C + E(F) A_v) P_S X + P_O A_v P_S ((L u^T X) . F)],
-//                right-preconditioned by the semi-implicit step's linear map at the iterate's field
-//                (x half step, per-point solves with factors formed once per Newton iteration, x
-//                half step). Orthogonalisation by classical Gram-Schmidt applied twice; the small
-//                Hessenberg least-squares problem on the host. All vectors FP64 on the device.
+//                (inflow rows R = F), each Newton system by restarted flexible GMRES on the Jacobian
+//                action J X = X + dt [A_x X D_x^T - P_O (C + E(F) A_v) P_S X
+//                + P_O A_v P_S ((L u^T X) . F)], right-preconditioned at the iterate's field by the
+//                per-point solves (factors formed once per Newton iteration) followed by one full x
+//                step (default), or by the semi-implicit step's map; the preconditioned vectors are
+//                kept, so the update is exact for the basis GMRES built. Orthogonalisation by
+//                classical Gram-Schmidt applied twice; the small Hessenberg least-squares problem on
+//                the host. All vectors FP64 on the device.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -455,6 +457,7 @@ bte_status implicit_setup(bte_handle* h, int m, bool full_q) {
     if (s == BTE_OK) s = halloc(h, &h->El, h->ops.nx);
   }
   if (s == BTE_OK) s = halloc(h, &h->Vb, D * (m + 1));
+  if (s == BTE_OK) s = halloc(h, &h->Zb, D * m);
   if (s == BTE_OK) s = halloc(h, &h->part, static_cast<size_t>(kDotGrid) * (m + 1));
   if (s == BTE_OK) s = halloc(h, &h->dsum, m + 1);
   if (s != BTE_OK) return s;
@@ -687,6 +690,11 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
   bool conv = rn <= rtol * fn;
   int newton = 0, gm_total = 0;
   std::vector<double> H(static_cast<size_t>(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hv;
+  // forcing term of the current Newton iteration: a failed line search (no sufficient decrease
+  // along a direction GMRES solved only to grtol) retries the iteration with a 100x tighter
+  // linear solve, at most twice, before the step gives up
+  double eta = grtol;
+  int retries = 0;
   while (!conv && newton < newton_max) {
     // the iterate's field, frozen for the preconditioner and the Jacobian; factors at that field
     BH_CUDA(h, cudaMemcpyAsync(h->Ek, h->Esc, nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -703,7 +711,7 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
         multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, -1.0, nullptr, D, 0, nullptr, 0.0, D);
         axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, -1.0, h->Rv, D);
         if ((s = norm(h->Vb, rc)) != BTE_OK) return s;
-        if (rc <= grtol * rn) break;
+        if (rc <= eta * rn) break;
         multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Vb, 1.0 / rc, nullptr, D, 0, nullptr, 0.0, D);
       } else {
         BH_CUDA(h, cudaMemcpyAsync(h->Vb, h->Rv, D * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -717,8 +725,9 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
       for (int j = 0; j < m && inner < gmax; ++j, ++inner) {
         double* Vj = h->Vb + static_cast<size_t>(j) * D;
         double* Vn = h->Vb + static_cast<size_t>(j + 1) * D;
-        if ((s = pinv(Vj, h->Pz)) != BTE_OK) return s;
-        jac(h->Pz, Vn);
+        double* Zj = h->Zb + static_cast<size_t>(j) * D;
+        if ((s = pinv(Vj, Zj)) != BTE_OK) return s;
+        jac(Zj, Vn);
         for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
           if ((s = bte::host_dots(h, h->Vb, D, j + 1, Vn, hv)) != BTE_OK) return s;
           for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] += hv[i];
@@ -743,7 +752,7 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
         g[j + 1] = -sn[j] * g[j];
         g[j] = cs[j] * g[j];
         k = j + 1;
-        if (std::fabs(g[j + 1]) <= grtol * rn || hn == 0.0) {
+        if (std::fabs(g[j + 1]) <= eta * rn || hn == 0.0) {
           done = true;
           ++inner;
           break;
@@ -754,12 +763,13 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
         for (int q = i + 1; q < k; ++q) v -= H[static_cast<size_t>(i) * m + q] * y[q];
         y[i] = v / H[static_cast<size_t>(i) * m + i];
       }
-      // delta += P^-1 (V y)
+      // delta += Z y with the stored Z_j = P^-1 V_j (flexible GMRES): the Arnoldi relation
+      // J Z = V H holds for whatever the preconditioner returned, so the residual the rotations
+      // track is the true one even where the FP32 solves inside P^-1 are far from linear (stiff
+      // velocity systems: relative rounding kappa eps_32 of order one)
       std::copy(y.begin(), y.begin() + k, h->dsum_host);
       BH_CUDA(h, cudaMemcpyAsync(h->dsum, h->dsum_host, k * sizeof(double), cudaMemcpyHostToDevice, st));
-      multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Zx, 0.0, h->Vb, D, k, h->dsum, 1.0, D);
-      if ((s = pinv(h->Zx, h->Pz)) != BTE_OK) return s;
-      axpy_kernel<<<vg, 256, 0, st>>>(h->Dl, 1.0, h->Pz, D);
+      multi_axpy_kernel<<<vg, 256, 0, st>>>(h->Dl, 1.0, h->Zb, D, k, h->dsum, 1.0, D);
       if (done) break;
     }
     gm_total += inner;
@@ -774,8 +784,21 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
       if (rt <= (1.0 - 1e-4 * lam) * rn) acc = true;
       else lam *= 0.5;
     }
+    if (!acc) {
+      if (retries < 2 && inner > 0) {
+        eta *= 1e-2;
+        ++retries;
+        // the residual of the iterate again (the line search overwrote Rv and the field)
+        residual(h->Fk, h->Rv);
+        if ((s = norm(h->Rv, rn)) != BTE_OK) return s;
+        continue;
+      }
+      ++newton;
+      break;
+    }
     ++newton;
-    if (!acc) break;
+    eta = grtol;
+    retries = 0;
     std::swap(h->Fk, h->Wv);
     rn = rt;
     conv = rn <= rtol * fn;
