@@ -231,27 +231,6 @@ __global__ void dense_solve_smem_kernel(const double* __restrict__ Ag, const dou
   for (int i = tid; i < n; i += nt) x[i] = A[i * ld + n];
 }
 
-// Y2[a][i][:] = lam_i mu_a D_x Y[a][i][:] (the x-advection operator in the eigen basis of
-// M_v^-1 G_v), one CTA per (ordinate, eigen-index), a warp per row.
-__global__ void x_dx_kernel(const double* __restrict__ Dx, const double* __restrict__ lam,
-                            const double* __restrict__ mu, const double* __restrict__ Y, double* __restrict__ Y2,
-                            int nx, int nr) {
-  extern __shared__ double ys[];
-  const size_t b = blockIdx.x;
-  const int a = static_cast<int>(b / nr), i = static_cast<int>(b % nr);
-  for (int c = threadIdx.x; c < nx; c += blockDim.x) ys[c] = Y[b * nx + c];
-  __syncthreads();
-  const double s0 = lam[i] * mu[a];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = warp; r < nx; r += nw) {
-    const double* d = Dx + static_cast<size_t>(r) * nx;
-    double s = 0.0;
-    for (int c = lane; c < nx; c += 32) s = fma(__ldg(d + c), ys[c], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) Y2[b * nx + r] = s0 * s;
-  }
-}
-
 // out_i = P_O (c C_s + e_i A_s) P_S X_i per point (one CTA per point): c = 1 and e_i = E[i] for
 // the velocity operator at a field, c = 0 and e_i = 1 for P_O A_v P_S alone. Structured operators
 // as in the refinement residual (Algorithm 2).
@@ -472,7 +451,7 @@ void enqueue_xop(bte_handle* h, const double* X, double* out) {
   const HostOps& o = h->ops;
   cudaStream_t st = h->st;
   launch_x_to_eigen(X, h->Uinv, h->Y, o.nx, o.nt, o.nr, h->status, st);
-  x_dx_kernel<<<o.nt * o.nr, 256, sizeof(double) * o.nx, st>>>(h->Dxd, h->lamd, h->mud, h->Y, h->Y2, o.nx, o.nr);
+  launch_x_matvec(h->Dxd, false, h->lamd, h->mud, h->Y, h->Y2, o.nx, o.nt, o.nr, st);  // lam_i mu_a D_x Y
   launch_x_from_eigen(h->Y2, h->U, out, o.nx, o.nt, o.nr, nullptr, st);
 }
 

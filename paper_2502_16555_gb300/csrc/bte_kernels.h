@@ -29,6 +29,10 @@ void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned
 void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
 void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
 
+// Y2[b] = s_b M_b Y[b] for the nt * nr pairs b = a nr + i: M_b = M + b nx^2 (per_pair) or the one
+// matrix M; s_b = lam[i] mu[a] when lam is given (device arrays), else 1. Y, Y2 are [nt][nr][nx].
+void launch_x_matvec(const double* M, bool per_pair, const double* lam, const double* mu, const double* Y,
+                     double* Y2, int nx, int nt, int nr, cudaStream_t st);
 // ---- x half step (Algorithm 1): eigen-basis transform, Q_ij apply, back transform
 void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, int nt, int nr,
                        unsigned* status, cudaStream_t st);

@@ -43,56 +43,46 @@ __global__ void x_to_eigen_kernel(const double* __restrict__ F, const double* __
   }
 }
 
-// Y2[b] = Q[b] Y[b] for every (ordinate, eigen-index) pair b: one CTA per pair, a warp per row,
-// lanes across the row (coalesced stream of Q).
-__global__ void x_apply_q_kernel(const double* __restrict__ Q, const double* __restrict__ Y,
-                                 double* __restrict__ Y2, int nx) {
+// Y2[b] = s_b M_b Y[b] for every (ordinate, eigen-index) pair b = a nr + i, M_b = M + b mstride
+// (mstride = nx^2: the per-pair Q_ij of Algorithm 1; 0: one shared matrix), s_b = lam[i] mu[a]
+// when lam is given, else 1. One CTA per pair; a warp owns 32 consecutive rows, lane l sums the
+// columns c = l + 32 k of all 32 rows (each Q row chunk a coalesced 256-byte load), and a
+// transpose reduction (shuffle offsets 16, 8, 4, 2, 1 exchanging half of the remaining rows) leaves
+// row r0 + l's sum on lane l: 31 FP64 additions per lane for 32 rows instead of 5 per row and lane.
+__global__ void x_matvec_kernel(const double* __restrict__ M, size_t mstride, const double* __restrict__ lam,
+                                const double* __restrict__ mu, const double* __restrict__ Y,
+                                double* __restrict__ Y2, int nx, int nr) {
   extern __shared__ double ys[];
   const size_t b = blockIdx.x;
   const double* y = Y + b * nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) ys[i] = y[i];
   __syncthreads();
-  const double* Qb = Q + b * nx * nx;
+  const double sb = lam ? lam[b % nr] * mu[b / nr] : 1.0;
+  const double* Mb = M + b * mstride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = warp; r < nx; r += nw) {
-    const double* q = Qb + static_cast<size_t>(r) * nx;
-    double s = 0.0;
-    for (int c = lane; c < nx; c += 32) s = fma(__ldg(q + c), ys[c], s);
+  for (int r0 = 32 * warp; r0 < nx; r0 += 32 * nw) {
+    const int nrow = min(32, nx - r0);
+    const double* q = Mb + static_cast<size_t>(r0) * nx;
+    double acc[32];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) Y2[b * nx + r] = s;
-  }
-}
-
-// The same for even nx: each warp takes 4 rows at a time in 16-byte loads, so a lane has 8 loads in
-// flight per pass (nx = 128) and the Q stream keeps the memory system busy.
-__global__ void x_apply_q2_kernel(const double* __restrict__ Q, const double* __restrict__ Y,
-                                  double* __restrict__ Y2, int nx) {
-  extern __shared__ double ys[];
-  const size_t b = blockIdx.x;
-  const double* y = Y + b * nx;
-  for (int i = threadIdx.x; i < nx; i += blockDim.x) ys[i] = y[i];
-  __syncthreads();
-  const int h = nx >> 1;  // 16-byte pairs per row
-  const double2* Qb = reinterpret_cast<const double2*>(Q + b * nx * nx);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r0 = 4 * warp; r0 < nx; r0 += 4 * nw) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 2
-    for (int c = lane; c < h; c += 32) {
-      double2 q[4];
+    for (int rr = 0; rr < 32; ++rr) acc[rr] = 0.0;
+    for (int c = lane; c < nx; c += 32) {
+      const double yc = ys[c];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        q[u] = r0 + u < nx ? __ldg(Qb + static_cast<size_t>(r0 + u) * h + c) : make_double2(0.0, 0.0);
-      const double y0 = ys[2 * c], y1 = ys[2 * c + 1];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) s[u] = fma(q[u].y, y1, fma(q[u].x, y0, s[u]));
+      for (int rr = 0; rr < 32; ++rr)
+        if (rr < nrow) acc[rr] = fma(__ldg(q + static_cast<size_t>(rr) * nx + c), yc, acc[rr]);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int o = 16; o > 0; o >>= 1) {
+      const bool hi = (lane & o) != 0;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
-    if (lane < 4 && r0 + lane < nx) Y2[b * nx + r0 + lane] = lane == 0 ? s[0] : lane == 1 ? s[1] : lane == 2 ? s[2] : s[3];
+      for (int k = 0; k < o; ++k) {
+        const double send = hi ? acc[k] : acc[k + o];
+        const double keep = hi ? acc[k + o] : acc[k];
+        acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    if (lane < nrow) Y2[b * nx + r0 + lane] = sb * acc[0];
   }
 }
 
@@ -292,12 +282,17 @@ void launch_x_to_eigen(const double* F, const double* Uinv, double* Y, int nx, i
   x_to_eigen_kernel<<<grid, 256, smem, st>>>(F, Uinv, Y, nx, nt, nr, status);
 }
 
+void launch_x_matvec(const double* M, bool per_pair, const double* lam, const double* mu, const double* Y,
+                     double* Y2, int nx, int nt, int nr, cudaStream_t st) {
+  const int groups = (nx + 31) / 32;
+  const int threads = 32 * (groups < 8 ? groups : 8);
+  x_matvec_kernel<<<nt * nr, threads, sizeof(double) * nx, st>>>(
+      M, per_pair ? static_cast<size_t>(nx) * nx : 0, lam, mu, Y, Y2, nx, nr);
+}
+
 void launch_x_apply_q(const double* Q, const double* Y, double* Y2, int nx, int nt, int nr,
                       cudaStream_t st) {
-  if ((nx & 1) == 0)
-    x_apply_q2_kernel<<<nt * nr, 256, sizeof(double) * nx, st>>>(Q, Y, Y2, nx);
-  else
-    x_apply_q_kernel<<<nt * nr, 256, sizeof(double) * nx, st>>>(Q, Y, Y2, nx);
+  launch_x_matvec(Q, true, nullptr, nullptr, Y, Y2, nx, nt, nr, st);
 }
 
 void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, int nt, int nr,
