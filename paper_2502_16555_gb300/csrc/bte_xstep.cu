@@ -10,13 +10,14 @@ namespace bte {
 namespace {
 
 constexpr int kXT = 32;  // x points per CTA in the eigen-basis transforms
-constexpr int kIC = 64;  // eigen (to) or B-spline (from) indices per CTA: a third grid dimension
+constexpr int kIC = 32;  // eigen (to) or B-spline (from) indices per CTA: a third grid dimension
+constexpr int kG = 4;    // output indices per thread in the transforms (one staged operand, four FMAs)
 
 __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 
 // Y[a][i][x] = sum_k Uinv[i][k] F[x][a][k]  (the U^-1 contraction of Algorithm 1) for the kXT
-// points and kIC eigen indices of this CTA: a warp shares i (the Uinv row is a broadcast) and its
-// lanes run over x. Flags non-finite inputs (blockIdx.z == 0 only), which is where a NaN handed in
+// points and kIC eigen indices of this CTA: a thread takes kG consecutive i at one x, a warp shares
+// them (the Uinv rows are broadcasts) and its lanes run over x. Flags non-finite inputs (blockIdx.z == 0 only), which is where a NaN handed in
 // by the caller is first seen.
 __global__ void x_to_eigen_kernel(const double* __restrict__ F, const double* __restrict__ Uinv,
                                   double* __restrict__ Y, int nx, int nt, int nr,
@@ -33,13 +34,24 @@ __global__ void x_to_eigen_kernel(const double* __restrict__ F, const double* __
     sm[xx * ld + k] = v;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nit * kXT; idx += blockDim.x) {
-    const int i = i0 + idx / kXT, xx = idx % kXT;
+  const int ngr = (nit + kG - 1) / kG;
+  for (int idx = threadIdx.x; idx < ngr * kXT; idx += blockDim.x) {
+    const int ib = i0 + (idx / kXT) * kG, xx = idx % kXT;
     if (xx >= nxt) continue;
-    const double* u = Uinv + static_cast<size_t>(i) * nr;
-    double s = 0.0;
-    for (int k = 0; k < nr; ++k) s = fma(__ldg(u + k), sm[xx * ld + k], s);
-    Y[(static_cast<size_t>(a) * nr + i) * nx + x0 + xx] = s;
+    const int nu = min(kG, i0 + nit - ib);
+    const double* u = Uinv + static_cast<size_t>(ib) * nr;
+    double s[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) s[g] = 0.0;
+    for (int k = 0; k < nr; ++k) {
+      const double f = sm[xx * ld + k];
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+        if (g < nu) s[g] = fma(__ldg(u + static_cast<size_t>(g) * nr + k), f, s[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < kG; ++g)
+      if (g < nu) Y[(static_cast<size_t>(a) * nr + ib + g) * nx + x0 + xx] = s[g];
   }
 }
 
@@ -87,8 +99,8 @@ __global__ void x_matvec_kernel(const double* __restrict__ M, size_t mstride, co
 }
 
 // F[x][a][k] = sum_i U[k][i] Y2[a][i][x] for the kXT points and kIC B-spline indices of this CTA:
-// a warp shares k (the U row is a broadcast) and its lanes run over x (consecutive shared-memory
-// words); flags non-finite results.
+// a thread takes kG consecutive k at one x, a warp shares them (the U rows are broadcasts) and its
+// lanes run over x (consecutive shared-memory words); flags non-finite results.
 __global__ void x_from_eigen_kernel(const double* __restrict__ Y2, const double* __restrict__ U,
                                     double* __restrict__ F, int nx, int nt, int nr,
                                     unsigned* status) {
@@ -101,14 +113,27 @@ __global__ void x_from_eigen_kernel(const double* __restrict__ Y2, const double*
   }
   __syncthreads();
   bool bad = false;
-  for (int idx = threadIdx.x; idx < nkt * kXT; idx += blockDim.x) {
-    const int k = k0 + idx / kXT, xx = idx % kXT;
+  const int ngr = (nkt + kG - 1) / kG;
+  for (int idx = threadIdx.x; idx < ngr * kXT; idx += blockDim.x) {
+    const int kb = k0 + (idx / kXT) * kG, xx = idx % kXT;
     if (xx >= nxt) continue;
-    const double* u = U + static_cast<size_t>(k) * nr;
-    double s = 0.0;
-    for (int i = 0; i < nr; ++i) s = fma(__ldg(u + i), sm[i * (kXT + 1) + xx], s);
-    bad |= !finite(s);
-    F[(static_cast<size_t>(x0 + xx) * nt + a) * nr + k] = s;
+    const int nu = min(kG, k0 + nkt - kb);
+    const double* u = U + static_cast<size_t>(kb) * nr;
+    double s[kG];
+#pragma unroll
+    for (int g = 0; g < kG; ++g) s[g] = 0.0;
+    for (int i = 0; i < nr; ++i) {
+      const double y = sm[i * (kXT + 1) + xx];
+#pragma unroll
+      for (int g = 0; g < kG; ++g)
+        if (g < nu) s[g] = fma(__ldg(u + static_cast<size_t>(g) * nr + i), y, s[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < kG; ++g)
+      if (g < nu) {
+        bad |= !finite(s[g]);
+        F[(static_cast<size_t>(x0 + xx) * nt + a) * nr + kb + g] = s[g];
+      }
   }
   if (status && bad) atomicOr(status, kNonFinite);
 }
