@@ -491,3 +491,35 @@ def test_spectral_self_convergence_shape():
     e1 = np.max(np.abs(ne[0] - ne[2])) / np.max(np.abs(ne[2]))
     e2 = np.max(np.abs(ne[1] - ne[2])) / np.max(np.abs(ne[2]))
     assert e2 < 0.5 * e1, (e1, e2)
+
+
+# ------------------------------------------------------------------------------------ reduced system
+
+@pytest.mark.parametrize("nl", [1, 3, 7])
+def test_reduced_velocity_system_identity(nl):
+    """With N_l <= N_theta harmonics, A = I - dt P_O B P_S (B = C + E A_v in the harmonic basis)
+    satisfies A^-1 f = f + P_O ((I - dt B)^-1 - I) P_S f because P_S P_O = I (Section 3.3): the
+    reduced order-(N_l Nr) solve reproduces the dense Nv x Nv one. Checked with the oracle's own
+    K_C, K_A against B assembled from its harmonic blocks, and A_v coupling only l -> l +- 1."""
+    ops = O.Operators(tiny_cfg(nx=3, nr=10, nt=8, nl=nl, procs=[W.P1_ELASTIC, W.P2_EXC, W.P3_ION]))
+    nr, nt, nv = ops.nr, ops.nt, ops.nv
+    m = nl * nr
+    for q in range(nl):
+        for l in range(nl):
+            if abs(q - l) != 1:
+                assert np.all(ops.As[q, l] == 0.0)
+    P_S = np.kron(ops.T_S, np.eye(nr))   # (l, k) <- (a, k)
+    P_O = np.kron(ops.T_O, np.eye(nr))   # (a, k) <- (l, k)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(nv)
+    for E in (0.0, 3.7e3, -8.1e3):
+        B = np.zeros((m, m))
+        for q in range(nl):
+            B[q * nr:(q + 1) * nr, q * nr:(q + 1) * nr] += ops.Cs[q]
+            for l in range(nl):
+                B[q * nr:(q + 1) * nr, l * nr:(l + 1) * nr] += E * ops.As[q, l]
+        A = np.eye(nv) - ops.dt * (ops.KC + E * ops.KA)
+        dense = np.linalg.solve(A, f)
+        y = P_S @ f
+        reduced = f + P_O @ (np.linalg.solve(np.eye(m) - ops.dt * B, y) - y)
+        assert np.linalg.norm(reduced - dense) <= 1e-12 * np.linalg.norm(dense), E
