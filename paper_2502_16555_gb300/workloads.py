@@ -7,7 +7,7 @@ feeds the two sides exactly the same numbers.
 Shapes follow the paper's discharge set-up (Table "model parameters", Section 4.3: gap
 L = 2.54 cm, 13.56 MHz drive, T0 = 300 K) with analytic stand-ins for the argon cross sections
 (Section 3.2, Table "three species Ar collisional model"); the LXCat data the paper uses is not
-part of this build.
+shipped with this package.
 """
 from __future__ import annotations
 
