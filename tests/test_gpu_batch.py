@@ -90,3 +90,39 @@ def test_batch_recaptures_for_new_states_and_isolates_errors():
     for k in (0, 2):
         ref = O.run(cfgs[k], steps=2, F0=F0[k], t0=0.0)[0]
         assert rel_l2(Fs[k].cpu().numpy(), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_with_reduced_velocity_systems(precision):
+    """A batch mixing a full-harmonic discharge with two N_l < N_theta ones (reduced order-N_l Nr
+    factorisations, one of them over three panels on the tensor cores in the mixed path): the
+    captured graph steps each like its own handle and like the oracle."""
+    from paper_2502_16555_gb300 import bte
+    cfgs = [W.scaled(W.SMALL, nx=9, nr=16, ntheta=16, p_Torr=0.3, V0=120.0),
+            W.scaled(W.SMALL, nx=8, nr=96, ntheta=8, nl=3, p_Torr=1.0, V0=150.0),
+            W.scaled(W.SMALL, nx=6, nr=20, ntheta=12, nl=4, p_Torr=0.5, V0=80.0)]
+    sb = [bte.Solver(c, precision) for c in cfgs]
+    assert [s.info()["solve_n"] for s in sb] == [256, 288, 80]
+    F0 = [W.random_state(c["nx"], c["ntheta"], c["nr"], seed=70 + k) for k, c in enumerate(cfgs)]
+    t0 = 0.21 / W.RF_FREQ_HZ
+    Fb = [torch.from_numpy(f.copy()).cuda() for f in F0]
+    batch = bte.Batch(sb)
+    assert batch.run(Fb, 2, t0) == [bte.OK] * 3
+    # two steps, each within the per-step bar (1e-10 FP64, 1e-9 mixed) of the oracle
+    tol = 2 * (1e-10 if precision == "fp64" else 1e-9)
+    for k, c in enumerate(cfgs):
+        si = bte.Solver(c, precision)
+        Fi = torch.from_numpy(F0[k].copy()).cuda()
+        si.run(Fi, 2, t0)
+        assert rel_l2(Fb[k].cpu().numpy(), Fi.cpu().numpy()) <= 1e-12
+        ops = O.Operators(c)
+        ref = ops.step(ops.step(F0[k], t0), t0 + ops.dt)
+        assert rel_l2(Fb[k].cpu().numpy(), ref) <= tol
+        if c["nl"] < c["ntheta"]:
+            # the same solution through the full Nv x Nv factorisation, which is the less accurate
+            # of the two here (FP64, Nr = 96: 5.9e-10 from the reduced result after two steps,
+            # which is itself 1.6e-10 from the oracle): a same-solution check, not the bar
+            Ff = torch.from_numpy(F0[k].copy()).cuda()
+            bte.Solver(c, precision, full_v=True).run(Ff, 2, t0)
+            assert rel_l2(Fb[k].cpu().numpy(), Ff.cpu().numpy()) <= 1e-8
+    batch.close()
