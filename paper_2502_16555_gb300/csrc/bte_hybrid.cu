@@ -153,12 +153,11 @@ __global__ void dense_solve_kernel(double* __restrict__ A, double* __restrict__ 
     }
     __syncthreads();
     const double inv = 1.0 / A[static_cast<size_t>(k) * n + k];
-    const int m = n - k - 1;
-    for (int idx = tid; idx < m * (m + 1); idx += nt) {
-      const int i = k + 1 + idx / (m + 1), j = k + 1 + idx % (m + 1);  // j == n: right-hand side
+    // rows below the pivot: a warp per row, lanes over the columns (lane 0 also takes b)
+    for (int i = k + 1 + warp; i < n; i += nt >> 5) {
       const double l = A[static_cast<size_t>(i) * n + k] * inv;
-      if (j < n) A[static_cast<size_t>(i) * n + j] -= l * A[static_cast<size_t>(k) * n + j];
-      else b[i] -= l * b[k];
+      for (int j = k + 1 + lane; j < n; j += 32) A[static_cast<size_t>(i) * n + j] -= l * A[static_cast<size_t>(k) * n + j];
+      if (lane == 0) b[i] -= l * b[k];
     }
     __syncthreads();
   }
@@ -181,9 +180,9 @@ __global__ void dense_solve_smem_kernel(const double* __restrict__ Ag, const dou
   const int ld = n + 1;          // padded rows; column n holds b
   double* A = sm;
   __shared__ int piv;
-  __shared__ double red[32];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
-  for (int idx = tid; idx < n * n; idx += nt) A[(idx / n) * ld + idx % n] = Ag[idx];
+  for (int i = tid >> 5; i < n; i += nt >> 5)
+    for (int j = lane; j < n; j += 32) A[i * ld + j] = Ag[static_cast<size_t>(i) * n + j];
   for (int i = tid; i < n; i += nt) A[i * ld + n] = bg[i];
   __syncthreads();
   for (int k = 0; k < n; ++k) {
@@ -214,20 +213,24 @@ __global__ void dense_solve_smem_kernel(const double* __restrict__ Ag, const dou
       }
     __syncthreads();
     const double inv = 1.0 / A[k * ld + k];
-    const int m = n - k - 1;
-    for (int idx = tid; idx < m * (m + 1); idx += nt) {
-      const int i = k + 1 + idx / (m + 1), j = k + 1 + idx % (m + 1);  // j == n: right-hand side
-      A[i * ld + j] -= A[i * ld + k] * inv * A[k * ld + j];
+    // rows below the pivot: a warp per row, lanes over the columns (column n: right-hand side)
+    for (int i = k + 1 + (tid >> 5); i < n; i += nt >> 5) {
+      const double l = A[i * ld + k] * inv;
+      for (int j = k + 1 + lane; j <= n; j += 32) A[i * ld + j] -= l * A[k * ld + j];
     }
     __syncthreads();
   }
-  for (int i = n - 1; i >= 0; --i) {
-    double s = 0.0;
-    for (int j = i + 1 + tid; j < n; j += nt) s = fma(A[i * ld + j], A[j * ld + n], s);
-    s = block_sum(s, red);
-    if (tid == 0) A[i * ld + n] = (A[i * ld + n] - s) / A[i * ld + i];
-    __syncthreads();
+  // back substitution by warp 0 alone (lanes over the row, shuffle sums): no block barriers
+  if (tid < 32) {
+    for (int i = n - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int j = i + 1 + lane; j < n; j += 32) s = fma(A[i * ld + j], A[j * ld + n], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) A[i * ld + n] = (A[i * ld + n] - s) / A[i * ld + i];
+      __syncwarp();
+    }
   }
+  __syncthreads();
   for (int i = tid; i < n; i += nt) x[i] = A[i * ld + n];
 }
 
