@@ -441,10 +441,10 @@ bte_status implicit_setup(bte_handle* h, int m, bool full_q) {
   if (s == BTE_OK) s = halloc(h, &h->Vb, D * (m + 1));
   if (s == BTE_OK) s = halloc(h, &h->Zb, D * m);
   if (s == BTE_OK) s = halloc(h, &h->part, static_cast<size_t>(kDotGrid) * (m + 1));
-  if (s == BTE_OK) s = halloc(h, &h->dsum, m + 1);
+  if (s == BTE_OK) s = halloc(h, &h->dsum, 3 * (m + 1));  // two Gram-Schmidt passes and a norm
   if (s != BTE_OK) return s;
   if (h->dsum_host) cudaFreeHost(h->dsum_host);
-  BH_CUDA(h, cudaMallocHost(reinterpret_cast<void**>(&h->dsum_host), (m + 1) * sizeof(double)));
+  BH_CUDA(h, cudaMallocHost(reinterpret_cast<void**>(&h->dsum_host), 3 * (m + 1) * sizeof(double)));
   h->gm = m;
   return BTE_OK;
 }
@@ -462,6 +462,13 @@ void enqueue_vapply(bte_handle* h, const double* X, const double* E, double c, d
   const HostOps& o = h->ops;
   const size_t smem = sizeof(double) * (static_cast<size_t>(o.nv) + 2 * o.nl * o.nr);
   v_apply_kernel<<<o.nx, 256, smem, h->st>>>(X, E, c, h->Cs, h->Alo, h->Aup, h->TO, h->TS, out, o.nt, o.nr, o.nl);
+}
+
+// out_dev[j] = V_j . w for j < k on the device (stream-ordered; no host synchronisation)
+void enqueue_dots(bte_handle* h, const double* V, size_t ld, int k, const double* w, double* out_dev) {
+  const size_t D = static_cast<size_t>(h->ops.nx) * h->ops.nv;
+  multi_dot_kernel<<<kDotGrid, kDotBlock, 0, h->st>>>(V, ld, k, w, D, h->part);
+  sum_partials_kernel<<<k, 128, 0, h->st>>>(h->part, kDotGrid, k, out_dev);
 }
 
 // dots[j] = V_j . w for j < k into the pinned host array (synchronises the stream)
@@ -671,7 +678,7 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
   if ((s = norm(h->Rv, rn)) != BTE_OK) return s;
   bool conv = rn <= rtol * fn;
   int newton = 0, gm_total = 0;
-  std::vector<double> H(static_cast<size_t>(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), hv;
+  std::vector<double> H(static_cast<size_t>(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   // forcing term of the current Newton iteration: a failed line search (no sufficient decrease
   // along a direction GMRES solved only to grtol) retries the iteration with a 100x tighter
   // linear solve, at most twice, before the step gives up
@@ -710,14 +717,21 @@ bte_status bte_step_implicit(bte_handle* h, double* F_dev, const double* ni_dev,
         double* Zj = h->Zb + static_cast<size_t>(j) * D;
         if ((s = pinv(Vj, Zj)) != BTE_OK) return s;
         jac(Zj, Vn);
-        for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
-          if ((s = bte::host_dots(h, h->Vb, D, j + 1, Vn, hv)) != BTE_OK) return s;
-          for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] += hv[i];
-          multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0, h->Vb, D, j + 1, h->dsum, -1.0, D);
+        // classical Gram-Schmidt twice, then the norm: the projections stay on the device (the
+        // axpys read them there), so the host waits once per iteration for all three results
+        const size_t stride = static_cast<size_t>(m) + 1;
+        for (int pass = 0; pass < 2; ++pass) {
+          double* dp = h->dsum + pass * stride;
+          bte::enqueue_dots(h, h->Vb, D, j + 1, Vn, dp);
+          multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0, h->Vb, D, j + 1, dp, -1.0, D);
           launches += 3;
         }
-        double hn = 0.0;
-        if ((s = norm(Vn, hn)) != BTE_OK) return s;
+        bte::enqueue_dots(h, Vn, 0, 1, Vn, h->dsum + 2 * stride);
+        launches += 2;
+        BH_CUDA(h, cudaMemcpyAsync(h->dsum_host, h->dsum, 3 * stride * sizeof(double), cudaMemcpyDeviceToHost, st));
+        BH_CUDA(h, cudaStreamSynchronize(st));
+        for (int i = 0; i <= j; ++i) H[static_cast<size_t>(i) * m + j] += h->dsum_host[i] + h->dsum_host[stride + i];
+        const double hn = std::sqrt(h->dsum_host[2 * stride]);
         H[static_cast<size_t>(j + 1) * m + j] = hn;
         if (hn > 0.0) multi_axpy_kernel<<<vg, 256, 0, st>>>(Vn, 1.0 / hn, nullptr, D, 0, nullptr, 0.0, D);
         for (int i = 0; i < j; ++i) {  // earlier rotations on the new column
