@@ -189,6 +189,76 @@ def test_collision_energy_moment(proc):
     assert np.allclose(lhs, rhs, rtol=1e-9, atol=1e-10 * np.abs(rhs).max())
 
 
+def _energy_weights(t):
+    """w with sum_p w_p phi_p(v) = v^2 exactly (cubic splines reproduce quadratics), found by
+    collocation at the Greville abscissae: no quadrature and no Galerkin matrix involved."""
+    g = (t[1:-3] + t[2:-2] + t[3:-1]) / 3.0
+    return np.linalg.solve(O.bspline_eval(t, g), g**2)
+
+
+def _int_v2_phi(t):
+    """int_0^vmax v^2 phi_k dv by 8-point Gauss-Legendre on every knot interval (exact: degree 5)."""
+    xg, wg = np.polynomial.legendre.leggauss(8)
+    out = np.zeros(t.size - 4)
+    for a, b in zip(t[:-1], t[1:]):
+        if b > a:
+            xs = 0.5 * (a + b) + 0.5 * (b - a) * xg
+            out += (O.bspline_eval(t, xs) * (0.5 * (b - a) * wg * xs**2)[:, None]).sum(0)
+    return out
+
+
+def test_collision_T0_energy_moment_closed_form():
+    """Heavy-temperature term (Section 3.3, eq. "c_T0_mat_1d") under a constant collision
+    frequency, sigma = nu/(n0 v), so that v^3 sigma = nu v^2/n0. With the energy weights w
+    (sum_p w_p phi_p = v^2, hence sum_p w_p phi_p' = 2v), integration by parts gives exactly
+        (w^T C_T)_k = (2 kB T0 nu/m0) (3 int v^2 phi_k dv - vmax^3 phi_k(vmax)).
+    A flipped sign, a lost factor (kB T0/m0, n0) or a missing derivative fails it."""
+    nu = 2.5e9
+    n0 = O.neutral_density(1.0, 300.0)
+    proc = W.process("elastic", "nu", nu / n0)
+    ops = _ops(tiny_cfg(nr=14, procs=[proc]))
+    t = ops.knots
+    CT = O.collision_T0(t, [proc], ops.n0, ops.T0, ops.m0)
+    phi_end = O.bspline_eval(t, [ops.vmax])[0]
+    expect = 2.0 * O.K_B * ops.T0 * nu / ops.m0 * (3.0 * _int_v2_phi(t) - ops.vmax**3 * phi_end)
+    got = _energy_weights(t) @ CT
+    assert np.max(np.abs(got - expect)) <= 1e-12 * np.max(np.abs(expect))
+    # only the (0, 0) block carries it
+    C_noT = O.Operators(tiny_cfg(nr=14, procs=[proc], T0_K=300.0, m0_amu=1e40)).C_raw
+    np.testing.assert_array_equal(ops.C_raw[1:], C_noT[1:])
+
+
+@pytest.mark.parametrize("T0", [300.0, 5000.0])
+def test_elastic_energy_relaxation_toward_T0(T0):
+    """Constant collision frequency, elastic only, E = 0: the mean energy of a Maxwellian relaxes as
+    d<eps>/dt = -2 (m_e/m0) nu (<eps> - 3/2 kB T0) (continuum; loss + gain give the first part,
+    the heavy-temperature term the second). The discrete rate w^T C F / 1^T M F of a projected 2 eV
+    Maxwellian (negligible beyond vmax) must match it to the truncation level."""
+    nu = 2.5e9
+    n0 = O.neutral_density(1.0, T0)
+    proc = W.process("elastic", "nu", nu / n0)
+    ops = _ops(tiny_cfg(nx=3, nr=24, procs=[proc], T0_K=T0))
+    w = _energy_weights(ops.knots)
+    F = ops.maxwellian_coeffs(2.0)
+    dens = _int_v2_phi(ops.knots) @ F
+    eps = 0.5 * O.M_E * (w @ ops.M @ F) / dens
+    rate = 0.5 * O.M_E * (w @ ops.C_raw[0] @ F) / dens
+    expect = -2.0 * O.M_E / ops.m0 * nu * (eps - 1.5 * O.K_B * T0)
+    assert abs(rate / expect - 1.0) < 1e-5, (rate, expect)
+
+
+def test_maxwellian_at_T0_is_null_vector_of_elastic_operator():
+    """With loss + gain + C_T the Maxwellian at the gas temperature is an equilibrium, up to the
+    O(m_e/m0) difference between the exact elastic kernel and its diffusion limit. kB T0 = 1 eV
+    so that the Maxwellian is resolved by the B-splines; constant cross section."""
+    T0 = O.E_CHARGE / O.K_B
+    ops = _ops(tiny_cfg(nx=3, nr=48, procs=[W.P1_ELASTIC], T0_K=T0))
+    F = ops.maxwellian_coeffs(1.0)
+    CT = O.collision_T0(ops.knots, [W.P1_ELASTIC], ops.n0, ops.T0, ops.m0)
+    r = ops.C_raw[0] @ F
+    assert np.linalg.norm(r) < 1e-4 * np.linalg.norm(CT @ F)
+
+
 @pytest.mark.parametrize("proc", [W.P2_EXC, W.P3_ION, W.P1_ELASTIC])
 def test_collision_gain_against_direct_quadrature(proc):
     """The gain integral done in the post-collision speed agrees with a brute-force, heavily
