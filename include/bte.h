@@ -198,12 +198,14 @@ bte_status bte_profile(bte_handle* h, int enable, double* ms_out, unsigned long 
  * BTE_FLAG_HOST_ONLY, which holds no device memory. The paper has no counterpart; this is an
  * interface convenience. F_dev[nx][ntheta][nr] and ne_dev[nx] are device buffers of the caller.
  * Scratch: the nr Maxwellian coefficients are staged in a file-scope __device__ array of 4096 doubles
- * (32 KB) that every GPU loading libbte holds until the process exits; nr > 4096 gives BTE_EINVAL.
- * The first call on a device looks up that array's device address with the device current; make
- * that first call before any stream capture. All calls share the array and it keeps the last call's
- * coefficients (nothing in it needs to start at zero: each call writes the entries it reads); calls
- * whose work overlaps on the GPU (other streams, or other threads) race on it. Work is enqueued on
- * the handle's stream without synchronising it. */
+ * (32 KB) that every GPU loading libbte holds until the process exits; nr > 4096 gives BTE_EINVAL
+ * (bte_create limits nr to 880 today, so no handle reaches it). The first call on a device looks up
+ * that array's device address with the device current. The call copies the coefficients from a
+ * host buffer that is freed when it returns, so it must not be recorded into a CUDA graph: while
+ * the handle's stream is capturing it returns BTE_ESTATE and enqueues nothing. All calls share the
+ * array and it keeps the last call's coefficients (nothing in it needs to start at zero: each call
+ * writes the entries it reads); calls whose work overlaps on the GPU (other streams, or other
+ * threads) race on it. Work is enqueued on the handle's stream without synchronising it. */
 bte_status bte_init_maxwellian_static(const bte_handle* h, double* F_dev, const double* ne_dev, double Te_eV);
 
 /* ---- Adjoint of the step ----------------------------------------------------------------------

@@ -8,6 +8,8 @@
 // The only device scratch this needs (the nr B-spline coefficients of the unit Maxwellian, which
 // bte_init_maxwellian keeps in a buffer of the handle) lives in the file-scope array below, sized for
 // at most kMaxCoef coefficients. Every GPU that loads libbte holds it (32 KB) until the process exits.
+// bte_create already limits nr to 880, so the kMaxCoef check guards the array should that limit
+// ever be raised.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -38,8 +40,18 @@ extern "C" bte_status bte_init_maxwellian_static(const bte_handle* h, double* F_
     return bte::handle_fail(h, BTE_EINVAL,
                             "nr = " + std::to_string(o.nr) + " exceeds the " + std::to_string(kMaxCoef) +
                                 "-coefficient static scratch of bte_init_maxwellian_static");
+  // the coefficient copy below reads a host vector that is freed when this call returns, so it
+  // must not be recorded into a graph: refuse while the handle's stream is capturing
+  cudaStream_t st = bte::handle_stream(h);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess)
+    return bte::handle_fail(h, BTE_ECUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cs != cudaStreamCaptureStatusNone)
+    return bte::handle_fail(h, BTE_ESTATE,
+                            "bte_init_maxwellian_static must not be called while the handle's stream is capturing");
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return bte::handle_fail(h, BTE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return bte::handle_fail(h, BTE_EINVAL, "device ordinal out of range");
   double* scratch = nullptr;
@@ -55,7 +67,6 @@ extern "C" bte_status bte_init_maxwellian_static(const bte_handle* h, double* F_
     }
     scratch = g_coef_addr[dev];
   }
-  cudaStream_t st = bte::handle_stream(h);
   const std::vector<double> c = bte::maxwellian_coeffs(o, Te_eV);
   // the host vector is pageable, so this copy has taken the data before it returns
   e = cudaMemcpyAsync(scratch, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice, st);

@@ -132,6 +132,22 @@ def test_host_only_handle_refuses_device_work(lib):
     assert lib.bte_destroy(None) == bte.OK
 
 
+def test_static_fill_bound_and_arguments_without_device_work(lib):
+    """bte_init_maxwellian_static stages at most 4096 coefficients in its file-scope array; bte_create
+    already refuses nr > 880 (here nr = 4097 on a host-only handle), so no handle can reach that
+    bound. Bad arguments are refused before any CUDA call."""
+    import ctypes as C
+    from paper_2502_16555_gb300 import bte
+    with pytest.raises(bte.BteError) as e:
+        bte.Solver(W.scaled(W.SMALL, nx=3, nr=4097, ntheta=2), host_only=True)
+    assert e.value.status == bte.EINVAL
+    s = _solver(W.scaled(W.SMALL, nx=5, nr=6, ntheta=4))
+    assert lib.bte_init_maxwellian_static(s.h, None, C.c_void_p(8), 2.0) == bte.EINVAL
+    assert lib.bte_init_maxwellian_static(s.h, C.c_void_p(8), None, 2.0) == bte.EINVAL
+    assert lib.bte_init_maxwellian_static(s.h, C.c_void_p(8), C.c_void_p(8), -1.0) == bte.EINVAL
+    assert lib.bte_init_maxwellian_static(None, C.c_void_p(8), C.c_void_p(8), 2.0) == bte.EINVAL
+
+
 def test_batch_create_validates_before_any_device_work():
     """bte_batch_create refuses NULL/empty input and handles without device buffers (host-only),
     without touching a GPU."""
