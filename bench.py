@@ -35,10 +35,9 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # Nominal ratio TF32 : BF16 dense tensor throughput (1.1 : 2.25 PFLOP/s) applied to the measured
 # BF16 peak; TF32x3 spends three tensor products per FP32-accurate product.
 TF32_OVER_BF16 = 1.1 / 2.25
-# FP32 SIMT peak from unit counts and clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
-FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP64 peak: cuBLAS DGEMM (8192^3) measured on this machine's GB300 with `bench.py --peaks`.
-FP64_PEAK_TFLOPS = 1.10
+# FP32 SIMT peak from unit counts and clock: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (used when the
+# library FP32 GEMM measured in the run is not a plain CUDA-core GEMM).
+FP32_SIMT_UNITS_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the first-panel launch (k0 = 0) of
 # the kernels captured with ncu on this workload (the commands are in profiles/); the per-launch
 # figure reported is scaled to the step's average launch by the algorithmic bytes. Remove an entry
@@ -50,9 +49,75 @@ def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
             p = json.load(f)
-        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"], "src": "measured"}
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"], "src": "measured",
+                "when": p.get("when")}
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback", "when": None}
+
+
+def library_peaks(torch, n64=4096, n32=8192):
+    """cuBLAS GEMM throughput on this GPU, measured now (torch.matmul, best of several, CUDA
+    events): FP64 (DGEMM, n64^3), FP32 on the CUDA cores (SGEMM without TF32, n32^3) and TF32
+    (n32^3). TFLOP/s = 2 n^3 / time."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    for name, dt, tf32, n, it in (("fp64", torch.float64, False, n64, 3), ("fp32", torch.float32, False, n32, 4),
+                                  ("tf32", torch.float32, True, n32, 8)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        a @ b
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(it):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        out[name + "_tflops"] = 2.0 * n**3 / best / 1e12
+        del a, b
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
+def roofline_peaks(file_peaks, lib=None, clocks=None):
+    """The denominators of the roofline fractions, each with where it comes from:
+      hbm      copy bandwidth from MEASURED_PEAKS.json;
+      tensor   TF32x3 = the TF32 library GEMM measured in this run / 3 products (the BF16 peak of
+               MEASURED_PEAKS.json x 1.1/2.25 / 3 is reported beside it);
+      fp64     the FP64 library GEMM measured in this run;
+      fp32     the FP32 CUDA-core library GEMM measured in this run, unless it runs faster than the
+               unit-count peak (then it is not a CUDA-core GEMM and the unit count is used)."""
+    bf16_derived = file_peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0
+    p = {"hbm_gbs": file_peaks["hbm_gbs"],
+         "hbm_src": "MEASURED_PEAKS.json hbm_gbs (%s%s)" % (file_peaks["src"],
+                                                           ", " + file_peaks["when"] if file_peaks.get("when") else ""),
+         "tensor_tflops_bf16_derived": bf16_derived}
+    run = "measured in this run (cuBLAS via torch.matmul, best of several)"
+    if lib:
+        p["tensor_tflops"] = lib["tf32_tflops"] / 3.0
+        p["tensor_src"] = "TF32 GEMM 8192^3 %s: %.1f TFLOP/s / 3 products" % (run, lib["tf32_tflops"])
+        p["fp64_tflops"] = lib["fp64_tflops"]
+        p["fp64_src"] = "FP64 GEMM 4096^3 " + run
+        if lib["fp32_tflops"] <= 1.15 * FP32_SIMT_UNITS_TFLOPS:
+            p["fp32_tflops"] = lib["fp32_tflops"]
+            p["fp32_src"] = "FP32 CUDA-core GEMM 8192^3 " + run
+        else:
+            p["fp32_tflops"] = FP32_SIMT_UNITS_TFLOPS
+            p["fp32_src"] = ("unit counts (152 SMs x 128 lanes x 2 flop x 2.07 GHz); the FP32 library GEMM "
+                             "measured %.1f TFLOP/s, above that, so not a CUDA-core GEMM" % lib["fp32_tflops"])
+        p["library"] = dict(lib, clocks=clocks)
+    else:
+        p["tensor_tflops"] = bf16_derived
+        p["tensor_src"] = "MEASURED_PEAKS.json bf16_tflops x 1.1/2.25 (TF32) / 3 products"
+        p["fp64_tflops"] = 1.10
+        p["fp64_src"] = "FP64 GEMM measured on a GB300 of this pool in an earlier run"
+        p["fp32_tflops"] = FP32_SIMT_UNITS_TFLOPS
+        p["fp32_src"] = "unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
+    return p
 
 
 # ---------------------------------------------------------------------------------- clocks
@@ -137,10 +202,13 @@ def algorithmic(cfg, precision, kernel, tc, pair=True):
       lu_swap_trsm U12 = inv(L11) P A12, 2 * 128 * M * 128 flop per point and panel; in pairs
                    2 * 128 * kb2 * 128 plus 2 * 3 * 128^2 * M2 (the nonzero blocks of the pair's
                    inv(L11)) plus 2 * 128^3 for that inverse's off-diagonal block;
-      lu_solve     one read of the FP32 factors per solve launch (4 B * Nv^2 per point);
+      lu_solve     per point solve: the strictly block-lower and block-upper factors and the
+                   panels' two diagonal-block inverses, esz * (n^2 + n * nb) (n = the order factored);
       x_apply_q    the FP64 Q stream (8 B Nv Nx^2) plus Y in/out, per half step;
       v_form       write of the per-point matrices plus the K_C/K_A read;
-      residual     FP64 flops of the structured residual (Algorithm 2) per sweep."""
+      residual     FP64 flops of the structured residual (Algorithm 2) per point evaluation.
+    The refinement kernels skip converged points, so those two count point-solves and point
+    evaluations (the library's exact count of residual evaluations per point and step)."""
     nx, nr, nt = cfg["nx"], cfg["nr"], cfg["ntheta"]
     nv = nr * nt
     nl = cfg.get("nl") or nt
@@ -163,7 +231,8 @@ def algorithmic(cfg, precision, kernel, tc, pair=True):
                        for k0, kb2, m2 in tc_pairs(nv)) * nx, "flop", "tensor"
         return sum(2.0 * kb * (nv - k0 - kb) * kb for k0, kb in panels) * nx, "flop", "tensor" if tc else "alu"
     if kernel == "lu_solve":
-        return float(esz) * nx * nv * nv, "byte/launch", "hbm"
+        n = nl * nr if nl < nt else nv
+        return float(esz) * (n * n + n * nb), "byte/point", "hbm"
     if kernel == "x_apply_q":
         return 2 * (8.0 * nv * nx * nx + 16.0 * nv * nx), "byte", "hbm"
     if kernel == "x_apply_q_flops":
@@ -171,7 +240,7 @@ def algorithmic(cfg, precision, kernel, tc, pair=True):
     if kernel == "v_form":
         return float(esz) * nx * nv * nv + 16.0 * nv * nv, "byte", "hbm"
     if kernel == "residual":
-        return 2.0 * nx * (2 * nl * nt * nr + 3 * nl * nr * nr), "flop/launch", "alu"
+        return 2.0 * (2 * nl * nt * nr + 3 * nl * nr * nr), "flop/point", "alu"
     return None, None, None
 
 
@@ -196,40 +265,41 @@ def traffic_per_launch(cfg, kernel, launches_per_step):
     return TRAFFIC_K0[kernel] * (sum(per) / len(per)) / per[0]
 
 
-def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc, sweeps=None, measured=True):
+def roofline_of(cfg, precision, kernel, prof, steps, peaks, tc, evals=None, measured=True):
     amount, unit, bound = algorithmic(cfg, precision, kernel, tc)
     ms, launches = prof.get(kernel, (0.0, 0))
     if amount is None or launches == 0 or ms <= 0:
         return None
-    eff = launches
-    if unit.endswith("/launch") and sweeps is not None:
-        # refinement launches after a point converged return at once: count the ones that worked
-        eff = steps * (1 + sweeps)
-    total = amount * (eff if unit.endswith("/launch") else steps)
+    if unit.endswith("/point"):
+        # one solve and one residual evaluation per point and evaluation (converged points skip)
+        if evals is None:
+            return None
+        units = steps * cfg["nx"] * evals
+    else:
+        units = steps
+    total = amount * units
     rate = total / (ms / 1e3)
     if bound == "hbm":
-        achieved, peak, u = rate / 1e9, peaks["hbm_gbs"], "GB/s"
-        src = "MEASURED_PEAKS.json hbm_gbs (" + peaks["src"] + ")"
+        achieved, peak, u, src = rate / 1e9, peaks["hbm_gbs"], "GB/s", peaks["hbm_src"]
     elif bound == "tensor":
-        achieved, peak, u = rate / 1e12, peaks["bf16_tflops"] * TF32_OVER_BF16 / 3.0, "TFLOP/s"
-        src = "measured BF16 x 1.1/2.25 (TF32) / 3 products (" + peaks["src"] + ")"
+        achieved, peak, u, src = rate / 1e12, peaks["tensor_tflops"], "TFLOP/s", peaks["tensor_src"]
     elif precision == "fp64" or kernel == "residual":
-        achieved, peak, u = rate / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s"
-        src = "FP64 DGEMM measured on this GB300 (bench.py --peaks)"
+        achieved, peak, u, src = rate / 1e12, peaks["fp64_tflops"], "TFLOP/s", peaks["fp64_src"]
     else:
-        achieved, peak, u = rate / 1e12, FP32_SIMT_PEAK_TFLOPS, "TFLOP/s"
-        src = "FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"
-    return {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
-            "frac": achieved / peak,
-            "traffic": traffic_per_launch(cfg, kernel, launches / steps) if measured else None,
-            "launches_per_step": launches / steps, "working_launches_per_step": eff / steps,
-            "ms_per_step": ms / steps, "peak_source": src}
+        achieved, peak, u, src = rate / 1e12, peaks["fp32_tflops"], "TFLOP/s", peaks["fp32_src"]
+    out = {"kernel": kernel, "bound": bound, "achieved": achieved, "peak": peak, "unit": u,
+           "frac": achieved / peak,
+           "traffic": traffic_per_launch(cfg, kernel, launches / steps) if measured else None,
+           "launches_per_step": launches / steps, "ms_per_step": ms / steps, "peak_source": src}
+    if unit.endswith("/point"):
+        out["point_units_per_step"] = cfg["nx"] * evals
+    return out
 
 
-def rooflines(cfg, precision, prof, steps, peaks, tc, sweeps=None, measured=True):
+def rooflines(cfg, precision, prof, steps, peaks, tc, evals=None, measured=True):
     out = {}
     for k in prof:
-        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc, sweeps, measured)
+        r = roofline_of(cfg, precision, k, prof, steps, peaks, tc, evals, measured)
         if r:
             out[k] = r
     dom = max(out, key=lambda k: out[k]["ms_per_step"])
@@ -310,7 +380,10 @@ def run_ours(args, rank, world):
         cfg = W.scaled(cfg, nx=args.nx)
     dof = cfg["nx"] * cfg["nr"] * cfg["ntheta"]
     dt = cfg["dt_s"]
-    peaks = load_peaks()
+    # roofline denominators: the copy bandwidth from MEASURED_PEAKS.json, the library GEMM rates now
+    with ClockSampler(local) as pclk:
+        lib = library_peaks(torch)
+    peaks = roofline_peaks(load_peaks(), lib, pclk.summary())
 
     # ---- mixed precision (the headline)
     s = bte.Solver(cfg, precision="mixed")
@@ -330,14 +403,18 @@ def run_ours(args, rank, world):
         prof = s.profile_stop()
     launches = s.info()["launches"] - launches0
     sweeps = s.info()["last_refine_sweeps"]
+    evals = s.info()["last_refine_evals"]
     ms = ev0.elapsed_time(ev1) / args.steps
-    # the same timing again without event bracketing of every kernel
+    # the same timing again without event bracketing of every kernel (the end-to-end leg below
+    # repeats exactly these steps: same start state, same times)
     s.run(F, 1, (args.warmup + args.steps) * dt)
     Fq = F.clone()
+    F_e2e = F.clone()
+    t_q = (args.warmup + args.steps + 1) * dt
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    s.run(Fq, args.steps, (args.warmup + args.steps + 1) * dt)
+    s.run(Fq, args.steps, t_q)
     e1.record()
     barrier()
     ms_plain = e0.elapsed_time(e1) / args.steps
@@ -397,30 +474,30 @@ def run_ours(args, rank, world):
             structured[prec] = entry
             del ss
 
-    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region:
+    # the device-timed plain run's steps again, from its start state at its times
     e2e = None
     if not args.no_e2e:
         Fh = torch.empty(F.shape, dtype=torch.float64, pin_memory=True).numpy()
-        Fh[...] = F0.cpu().numpy()
-        s.step_host(Fh, 0.0)
-        n_e2e = max(3, min(args.steps, 20))
+        Fh[...] = F_e2e.cpu().numpy()
         barrier()
         t0 = time.perf_counter()
-        for i in range(n_e2e):
-            s.step_host(Fh, (i + 1) * dt)
-        e2e_s = (time.perf_counter() - t0) / n_e2e
+        for i in range(args.steps):
+            s.step_host(Fh, t_q + i * dt)
+        e2e_s = (time.perf_counter() - t0) / args.steps
         e2e = {"value": world * dof / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * dof,
-               "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_s * 1e3, "api": "bte_step_host"}
+               "d2h_bytes_per_step": 8 * dof, "ms_per_step": e2e_s * 1e3, "api": "bte_step_host",
+               "steps": "the device-timed plain run's %d steps: same start state and times" % args.steps,
+               "matches_device_run": bool(np.array_equal(Fh, Fq.cpu().numpy()))}
 
     # the measured DRAM traffic was captured on the default workload only
     measured = name == WORKLOAD and not args.nx
-    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc, sweeps=sweeps, measured=measured)
+    rf_dom, rf_all = rooflines(cfg, "mixed", prof, args.steps, peaks, tc, evals=evals, measured=measured)
     # kernels with a flop and a byte floor are measured against the binding one: the panel's FP32
-    # flops (SIMT peak) and the Q apply's FP64 flops (FP64 peak) take longer than their bytes
+    # flops (CUDA-core peak) and the Q apply's FP64 flops (FP64 peak) take longer than their bytes
     for kern, fkey, fpeak, fsrc in (
-            ("lu_panel", "lu_panel_flops", FP32_SIMT_PEAK_TFLOPS,
-             "FP32 SIMT from unit counts: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"),
-            ("x_apply_q", "x_apply_q_flops", FP64_PEAK_TFLOPS, "FP64 DGEMM measured on this GB300 (bench.py --peaks)")):
+            ("lu_panel", "lu_panel_flops", peaks["fp32_tflops"], peaks["fp32_src"]),
+            ("x_apply_q", "x_apply_q_flops", peaks["fp64_tflops"], peaks["fp64_src"])):
         if kern not in prof or not prof[kern][1] or kern not in rf_all:
             continue
         fl, _, _ = algorithmic(cfg, "mixed", fkey, tc)
@@ -442,7 +519,8 @@ def run_ours(args, rank, world):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32x3+f64" if prof["lu_gemm"][1] and tc else "f32+f64",
+        "vs_baseline": None,
+        "dtype": "fp32-panel+tf32x3+f64-refine" if prof["lu_gemm"][1] and tc else "fp32+f64-refine",
         "data": "synthetic",
         "config": {"workload": name, "nx": cfg["nx"], "nr": cfg["nr"], "ntheta": cfg["ntheta"],
                    "nv": cfg["nr"] * cfg["ntheta"], "dof": dof, "precision": "mixed",
@@ -457,6 +535,8 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "roofline": rf_dom,
         "rooflines": rf_all,
+        "peaks": peaks,
+        "refinement": {"sweeps_rounded_up": sweeps, "residual_evals_per_point_step": evals},
         "kernels_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
     }
     if world == 1 and not args.no_cpu:

@@ -16,7 +16,10 @@
  *  - Units: SI, energies in eV. The field E is in V/m; the electron force is -eE.
  *  - Errors are returned as bte_status, never thrown or trapped. bte_last_error() gives a message.
  *    A failed bte_step leaves F unchanged (BTE_ESINGULAR / BTE_ENOCONV / BTE_ENONFINITE) and the
- *    handle usable. Arguments are validated before anything is launched.
+ *    handle usable. Arguments are validated before anything is launched. Where a step meets
+ *    several failures the first of these is reported: an expired device wait (BTE_ECUDA), a
+ *    non-finite state or field handed in (BTE_ENONFINITE), a failed factorisation (BTE_ESINGULAR),
+ *    a non-finite result (BTE_ENONFINITE), refinement short of its tolerance (BTE_ENOCONV).
  *  - Streams: all device work is enqueued on bte_config.stream (a cudaStream_t, NULL = legacy
  *    default stream). Entry points do not synchronise the device except where stated.
  *  - Threading: a handle is used by one host thread at a time.
@@ -39,8 +42,8 @@ typedef enum {
   BTE_ECUDA = 3,       /* a CUDA runtime call or launch failed, or a CUDA error was already pending when
                           the call began (message in bte_last_error; a pending error is cleared) */
   BTE_ESINGULAR = 4,   /* a zero or non-finite pivot in some per-point factorisation */
-  BTE_ENOCONV = 5,     /* iterative refinement did not reach refine_tol within refine_max sweeps */
-  BTE_ENONFINITE = 6,  /* the input or the result of a step holds NaN/Inf */
+  BTE_ENOCONV = 5,     /* iterative refinement did not reach refine_tol within its sweeps */
+  BTE_ENONFINITE = 6,  /* the input (state or field) or the result of a step holds NaN/Inf */
   BTE_ESTATE = 7       /* call out of order (e.g. bte_step before bte_set_cross_sections) */
 } bte_status;
 
@@ -71,6 +74,11 @@ typedef enum {
                                    through A^-1 f = f + P_O((I - dt B)^-1 - I) P_S f: the same solution,
                                    (nv / (nl nr))^3 fewer factorisation flops and (nv / (nl nr))^2 less
                                    factor memory. bte_step_adjoint needs the full factors. */
+#define BTE_FLAG_DIAG_TC_TIMEOUT 32u  /* diagnostic, for testing the timeout path: every tensor-core
+                                   launch first waits (about 1 ms, before it issues any copy or MMA)
+                                   on a barrier that nothing signals, so the bounded wait expires,
+                                   the launch does no work and the step returns BTE_ECUDA with F
+                                   unchanged. Never set it for real work. */
 
 typedef struct {
   int nx;            /* Chebyshev-Gauss-Lobatto points, >= 3 */
@@ -84,8 +92,15 @@ typedef struct {
   double m0_amu;     /* neutral mass [u] */
   double dt_s;       /* time step [s] */
   int precision;     /* bte_precision */
-  double refine_tol; /* stop refining a point when max|r| <= refine_tol * max|b| (<= 0: default) */
-  int refine_max;    /* maximum refinement sweeps per step (< 0: default: 0 FP64, 4 mixed) */
+  double refine_tol; /* stop refining a point when max|r| <= refine_tol * max|b|, or when its normwise
+                        backward error is at FP64 rounding level: max|r| <= min(256 eps, refine_tol)
+                        (|A_i| max|x| + max|b|), |A_i| bounded by the infinity norms of dt K_C, dt K_A
+                        (<= 0: default 1e-13 FP64, 1e-12 mixed) */
+  int refine_max;    /* maximum refinement sweeps per step (< 0: default: 0 FP64, 4 mixed). BTE_MIXED
+                        with nr <= 64: points still short of the test after refine_max sweeps through
+                        the FP32 factors (cond(A_i) eps_32 near 1 or above: strong fields) are solved
+                        again by the FP64 block-tridiagonal solve and refined through it, two more
+                        sweeps, before BTE_ENOCONV is reported */
   void* stream;      /* cudaStream_t for all device work */
   unsigned flags;    /* BTE_FLAG_* */
 } bte_config;
@@ -122,12 +137,15 @@ typedef struct {
   int last_refine_sweeps; /* correction sweeps per point and step of the last bte_step / bte_run, averaged
                              over points and steps and rounded up (counted on the device) */
   double last_residual;   /* max over points of max|r|/max|b| after the last step */
-  unsigned last_flags;    /* device status bits of the last step (1 zero pivot, 2 non-finite,
-                             4 not converged) */
+  unsigned last_flags;    /* device status bits of the last step (1 zero pivot, 2 non-finite result,
+                             4 not converged, 8 expired device wait, 16 non-finite input) */
   unsigned long long launches; /* kernels launched by this handle so far */
   int tensor_cores;       /* 1 if the trailing updates run on tcgen05 (TF32x3) */
   int solve_n;            /* order of the per-point factorisation: nv, or nl * nr for the reduced
                              system (nl < ntheta without BTE_FLAG_FULL_V); 0 with BTE_FLAG_STRUCTURED */
+  double last_refine_evals; /* refinement residuals evaluated per point and step of the last bte_step /
+                             bte_run, averaged over points and steps (not rounded); each evaluation
+                             but a point's last is followed by one correction solve of that point */
 } bte_info;
 
 /* Kernel classes reported by bte_profile (index into its output arrays). */

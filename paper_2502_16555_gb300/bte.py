@@ -28,6 +28,7 @@ FLAG_SIMT_GEMM = 2
 FLAG_STRUCTURED = 4
 FLAG_TC_SINGLE = 8
 FLAG_FULL_V = 16
+FLAG_DIAG_TC_TIMEOUT = 32
 KINDS = {"elastic": 0, "excitation": 1, "ionization": 2}
 FORMS = {"const": 0, "linear": 1, "log": 2, "table": 3, "nu": 4}
 OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "Uinv": 7, "Q": 8,
@@ -69,7 +70,7 @@ class Info(C.Structure):
                 ("vmax_ms", C.c_double), ("device_bytes", C.c_size_t),
                 ("last_refine_sweeps", C.c_int), ("last_residual", C.c_double),
                 ("last_flags", C.c_uint), ("launches", C.c_ulonglong), ("tensor_cores", C.c_int),
-                ("solve_n", C.c_int)]
+                ("solve_n", C.c_int), ("last_refine_evals", C.c_double)]
 
 
 _lib = None
@@ -156,7 +157,7 @@ class Solver:
     def __init__(self, cfg: dict, precision: str = "fp64", refine_tol: float = 0.0,
                  refine_max: int = -1, stream=None, host_only: bool = False, device=None,
                  simt_gemm: bool = False, structured: bool = False, tc_single: bool = False,
-                 full_v: bool = False):
+                 full_v: bool = False, diag_tc_timeout: bool = False):
         self.lib = load()
         self.cfg = dict(cfg)
         self.host_only = host_only
@@ -178,7 +179,7 @@ class Solver:
         c.stream = None if host_only else C.c_void_p(stream.cuda_stream)
         c.flags = ((FLAG_HOST_ONLY if host_only else 0) | (FLAG_SIMT_GEMM if simt_gemm else 0) |
                    (FLAG_STRUCTURED if structured else 0) | (FLAG_TC_SINGLE if tc_single else 0) |
-                   (FLAG_FULL_V if full_v else 0))
+                   (FLAG_FULL_V if full_v else 0) | (FLAG_DIAG_TC_TIMEOUT if diag_tc_timeout else 0))
         h = C.c_void_p()
         st = self.lib.bte_create(C.byref(c), C.byref(h))
         if st != OK:

@@ -632,6 +632,19 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       }
     }
 
+  // infinity norms of K_C and K_A (the refinement's backward-error test bounds |A_i| by them)
+  o.kc_inf = 0.0;
+  o.ka_inf = 0.0;
+  for (int r = 0; r < nv; ++r) {
+    double sc = 0.0, sa = 0.0;
+    for (int c = 0; c < nv; ++c) {
+      sc += std::fabs(o.KC[static_cast<size_t>(r) * nv + c]);
+      sa += std::fabs(o.KA[static_cast<size_t>(r) * nv + c]);
+    }
+    o.kc_inf = std::max(o.kc_inf, sc);
+    o.ka_inf = std::max(o.ka_inf, sa);
+  }
+
   // moment vectors: 2 pi w_a int v^2 phi_k {1, m_e v^2/(2e), v sigma_j}
   o.n_proc = static_cast<int>(procs.size());
   std::vector<double> mn(nr, 0.0), me(nr, 0.0);

@@ -169,8 +169,9 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
   BA_CUDA(h, cudaStreamSynchronize(st));
   const unsigned f = *h->status_host;
   h->last_flags = f;
-  if (f & bte::kNonFinite) return afail(h, BTE_ENONFINITE, "non-finite values in the adjoint step");
+  if (f & bte::kNonFiniteIn) return afail(h, BTE_ENONFINITE, "non-finite values in the state or adjoint handed in");
   if (f & bte::kZeroPivot) return afail(h, BTE_ESINGULAR, "zero or non-finite pivot in a per-point factorisation");
+  if (f & bte::kNonFinite) return afail(h, BTE_ENONFINITE, "non-finite values in the adjoint step");
   return BTE_OK;
 }
 

@@ -217,8 +217,8 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
         auto single = [&](int k0, int ncols) {
           BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack(fac, h->perm, nx, n, k0, nb, nb, ncols, ks, ws[2],
                                                                   ws[3], ws[0], ws[1], st));
-          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, ncols, h->tcws, h->status, st));
-          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, ncols, h->tcws, h->status, st));
+          BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12(fac, nx, n, k0, ncols, h->tcws, h->status, st, h->tc_probe));
+          BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm(fac, nx, n, k0, ncols, h->tcws, h->status, st, h->tc_probe));
           return BTE_OK;
         };
         if (!h->tc_pair) {
@@ -242,8 +242,8 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
             BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_pair_linv(fac, h->perm, linv, nx, n, k0, ws[8], ws[9], st));
             BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack_pair(fac, h->perm, nx, n, k0, ks, ws[2], ws[3],
                                                                          ws[0], ws[1], st));
-            BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12_pair(fac, nx, n, k0, h->tcws, h->status, st));
-            BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st));
+            BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12_pair(fac, nx, n, k0, h->tcws, h->status, st, h->tc_probe));
+            BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st, h->tc_probe));
           }
         }
       } else {
@@ -267,6 +267,10 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
   return BTE_OK;
 }
 
+// Residual evaluations of the mixed path's FP64 escalation (the first follows the fresh FP64 solve,
+// each later one a correction through it).
+constexpr int kEscalationSweeps = 3;
+
 // One semi-implicit step of F_in into F_out (F_out is written only if the status word stays 0).
 bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const double* E_dev,
                         double t, double V0, double freq, const double* ni_dev = nullptr) {
@@ -274,6 +278,8 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   const int nx = o.nx, nt = o.nt, nr = o.nr, nv = o.nv, nl = o.nl;
   const double Eu = V0 / o.L * std::sin(2.0 * bte::kPi * freq * (t + 0.5 * o.dt));
   cudaStream_t st = h->st;
+  // a non-finite field is an input error like a non-finite state (the uniform one is known here)
+  if (!E_dev && !ni_dev && !std::isfinite(Eu)) return fail(h, BTE_ENONFINITE, "non-finite field (V0, freq_Hz or t_s)");
   // x half step #1 (eq. "bte_semi_implicit_xspace0")
   BTE_LAUNCH(BTE_K_X_TO_EIGEN, bte::launch_x_to_eigen(F_in, h->Uinv, h->Y, nx, nt, nr, h->status, st));
   BTE_LAUNCH(BTE_K_X_APPLY_Q, bte::launch_x_apply_q(h->Q, h->Y, h->Y2, nx, nt, nr, st));
@@ -285,7 +291,9 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     if (fs != BTE_OK) return fs;
     E_dev = h->Esc;
   }
-  // velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system")
+  // velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system"); a caller's field
+  // array is checked like the state
+  if (E_dev && !ni_dev) BTE_LAUNCH(BTE_K_OTHER, bte::launch_check_field(E_dev, nx, h->status, st));
   {
     const bte_status vs = enqueue_vsolve(h, h->Fa, h->Fb, E_dev, Eu, true);
     if (vs != BTE_OK) return vs;
@@ -295,7 +303,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
     BTE_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(int) * nx, st));
     for (int s = 0; s <= h->refine_max; ++s) {
       BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
-                                                      h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, nx,
+                                                      h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, o.kc_inf, o.ka_inf, nx,
                                                       nt, nr, nl, h->status, st));
       if (s == h->refine_max) break;
       if (h->structured && h->precision == BTE_FP64)
@@ -308,6 +316,23 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
                                                                     nr, nl, h->conv, 1, nullptr, st));
       else
         BTE_TRY(enqueue_lu_solve(h, h->R, h->Fb, h->conv, 1));
+    }
+    if (h->xs64) {
+      // points whose refinement with the FP32 factors has not converged (cond(A_i) * eps_32 near or
+      // above 1: strong fields) are solved again with the FP64 block-tridiagonal solve and refined
+      // through it; converged points return at once from every launch here
+      BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->Fa, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                                   h->TO, h->TS, h->xs64, nx, nt, nr, nl, h->conv, 0,
+                                                                   nullptr, st));
+      for (int s = 0; s < kEscalationSweeps; ++s) {
+        BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
+                                                        h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, o.kc_inf, o.ka_inf, nx,
+                                                        nt, nr, nl, h->status, st));
+        if (s + 1 == kEscalationSweeps) break;
+        BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->R, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo,
+                                                                     h->Aup, h->TO, h->TS, h->xs64, nx, nt, nr, nl,
+                                                                     h->conv, 1, nullptr, st));
+      }
     }
     BTE_LAUNCH(BTE_K_OTHER, bte::launch_check_conv(h->conv, nx, h->status, st));
   }
@@ -329,9 +354,11 @@ bte_status read_status(bte_handle* h, int steps = 1) {
   // point and step one more than the correction sweeps
   if (h->refine_max > 0 && steps > 0) {
     const double per = static_cast<double>(h->status_host[1]) / (static_cast<double>(h->ops.nx) * steps);
+    h->last_evals = per;
     h->last_sweeps = static_cast<int>(std::ceil(per - 1.0 - 1e-9));
     if (h->last_sweeps < 0) h->last_sweeps = 0;
   } else {
+    h->last_evals = 0.0;
     h->last_sweeps = 0;
   }
   if (h->refine_max > 0) {
@@ -342,9 +369,12 @@ bte_status read_status(bte_handle* h, int steps = 1) {
     for (double v : r) m = std::max(m, v);
     h->last_resid = m;
   }
+  // a non-finite input explains whatever follows from it; otherwise a failed factorisation explains
+  // a non-finite result
   if (f & bte::kTimeout) return fail(h, BTE_ECUDA, "a bounded device-side wait expired in the tensor-core update");
-  if (f & bte::kNonFinite) return fail(h, BTE_ENONFINITE, "non-finite values in the input or the result of a step");
+  if (f & bte::kNonFiniteIn) return fail(h, BTE_ENONFINITE, "non-finite values in the state or field handed in");
   if (f & bte::kZeroPivot) return fail(h, BTE_ESINGULAR, "zero or non-finite pivot in a per-point factorisation");
+  if (f & bte::kNonFinite) return fail(h, BTE_ENONFINITE, "non-finite values in the result of a step");
   if (f & bte::kNoConv) return fail(h, BTE_ENOCONV, "iterative refinement did not converge");
   return BTE_OK;
 }
@@ -438,6 +468,7 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   h->nb = cfg->precision == BTE_FP64 ? 64 : 128;
   h->structured = (cfg->flags & BTE_FLAG_STRUCTURED) != 0;
   h->tc_pair = (cfg->flags & BTE_FLAG_TC_SINGLE) == 0;
+  h->tc_probe = (cfg->flags & BTE_FLAG_DIAG_TC_TIMEOUT) != 0 ? 1 : 0;
   {
     const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
     h->reduced = !h->structured && nl < cfg->ntheta && (cfg->flags & BTE_FLAG_FULL_V) == 0;
@@ -492,8 +523,13 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
         float* x = nullptr;
         ok = chk(dalloc(h, &x, xsz));
         h->xs = x;
+        if (ok && bte::struct_smem_bytes(o.nr, o.nl, sizeof(double)) <= 200 * 1024)
+          ok = chk(dalloc(h, &h->xs64, xsz));
       }
     } else if (ok) {
+      // the mixed path's escalation for ill-conditioned points: the FP64 block-tridiagonal solve
+      if (h->precision == BTE_MIXED && o.nr <= 64 && bte::struct_smem_bytes(o.nr, o.nl, sizeof(double)) <= 200 * 1024)
+        ok = chk(dalloc(h, &h->xs64, static_cast<size_t>(o.nx) * o.nl * o.nr * o.nr));
       if (h->reduced)
         ok = chk(dalloc(h, &h->yred, static_cast<size_t>(o.nx) * h->nlu)) &&
              chk(dalloc(h, &h->zred, static_cast<size_t>(o.nx) * h->nlu));
@@ -700,6 +736,7 @@ bte_status bte_get_info(const bte_handle* hc, bte_info* info) {
   info->launches = hc->launches;
   info->tensor_cores = hc->use_tc ? 1 : 0;
   info->solve_n = hc->structured ? 0 : hc->nlu;
+  info->last_refine_evals = hc->last_evals;
   return BTE_OK;
 }
 

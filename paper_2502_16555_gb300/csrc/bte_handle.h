@@ -21,6 +21,8 @@ struct bte_handle {
   int refine_max = 0;
   bool structured = false;  // block-tridiagonal velocity solve instead of the dense LU
   void* xs = nullptr;       // its per-point scratch (nx * nl * nr * nr values)
+  double* xs64 = nullptr;   // mixed path: FP64 scratch of the structured solve that takes over points
+                            // whose refinement with the FP32 factors stalls (nx * nl * nr * nr)
   bool reduced = false;     // dense LU of I - dt B_i (order nl * nr) instead of A_i (order nv)
   int nlu = 0;              // order of the per-point factorisation (nv, or nl * nr when reduced)
   double *yred = nullptr, *zred = nullptr;  // P_S f and the reduced solution (nx * nlu each)
@@ -28,6 +30,7 @@ struct bte_handle {
   bool have_tc = false;   // the tensor-core workspace exists (use_tc may be switched on)
   int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)
   bool tc_pair = true;    // tensor-core updates two panels at a time (K = 256)
+  int tc_probe = 0;      // BTE_FLAG_DIAG_TC_TIMEOUT: tensor-core launches expire a wait first
   size_t bytes = 0;
   std::vector<void*> allocs;
 
@@ -62,6 +65,7 @@ struct bte_handle {
   double *Dl = nullptr, *Qfull = nullptr;       // Newton direction; full-step Q_ij of the preconditioner
   double* dsum_host = nullptr;                  // pinned
   int last_sweeps = 0;
+  double last_evals = 0.0;   // residual evaluations per point and step of the last run
   double last_resid = 0.0;
   unsigned last_flags = 0;
   unsigned long long launches = 0;

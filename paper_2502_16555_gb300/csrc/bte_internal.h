@@ -44,6 +44,7 @@ struct HostOps {
   std::vector<double> Cs;               // [nl][nr][nr]  M^-1 C (l-block diagonal)
   std::vector<double> As_lo, As_up;     // [nl][nr][nr]  M^-1 A_v blocks (q, q-1) and (q, q+1)
   std::vector<double> KC, KA;           // [nv][nv]  P_O C P_S, P_O A_v P_S
+  double kc_inf = 0.0, ka_inf = 0.0;    // their infinity norms (largest absolute row sums)
   std::vector<double> mom_n, mom_e;     // [nv]
   std::vector<double> mom_r;            // [n_proc][nv]
 };

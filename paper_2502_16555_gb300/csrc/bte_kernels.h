@@ -8,10 +8,11 @@
 namespace bte {
 
 enum StatusBits : unsigned {
-  kZeroPivot = 1u,   // a zero or non-finite pivot in some per-point LU
-  kNonFinite = 2u,   // NaN/Inf in the input or the result of a step
-  kNoConv = 4u,      // refinement did not reach the tolerance
-  kTimeout = 8u,     // a bounded device-side wait expired (tensor-core pipeline)
+  kZeroPivot = 1u,     // a zero or non-finite pivot in some per-point LU
+  kNonFinite = 2u,     // NaN/Inf in the result of a step
+  kNoConv = 4u,        // refinement did not reach the tolerance
+  kTimeout = 8u,       // a bounded device-side wait expired (tensor-core pipeline)
+  kNonFiniteIn = 16u,  // NaN/Inf in an input: the state handed in, or the field array
 };
 
 // tensor-core (tcgen05) trailing updates of the FP32 LU; workspace of tc_workspace_bytes(), parts
@@ -23,11 +24,14 @@ float* tc_ws_part(void* ws, int nx, int n, int part);
 constexpr int kTcKs = 256;  // K capacity (row length) of the operand parts
 // One 128-wide panel at k0: U12 = inv(L11) (P A12) for the first ncols trailing columns (written
 // into the matrix and, transposed and split, into parts 6-7), then A22 -= L21 U12 on those columns.
-void tc_lu_u12(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st);
-void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st);
+// probe != 0: every CTA's bounded wait expires before any work (testing the timeout path).
+void tc_lu_u12(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st,
+               int probe = 0);
+void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st,
+                int probe = 0);
 // The two panels at k0 and k0 + 128 together (K = 256) on every column right of k0 + 256.
-void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
-void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st);
+void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe = 0);
+void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe = 0);
 
 // Y2[b] = s_b M_b Y[b] for the nt * nr pairs b = a nr + i: M_b = M + b nx^2 (per_pair) or the one
 // matrix M; s_b = lam[i] mu[a] when lam is given (device arrays), else 1. Y, Y2 are [nt][nr][nx].
@@ -42,6 +46,8 @@ void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, i
                          unsigned* status, cudaStream_t st);
 
 // ---- velocity step
+// kNonFiniteIn in status if any of the nx field values E[i] is NaN or infinite
+void launch_check_field(const double* E, int nx, unsigned* status, cudaStream_t st);
 // A_i = I - dt (K_C + E_i K_A) in storage type T (float or double), row-major per point
 template <typename T>
 void launch_v_form(const double* KC, const double* KA, const double* E, double E_uniform, double dt,
@@ -125,8 +131,8 @@ void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, i
 // (Algorithm 2), per-point ratio max|r|/max|b|; marks conv[i] = 1 when ratio <= tol.
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
                      const double* Cs, const double* Alo, const double* Aup, const double* TO,
-                     const double* TS, double* r, double* ratio, int* conv, double tol, int nx,
-                     int nt, int nr, int nl, unsigned* status, cudaStream_t st);
+                     const double* TS, double* r, double* ratio, int* conv, double tol, double kc_inf,
+                     double ka_inf, int nx, int nt, int nr, int nl, unsigned* status, cudaStream_t st);
 void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st);
 
 // ---- misc

@@ -21,7 +21,10 @@
 // into the panel rows of the matrix and its transposed TF32 split over the B operand, where the
 // trailing update then reads it.
 // Every mbarrier wait is bounded (about 2 s of SM clock); on expiry the kernel records a status bit,
-// stops issuing work, drains the copies it issued, frees its TMEM and returns.
+// stops issuing work, drains the copies it issued, frees its TMEM and returns. For testing that path
+// (args.probe) each CTA first waits, before anything is in flight, on a barrier that nothing
+// signals, with a limit of about 1 ms: the wait expires, the status bit is set and the CTA goes
+// straight to its teardown.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -64,6 +67,7 @@ constexpr int CSLOTS = BTE_TC_CSLOTS;             // C staging slots
 constexpr int CSLOT_BYTES = BM * CW * 4;          // 16 or 8 KB
 constexpr int NTHREADS = 192;
 constexpr long long kWaitCycles = 1ll << 32;     // ~2 s at 2 GHz
+constexpr long long kProbeCycles = 1ll << 21;    // ~1 ms: the probe's wait
 constexpr unsigned kTimeoutBit = 8u;
 
 // instruction descriptor, kind::tf32 (formed per tile shape in the kernel): D = F32 (bits 4-5 = 1),
@@ -79,6 +83,7 @@ struct Smem {
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t drain;
+  uint64_t never;  // signalled by nothing: the probe's wait
   uint32_t tmem_base;
   int abort;
   int issued;    // K-chunks whose loads the producer issued
@@ -275,6 +280,7 @@ struct TcArgs {
   float* bt_hi;
   float* bt_lo;
   unsigned* status;
+  int probe;         // nonzero: the probe's expiring wait before any work (testing)
 };
 
 // CG = 1: one CTA per 128 x BN output tile. CG = 2: a cluster of two CTAs per 256 x 256 tile (each
@@ -305,6 +311,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < 2; ++i) mbar_init(&s.tfull[i], 1), mbar_init(&s.tempty[i], 4 * CG);
     for (int i = 0; i < CSLOTS; ++i) mbar_init(&s.cfull[i], 1);
     mbar_init(&s.drain, 1);
+    mbar_init(&s.never, 1);
     s.abort = 0;
     s.issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -327,9 +334,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s.tmem_base;
   const int per_point = args.tiles_m * args.tiles_n;
+  if (args.probe) {
+    // nothing is in flight yet: the wait expires, and every role below sees the abort and skips
+    // its work
+    if (threadIdx.x == 0) {
+      const long long t0 = clock64();
+      while (!mbar_try(&s.never, 0)) {
+        if (clock64() - t0 > kProbeCycles) {
+          s.abort = 1;
+          atomicOr(status, kTimeoutBit);
+          break;
+        }
+      }
+    }
+    __syncwarp();
+    if constexpr (CG == 2) cluster_sync();
+    else __syncthreads();
+  }
+  const bool run = !*reinterpret_cast<volatile int*>(&s.abort);
 
   if (warp == 0) {
-    if (lane == 0) {  // ---------------------------------------------------------------- producer
+    if (lane == 0 && run) {  // --------------------------------------------------------- producer
       int st = 0;
       uint32_t ph = 0;
       for (int t = cid; t < total; t += ncl) {
@@ -376,7 +401,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0 && rank == 0) {  // ------------------------------------------------ MMA issuer
+    if (lane == 0 && rank == 0 && run) {  // ----------------------------------------- MMA issuer
       int st = 0, acc = 0;
       uint32_t ph = 0, aph = 0;
       int consumed = 0;
@@ -442,7 +467,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       chq = q % NCC;
     };
     int c_issued = 0, c_done = 0;  // leader's count of C loads issued and waited for
-    if (leader && load_c)
+    if (leader && load_c && run)
       for (int q = 0; q < CSLOTS; ++q) {
         int tq, chq;
         chunk_at(q, tq, chq);
@@ -452,7 +477,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     int acc = 0, g = 0;
     uint32_t aph = 0;
-    bool stop = false;
+    bool stop = !run;
     for (int t = cid; t < total && !stop; t += ncl) {
       const int p = t / per_point, r = t % per_point;
       const int row = (r / args.tiles_n) * TM + rank * BM + trow;
@@ -691,7 +716,7 @@ void launch_pair(const Maps& mp, const TcArgs& a, cudaStream_t st) {
 // C -= A B^T over the block of C at (row0, col0) of every point: A = L21 split (parts 0, 1), B =
 // U12^T split (parts 6, 7), depth nchunk * 32
 void gemm(Maps& mp, float* fac, int nx, int n, int row0, int col0, int M, int N, int nchunk, unsigned* status,
-          cudaStream_t st) {
+          cudaStream_t st, int probe) {
   if (M <= 0 || N <= 0 || !mp.ok) return;
   TcArgs a{};
   a.fac = fac;
@@ -707,6 +732,7 @@ void gemm(Maps& mp, float* fac, int nx, int n, int row0, int col0, int M, int N,
   a.nchunk = a.nchunk_m0 = nchunk;
   a.mode = 0;
   a.status = status;
+  a.probe = probe;
   launch(mp, 0, 6, a, st);
 }
 
@@ -714,7 +740,7 @@ void gemm(Maps& mp, float* fac, int nx, int n, int row0, int col0, int M, int N,
 // the inverse split (parts 4, 5 or 8, 9), B = (P A12)^T split (parts 2, 3); U12 goes into the matrix
 // and, transposed and split, into parts 6, 7
 void u12(Maps& mp, float* fac, void* ws, int nx, int n, int row0, int col0, int M, int N, unsigned* status,
-         cudaStream_t st) {
+         cudaStream_t st, int probe) {
   if (N <= 0 || !mp.ok) return;
   TcArgs a{};
   a.fac = fac;
@@ -734,6 +760,7 @@ void u12(Maps& mp, float* fac, void* ws, int nx, int n, int row0, int col0, int 
   a.bt_hi = tc_ws_part(ws, nx, n, 6);
   a.bt_lo = tc_ws_part(ws, nx, n, 7);
   a.status = status;
+  a.probe = probe;
   launch(mp, M == KP ? 4 : 8, 2, a, st);
 }
 
@@ -768,27 +795,29 @@ bool tc_available() {
   return get_encode() != nullptr;
 }
 
-void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st) {
+void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st,
+                int probe) {
   Maps& mp = maps_for(fac, ws, nx, n);
-  gemm(mp, fac, nx, n, k0 + KP, k0 + KP, n - k0 - KP, ncols, KP / BK, status, st);
+  gemm(mp, fac, nx, n, k0 + KP, k0 + KP, n - k0 - KP, ncols, KP / BK, status, st, probe);
 }
 
-void tc_lu_u12(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st) {
+void tc_lu_u12(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned* status, cudaStream_t st,
+               int probe) {
   Maps& mp = maps_for(fac, ws, nx, n);
-  u12(mp, fac, ws, nx, n, k0, k0 + KP, KP, ncols, status, st);
+  u12(mp, fac, ws, nx, n, k0, k0 + KP, KP, ncols, status, st, probe);
 }
 
-void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
+void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe) {
   Maps& mp = maps_for(fac, ws, nx, n);
-  u12(mp, fac, ws, nx, n, k0, k0 + KS, KS, n - k0 - KS, status, st);
+  u12(mp, fac, ws, nx, n, k0, k0 + KS, KS, n - k0 - KS, status, st, probe);
 }
 
-void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st) {
+void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe) {
   Maps& mp = maps_for(fac, ws, nx, n);
   const int M = n - k0 - KS;
   if (M <= 0 || !mp.ok) return;
   if (pair_clusters() < 1) {
-    gemm(mp, fac, nx, n, k0 + KS, k0 + KS, M, M, KS / BK, status, st);
+    gemm(mp, fac, nx, n, k0 + KS, k0 + KS, M, M, KS / BK, status, st, probe);
     return;
   }
   TcArgs a{};
@@ -802,6 +831,7 @@ void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* stat
   a.nchunk = a.nchunk_m0 = KS / BK;
   a.mode = 0;
   a.status = status;
+  a.probe = probe;
   launch_pair(mp, a, st);
 }
 

@@ -30,7 +30,7 @@ __global__ void x_to_eigen_kernel(const double* __restrict__ F, const double* __
   for (int idx = threadIdx.x; idx < nxt * nr; idx += blockDim.x) {
     const int xx = idx / nr, k = idx % nr;
     const double v = F[(static_cast<size_t>(x0 + xx) * nt + a) * nr + k];
-    if (check && !finite(v)) atomicOr(status, kNonFinite);
+    if (check && !finite(v)) atomicOr(status, kNonFiniteIn);
     sm[xx * ld + k] = v;
   }
   __syncthreads();
@@ -155,14 +155,23 @@ __global__ void v_form_kernel(const double* __restrict__ KC, const double* __res
 }
 
 // Refinement residual of one point (CTA per point), Algorithm 2 with the structured operators:
-// xS = P_S x, g = (C_s + E_i A_s) xS, r = b - x + dt P_O g.
+// xS = P_S x, g = (C_s + E_i A_s) xS, r = b - x + dt P_O g. The point has converged when
+// max|r| <= tol max|b|, or when max|r| is already at the rounding level of an FP64 product A_i x,
+// max|r| <= min(kBackwardFloor, tol) (|A_i| max|x| + max|b|) with |A_i| <= 1 + dt (|K_C| +
+// |E_i| |K_A|) (infinity norms): a normwise backward error no refinement can improve on. The second
+// test decides only for ill-conditioned A_i, where |A_i| |x| is far above |b|.
+// 256 unit roundoffs of FP64: the normwise backward error at which a residual computed in FP64 is
+// rounding noise.
+constexpr double kBackwardFloor = 256.0 * 1.1102230246251565e-16;
+
 __global__ void residual_kernel(const double* __restrict__ X, const double* __restrict__ B,
                                 const double* __restrict__ E, double E_uniform, double dt,
                                 const double* __restrict__ Cs, const double* __restrict__ Alo,
                                 const double* __restrict__ Aup, const double* __restrict__ TO,
                                 const double* __restrict__ TS, double* __restrict__ R,
                                 double* __restrict__ ratio, int* __restrict__ conv, double tol,
-                                int nt, int nr, int nl, unsigned* __restrict__ status) {
+                                double kc_inf, double ka_inf, int nt, int nr, int nl,
+                                unsigned* __restrict__ status) {
   extern __shared__ double sm[];
   const int i = blockIdx.x;
   // a point that has converged keeps its iterate (the solves skip it), so its residual is final
@@ -171,7 +180,7 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
   double* xs = sm;             // nv
   double* xS = xs + nv;        // nl*nr
   double* g = xS + nl * nr;    // nl*nr
-  __shared__ double red_r[32], red_b[32];
+  __shared__ double red_r[32], red_b[32], red_x[32];
   const double* x = X + static_cast<size_t>(i) * nv;
   const double* b = B + static_cast<size_t>(i) * nv;
   const double Ei = E ? E[i] : E_uniform;
@@ -196,7 +205,7 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
     g[idx] = c + Ei * f;
   }
   __syncthreads();
-  double mr = 0.0, mb = 0.0;
+  double mr = 0.0, mb = 0.0, mx = 0.0;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const int a = v / nr, p = v % nr;
     double s = 0.0;
@@ -206,20 +215,30 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
     R[static_cast<size_t>(i) * nv + v] = rv;
     mr = fmax(mr, fabs(rv));
     mb = fmax(mb, fabs(bv));
+    mx = fmax(mx, fabs(xs[v]));
   }
   for (int o = 16; o > 0; o >>= 1) {
     mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
     mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   }
-  if ((threadIdx.x & 31) == 0) red_r[threadIdx.x >> 5] = mr, red_b[threadIdx.x >> 5] = mb;
+  if ((threadIdx.x & 31) == 0) red_r[threadIdx.x >> 5] = mr, red_b[threadIdx.x >> 5] = mb, red_x[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) mr = fmax(mr, red_r[w]), mb = fmax(mb, red_b[w]);
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w)
+      mr = fmax(mr, red_r[w]), mb = fmax(mb, red_b[w]), mx = fmax(mx, red_x[w]);
     const double q = mb > 0.0 ? mr / mb : (mr > 0.0 ? INFINITY : 0.0);
+    const double nA = 1.0 + dt * (kc_inf + fabs(Ei) * ka_inf);
     ratio[i] = q;
-    conv[i] = (q <= tol) ? 1 : 0;
+    conv[i] = (q <= tol || mr <= fmin(kBackwardFloor, tol) * (nA * mx + mb)) ? 1 : 0;
     atomicAdd(status + 1, 1u);  // residual evaluations (refinement accounting)
   }
+}
+
+__global__ void check_field_kernel(const double* __restrict__ E, int nx, unsigned* status) {
+  bool bad = false;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) bad |= !isfinite(E[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, kNonFiniteIn);
 }
 
 __global__ void check_conv_kernel(const int* conv, int nx, unsigned* status) {
@@ -328,6 +347,10 @@ void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, i
   x_from_eigen_kernel<<<grid, 256, smem, st>>>(Y2, U, F, nx, nt, nr, status);
 }
 
+void launch_check_field(const double* E, int nx, unsigned* status, cudaStream_t st) {
+  check_field_kernel<<<1, 256, 0, st>>>(E, nx, status);
+}
+
 template <typename T>
 void launch_v_form(const double* KC, const double* KA, const double* E, double E_uniform, double dt,
                    T* fac, int nx, int nv, cudaStream_t st) {
@@ -341,8 +364,8 @@ template void launch_v_form<float>(const double*, const double*, const double*, 
 
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
                      const double* Cs, const double* Alo, const double* Aup, const double* TO,
-                     const double* TS, double* r, double* ratio, int* conv, double tol, int nx,
-                     int nt, int nr, int nl, unsigned* status, cudaStream_t st) {
+                     const double* TS, double* r, double* ratio, int* conv, double tol, double kc_inf,
+                     double ka_inf, int nx, int nt, int nr, int nl, unsigned* status, cudaStream_t st) {
   const size_t smem = sizeof(double) * (static_cast<size_t>(nt) * nr + 2 * nl * nr);
   static bool attr_set = false;
   if (!attr_set) {
@@ -350,7 +373,7 @@ void launch_residual(const double* x, const double* b, const double* E, double E
     attr_set = true;
   }
   residual_kernel<<<nx, 256, smem, st>>>(x, b, E, E_uniform, dt, Cs, Alo, Aup, TO, TS, r, ratio,
-                                         conv, tol, nt, nr, nl, status);
+                                         conv, tol, kc_inf, ka_inf, nt, nr, nl, status);
 }
 
 void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st) {

@@ -73,3 +73,25 @@ def test_autograd_function_backward():
     J.backward()
     _, saved = m.forward(m.theta0())
     assert np.allclose(th.grad.numpy(), m.gradient(saved), rtol=1e-12, atol=0.0)
+
+
+def test_gradient_at_the_adjoint_workload_size():
+    """The adjoint workload's grid (Nx=64, Nr=32, Ntheta=16, Nv=512, 1 Torr, 100 V, four
+    processes), 100 steps with a checkpoint every 50: the adjoint gradient with respect to V0 and
+    the elastic cross-section scale against central differences of the forward run (h = 1e-6
+    relative), each component to 1e-5."""
+    from paper_2502_16555_gb300 import adjoint
+    cfg = W.ADJOINT
+    m = adjoint.CycleDensity(cfg, steps=100, checkpoint=50)
+    th = m.theta0()
+    J, saved = m.forward(th)
+    g = m.gradient(saved)
+    names = m.names()
+    for k in (0, th.size - 1):
+        h = 1e-6 * max(1.0, abs(th[k]))
+        up, dn = th.copy(), th.copy()
+        up[k] += h
+        dn[k] -= h
+        fd = (m.forward(up)[0] - m.forward(dn)[0]) / (2 * h)
+        print("%s: adjoint %.10e  central difference %.10e" % (names[k], g[k], fd))
+        assert abs(g[k] - fd) <= 1e-5 * abs(fd), (names[k], g[k], fd)
