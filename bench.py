@@ -582,7 +582,7 @@ def run_batched(args, rank, world):
     inst = W.batched_instances()
     mine = [inst[k] for k in shard(len(inst), rank, world)]
 
-    def leg(precision, steps, warmup):
+    def leg(precision, steps, warmup, sequential=False):
         sv = [bte.Solver(c, precision=precision) for c in mine]
         Fs = [s.initial_state() for s in sv]
         t_setup = time.perf_counter()
@@ -590,6 +590,7 @@ def run_batched(args, rank, world):
         t_setup = time.perf_counter() - t_setup
         b.run(Fs, warmup, 0.0)
         t0 = [warmup * c["dt_s"] for c in mine]
+        Fseq = [F.clone() for F in Fs] if sequential else None
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -601,18 +602,47 @@ def run_batched(args, rank, world):
             torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist)
         info = [b.info(i) for i in range(len(sv))]
+        seq = None
+        if sequential:
+            # the same instances, variants, states and times, stepped one discharge after another
+            # (each through bte_run on its own stream): what batching buys over a loop of handles
+            per = []
+            torch.cuda.synchronize()
+            for k, (sk, F) in enumerate(zip(sv, Fseq)):
+                q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                q0.record(sk.stream)
+                sk.run(F, steps, t0[k])
+                q1.record(sk.stream)
+                torch.cuda.synchronize()
+                per.append(q0.elapsed_time(q1) / steps)
+            same = max(float(torch.linalg.norm(a - c) / torch.linalg.norm(c)) for a, c in zip(Fseq, Fs))
+            seq = {"ms_per_step": sum(per), "instance_ms_min": min(per), "instance_ms_max": max(per),
+                   "batch_speedup": sum(per) / ms,
+                   "max_rel_l2_vs_batch": same}
         ne = [s.moments(F)[0] for s, F in zip(sv, Fs)]
         b.close()
-        del sv, Fs
+        del sv, Fs, Fseq
         torch.cuda.empty_cache()
-        return ms, info, clk.summary(), t_setup, ne
+        return ms, info, clk.summary(), t_setup, ne, seq
 
     dof_all = sum(c["nx"] * c["nr"] * c["ntheta"] for c in inst)
-    ms, info, clocks, t_setup, ne_m = leg("mixed", args.steps, args.warmup)
+
+    def variant_name(i):
+        if not i["tensor_cores"]:
+            return "cuda-core update"
+        if not i["tc_pair"]:
+            return "tensor cores, single panels (K=128, 128x128 tiles)"
+        return "tensor cores, panel pairs (K=256, %s)" % ("256x256 CTA-pair tiles" if i["tc_cg"] == 2
+                                                        else "128x128 one-CTA tiles")
+    ms, info, clocks, t_setup, ne_m, seq = leg("mixed", args.steps, args.warmup, sequential=True)
+    shapes = {}
+    for c, i in zip(mine, info):
+        key = "nx%d_nr%d_nt%d" % (c["nx"], c["nr"], c["ntheta"])
+        shapes[key] = "%s; panel block %s" % (variant_name(i), "8x8" if i["panel_w"] == 8 else "16x4")
     out = {
         "metric": METRIC, "value": dof_all / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
-        "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "fp32-panel+tf32x3+f64-refine", "data": "synthetic",
         "config": {"workload": "batched64_uneven", "instances": len(inst), "dof": dof_all,
                    "graph": "one CUDA graph launch per step, instances as concurrent branches",
                    "l2": "working set > L2", "parallelism": f"instances sharded over {world} rank(s)"},
@@ -620,10 +650,12 @@ def run_batched(args, rank, world):
         "gpu_launches": int(info[0]["launches_per_step"] * args.steps) if info else 0,
         "autotune": {"setup_s": t_setup,
                      "tensor_core_instances": sum(i["tensor_cores"] for i in info),
-                     "panel_w8_instances": sum(1 for i in info if i["panel_w"] == 8)},
+                     "panel_w8_instances": sum(1 for i in info if i["panel_w"] == 8),
+                     "choice_per_shape": shapes},
+        "sequential": seq,
     }
     if args.batched_fp64:
-        ms64, _, _, _, ne_d = leg("fp64", 1, 1)
+        ms64, _, _, _, ne_d, _ = leg("fp64", 1, 1)
         out["fp64"] = {"value": dof_all / (ms64 / 1e3), "ms_per_step": ms64, "unit": UNIT}
         out["speedup_mixed_over_fp64"] = ms64 / ms
     if rank == 0:
@@ -668,7 +700,7 @@ def run_hybrid(args, rank, world):
     s = bte.Solver(cfg, precision="mixed")
     F0 = s.initial_state()
     out = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-           "higher_is_better": True, "data": "synthetic", "dtype": "tf32x3+f64",
+           "higher_is_better": True, "data": "synthetic", "dtype": "fp32-panel+tf32x3+f64-refine",
            "config": {"workload": HYBRID, "nx": cfg["nx"], "nr": cfg["nr"], "ntheta": cfg["ntheta"],
                       "dof": dof, "precision": "mixed", "ions": "parabolic, peak 1.05e15 m^-3"}}
     # ions
@@ -795,7 +827,7 @@ def run_hybrid_table(args, rank, world):
         rows.append(row)
     out = {"metric": "hybrid step time, semi-implicit vs fully-implicit electrons (ions included)",
            "unit": "ms/step", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "data": "synthetic", "dtype": "tf32x3+f64",
+           "warmup": args.warmup, "data": "synthetic", "dtype": "fp32-panel+tf32x3+f64-refine",
            "config": {"workload": HYBRID_TABLE, "precision": "mixed", "p_Torr": 1.0, "V0": 100.0,
                       "ions": "parabolic, peak 1.05e15 m^-3"},
            "rows": rows}

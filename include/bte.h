@@ -74,6 +74,9 @@ typedef enum {
                                    through A^-1 f = f + P_O((I - dt B)^-1 - I) P_S f: the same solution,
                                    (nv / (nl nr))^3 fewer factorisation flops and (nv / (nl nr))^2 less
                                    factor memory. bte_step_adjoint needs the full factors. */
+#define BTE_FLAG_TC_ONE_CTA 64u  /* BTE_MIXED on the tensor cores, panels in pairs: run the K = 256 update
+                                   on 128 x 128 tiles of single CTAs instead of 256 x 256 tiles of CTA
+                                   pairs (same products, twice the operand bytes staged per flop) */
 #define BTE_FLAG_DIAG_TC_TIMEOUT 32u  /* diagnostic, for testing the timeout path: every tensor-core
                                    launch first waits (about 1 ms, before it issues any copy or MMA)
                                    on a barrier that nothing signals, so the bounded wait expires,
@@ -334,8 +337,10 @@ typedef struct bte_batch bte_batch;
 /* flags for bte_batch_create */
 #define BTE_BATCH_AUTOTUNE 1u  /* per distinct instance shape (nx, nr, ntheta, nl, precision), time
                                   one short run of every algorithm variant (tensor-core or CUDA-core
-                                  trailing update; panel column-block width) on a scratch Maxwellian
-                                  state and keep the fastest for the instances of that shape */
+                                  trailing update; on the tensor cores panels in pairs on CTA-pair or
+                                  single-CTA tiles, or one panel at a time; panel column-block
+                                  width) on a scratch Maxwellian state and keep the fastest for the
+                                  instances of that shape */
 
 /* Group `count` (1..4096) distinct handles, created with device buffers and with cross sections
  * set. Handles stay owned by the caller and must outlive the batch; the autotuner (if asked) sets
@@ -354,10 +359,13 @@ bte_status bte_batch_create(int count, bte_handle* const* handles, void* stream,
 bte_status bte_batch_run(bte_batch* b, double* const* F_dev, int n_steps, const double* t0_s,
                          const double* V0, const double* freq_Hz, bte_status* status_out);
 
-/* Variant used by instance i (1 = tensor-core trailing update; panel column-block width, 0 = by
- * shape) and the kernels launched per batched step (all instances, after the first run). */
-bte_status bte_batch_get_info(const bte_batch* b, int i, int* tensor_cores, int* panel_w,
-                              unsigned long long* launches_per_step);
+/* Variant used by instance i: tensor_cores 1 = tensor-core trailing update; panel_w the panel
+ * column-block width (0 = by shape); tc_pair 1 = panels applied in pairs (K = 256), 0 = one at a
+ * time (K = 128); tc_cg 2 = the pair update on 256 x 256 tiles of CTA pairs, 1 = on 128 x 128 tiles
+ * of single CTAs; and the kernels launched per batched step (all instances, after the first run).
+ * Any output pointer may be NULL. */
+bte_status bte_batch_get_info(const bte_batch* b, int i, int* tensor_cores, int* panel_w, int* tc_pair,
+                              int* tc_cg, unsigned long long* launches_per_step);
 
 /* Release the batch (synchronises its stream; the handles are not touched). NULL is accepted. */
 bte_status bte_batch_destroy(bte_batch* b);

@@ -29,6 +29,7 @@ FLAG_STRUCTURED = 4
 FLAG_TC_SINGLE = 8
 FLAG_FULL_V = 16
 FLAG_DIAG_TC_TIMEOUT = 32
+FLAG_TC_ONE_CTA = 64
 KINDS = {"elastic": 0, "excitation": 1, "ionization": 2}
 FORMS = {"const": 0, "linear": 1, "log": 2, "table": 3, "nu": 4}
 OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "Uinv": 7, "Q": 8,
@@ -103,7 +104,8 @@ def load(path: str = LIB_PATH):
     lib.bte_last_error.restype = C.c_char_p
     lib.bte_batch_create.argtypes = [i, C.POINTER(vp), vp, u, C.POINTER(vp)]
     lib.bte_batch_run.argtypes = [vp, C.POINTER(vp), i, pd, pd, pd, C.POINTER(C.c_int)]
-    lib.bte_batch_get_info.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]
+    lib.bte_batch_get_info.argtypes = [vp, i, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]
     lib.bte_batch_destroy.argtypes = [vp]
     lib.bte_step_adjoint.argtypes = [vp, vp, vp, d, d, d, vp, d, vp, vp]
     lib.bte_adjoint_gradient.argtypes = [vp, vp, vp, d, pd]
@@ -157,7 +159,7 @@ class Solver:
     def __init__(self, cfg: dict, precision: str = "fp64", refine_tol: float = 0.0,
                  refine_max: int = -1, stream=None, host_only: bool = False, device=None,
                  simt_gemm: bool = False, structured: bool = False, tc_single: bool = False,
-                 full_v: bool = False, diag_tc_timeout: bool = False):
+                 full_v: bool = False, diag_tc_timeout: bool = False, tc_one_cta: bool = False):
         self.lib = load()
         self.cfg = dict(cfg)
         self.host_only = host_only
@@ -179,7 +181,8 @@ class Solver:
         c.stream = None if host_only else C.c_void_p(stream.cuda_stream)
         c.flags = ((FLAG_HOST_ONLY if host_only else 0) | (FLAG_SIMT_GEMM if simt_gemm else 0) |
                    (FLAG_STRUCTURED if structured else 0) | (FLAG_TC_SINGLE if tc_single else 0) |
-                   (FLAG_FULL_V if full_v else 0) | (FLAG_DIAG_TC_TIMEOUT if diag_tc_timeout else 0))
+                   (FLAG_FULL_V if full_v else 0) | (FLAG_DIAG_TC_TIMEOUT if diag_tc_timeout else 0) |
+                   (FLAG_TC_ONE_CTA if tc_one_cta else 0))
         h = C.c_void_p()
         st = self.lib.bte_create(C.byref(c), C.byref(h))
         if st != OK:
@@ -416,8 +419,10 @@ class Batch:
         return list(status)
 
     def info(self, i: int) -> dict:
-        tc, w, lps = C.c_int(), C.c_int(), C.c_ulonglong()
-        st = self.lib.bte_batch_get_info(self.b, int(i), C.byref(tc), C.byref(w), C.byref(lps))
+        tc, w, pr, cg, lps = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_ulonglong()
+        st = self.lib.bte_batch_get_info(self.b, int(i), C.byref(tc), C.byref(w), C.byref(pr), C.byref(cg),
+                                         C.byref(lps))
         if st != OK:
             raise BteError(st, self.lib.bte_batch_last_error(self.b).decode())
-        return {"tensor_cores": tc.value, "panel_w": w.value, "launches_per_step": lps.value}
+        return {"tensor_cores": tc.value, "panel_w": w.value, "tc_pair": pr.value, "tc_cg": cg.value,
+                "launches_per_step": lps.value}

@@ -243,7 +243,7 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
             BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::launch_lu_swap_pack_pair(fac, h->perm, nx, n, k0, ks, ws[2], ws[3],
                                                                          ws[0], ws[1], st));
             BTE_LAUNCH(BTE_K_LU_SWAP_TRSM, bte::tc_lu_u12_pair(fac, nx, n, k0, h->tcws, h->status, st, h->tc_probe));
-            BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st, h->tc_probe));
+            BTE_LAUNCH(BTE_K_LU_GEMM, bte::tc_lu_gemm_pair(fac, nx, n, k0, h->tcws, h->status, st, h->tc_probe, h->tc_cg));
           }
         }
       } else {
@@ -438,13 +438,19 @@ bool handle_profiling(const bte_handle* h) { return h->prof; }
 unsigned long long handle_launches(const bte_handle* h) { return h->launches; }
 void handle_add_launches(bte_handle* h, unsigned long long n) { h->launches += n; }
 bool handle_has_tc(const bte_handle* h) { return h->have_tc; }
-void handle_set_variant(bte_handle* h, bool tc, int panel_w) {
-  h->use_tc = tc && h->have_tc;
-  h->panel_w = panel_w;
+void handle_set_variant(bte_handle* h, const Variant& v) {
+  h->use_tc = v.tc && h->have_tc;
+  h->panel_w = v.panel_w;
+  h->tc_pair = v.pair;
+  h->tc_cg = v.cg == 1 ? 1 : 2;
 }
-void handle_get_variant(const bte_handle* h, bool& tc, int& panel_w) {
-  tc = h->use_tc;
-  panel_w = h->panel_w;
+Variant handle_get_variant(const bte_handle* h) {
+  Variant v;
+  v.tc = h->use_tc;
+  v.panel_w = h->panel_w;
+  v.pair = h->tc_pair;
+  v.cg = h->tc_cg;
+  return v;
 }
 const HostOps* handle_ops(const bte_handle* h) { return &h->ops; }
 void* handle_stream_ptr(const bte_handle* h) { return static_cast<void*>(h->st); }
@@ -469,6 +475,7 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   h->structured = (cfg->flags & BTE_FLAG_STRUCTURED) != 0;
   h->tc_pair = (cfg->flags & BTE_FLAG_TC_SINGLE) == 0;
   h->tc_probe = (cfg->flags & BTE_FLAG_DIAG_TC_TIMEOUT) != 0 ? 1 : 0;
+  h->tc_cg = (cfg->flags & BTE_FLAG_TC_ONE_CTA) != 0 ? 1 : 2;
   {
     const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
     h->reduced = !h->structured && nl < cfg->ntheta && (cfg->flags & BTE_FLAG_FULL_V) == 0;

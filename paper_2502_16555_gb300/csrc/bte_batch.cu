@@ -8,7 +8,9 @@
 //
 // Autotuner: for every distinct instance shape (nx, nr, ntheta, nl, precision) it times one
 // short run of each algorithm variant on a scratch Maxwellian state and keeps the fastest for all
-// instances of that shape: the tensor-core (TF32x3) or CUDA-core trailing update, and the panel
+// instances of that shape: the tensor-core (TF32x3) or CUDA-core trailing update; on the tensor
+// cores the update's tile shape: panels in pairs (K = 256) on 256 x 256 tiles of CTA pairs or on
+// 128 x 128 tiles of single CTAs, or one panel at a time (K = 128, 128 x 128 tiles); and the panel
 // kernel's column-block width (16 columns x 4 rows per thread, or 8 x 8).
 #include <cuda_runtime.h>
 
@@ -39,7 +41,7 @@ struct bte_batch {
   std::vector<double*> F_captured;
   unsigned long long launches_per_step = 0;
   std::vector<unsigned long long> inst_launches;  // per instance and step
-  std::vector<std::pair<bool, int>> variant;
+  std::vector<bte::Variant> variant;
   std::string err;
 };
 
@@ -149,7 +151,7 @@ bte_status time_variant(bte_batch* b, bte_handle* h, double* F, int steps, float
 
 bte_status autotune(bte_batch* b) {
   using Key = std::tuple<int, int, int, int, int>;
-  std::map<Key, std::pair<bool, int>> best;
+  std::map<Key, bte::Variant> best;
   for (size_t i = 0; i < b->hs.size(); ++i) {
     bte_handle* h = b->hs[i];
     const bte::HostOps& o = *bte::handle_ops(h);
@@ -166,15 +168,20 @@ bte_status autotune(bte_batch* b) {
       std::vector<double> one(o.nx, 1e15);
       cudaMemcpy(ne, one.data(), o.nx * sizeof(double), cudaMemcpyHostToDevice);
       bte_status s = bte_init_maxwellian(h, F, ne, 2.0);
-      std::vector<std::pair<bool, int>> cands;
-      for (int w : {0, info.precision == BTE_MIXED ? 8 : 4})
-        for (bool tc : {true, false})
-          if (!tc || bte::handle_has_tc(h)) cands.push_back({tc, w});
+      std::vector<bte::Variant> cands;
+      for (int w : {0, info.precision == BTE_MIXED ? 8 : 4}) {
+        if (bte::handle_has_tc(h)) {
+          cands.push_back({true, w, true, 2});
+          cands.push_back({true, w, true, 1});
+          cands.push_back({true, w, false, 1});
+        }
+        cands.push_back({false, w, true, 2});
+      }
       float tbest = 1e30f;
-      std::pair<bool, int> win{bte::handle_has_tc(h), 0};
+      bte::Variant win = bte::handle_get_variant(h);
       for (auto& c : cands) {
         if (s != BTE_OK) break;
-        bte::handle_set_variant(h, c.first, c.second);
+        bte::handle_set_variant(h, c);
         float ms = 0.f;
         s = time_variant(b, h, F, 2, ms);
         if (s == BTE_OK && ms < tbest) tbest = ms, win = c;
@@ -184,7 +191,7 @@ bte_status autotune(bte_batch* b) {
       if (s != BTE_OK) return bfail(b, s, "autotuning: a trial step failed");
       it = best.emplace(key, win).first;
     }
-    bte::handle_set_variant(h, it->second.first, it->second.second);
+    bte::handle_set_variant(h, it->second);
     b->variant[i] = it->second;
   }
   return BTE_OK;
@@ -245,12 +252,7 @@ bte_status bte_batch_create(int count, bte_handle* const* handles, void* stream,
       cudaMemcpy(b->dE, b->E.data(), sizeof(double*) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->dnx, nx.data(), sizeof(int) * count, cudaMemcpyHostToDevice) != cudaSuccess)
     return bad(bfail(b, BTE_ECUDA, "uploading batch parameters"));
-  for (int i = 0; i < count; ++i) {
-    bool tc;
-    int w;
-    bte::handle_get_variant(b->hs[i], tc, w);
-    b->variant[i] = {tc, w};
-  }
+  for (int i = 0; i < count; ++i) b->variant[i] = bte::handle_get_variant(b->hs[i]);
   if (flags & BTE_BATCH_AUTOTUNE) {
     bte_status s = autotune(b);
     if (s != BTE_OK) return bad(s);
@@ -297,12 +299,14 @@ bte_status bte_batch_run(bte_batch* b, double* const* F_dev, int n_steps, const 
   return first;
 }
 
-bte_status bte_batch_get_info(const bte_batch* b, int i, int* tensor_cores, int* panel_w,
-                              unsigned long long* launches_per_step) {
+bte_status bte_batch_get_info(const bte_batch* b, int i, int* tensor_cores, int* panel_w, int* tc_pair,
+                              int* tc_cg, unsigned long long* launches_per_step) {
   if (!b) return bfail(nullptr, BTE_EINVAL, "batch is NULL");
   if (i < 0 || i >= static_cast<int>(b->hs.size())) return bfail(const_cast<bte_batch*>(b), BTE_EINVAL, "index out of range");
-  if (tensor_cores) *tensor_cores = b->variant[i].first ? 1 : 0;
-  if (panel_w) *panel_w = b->variant[i].second;
+  if (tensor_cores) *tensor_cores = b->variant[i].tc ? 1 : 0;
+  if (panel_w) *panel_w = b->variant[i].panel_w;
+  if (tc_pair) *tc_pair = b->variant[i].pair ? 1 : 0;
+  if (tc_cg) *tc_cg = b->variant[i].cg;
   if (launches_per_step) *launches_per_step = b->launches_per_step;
   return BTE_OK;
 }

@@ -31,6 +31,7 @@ struct bte_handle {
   int panel_w = 0;        // preferred column-block width of the panel kernel (0: by shape)
   bool tc_pair = true;    // tensor-core updates two panels at a time (K = 256)
   int tc_probe = 0;      // BTE_FLAG_DIAG_TC_TIMEOUT: tensor-core launches expire a wait first
+  int tc_cg = 2;          // pair update on CTA pairs (2) or single CTAs (1)
   size_t bytes = 0;
   std::vector<void*> allocs;
 

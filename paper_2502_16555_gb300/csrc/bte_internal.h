@@ -94,9 +94,18 @@ bte_status enqueue_field(bte_handle* h, const double* F_dev, const double* ni_de
 // Reads the status word back on the handle's stream (synchronising it) and maps it to a status.
 bte_status handle_read_status(bte_handle* h);
 // Algorithm variants the batch autotuner chooses between: the tensor-core trailing update (only
-// if the handle holds its workspace) and the panel kernel's column-block width (0: by shape).
+// if the handle holds its workspace) or the CUDA-core one; on the tensor cores, panels applied in
+// pairs (K = 256) or one at a time (K = 128), and the pair update on 256 x 256 tiles of CTA pairs
+// (cg 2) or on 128 x 128 tiles of single CTAs (cg 1); the panel kernel's column-block width
+// (0: by shape).
+struct Variant {
+  bool tc = false;
+  int panel_w = 0;
+  bool pair = true;
+  int cg = 2;
+};
 bool handle_has_tc(const bte_handle* h);
-void handle_set_variant(bte_handle* h, bool tc, int panel_w);
-void handle_get_variant(const bte_handle* h, bool& tc, int& panel_w);
+void handle_set_variant(bte_handle* h, const Variant& v);
+Variant handle_get_variant(const bte_handle* h);
 
 }  // namespace bte

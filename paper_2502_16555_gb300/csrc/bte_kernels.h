@@ -31,7 +31,10 @@ void tc_lu_gemm(float* fac, int nx, int n, int k0, int ncols, void* ws, unsigned
                 int probe = 0);
 // The two panels at k0 and k0 + 128 together (K = 256) on every column right of k0 + 256.
 void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe = 0);
-void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe = 0);
+// cg = 2: 256 x 256 tiles on CTA pairs (where the GPU can co-schedule them); cg = 1: 128 x 128 tiles
+// on single CTAs.
+void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe = 0,
+                     int cg = 2);
 
 // Y2[b] = s_b M_b Y[b] for the nt * nr pairs b = a nr + i: M_b = M + b nx^2 (per_pair) or the one
 // matrix M; s_b = lam[i] mu[a] when lam is given (device arrays), else 1. Y, Y2 are [nt][nr][nx].

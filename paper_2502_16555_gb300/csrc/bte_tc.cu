@@ -812,11 +812,12 @@ void tc_lu_u12_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* statu
   u12(mp, fac, ws, nx, n, k0, k0 + KS, KS, n - k0 - KS, status, st, probe);
 }
 
-void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe) {
+void tc_lu_gemm_pair(float* fac, int nx, int n, int k0, void* ws, unsigned* status, cudaStream_t st, int probe,
+                     int cg) {
   Maps& mp = maps_for(fac, ws, nx, n);
   const int M = n - k0 - KS;
   if (M <= 0 || !mp.ok) return;
-  if (pair_clusters() < 1) {
+  if (cg == 1 || pair_clusters() < 1) {
     gemm(mp, fac, nx, n, k0 + KS, k0 + KS, M, M, KS / BK, status, st, probe);
     return;
   }

@@ -70,6 +70,7 @@ def test_batch_autotuned_against_oracle():
         assert rel_l2(Fs[k].cpu().numpy(), ref) <= 1e-9
         info = batch.info(k)
         assert info["tensor_cores"] in (0, 1) and info["panel_w"] in (0, 8)
+        assert info["tc_pair"] in (0, 1) and info["tc_cg"] in (1, 2)
 
 
 def test_batch_recaptures_for_new_states_and_isolates_errors():

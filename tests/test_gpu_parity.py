@@ -300,6 +300,11 @@ def test_tensor_core_panel_pairs_match_single_panels(shape):
     assert rel_l2(out[False, 0], out[True, 0]) <= 4 * e_single + 1e-9
     assert rel_l2(out[False, -1], ref) <= 1e-9
     assert rel_l2(out[True, -1], ref) <= 1e-9
+    # the K = 256 pair update on single-CTA tiles: the same products as on CTA pairs
+    s1 = solver(cfg, "mixed", tc_one_cta=True, refine_max=0)
+    F = to_dev(F0)
+    s1.step(F, t)
+    assert rel_l2(F.cpu().numpy(), out[False, 0]) <= e_pair
 
 
 # ------------------------------------------------------------------ entry points and errors
