@@ -386,7 +386,7 @@ def run_ours(args, rank, world):
     peaks = roofline_peaks(load_peaks(), lib, pclk.summary())
 
     # ---- mixed precision (the headline)
-    s = bte.Solver(cfg, precision="mixed")
+    s = bte.Solver(cfg, precision="mixed", panel_tc=args.panel_tc)
     tc = bool(s.info()["tensor_cores"])
     F = s.initial_state()
     F0 = F.clone()
@@ -925,6 +925,8 @@ def main():
                          "or the paper's semi- vs fully-implicit table rows")
     ap.add_argument("--adjoint-steps", type=int, default=0, help="adjoint workload: steps (0 = one RF cycle)")
     ap.add_argument("--batched-fp64", action="store_true", help="batched workload: also time the FP64 batch")
+    ap.add_argument("--panel-tc", action="store_true",
+                    help="mixed path: the panel's left-looking updates on the tensor cores (BTE_FLAG_PANEL_TC)")
     ap.add_argument("--nx", type=int, default=0,
                     help="profiling only: run the default workload with this many x points instead of 128")
     args = ap.parse_args()

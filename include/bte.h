@@ -77,6 +77,10 @@ typedef enum {
 #define BTE_FLAG_TC_ONE_CTA 64u  /* BTE_MIXED on the tensor cores, panels in pairs: run the K = 256 update
                                    on 128 x 128 tiles of single CTAs instead of 256 x 256 tiles of CTA
                                    pairs (same products, twice the operand bytes staged per flop) */
+#define BTE_FLAG_PANEL_TC 128u  /* BTE_MIXED on the tensor cores: run the left-looking updates inside each
+                                   128-column panel factorisation as TF32x3 tcgen05 MMAs (L tiles by
+                                   TMA, products accumulated in tensor memory) instead of CUDA-core
+                                   FMAs; same pivots up to rounding */
 #define BTE_FLAG_DIAG_TC_TIMEOUT 32u  /* diagnostic, for testing the timeout path: every tensor-core
                                    launch first waits (about 1 ms, before it issues any copy or MMA)
                                    on a barrier that nothing signals, so the bounded wait expires,

@@ -30,6 +30,7 @@ FLAG_TC_SINGLE = 8
 FLAG_FULL_V = 16
 FLAG_DIAG_TC_TIMEOUT = 32
 FLAG_TC_ONE_CTA = 64
+FLAG_PANEL_TC = 128
 KINDS = {"elastic": 0, "excitation": 1, "ionization": 2}
 FORMS = {"const": 0, "linear": 1, "log": 2, "table": 3, "nu": 4}
 OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "Uinv": 7, "Q": 8,
@@ -159,7 +160,8 @@ class Solver:
     def __init__(self, cfg: dict, precision: str = "fp64", refine_tol: float = 0.0,
                  refine_max: int = -1, stream=None, host_only: bool = False, device=None,
                  simt_gemm: bool = False, structured: bool = False, tc_single: bool = False,
-                 full_v: bool = False, diag_tc_timeout: bool = False, tc_one_cta: bool = False):
+                 full_v: bool = False, diag_tc_timeout: bool = False, tc_one_cta: bool = False,
+                 panel_tc: bool = False):
         self.lib = load()
         self.cfg = dict(cfg)
         self.host_only = host_only
@@ -182,7 +184,7 @@ class Solver:
         c.flags = ((FLAG_HOST_ONLY if host_only else 0) | (FLAG_SIMT_GEMM if simt_gemm else 0) |
                    (FLAG_STRUCTURED if structured else 0) | (FLAG_TC_SINGLE if tc_single else 0) |
                    (FLAG_FULL_V if full_v else 0) | (FLAG_DIAG_TC_TIMEOUT if diag_tc_timeout else 0) |
-                   (FLAG_TC_ONE_CTA if tc_one_cta else 0))
+                   (FLAG_TC_ONE_CTA if tc_one_cta else 0) | (FLAG_PANEL_TC if panel_tc else 0))
         h = C.c_void_p()
         st = self.lib.bte_create(C.byref(c), C.byref(h))
         if st != OK:

@@ -210,7 +210,7 @@ bte_status enqueue_vsolve(bte_handle* h, const double* in, double* out, const do
           // the L21 split for the tensor cores is written by lu_swap_pack
           BTE_LAUNCH(BTE_K_LU_PANEL, bte::launch_lu_panel<float>(fac, h->piv, h->perm, linv, uinv, nx, n, k0, kb, nb,
                                                                  h->status, nullptr, nullptr, ws[4], ws[5],
-                                                                 h->panel_w, st));
+                                                                 h->panel_w, st, h->panel_tc));
           return BTE_OK;
         };
         // the panel at k0 applied to the next ncols columns (U12, then A22 -= L21 U12)
@@ -476,6 +476,7 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
   h->tc_pair = (cfg->flags & BTE_FLAG_TC_SINGLE) == 0;
   h->tc_probe = (cfg->flags & BTE_FLAG_DIAG_TC_TIMEOUT) != 0 ? 1 : 0;
   h->tc_cg = (cfg->flags & BTE_FLAG_TC_ONE_CTA) != 0 ? 1 : 2;
+  h->panel_tc = (cfg->flags & BTE_FLAG_PANEL_TC) != 0;
   {
     const int nl = cfg->nl > 0 ? cfg->nl : cfg->ntheta;
     h->reduced = !h->structured && nl < cfg->ntheta && (cfg->flags & BTE_FLAG_FULL_V) == 0;

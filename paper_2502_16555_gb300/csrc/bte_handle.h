@@ -32,6 +32,7 @@ struct bte_handle {
   bool tc_pair = true;    // tensor-core updates two panels at a time (K = 256)
   int tc_probe = 0;      // BTE_FLAG_DIAG_TC_TIMEOUT: tensor-core launches expire a wait first
   int tc_cg = 2;          // pair update on CTA pairs (2) or single CTAs (1)
+  bool panel_tc = false;  // the panel's left-looking updates on the tensor cores
   size_t bytes = 0;
   std::vector<void*> allocs;
 

@@ -19,6 +19,9 @@ enum StatusBits : unsigned {
 // 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11) split, 6-7 U12^T split, 8-9 a
 // two-panel block's inv(L11) split (layout in bte_tc.cu)
 bool tc_available();
+// Tensor map (128 bytes into map) of the per-point FP32 matrices as a 3-D array [nx][n][n], boxes of
+// 128 rows x 32 columns, 128-byte swizzle: the K-major operand tiles the tensor cores read.
+bool tc_matrix_map(void* map, float* fac, int nx, int n);
 size_t tc_workspace_bytes(int nx, int n, int nbmax);
 float* tc_ws_part(void* ws, int nx, int n, int part);
 constexpr int kTcKs = 256;  // K capacity (row length) of the operand parts
@@ -66,9 +69,11 @@ int perm_record_ints(int nbmax);
 // mark-pivoting panel kernel, i.e. when lu_panel_fuses_uinv<T>(n, nbmax) holds.
 // w_pref: preferred column-block width of the mark-pivoting kernel (0: chosen by shape).
 template <typename T>
+// tc_ll (FP32, full 128-column panels of at most 2048 rows): the left-looking updates inside the
+// panel run as TF32x3 tcgen05 MMAs instead of CUDA-core FMAs.
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, int w_pref,
-                     cudaStream_t st);
+                     cudaStream_t st, bool tc_ll = false);
 template <typename T>
 bool lu_panel_fuses_uinv(int n, int nbmax, int w_pref);
 // Tensor-core path: for the first ncols columns right of the panel, the displaced-row writes of the

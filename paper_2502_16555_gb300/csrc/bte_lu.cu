@@ -13,10 +13,12 @@
 // Row swaps are not applied to the columns left of a panel ("lazy" swaps): the forward solve
 // applies each panel's pivots to the right-hand side just before eliminating with that panel's
 // columns, which is the same elimination order the factorisation used.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "bte_kernels.h"
 #include "bte_tf32.cuh"
@@ -588,6 +590,109 @@ __host__ __device__ inline int lazy_tmp_elems(int nb) {
   return a > b ? a : b;
 }
 
+// ---- tensor-core left-looking update of the panel (FP32 factors): PTX helpers and shared state.
+// The L tiles come from the matrix by TMA (128 rows x 32 columns, 128-byte swizzle, K-major), a
+// converter splits them into TF32 head and remainder in shared memory, and one thread issues
+// tcgen05 TF32 MMAs (M = 128 rows, N = 16 block columns, K = 8) accumulating L U in tensor memory.
+constexpr int kTcllTile = 128 * 32 * 4;           // one L tile: 16 KB
+constexpr int kTcllBTile = 16 * 32 * 4;           // one 32-deep chunk of U^T: 2 KB
+constexpr int kTcllBChunks = 4;                   // K <= 128 - 16
+constexpr long long kTcllWait = 1ll << 31;        // ~1 s of SM clock
+// tensor-core state bytes in the dynamic area after the diagonal block: 1 KB alignment slack, two
+// stages of (head, remainder) tiles, the U^T head and remainder chunks
+constexpr size_t kTcllBytes = 1024 + 2ull * 2 * kTcllTile + 2ull * kTcllBChunks * kTcllBTile;
+// instruction descriptor, kind::tf32: D F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9, 10-12 = 2), both
+// K-major, N >> 3 = 2 at bits 17-22, M >> 4 = 8 at bits 24-28
+constexpr uint32_t kTcllIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (2u << 17) | (8u << 24);
+
+template <bool kTc>
+struct TcllShared {};
+template <>
+struct TcllShared<true> {
+  alignas(8) uint64_t full[2];   // L tile landed (TMA transaction count)
+  uint64_t conv[2];              // tile split (four converter warps arrive)
+  uint64_t empty[2];             // the MMAs that read the stage have completed
+  uint64_t done;                 // every MMA of the block has completed
+  uint64_t drain;
+  uint32_t tmem;
+  int abort;
+  float Rall[128][16];           // earlier blocks' pivot rows, this block's columns
+  float Uall[128][16];           // ... as U rows
+};
+
+__device__ __forceinline__ uint32_t tcll_saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void tcll_mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tcll_saddr(b)), "r"(count));
+}
+__device__ __forceinline__ void tcll_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tcll_saddr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tcll_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tcll_saddr(b)) : "memory");
+}
+__device__ __forceinline__ bool tcll_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(tcll_saddr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false when the phase did not complete within kTcllWait cycles (the abort flag is set
+// and the status bit recorded) or another thread has aborted.
+__device__ bool tcll_wait(uint64_t* b, uint32_t parity, int* abort, unsigned* status) {
+  const long long t0 = clock64();
+  while (!tcll_try(b, parity)) {
+    if (*reinterpret_cast<volatile int*>(abort)) return false;
+    if (clock64() - t0 > kTcllWait) {
+      atomicExch(abort, 1);
+      atomicOr(status, kTimeout);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tcll_tma_load3(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(tcll_saddr(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(tcll_saddr(bar))
+      : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t tcll_sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+__device__ __forceinline__ void tcll_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(kTcllIdesc), "r"(accum));
+}
+__device__ __forceinline__ void tcll_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tcll_saddr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tcll_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 // Panel factorisation with pivots as marks (same contract as lu_panel_kernel, plus inv(U11); the
 // TF32 split of L21 is left to lu_swap_pack). One CTA of 1024 threads per point; thread t holds
 // physical panel rows t + 1024 q (q < RPT) of the current W-wide column block in registers. Rows do
@@ -604,14 +709,23 @@ __host__ __device__ inline int lazy_tmp_elems(int nb) {
 // At the end the rows are put in the order of the equivalent swap sequence (only displaced rows
 // move), the panel record and the LAPACK-style pivots are written, and inv(L11) (+ split) and,
 // when uinv is given, inv(U11) are formed from the final diagonal block.
-template <typename T, int W, int RPT, int NT>
+// kTcLL (FP32, W = 16, 4 rows x 512 threads): the left-looking update of a column block runs on the
+// tensor cores instead. The earlier blocks' pivot rows post their entries and U = inv(L11) (posted
+// entries) is formed in shared memory by block forward substitution (L11: those rows' L entries in
+// pivot order, copied to shared memory as each block is finished); then D = L[rows, 0:s0] U
+// accumulates in tensor memory, 128 rows x 16 columns per row group, by TF32x3 MMAs (the L tiles by
+// TMA from the matrix, split into head and remainder in shared memory), and every thread subtracts
+// its rows of D.
+template <typename T, int W, int RPT, int NT, bool kTcLL>
 __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fac, int* __restrict__ piv,
                                                                int* __restrict__ perm, T* __restrict__ linv,
                                                                T* __restrict__ uinv, int n, int k0, int nb,
                                                                int nbmax, unsigned* status,
-                                                               float* __restrict__ li_hi, float* __restrict__ li_lo) {
+                                                               float* __restrict__ li_hi, float* __restrict__ li_lo,
+                                                               const __grid_constant__ CUtensorMap mFac) {
   constexpr int VE = Vec16<T>::n, NONE = 1 << 30, MAXB = 128 / W, NW = NT / 32;
   static_assert(NT % 64 == 0 && NT <= 1024 && W * W <= NT, "block shape");
+  static_assert(!kTcLL || (sizeof(T) == 4 && W == 16 && RPT == 4 && NT == 512), "tensor-core left-looking shape");
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ T LinvB[MAXB][W][W + 1];             // inverse of the unit-lower part of each block's diagonal block
   __shared__ T Tb[W][W + 1];                      // the diagonal block of the block just eliminated
@@ -623,6 +737,7 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
   __shared__ __align__(16) T red_row[2][32][W];
   __shared__ int pphys[128];
   __shared__ int s_cnt, s_cnt2;
+  __shared__ TcllShared<kTcLL> tls;
 
   const int m0 = n - k0;
   int* orig = reinterpret_cast<int*>(smraw);  // logical position -> physical row (panel-relative)
@@ -638,6 +753,31 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
   int* ip = piv + static_cast<size_t>(mat) * n;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int npan = (n + nbmax - 1) / nbmax, pan = k0 / nbmax;
+  // tensor-core left-looking state: L11 in the diagonal-block area, the tiles after it (1 KB aligned)
+  T* L11s = triD;
+  unsigned char* tcb = nullptr;
+  uint32_t tmem = 0, gt = 0, done_ph = 0;
+  if constexpr (kTcLL) {
+    const uint32_t x = tcll_saddr(triX);
+    tcb = reinterpret_cast<unsigned char*>(triX) + (((x + 1023u) & ~1023u) - x);
+    if (tid == 0) {
+      for (int i = 0; i < 2; ++i) tcll_mbar_init(&tls.full[i], 1), tcll_mbar_init(&tls.conv[i], 4),
+                                  tcll_mbar_init(&tls.empty[i], 1);
+      tcll_mbar_init(&tls.done, 1);
+      tcll_mbar_init(&tls.drain, 1);
+      tls.abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(tcll_saddr(&tls.tmem)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = tls.tmem;
+  }
   for (int r = tid; r < m0; r += NT) orig[r] = r, pos[r] = r;
   int pc[RPT];
 #pragma unroll
@@ -662,66 +802,231 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
         for (int v = 0; v < W; v += VE) vload(A + static_cast<size_t>(k0 + r) * n + c0 + v, &a[q][v]);
       }
     }
-    // left-looking: earlier blocks t of this panel
-    for (int t = 0; t < b; ++t) {
-      const int t0 = t * W;
+    if constexpr (kTcLL) {
+      if (b > 0) {
+        float* stage = reinterpret_cast<float*>(tcb);              // [2][head, remainder] L tiles
+        float* bhi = reinterpret_cast<float*>(tcb + 4 * kTcllTile);  // U^T head, [chunk][16][32] swizzled
+        float* blo = bhi + kTcllBChunks * kTcllBTile / 4;
+        // (1) the earlier blocks' pivot rows post their entries; U[0:s0, :] = inv(L11) Rall by block
+        //     forward substitution
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        if (pc[q] >= t0 && pc[q] < t0 + W) {
+        for (int q = 0; q < RPT; ++q) {
+          if (pc[q] < s0) {
 #pragma unroll
-          for (int v = 0; v < W; v += VE) vstore(&Raw[pc[q] - t0][v], &a[q][v]);
+            for (int v = 0; v < W; v += VE) vstore(&tls.Rall[pc[q]][v], &a[q][v]);
+          }
         }
-      }
-      __syncthreads();
-      T (*U)[W] = Ub[t & 1];
-      if (tid < W * W) {
-        const int i = tid / W, jj = tid % W;
-        T acc = Raw[i][jj];
-        for (int k = 0; k < i; ++k) acc += LinvB[t][i][k] * Raw[k][jj];
-        U[i][jj] = acc;
-      }
-      __syncthreads();
-      // pivot rows of block t take their U values; rows below block t (unmarked, or marked by a
-      // later block) take the rank-W update, each U row chunk read once for all of a thread's rows.
-      // A row's L entries are fetched one 32-byte sector (two 16-byte vectors) at a time.
-      constexpr int KC = 32 / sizeof(T) < W ? 32 / sizeof(T) : W;
-      bool upd[RPT];
-      const T* lr[RPT];
+        __syncthreads();
+        for (int t = 0; t < b; ++t) {
+          const int t0 = t * W;
+          for (int e = tid; e < W * W; e += NT) {
+            const int i = e / W, jj = e % W;
+            float acc = tls.Rall[t0 + i][jj];
+            for (int k = 0; k < i; ++k) acc += LinvB[t][i][k] * tls.Rall[t0 + k][jj];
+            tls.Uall[t0 + i][jj] = acc;
+          }
+          __syncthreads();
+          if (t + 1 < b) {
+            const int r0 = t0 + W;
+            for (int e = tid; e < (s0 - r0) * W; e += NT) {
+              const int i = r0 + e / W, jj = e % W;
+              const float* lr = L11s + static_cast<size_t>(i) * ldl + t0;
+              float acc = tls.Rall[i][jj];
 #pragma unroll
-      for (int q = 0; q < RPT; ++q) {
-        const int r = tid + q * NT;
-        upd[q] = r < m0 && pc[q] >= t0 + W;
-        lr[q] = A + static_cast<size_t>(k0 + (r < m0 ? r : 0)) * n + k0 + t0;
-        if (r < m0 && pc[q] >= t0 && pc[q] < t0 + W) {
-          const int i = pc[q] - t0;
-#pragma unroll
-          for (int v = 0; v < W; v += VE) vload(&U[i][v], &a[q][v]);
+              for (int k = 0; k < W; ++k) acc -= lr[k] * tls.Uall[t0 + k][jj];
+              tls.Rall[i][jj] = acc;
+            }
+            __syncthreads();
+          }
         }
-      }
-      if (active) {
+        // (2) U^T into the MMA's B operand: head and remainder, K-major, 128-byte swizzle (the 16-byte
+        //     chunk j of row nn sits at j ^ (nn % 8)); pivot rows take their U rows
+        for (int e = tid; e < s0 * W; e += NT) {
+          const int k = e / W, nn = e % W, c = k >> 5, kk = k & 31;
+          float h, l;
+          split_tf32(tls.Uall[k][nn], h, l);
+          const int off = c * (kTcllBTile / 4) + (nn >> 3) * 256 + (nn & 7) * 32 + ((((kk >> 2) ^ (nn & 7))) << 2) + (kk & 3);
+          bhi[off] = h;
+          blo[off] = l;
+        }
+        unsigned upd = 0u;
 #pragma unroll
-        for (int kv = 0; kv < W; kv += KC) {
-          T l[RPT][KC];
+        for (int q = 0; q < RPT; ++q) {
+          if (pc[q] < s0) {
 #pragma unroll
-          for (int q = 0; q < RPT; ++q) {
+            for (int v = 0; v < W; v += VE) vload(&tls.Uall[pc[q]][v], &a[q][v]);
+          } else if (tid + q * NT < m0) {
+            upd |= 1u << q;
+          }
+        }
+        // the tensor-core reads (TMA of the L entries this CTA stored, MMA of the U^T tiles) come after
+        // every thread's ordinary writes
+        asm volatile("fence.proxy.async;" ::: "memory");
+        __syncthreads();
+        // (3) D = L[rows, 0:s0] U: row group g (rows 128 g ..), 32-column chunk c of K per tile
+        const int G = (m0 + 127) / 128, C = (s0 + 31) / 32, ntile = G * C;
+        const bool run = !*reinterpret_cast<volatile int*>(&tls.abort);
+        if (run) {
+          if (warp == 0 && lane == 0) {
+            // producer: L tiles of the matrix into the two stages
+            uint32_t it = gt;
+            for (int i = 0; i < ntile; ++i, ++it) {
+              const int st = it & 1;
+              if (!tcll_wait(&tls.empty[st], ((it >> 1) & 1u) ^ 1u, &tls.abort, status)) break;
+              tcll_expect_tx(&tls.full[st], kTcllTile);
+              tcll_tma_load3(stage + st * 2 * (kTcllTile / 4), &mFac, k0 + 32 * (i % C), k0 + 128 * (i / C), mat,
+                             &tls.full[st]);
+            }
+          } else if (warp == 1 && lane == 0) {
+            // MMA issuer: three TF32 products per K step (remainder x head, head x remainder, head x head)
+            uint32_t it = gt;
+            for (int i = 0; i < ntile; ++i, ++it) {
+              const int st = it & 1;
+              if (!tcll_wait(&tls.conv[st], (it >> 1) & 1u, &tls.abort, status)) break;
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const int g = i / C, c = i % C;
+              const uint32_t d = tmem + 16 * g;
+              const uint32_t ah = tcll_saddr(stage + st * 2 * (kTcllTile / 4)), al = ah + kTcllTile;
+              const uint32_t bh = tcll_saddr(bhi) + c * kTcllBTile, bl = tcll_saddr(blo) + c * kTcllBTile;
 #pragma unroll
-            for (int c = 0; c < KC; c += VE) {
-              if (upd[q]) vload(lr[q] + kv + c, &l[q][c]);
-              else
+              for (int kk = 0; kk < 4; ++kk) {
+                if (32 * c + 8 * kk >= s0) break;
+                const uint32_t off = kk * 32;
+                tcll_mma(d, tcll_sdesc(al + off), tcll_sdesc(bh + off), (c | kk) ? 1u : 0u);
+                tcll_mma(d, tcll_sdesc(ah + off), tcll_sdesc(bl + off), 1u);
+                tcll_mma(d, tcll_sdesc(ah + off), tcll_sdesc(bh + off), 1u);
+              }
+              tcll_commit(&tls.empty[st]);
+            }
+            tcll_commit(&tls.done);
+          } else if (warp >= 2 && warp < 6) {
+            // converters: head = TF32 rounding in place, remainder beside it
+            const int ct = tid - 64;
+            uint32_t it = gt;
+            for (int i = 0; i < ntile; ++i, ++it) {
+              const int st = it & 1;
+              // one lane waits for the tile and the warp follows it, so the warp never splits
+              int ok = 0;
+              if (lane == 0) ok = tcll_wait(&tls.full[st], (it >> 1) & 1u, &tls.abort, status) ? 1 : 0;
+              ok = __shfl_sync(0xffffffffu, ok, 0);
+              __syncwarp();
+              if (!ok) break;
+              float4* hp = reinterpret_cast<float4*>(stage + st * 2 * (kTcllTile / 4));
+              float4* lp = hp + kTcllTile / 16;
 #pragma unroll
-                for (int u = 0; u < VE; ++u) l[q][c + u] = T(0);
+              for (int u = 0; u < kTcllTile / 16 / 128; ++u) {
+                const float4 x = hp[ct + 128 * u];
+                float4 h, l;
+                split_tf32(x.x, h.x, l.x);
+                split_tf32(x.y, h.y, l.y);
+                split_tf32(x.z, h.z, l.z);
+                split_tf32(x.w, h.w, l.w);
+                hp[ct + 128 * u] = h;
+                lp[ct + 128 * u] = l;
+              }
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) tcll_arrive(&tls.conv[st]);
             }
           }
+          gt += ntile;
+        }
+        __syncthreads();
+        if (run && tid == 0) tcll_wait(&tls.done, done_ph, &tls.abort, status);
+        if (run) done_ph ^= 1u;
+        __syncthreads();
+        if (*reinterpret_cast<volatile int*>(&tls.abort)) {
+          // an expired wait: let the copies and products in flight finish before the CTA moves on
+          if (warp == 0 && lane == 0) {
+            for (int st = 0; st < 2; ++st) {
+              const long long t1 = clock64();
+              while (!tcll_try(&tls.full[st], ((gt - 1 - st) >> 1) & 1u) && clock64() - t1 < kTcllWait) {
+              }
+            }
+          } else if (warp == 1 && lane == 0) {
+            tcll_commit(&tls.drain);
+            const long long t1 = clock64();
+            while (!tcll_try(&tls.drain, 0) && clock64() - t1 < kTcllWait) {
+            }
+          }
+          __syncthreads();
+        } else {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t lanes = static_cast<uint32_t>(32 * (warp & 3)) << 16;
 #pragma unroll
-          for (int u = 0; u < KC; ++u) {
+          for (int q = 0; q < RPT; ++q) {
+            float dv[16];
+            tcll_ld16(tmem + lanes + 16 * ((warp >> 2) + 4 * q), dv);
+            if ((upd >> q) & 1u) {
 #pragma unroll
-            for (int v = 0; v < W; v += VE) {
-              T uu[VE];
-              vload(&U[kv + u][v], uu);
-#pragma unroll
-              for (int q = 0; q < RPT; ++q)
-#pragma unroll
-                for (int e = 0; e < VE; ++e) a[q][v + e] -= l[q][u] * uu[e];
+              for (int j = 0; j < W; ++j) a[q][j] -= dv[j];
+            }
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+      }
+    } else {
+    // left-looking: earlier blocks t of this panel
+      for (int t = 0; t < b; ++t) {
+        const int t0 = t * W;
+  #pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          if (pc[q] >= t0 && pc[q] < t0 + W) {
+  #pragma unroll
+            for (int v = 0; v < W; v += VE) vstore(&Raw[pc[q] - t0][v], &a[q][v]);
+          }
+        }
+        __syncthreads();
+        T (*U)[W] = Ub[t & 1];
+        if (tid < W * W) {
+          const int i = tid / W, jj = tid % W;
+          T acc = Raw[i][jj];
+          for (int k = 0; k < i; ++k) acc += LinvB[t][i][k] * Raw[k][jj];
+          U[i][jj] = acc;
+        }
+        __syncthreads();
+        // pivot rows of block t take their U values; rows below block t (unmarked, or marked by a
+        // later block) take the rank-W update, each U row chunk read once for all of a thread's rows.
+        // A row's L entries are fetched one 32-byte sector (two 16-byte vectors) at a time.
+        constexpr int KC = 32 / sizeof(T) < W ? 32 / sizeof(T) : W;
+        bool upd[RPT];
+        const T* lr[RPT];
+  #pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+          const int r = tid + q * NT;
+          upd[q] = r < m0 && pc[q] >= t0 + W;
+          lr[q] = A + static_cast<size_t>(k0 + (r < m0 ? r : 0)) * n + k0 + t0;
+          if (r < m0 && pc[q] >= t0 && pc[q] < t0 + W) {
+            const int i = pc[q] - t0;
+  #pragma unroll
+            for (int v = 0; v < W; v += VE) vload(&U[i][v], &a[q][v]);
+          }
+        }
+        if (active) {
+  #pragma unroll
+          for (int kv = 0; kv < W; kv += KC) {
+            T l[RPT][KC];
+  #pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+  #pragma unroll
+              for (int c = 0; c < KC; c += VE) {
+                if (upd[q]) vload(lr[q] + kv + c, &l[q][c]);
+                else
+  #pragma unroll
+                  for (int u = 0; u < VE; ++u) l[q][c + u] = T(0);
+              }
+            }
+  #pragma unroll
+            for (int u = 0; u < KC; ++u) {
+  #pragma unroll
+              for (int v = 0; v < W; v += VE) {
+                T uu[VE];
+                vload(&U[kv + u][v], uu);
+  #pragma unroll
+                for (int q = 0; q < RPT; ++q)
+  #pragma unroll
+                  for (int e = 0; e < VE; ++e) a[q][v + e] -= l[q][u] * uu[e];
+              }
             }
           }
         }
@@ -842,6 +1147,18 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
       }
     }
     __syncthreads();
+    if constexpr (kTcLL) {
+      if (s0 + W < nb) {
+        // this block's pivot rows enter L11 for the later blocks: their entries in the panel's
+        // columns 0 .. s0+W (just stored), one 16-byte vector per thread and pass
+        const int nvec = (s0 + W) / VE;
+        for (int idx = tid; idx < W * nvec; idx += NT) {
+          const int i = idx / nvec, v = idx - i * nvec;
+          *reinterpret_cast<float4*>(L11s + static_cast<size_t>(s0 + i) * ldl + v * VE) =
+              *reinterpret_cast<const float4*>(A + static_cast<size_t>(k0 + pphys[s0 + i]) * n + k0 + v * VE);
+        }
+      }
+    }
     if (tid < W) {
       // column c of the inverse of the unit-lower part of Tb, in registers
       const int c = tid;
@@ -935,6 +1252,14 @@ __global__ void __launch_bounds__(NT, 1) lu_panel_lazy_kernel(T* __restrict__ fa
     }
     T* Y = uinv + (static_cast<size_t>(mat) * npan + pan) * nbmax * nbmax;
     for (int idx = tid; idx < nb * nb; idx += NT) Y[(idx / nb) * nbmax + idx % nb] = triX[(idx / nb) * ldl + idx % nb];
+  }
+  if constexpr (kTcLL) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+    }
   }
 }
 
@@ -1789,16 +2114,45 @@ static int panel_width(int n, int nb) {
 
 template <typename T, int W, int RPT>
 static void launch_lazy(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
-                        unsigned* status, float* li_hi, float* li_lo, cudaStream_t st) {
+                        unsigned* status, float* li_hi, float* li_lo, const CUtensorMap* map, cudaStream_t st) {
   constexpr int NT = 512;
+  constexpr bool kTc = std::is_same<T, float>::value && W == 16 && RPT == 4;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lu_panel_lazy_kernel<T, W, RPT, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    // static shared memory (18 KB; 35 KB with the tensor-core state) plus this cap within 227 KB
+    cudaFuncSetAttribute(lu_panel_lazy_kernel<T, W, RPT, NT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    if constexpr (kTc)
+      cudaFuncSetAttribute(lu_panel_lazy_kernel<T, W, RPT, NT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           190 * 1024);
     attr_set = true;
   }
   const size_t smem = panel_lazy_smem_bytes(n - k0, nb, nbmax, sizeof(T));
-  lu_panel_lazy_kernel<T, W, RPT, NT><<<nx, NT, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax, status,
-                                                           li_hi, li_lo);
+  CUtensorMap m{};
+  if constexpr (kTc) {
+    if (map) {
+      m = *map;
+      lu_panel_lazy_kernel<T, W, RPT, NT, true><<<nx, NT, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax,
+                                                                    status, li_hi, li_lo, m);
+      return;
+    }
+  }
+  lu_panel_lazy_kernel<T, W, RPT, NT, false><<<nx, NT, smem, st>>>(fac, piv, perm, linv, uinv, n, k0, nb, nbmax,
+                                                                 status, li_hi, li_lo, m);
+}
+
+// The tensor map of the per-point matrices for the panel's tensor-core left-looking update (cached
+// for the last (fac, nx, n)); NULL if it cannot be made.
+static const CUtensorMap* panel_matrix_map(float* fac, int nx, int n) {
+  static float* key_fac = nullptr;
+  static int key_nx = 0, key_n = 0;
+  static bool ok = false;
+  static CUtensorMap m;
+  if (fac != key_fac || nx != key_nx || n != key_n) {
+    ok = tc_matrix_map(&m, fac, nx, n);
+    key_fac = fac, key_nx = nx, key_n = n;
+  }
+  return ok ? &m : nullptr;
 }
 
 // Column-block width and rows per thread of the mark-pivoting panel kernel (512 threads) for a
@@ -1828,7 +2182,7 @@ bool lu_panel_fuses_uinv(int n, int nbmax, int w_pref) {
 template <typename T>
 void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int n, int k0, int nb, int nbmax,
                      unsigned* status, float* ws_hi, float* ws_lo, float* li_hi, float* li_lo, int w_pref,
-                     cudaStream_t st) {
+                     cudaStream_t st, bool tc_ll) {
   const bool trail = k0 + nb < n;
   float* wh = trail ? ws_hi : nullptr;
   float* lh = trail ? li_hi : nullptr;
@@ -1836,11 +2190,19 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int 
   lazy_shape<T>(n, n - k0, nb, nbmax, w_pref, W, rpt);
   constexpr int W2 = sizeof(T) == 4 ? 16 : 8, W4 = sizeof(T) == 4 ? 8 : 4;
   if (W == W2 && rpt == 4) {
-    launch_lazy<T, W2, 4>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, lh, li_lo, st);
+    // the tensor-core left-looking update needs a full 128-column panel (its tiles fit beside the
+    // diagonal block) and 16-byte aligned matrix rows
+    const CUtensorMap* map = nullptr;
+    if constexpr (sizeof(T) == 4) {
+      if (tc_ll && nb == 128 && nbmax == 128 && n % 4 == 0 &&
+          (static_cast<size_t>(nb) * (nb + 4) + lazy_tmp_elems(nb)) * sizeof(T) >= kTcllBytes)
+        map = panel_matrix_map(reinterpret_cast<float*>(fac), nx, n);
+    }
+    launch_lazy<T, W2, 4>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, lh, li_lo, map, st);
     return;
   }
   if (W == W4 && rpt == 8) {
-    launch_lazy<T, W4, 8>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, lh, li_lo, st);
+    launch_lazy<T, W4, 8>(fac, piv, perm, linv, uinv, nx, n, k0, nb, nbmax, status, lh, li_lo, nullptr, st);
     return;
   }
   const int Wf = panel_width<T>(n, nbmax);
@@ -1971,7 +2333,7 @@ void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const
 
 #define BTE_INST(T)                                                                                 \
   template void launch_lu_panel<T>(T*, int*, int*, T*, T*, int, int, int, int, int, unsigned*, float*,   \
-                                   float*, float*, float*, int, cudaStream_t);                      \
+                                   float*, float*, float*, int, cudaStream_t, bool);                      \
   template bool lu_panel_fuses_uinv<T>(int, int, int);                                              \
   template void launch_lu_uinv<T>(const T*, T*, int, int, int, cudaStream_t);                        \
   template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \

@@ -785,6 +785,11 @@ float* tc_ws_part(void* ws, int nx, int n, int part) {
   return f + 6 * big + 2 * small + (part - 8) * two;
 }
 
+bool tc_matrix_map(void* map, float* fac, int nx, int n) {
+  static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+  return CW == 32 && make_cmap(static_cast<CUtensorMap*>(map), fac, nx, n);
+}
+
 bool tc_available() {
   int dev = 0;
   cudaDeviceProp p;

@@ -307,6 +307,34 @@ def test_tensor_core_panel_pairs_match_single_panels(shape):
     assert rel_l2(F.cpu().numpy(), out[False, 0]) <= e_pair
 
 
+@pytest.mark.parametrize("shape", [(4, 64, 8), (3, 36, 20), (5, 32, 16)])
+def test_tensor_core_panel_left_looking(shape):
+    """BTE_FLAG_PANEL_TC: the left-looking updates inside each full 128-column panel as TF32x3
+    tcgen05 MMAs (nv = 512, 720 with a ragged last panel on the CUDA cores, 512 with 16 ordinates).
+    Unrefined, the factors match the CUDA-core panel's to FP32 accuracy; refined, the oracle's step."""
+    nx, nr, nt = shape
+    cfg = W.scaled(W.SMALL, nx=nx, nr=nr, ntheta=nt)
+    cfg["V0"] = 400.0
+    ops = O.Operators(cfg)
+    F0 = W.random_state(nx, nt, nr, seed=43)
+    t = 0.21 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t)
+    out = {}
+    for tc in (False, True):
+        for rmax in (0, -1):
+            # refined to a 1e-14 residual: these stiff cases (cond ~ 1e4, see the unrefined error) need it
+            # for a 1e-9 forward comparison
+            s = solver(cfg, "mixed", panel_tc=tc, refine_max=rmax, refine_tol=1e-14 if rmax else 0.0)
+            F = to_dev(F0)
+            s.step(F, t)
+            out[tc, rmax] = F.cpu().numpy()
+    e_simt, e_tc = rel_l2(out[False, 0], ref), rel_l2(out[True, 0], ref)
+    print("unrefined rel. error: CUDA-core panel %.3e tensor-core panel %.3e" % (e_simt, e_tc))
+    assert e_tc <= 4 * e_simt + 1e-9, (e_tc, e_simt)
+    assert rel_l2(out[True, -1], ref) <= 1e-9
+    assert rel_l2(out[True, -1], out[False, -1]) <= 1e-9
+
+
 # ------------------------------------------------------------------ entry points and errors
 
 def test_step_host_matches_device_step():
