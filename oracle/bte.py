@@ -409,9 +409,10 @@ class Operators:
         Minv = Rinv.T @ Rinv
         self.Cs = np.einsum("pq,lqk->lpk", Minv, self.C_raw)
         self.As = np.einsum("pr,qlrk->qlpk", Minv, self.A_raw)
-        # K_C = P_O C P_S, K_A = P_O A_v P_S in the ordinate layout v = a*Nr + k
-        self.KC = np.einsum("al,lpk,lb->apbk", self.T_O, self.Cs, self.T_S).reshape(self.nv, self.nv)
-        self.KA = np.einsum("aq,qlpk,lb->apbk", self.T_O, self.As, self.T_S).reshape(self.nv, self.nv)
+        # K_C = P_O C P_S, K_A = P_O A_v P_S in the ordinate layout v = a*Nr + k (contracted one
+        # factor at a time: the same sums, in another rounding order)
+        self.KC = np.einsum("al,lpk,lb->apbk", self.T_O, self.Cs, self.T_S, optimize=True).reshape(self.nv, self.nv)
+        self.KA = np.einsum("aq,qlpk,lb->apbk", self.T_O, self.As, self.T_S, optimize=True).reshape(self.nv, self.nv)
 
         # x-step: generalized symmetric eigenproblem G_v u = lambda M_v u, M_v^{-1} G_v = U Lam U^-1
         S = Rinv @ G @ Rinv.T
