@@ -115,14 +115,13 @@ def tangent(cfg, theta, steps, h_eV=1e-4):
             Fs = np.empty_like(G)
             rhs = np.empty_like(G)
             for i in range(ops.nx):
-                A = ops.v_matrix(E[i])
-                Fs[i] = np.linalg.solve(A, G[i].reshape(-1)).reshape(ops.nt, ops.nr)
+                Fs[i] = ops.v_solve(E[i], G[i].reshape(-1)).reshape(ops.nt, ops.nr)
                 if kind == "V0":
                     dKi = np.sin(2.0 * np.pi * base["freq_Hz"] * (t + 0.5 * ops.dt)) / ops.L * ops.KA
                 else:
                     dKi = dK
                 src = dG[i].reshape(-1) + ops.dt * (dKi @ Fs[i].reshape(-1))
-                rhs[i] = np.linalg.solve(A, src).reshape(ops.nt, ops.nr)
+                rhs[i] = ops.v_solve(E[i], src).reshape(ops.nt, ops.nr)
             F = ops.x_halfstep(Fs)
             dF = ops.x_halfstep(rhs)
             dJ += c @ ops.moments(dF)[0] / steps
