@@ -70,7 +70,8 @@ typedef enum {
                                    rounding order */
 #define BTE_FLAG_FULL_V 16u     /* with nl < ntheta, factor the full Nv x Nv matrix A_i per point. By
                                    default such a handle factors the reduced matrix I - dt B_i of order
-                                   nl * nr (B = C + E A_v in the harmonic basis, Section 3.3) and solves
+                                   nl * nr (B = C + E A_v in the harmonic basis, Section 3.3; both
+                                   multiplied by I (x) M_v, see bte_step) and solves
                                    through A^-1 f = f + P_O((I - dt B)^-1 - I) P_S f: the same solution,
                                    (nv / (nl nr))^3 fewer factorisation flops and (nv / (nl nr))^2 less
                                    factor memory. bte_step_adjoint needs the full factors. */
@@ -103,7 +104,10 @@ typedef struct {
                         backward error is at FP64 rounding level: max|r| <= min(256 eps, refine_tol)
                         (|A_i| max|x| + max|b|), |A_i| bounded by the infinity norms of dt K_C, dt K_A
                         (<= 0: default 1e-13 FP64, 1e-12 mixed) */
-  int refine_max;    /* maximum refinement sweeps per step (< 0: default: 0 FP64, 4 mixed). BTE_MIXED
+  int refine_max;    /* maximum refinement sweeps per step (< 0: default: 2 FP64, 4 mixed). The dense
+                        paths factor (I (x) M_v) A_i, not A_i itself; their first FP64 solve is
+                        accurate to about cond(M_v) eps, one FP64 sweep restores the backward error
+                        of a direct FP64 solve. BTE_MIXED
                         with nr <= 64: points still short of the test after refine_max sweeps through
                         the FP32 factors (cond(A_i) eps_32 near 1 or above: strong fields) are solved
                         again by the FP64 block-tridiagonal solve and refined through it, two more
@@ -182,7 +186,12 @@ bte_status bte_init_maxwellian(bte_handle* h, double* F_dev, const double* ne_de
 
 /* One semi-implicit step t -> t + dt of F_dev (device, in/out), eqs. "bte_semi_implicit".
  * The field of the velocity step is E_dev[nx] (device, V/m) if non-NULL, else the uniform
- * E = (V0/L) sin(2 pi freq (t + dt/2)). On BTE_ESINGULAR/ENOCONV/ENONFINITE F is left unchanged.
+ * E = (V0/L) sin(2 pi freq (t + dt/2)). The velocity step solves A_i x = b at every point
+ * (eq. "vspace_batched_system"); the dense paths factor (I (x) M_v) A_i = I (x) M_v -
+ * dt (P_O C P_S + E_i P_O A_v P_S), the same system before the mass scaling of Section 3.4 (LU with
+ * partial pivoting on the scaled A_i meets element growth of order 1e15 on speed grids of a few
+ * hundred B-splines), and refine against A_i itself in FP64 (Algorithm 2).
+ * On BTE_ESINGULAR/ENOCONV/ENONFINITE F is left unchanged.
  * Enqueues on the handle's stream; the status check reads back 4 bytes and synchronises it. */
 bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_s, double V0,
                     double freq_Hz);
@@ -205,8 +214,11 @@ bte_status bte_moments(bte_handle* h, const double* F_dev, double* ne_dev, doubl
  * which = 0 x[nx], 1 D_x[nx][nx], 2 mu[ntheta], 3 K_C[nv][nv], 4 K_A[nv][nv], 5 lambda[nr],
  * 6 U[nr][nr], 7 U^-1[nr][nr], 8 Q[ntheta][nr][nx][nx] (inflow column zeroed), 9 M_v[nr][nr],
  * 10 density moment vector [nv], 11 energy moment vector [nv], 12 rate vectors [n_proc][nv],
- * 13 Clenshaw-Curtis weights of the collocation points on [0, L] [nx].
- * Returns BTE_EINVAL if count does not match, BTE_ESTATE if the operator is not assembled yet. */
+ * 13 Clenshaw-Curtis weights of the collocation points on [0, L] [nx], 14 P_O C P_S[nv][nv] and
+ * 15 P_O A_v P_S[nv][nv] (before the mass scaling: (I (x) M_v) K_C and (I (x) M_v) K_A, the operators
+ * of the matrices the dense Nv x Nv path factors; formed only for handles on that path).
+ * Returns BTE_EINVAL if count does not match, BTE_ESTATE if the operator is not assembled yet
+ * (or, for 14 and 15, not formed for this handle). */
 bte_status bte_get_operator(const bte_handle* h, int which, double* host_out, size_t count);
 
 bte_status bte_get_info(const bte_handle* h, bte_info* info);

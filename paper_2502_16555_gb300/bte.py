@@ -34,7 +34,7 @@ FLAG_PANEL_TC = 128
 KINDS = {"elastic": 0, "excitation": 1, "ionization": 2}
 FORMS = {"const": 0, "linear": 1, "log": 2, "table": 3, "nu": 4}
 OPERATORS = {"x": 0, "Dx": 1, "mu": 2, "KC": 3, "KA": 4, "lambda": 5, "U": 6, "Uinv": 7, "Q": 8,
-             "M": 9, "mom_n": 10, "mom_e": 11, "mom_r": 12, "ccw": 13}
+             "M": 9, "mom_n": 10, "mom_e": 11, "mom_r": 12, "ccw": 13, "KCg": 14, "KAg": 15}
 EXPORTS = ("bte_create", "bte_set_cross_sections", "bte_init_maxwellian", "bte_step", "bte_run",
            "bte_step_host", "bte_moments", "bte_get_operator", "bte_get_info", "bte_profile",
            "bte_destroy", "bte_last_error", "bte_init_maxwellian_static", "bte_batch_create",
@@ -321,7 +321,8 @@ class Solver:
         sizes = {"x": (self.nx,), "Dx": (self.nx, self.nx), "mu": (self.nt,), "KC": (self.nv, self.nv),
                  "KA": (self.nv, self.nv), "lambda": (self.nr,), "U": (self.nr, self.nr),
                  "Uinv": (self.nr, self.nr), "Q": (self.nt, self.nr, self.nx, self.nx), "M": (self.nr, self.nr),
-                 "mom_n": (self.nv,), "mom_e": (self.nv,), "mom_r": (self.n_proc, self.nv), "ccw": (self.nx,)}
+                 "mom_n": (self.nv,), "mom_e": (self.nv,), "mom_r": (self.n_proc, self.nv), "ccw": (self.nx,),
+                 "KCg": (self.nv, self.nv), "KAg": (self.nv, self.nv)}
         out = np.empty(sizes[name], dtype=np.float64)
         self._check(self.lib.bte_get_operator(self.h, OPERATORS[name], out.ctypes.data_as(C.POINTER(C.c_double)),
                                               out.size))

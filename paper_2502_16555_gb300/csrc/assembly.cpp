@@ -429,6 +429,19 @@ std::string assemble_x(const bte_config& cfg, HostOps& o) {
       }
   });
 
+  // band of M (B-splines of degree 3 overlap only within 3 indices; entries outside stay 0)
+  o.mw = 0;
+  for (int p = 0; p < nr; ++p)
+    for (int k = 0; k < nr; ++k)
+      if (o.M[p * nr + k] != 0.0) o.mw = std::max(o.mw, std::abs(p - k));
+  {
+    const int bw = 2 * o.mw + 1;
+    o.Mband.assign(static_cast<size_t>(nr) * bw, 0.0);
+    for (int p = 0; p < nr; ++p)
+      for (int k = std::max(0, p - o.mw); k <= std::min(nr - 1, p + o.mw); ++k)
+        o.Mband[static_cast<size_t>(p) * bw + k - p + o.mw] = o.M[p * nr + k];
+  }
+
   // generalized symmetric eigenproblem G u = lambda M u via M = R R^T:
   // R^-1 G R^-T = Z diag(lam) Z^T, U = R^-T Z, U^-1 = Z^T R^T.
   std::vector<double> R = o.M;
@@ -563,7 +576,7 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       for (int k = std::max(i, j); k < nr; ++k) s += Ri[k * nr + i] * Ri[k * nr + j];
       Minv[i * nr + j] = s;
     }
-  auto mscale = [&](const std::vector<double>& A, double* out) {
+  auto mscale = [&](const double* A, double* out) {
     for (int i = 0; i < nr; ++i)
       for (int j = 0; j < nr; ++j) {
         double s = 0;
@@ -572,65 +585,81 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       }
   };
 
-  // collision blocks C_l = loss (+ gain + C_T for l = 0), scaled
+  // collision blocks C_l = loss (+ gain + C_T for l = 0), as assembled (Cg) and scaled (Cs)
   o.Cs.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
+  o.Cg.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   {
     std::vector<double> C0(nr * nr);
     for (int i = 0; i < nr * nr; ++i) C0[i] = loss[i] + gain[i] + cT[i];
-    mscale(C0, o.Cs.data());
-    for (int l = 1; l < nl; ++l) mscale(loss, o.Cs.data() + static_cast<size_t>(l) * nr * nr);
+    std::copy(C0.begin(), C0.end(), o.Cg.begin());
+    mscale(C0.data(), o.Cs.data());
+    for (int l = 1; l < nl; ++l) {
+      std::copy(loss.begin(), loss.end(), o.Cg.begin() + static_cast<size_t>(l) * nr * nr);
+      mscale(loss.data(), o.Cs.data() + static_cast<size_t>(l) * nr * nr);
+    }
   }
   // field blocks: (q, q-1): (e/m_e) a_q (Dv - (q-1) M1); (q, q+1): (e/m_e) a_{q+1} (Dv + (q+2) M1),
   // a_l = l / sqrt(4 l^2 - 1)
   o.As_lo.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   o.As_up.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
+  o.Ag_lo.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
+  o.Ag_up.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   {
-    std::vector<double> blk(nr * nr);
     const double em = kE / kMe;
     for (int q = 0; q < nl; ++q) {
       if (q >= 1) {
         const double aq = q / std::sqrt(4.0 * q * q - 1.0);
+        double* blk = o.Ag_lo.data() + static_cast<size_t>(q) * nr * nr;
         for (int i = 0; i < nr * nr; ++i) blk[i] = em * aq * (o.Dv[i] - (q - 1) * o.M1[i]);
         mscale(blk, o.As_lo.data() + static_cast<size_t>(q) * nr * nr);
       }
       if (q + 1 < nl) {
         const double aq = (q + 1) / std::sqrt(4.0 * (q + 1) * (q + 1) - 1.0);
+        double* blk = o.Ag_up.data() + static_cast<size_t>(q) * nr * nr;
         for (int i = 0; i < nr * nr; ++i) blk[i] = em * aq * (o.Dv[i] + (q + 2) * o.M1[i]);
         mscale(blk, o.As_up.data() + static_cast<size_t>(q) * nr * nr);
       }
     }
   }
 
-  // K_C[(a,p),(b,k)] = sum_l T_O[a][l] Cs_l[p][k] T_S[l][b];  K_A likewise over (q, l = q -+ 1)
-  o.KC.assign(static_cast<size_t>(nv) * nv, 0.0);
-  o.KA.assign(static_cast<size_t>(nv) * nv, 0.0);
+  // K_C[(a,p),(b,k)] = sum_l T_O[a][l] Cs_l[p][k] T_S[l][b];  K_A likewise over (q, l = q -+ 1).
+  // With want_kg the same sums over the blocks before the mass scaling give KCg, KAg.
+  auto project = [&](const std::vector<double>& C, const std::vector<double>& Alo, const std::vector<double>& Aup,
+                     std::vector<double>& KC, std::vector<double>& KA) {
+    KC.assign(static_cast<size_t>(nv) * nv, 0.0);
+    KA.assign(static_cast<size_t>(nv) * nv, 0.0);
 #pragma omp parallel for schedule(static)
-  for (int a = 0; a < nt; ++a)
-    for (int b = 0; b < nt; ++b) {
-      for (int l = 0; l < nl; ++l) {
-        const double cab = o.TO[a * nl + l] * o.TS[l * nt + b];
-        const double* C = o.Cs.data() + static_cast<size_t>(l) * nr * nr;
-        for (int p = 0; p < nr; ++p)
-          for (int k = 0; k < nr; ++k)
-            o.KC[static_cast<size_t>(a * nr + p) * nv + b * nr + k] += cab * C[p * nr + k];
-      }
-      for (int q = 0; q < nl; ++q) {
-        if (q >= 1) {
-          const double cab = o.TO[a * nl + q] * o.TS[(q - 1) * nt + b];
-          const double* A = o.As_lo.data() + static_cast<size_t>(q) * nr * nr;
+    for (int a = 0; a < nt; ++a)
+      for (int b = 0; b < nt; ++b) {
+        for (int l = 0; l < nl; ++l) {
+          const double cab = o.TO[a * nl + l] * o.TS[l * nt + b];
+          const double* Cl = C.data() + static_cast<size_t>(l) * nr * nr;
           for (int p = 0; p < nr; ++p)
-            for (int k = 0; k < nr; ++k)
-              o.KA[static_cast<size_t>(a * nr + p) * nv + b * nr + k] += cab * A[p * nr + k];
+            for (int k = 0; k < nr; ++k) KC[static_cast<size_t>(a * nr + p) * nv + b * nr + k] += cab * Cl[p * nr + k];
         }
-        if (q + 1 < nl) {
-          const double cab = o.TO[a * nl + q] * o.TS[(q + 1) * nt + b];
-          const double* A = o.As_up.data() + static_cast<size_t>(q) * nr * nr;
-          for (int p = 0; p < nr; ++p)
-            for (int k = 0; k < nr; ++k)
-              o.KA[static_cast<size_t>(a * nr + p) * nv + b * nr + k] += cab * A[p * nr + k];
+        for (int q = 0; q < nl; ++q) {
+          if (q >= 1) {
+            const double cab = o.TO[a * nl + q] * o.TS[(q - 1) * nt + b];
+            const double* A = Alo.data() + static_cast<size_t>(q) * nr * nr;
+            for (int p = 0; p < nr; ++p)
+              for (int k = 0; k < nr; ++k) KA[static_cast<size_t>(a * nr + p) * nv + b * nr + k] += cab * A[p * nr + k];
+          }
+          if (q + 1 < nl) {
+            const double cab = o.TO[a * nl + q] * o.TS[(q + 1) * nt + b];
+            const double* A = Aup.data() + static_cast<size_t>(q) * nr * nr;
+            for (int p = 0; p < nr; ++p)
+              for (int k = 0; k < nr; ++k) KA[static_cast<size_t>(a * nr + p) * nv + b * nr + k] += cab * A[p * nr + k];
+          }
         }
       }
-    }
+  };
+  project(o.Cs, o.As_lo, o.As_up, o.KC, o.KA);
+  if (o.want_kg) {
+    project(o.Cg, o.Ag_lo, o.Ag_up, o.KCg, o.KAg);
+  } else {
+    o.KCg.clear();
+    o.KAg.clear();
+  }
 
   // infinity norms of K_C and K_A (the refinement's backward-error test bounds |A_i| by them)
   o.kc_inf = 0.0;

@@ -3,7 +3,9 @@
 // (arXiv 2502.16555, Section 3.4) is linear in F: F^{n+1} = S_n F^n with S_n = X V_n X, X the x half
 // step (Algorithm 1) and V_n the per-point solves with A_i = I - dt (K_C + E_i K_A). Its transpose is
 // S_n^T = X^T V_n^T X^T: X^T applies U^T, the transposed Q_ij blocks and U^-T in place of U^-1, Q_ij
-// and U; V_n^T solves with A_i^T through the same LU factors. A parameter theta enters only through
+// and U; V_n^T solves with A_i^T through the same LU factors. The factors are those of
+// (I (x) M_v) A_i, so A_i^-1 g = LU^-1 (I (x) M_v) g and A_i^-T g = (I (x) M_v) LU^-T g (M_v is
+// symmetric). A parameter theta enters only through
 // A_i, and d(A^-1 G)/dtheta = -A^-1 (dA/dtheta) F*, so a step contributes
 //     dJ/dtheta += mu^T (dt dK/dtheta) F*,   mu = A^-T X^T lambda^{n+1},  F* = A^-1 X F^n,
 // per point; the library accumulates SC = sum mu F*^T (and SA with the weight dE/dV0) and contracts
@@ -128,7 +130,8 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
   bte::launch_x_to_eigen(F_dev, h->Uinv, h->Y, nx, nt, nr, h->status, st);
   bte::launch_x_apply_q(h->Q, h->Y, h->Y2, nx, nt, nr, st);
   bte::launch_x_from_eigen(h->Y2, h->U, h->Fa, nx, nt, nr, nullptr, st);
-  bte::launch_v_form<double>(h->KC, h->KA, nullptr, Eu, o.dt, fac, nx, nv, st);
+  const bte::MassBand mass{h->Mband, nr, o.mw};
+  bte::launch_v_form<double>(h->KCg, h->KAg, mass, nullptr, Eu, o.dt, fac, nx, nv, st);
   nl += 4;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = std::min(nb, n - k0);
@@ -142,12 +145,12 @@ bte_status bte_step_adjoint(bte_handle* h, const double* F_dev, double* lambda_d
       nl += 2;
     }
   }
-  bte::launch_lu_solve<double>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st);
+  bte::launch_lu_solve<double>(fac, h->piv, h->Fa, h->Fb, nx, n, nb, nullptr, 0, st, mass);
   // nu = X^T lambda (R), mu = A^-T nu (Fw), sensitivities, lambda <- X^T mu + w g
   bte::launch_x_to_eigen(lambda_dev, h->Ut, h->Y, nx, nt, nr, h->status, st);
   bte::launch_x_apply_q(h->Qt, h->Y, h->Y2, nx, nt, nr, st);
   bte::launch_x_from_eigen(h->Y2, h->Uinvt, h->R, nx, nt, nr, nullptr, st);
-  bte::launch_lu_solve_t(fac, h->piv, h->R, h->Fw, nx, n, nb, st);
+  bte::launch_lu_solve_t(fac, h->piv, h->R, h->Fw, nx, n, nb, st, mass);
   nl += 5;
   if (SC_dev || SA_dev) {
     dim3 grid((nv + 31) / 32, (nv + 31) / 32);

@@ -118,11 +118,14 @@ bte_status device_status(bte_handle* h) {
 }
 
 // out_i (+)= A_i^-1 in_i through the factors of the last factoring call (dense paths), at the
-// points with conv[i] == 0 (conv NULL: every point). With the reduced system (nl < ntheta) the
-// factors are those of G_i = I - dt B_i and A_i^-1 f = f + P_O (G_i^-1 - I) P_S f (Section 3.3).
+// points with conv[i] == 0 (conv NULL: every point). The factors are those of (I (x) M_v) A_i, so
+// every solve multiplies its right-hand side by I (x) M_v first. With the reduced system
+// (nl < ntheta) they are those of (I (x) M_v) G_i, G_i = I - dt B_i, and
+// A_i^-1 f = f + P_O (G_i^-1 - I) P_S f (Section 3.3).
 bte_status enqueue_lu_solve(bte_handle* h, const double* in, double* out, const int* conv, int accumulate) {
   const HostOps& o = h->ops;
   const int nx = o.nx, n = h->nlu, nb = h->nb;
+  const bte::MassBand mass{h->Mband, o.nr, o.mw};
   cudaStream_t st = h->st;
   const double* src = in;
   double* dst = out;
@@ -135,27 +138,31 @@ bte_status enqueue_lu_solve(bte_handle* h, const double* in, double* out, const 
   }
   if (h->precision == BTE_FP64)
     BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve<double>(static_cast<double*>(h->fac), h->piv, src, dst, nx, n, nb,
-                                                            conv, acc, st));
+                                                            conv, acc, st, mass));
   else
     BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_lu_solve_blocked<float>(static_cast<float*>(h->fac), h->perm,
                                                                    static_cast<float*>(h->linv),
                                                                    static_cast<float*>(h->uinv), src, dst, nx, n, nb,
-                                                                   conv, acc, st));
+                                                                   conv, acc, st, mass));
   if (h->reduced)
     BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_reduce_lift(in, h->yred, h->zred, h->TO, out, conv, accumulate, nx, o.nt,
                                                        o.nr, o.nl, st));
   return BTE_OK;
 }
 
-// The per-point matrices the dense paths factor: A_i = I - dt (K_C + E_i K_A), or G_i = I - dt B_i
-// (order nl * nr) for the reduced system.
+// The per-point matrices the dense paths factor: (I (x) M_v) A_i = I (x) M_v - dt (P_O C P_S +
+// E_i P_O A_v P_S), or (I (x) M_v) G_i (order nl * nr) for the reduced system. Multiplying by the
+// block-diagonal mass matrix leaves the solution unchanged; LU with partial pivoting on the
+// mass-scaled A_i meets element growth of order 1e15 on speed grids of a few hundred B-splines at
+// fields where dt e E / (m_e dv) is near 0.8, on this form it stays of order 1.
 template <typename T>
 void form_v(bte_handle* h, const double* E_dev, double Eu, T* fac) {
   const HostOps& o = h->ops;
+  const bte::MassBand mass{h->Mband, o.nr, o.mw};
   if (h->reduced)
-    bte::launch_v_form_reduced<T>(h->Cs, h->Alo, h->Aup, E_dev, Eu, o.dt, fac, o.nx, o.nr, o.nl, h->st);
+    bte::launch_v_form_reduced<T>(h->Cg, h->Aglo, h->Agup, mass, E_dev, Eu, o.dt, fac, o.nx, o.nr, o.nl, h->st);
   else
-    bte::launch_v_form<T>(h->KC, h->KA, E_dev, Eu, o.dt, fac, o.nx, o.nv, h->st);
+    bte::launch_v_form<T>(h->KCg, h->KAg, mass, E_dev, Eu, o.dt, fac, o.nx, o.nv, h->st);
 }
 
 // Velocity step (eq. "bte_semi_implicit_vspace" / "vspace_batched_system"): out_i = A_i^-1 in_i at
@@ -491,8 +498,10 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
     }
   }
   h->tol = cfg->refine_tol > 0 ? cfg->refine_tol : (cfg->precision == BTE_FP64 ? 1e-13 : 1e-12);
-  h->refine_max = cfg->refine_max >= 0 ? cfg->refine_max : (cfg->precision == BTE_FP64 ? 0 : 4);
+  h->refine_max = cfg->refine_max >= 0 ? cfg->refine_max : (cfg->precision == BTE_FP64 ? 2 : 4);
   std::string e = bte::assemble_x(*cfg, h->ops);
+  // handles that factor the Nv x Nv form keep its unscaled operators
+  h->ops.want_kg = !h->reduced && !h->structured;
   if (!e.empty()) {
     delete h;
     return fail(nullptr, BTE_EINVAL, e);
@@ -501,14 +510,19 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
     const HostOps& o = h->ops;
     const size_t D = static_cast<size_t>(o.nx) * o.nv;
     const size_t nn = static_cast<size_t>(h->nlu) * h->nlu;
-    // the dense K_C, K_A (nv x nv) serve only the full-matrix form and the adjoint
+    // the dense P_O C P_S, P_O A_v P_S (nv x nv) serve only the full-matrix form and the adjoint,
+    // the unscaled harmonic blocks only the reduced form; both forms multiply by the band of M
     const bool dense_k = !h->reduced && !h->structured;
+    const size_t blk = static_cast<size_t>(o.nl) * o.nr * o.nr;
     bte_status s;
     auto chk = [&](bte_status r) { s = r; return r == BTE_OK; };
     bool ok = chk(dalloc(h, &h->U, o.U.size())) && chk(dalloc(h, &h->Uinv, o.Uinv.size())) &&
               chk(dalloc(h, &h->Q, o.Q.size())) &&
-              (!dense_k || (chk(dalloc(h, &h->KC, static_cast<size_t>(o.nv) * o.nv)) &&
-                            chk(dalloc(h, &h->KA, static_cast<size_t>(o.nv) * o.nv)))) &&
+              (!dense_k || (chk(dalloc(h, &h->KCg, static_cast<size_t>(o.nv) * o.nv)) &&
+                            chk(dalloc(h, &h->KAg, static_cast<size_t>(o.nv) * o.nv)))) &&
+              (!h->reduced || (chk(dalloc(h, &h->Cg, blk)) && chk(dalloc(h, &h->Aglo, blk)) &&
+                               chk(dalloc(h, &h->Agup, blk)))) &&
+              (h->structured || chk(dalloc(h, &h->Mband, o.Mband.size()))) &&
               chk(dalloc(h, &h->Cs, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Alo, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Aup, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
@@ -569,7 +583,8 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
       if (ce != cudaSuccess) ok = false, s = cuda_fail(h, ce, "cudaMallocHost");
     }
     if (ok) ok = chk(upload(h, h->U, o.U)) && chk(upload(h, h->Uinv, o.Uinv)) && chk(upload(h, h->Q, o.Q)) &&
-                 chk(upload(h, h->TO, o.TO)) && chk(upload(h, h->TS, o.TS));
+                 chk(upload(h, h->TO, o.TO)) && chk(upload(h, h->TS, o.TS)) &&
+                 (!h->Mband || chk(upload(h, h->Mband, o.Mband)));
     if (ok) {
       cudaError_t ce = cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st);
       if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->st);
@@ -625,7 +640,9 @@ bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* 
     BTE_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->mom_r), sizeof(double) * o.mom_r.size()));
   }
   bte_status s;
-  if ((h->KC && (s = upload(h, h->KC, o.KC)) != BTE_OK) || (h->KA && (s = upload(h, h->KA, o.KA)) != BTE_OK) ||
+  if ((h->KCg && (s = upload(h, h->KCg, o.KCg)) != BTE_OK) || (h->KAg && (s = upload(h, h->KAg, o.KAg)) != BTE_OK) ||
+      (h->Cg && (s = upload(h, h->Cg, o.Cg)) != BTE_OK) || (h->Aglo && (s = upload(h, h->Aglo, o.Ag_lo)) != BTE_OK) ||
+      (h->Agup && (s = upload(h, h->Agup, o.Ag_up)) != BTE_OK) ||
       (s = upload(h, h->Cs, o.Cs)) != BTE_OK || (s = upload(h, h->Alo, o.As_lo)) != BTE_OK ||
       (s = upload(h, h->Aup, o.As_up)) != BTE_OK || (s = upload(h, h->mom_n, o.mom_n)) != BTE_OK ||
       (s = upload(h, h->mom_e, o.mom_e)) != BTE_OK || (o.n_proc > 0 && (s = upload(h, h->mom_r, o.mom_r)) != BTE_OK))
@@ -715,11 +732,15 @@ bte_status bte_get_operator(const bte_handle* hc, int which, double* out, size_t
     case 11: v = &o.mom_e; break;
     case 12: v = &o.mom_r; break;
     case 13: v = &o.ccw; break;
+    case 14: v = &o.KCg; break;
+    case 15: v = &o.KAg; break;
     default: return fail(h, BTE_EINVAL, "unknown operator id");
   }
-  const bool needs_v = which == 3 || which == 4 || (which >= 10 && which <= 12);
+  const bool needs_v = which == 3 || which == 4 || (which >= 10 && which <= 12) || which >= 14;
   if (needs_v && !o.have_v)
     return fail(h, BTE_ESTATE, "velocity operators not assembled yet");
+  if (which >= 14 && v->empty())
+    return fail(h, BTE_ESTATE, "this handle does not factor the Nv x Nv form (reduced or structured)");
   if (v->size() != count) return fail(h, BTE_EINVAL, "count does not match the operator size");
   std::memcpy(out, v->data(), count * sizeof(double));
   return BTE_OK;

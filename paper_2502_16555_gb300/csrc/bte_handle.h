@@ -38,8 +38,11 @@ struct bte_handle {
 
   // x-step operators
   double *U = nullptr, *Uinv = nullptr, *Q = nullptr;
-  // velocity operators
-  double *KC = nullptr, *KA = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
+  // velocity operators: KCg, KAg = P_O C P_S, P_O A_v P_S (Nv x Nv, before the mass scaling; the
+  // dense form only), Cs, Alo, Aup the mass-scaled harmonic blocks (residual, structured solve),
+  // Cg, Aglo, Agup the same blocks before the mass scaling (reduced form only), Mband the band of M
+  double *KCg = nullptr, *KAg = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
+  double *Cg = nullptr, *Aglo = nullptr, *Agup = nullptr, *Mband = nullptr;
   double *TO = nullptr, *TS = nullptr;
   double *mom_n = nullptr, *mom_e = nullptr, *mom_r = nullptr;
   // work

@@ -35,6 +35,8 @@ struct HostOps {
   std::vector<double> mu, wmu;          // nt Gauss-Legendre nodes (ascending) and weights
   std::vector<double> knots;            // nr + 4
   std::vector<double> M, G, Dv, M1;     // nr*nr radial Galerkin matrices
+  int mw = 0;                           // half bandwidth of M (M[p][k] = 0 for |p - k| > mw)
+  std::vector<double> Mband;            // nr x (2 mw + 1): Mband[p][k - p + mw] = M[p][k]
   std::vector<double> lam, U, Uinv;     // M^-1 G = U diag(lam) U^-1
   std::vector<double> Q;                // [nt][nr][nx][nx] inverse x half-step operators
   std::vector<double> TO, TS;           // T_O [nt][nl], T_S [nl][nt]
@@ -43,8 +45,12 @@ struct HostOps {
   int n_proc = 0;
   std::vector<double> Cs;               // [nl][nr][nr]  M^-1 C (l-block diagonal)
   std::vector<double> As_lo, As_up;     // [nl][nr][nr]  M^-1 A_v blocks (q, q-1) and (q, q+1)
-  std::vector<double> KC, KA;           // [nv][nv]  P_O C P_S, P_O A_v P_S
+  std::vector<double> Cg;               // [nl][nr][nr]  C before the mass scaling
+  std::vector<double> Ag_lo, Ag_up;     // [nl][nr][nr]  A_v blocks before the mass scaling
+  std::vector<double> KC, KA;           // [nv][nv]  P_O M^-1 C P_S, P_O M^-1 A_v P_S
   double kc_inf = 0.0, ka_inf = 0.0;    // their infinity norms (largest absolute row sums)
+  bool want_kg = false;                 // also form KCg, KAg (handles that factor the Nv x Nv form)
+  std::vector<double> KCg, KAg;         // [nv][nv]  P_O C P_S, P_O A_v P_S (no mass scaling)
   std::vector<double> mom_n, mom_e;     // [nv]
   std::vector<double> mom_r;            // [n_proc][nv]
 };

@@ -15,6 +15,15 @@ enum StatusBits : unsigned {
   kNonFiniteIn = 16u,  // NaN/Inf in an input: the state handed in, or the field array
 };
 
+// The block-diagonal Galerkin mass matrix I (x) M_v acting on one point's vector, in blocks of nr
+// (one block per ordinate, or per harmonic in the reduced form). M_v is banded with half width w and
+// stored as m[p * (2 w + 1) + k - p + w] = M_v[p][k]. m == nullptr stands for the identity.
+struct MassBand {
+  const double* m = nullptr;
+  int nr = 0;
+  int w = 0;
+};
+
 // tensor-core (tcgen05) trailing updates of the FP32 LU; workspace of tc_workspace_bytes(), parts
 // 0-1 L21 split, 2-3 (P A12)^T split, 4-5 one panel's inv(L11) split, 6-7 U12^T split, 8-9 a
 // two-panel block's inv(L11) split (layout in bte_tc.cu)
@@ -54,10 +63,12 @@ void launch_x_from_eigen(const double* Y2, const double* U, double* F, int nx, i
 // ---- velocity step
 // kNonFiniteIn in status if any of the nx field values E[i] is NaN or infinite
 void launch_check_field(const double* E, int nx, unsigned* status, cudaStream_t st);
-// A_i = I - dt (K_C + E_i K_A) in storage type T (float or double), row-major per point
+// The per-point matrix the dense path factors, (I (x) M_v) A_i = I (x) M_v - dt (KCg + E_i KAg)
+// with KCg = P_O C P_S and KAg = P_O A_v P_S (no mass scaling), in storage type T (float or
+// double), row-major per point. Its solves multiply the right-hand side by I (x) M_v first.
 template <typename T>
-void launch_v_form(const double* KC, const double* KA, const double* E, double E_uniform, double dt,
-                   T* fac, int nx, int nv, cudaStream_t st);
+void launch_v_form(const double* KCg, const double* KAg, MassBand mass, const double* E, double E_uniform,
+                   double dt, T* fac, int nx, int nv, cudaStream_t st);
 // ints per point of the panel permutation record written by lu_panel
 int perm_record_ints(int nbmax);
 // ws_hi/ws_lo (may be NULL): K-major TF32 head/remainder copies of L21 (panel) and of U12^T
@@ -95,10 +106,12 @@ void launch_lu_pair_linv(const float* fac, const int* perm, const float* linv, i
 // inv(U11) of every panel of every point, once the factorisation is complete ([point][panel]).
 template <typename T>
 void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_t st);
-// x = A^-1 b (x += when accumulate) through the per-panel block inverses; T is the arithmetic type.
+// x = A^-1 (I (x) M_v) b (x += when accumulate; plain A^-1 b when mass.m is NULL) through the
+// per-panel block inverses; T is the arithmetic type.
 template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
-                             double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st);
+                             double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st,
+                             MassBand mass = {});
 // ---- structure-exploiting velocity solve (block tridiagonal in l): Fout = A_i^-1 Fin per point
 // (Fout += when accumulate); T is the arithmetic of the block elimination; Xscratch holds
 // nx * nl * nr * nr values of T.
@@ -110,30 +123,34 @@ void launch_vsolve_struct(const double* Fin, double* Fout, const double* E, doub
                           unsigned* status, cudaStream_t st);
 
 // The reduced dense system of the same identity when N_l < N_theta (m = N_l Nr): G_i = I - dt B_i
-// formed densely as G[nx][m][m] (T the storage of the factorisation), y = P_S f and
-// out (+)= f + P_O (z - y) around the solve z = G_i^-1 y; Yr, Zr hold nx * m doubles; points with
-// conv[i] != 0 are skipped (conv may be NULL).
+// (B_i = M^-1 (C + E_i A_v) in the harmonic basis) is factored in its unscaled form
+// (I (x) M_v) G_i = I (x) M_v - dt (C + E_i A_v), formed densely as G[nx][m][m] from the blocks before
+// the mass scaling (T the storage of the factorisation); y = P_S f and out (+)= f + P_O (z - y)
+// around the solve z = G_i^-1 y (the solve multiplies y by I (x) M_v); Yr, Zr hold nx * m doubles;
+// points with conv[i] != 0 are skipped (conv may be NULL).
 template <typename T>
-void launch_v_form_reduced(const double* Cs, const double* Alo, const double* Aup, const double* E, double E_uniform,
-                           double dt, T* G, int nx, int nr, int nl, cudaStream_t st);
+void launch_v_form_reduced(const double* Cg, const double* Aglo, const double* Agup, MassBand mass, const double* E,
+                           double E_uniform, double dt, T* G, int nx, int nr, int nl, cudaStream_t st);
 void launch_reduce_project(const double* F, const double* TS, double* Yr, const int* conv, int nx, int nt, int nr,
                            int nl, cudaStream_t st);
 void launch_reduce_lift(const double* F, const double* Yr, const double* Zr, const double* TO, double* out,
                         const int* conv, int accumulate, int nx, int nt, int nr, int nl, cudaStream_t st);
 
-// y = A^-T b with the FP64 factors and pivots of the FP64 path (the adjoint of lu_solve).
+// y = (I (x) M_v) A^-T b with the FP64 factors and pivots of the FP64 path (the adjoint of lu_solve;
+// plain A^-T b when mass.m is NULL).
 void launch_lu_solve_t(const double* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
-                       cudaStream_t st);
+                       cudaStream_t st, MassBand mass = {});
 template <typename T>
 void launch_lu_swap_trsm(T* fac, const int* perm, const T* linv, int nx, int n, int k0, int nb,
                          int nbmax, float* ws_hi, float* ws_lo, cudaStream_t st);
 template <typename T>
 void launch_lu_gemm_simt(T* fac, int nx, int n, int k0, int nb, cudaStream_t st);
-// x = A^-1 b (pivots applied lazily, panel by panel); `conv` (may be NULL) skips converged points.
-// For T = float the arithmetic is FP32 and the result is ADDED to x when `accumulate` is set.
+// x = A^-1 (I (x) M_v) b (pivots applied lazily, panel by panel; plain A^-1 b when mass.m is NULL);
+// `conv` (may be NULL) skips converged points. For T = float the arithmetic is FP32; the result is
+// ADDED to x when `accumulate` is set.
 template <typename T>
 void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
-                     const int* conv, int accumulate, cudaStream_t st);
+                     const int* conv, int accumulate, cudaStream_t st, MassBand mass = {});
 
 // FP64 residual r = b - (x - dt P_O (C + E_i A_v) P_S x) through the structured operators
 // (Algorithm 2), per-point ratio max|r|/max|b|; marks conv[i] = 1 when ratio <= tol.

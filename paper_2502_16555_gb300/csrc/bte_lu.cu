@@ -1783,14 +1783,27 @@ __global__ void __launch_bounds__(256) lu_gemm_simt_kernel(T* __restrict__ fac, 
   }
 }
 
+// ((I (x) M_v) v)[r] for one point's vector v (global or shared memory): the banded row p = r mod nr
+// of M_v against the block of v that holds r.
+template <typename V>
+__device__ __forceinline__ double mass_row(const MassBand& mb, const V* v, int r) {
+  const int p = r % mb.nr, base = r - p;
+  const int k0 = max(0, p - mb.w), k1 = min(mb.nr - 1, p + mb.w);
+  const double* row = mb.m + static_cast<size_t>(p) * (2 * mb.w + 1) + mb.w - p;
+  double acc = 0.0;
+  for (int k = k0; k <= k1; ++k) acc = fma(__ldg(row + k), static_cast<double>(v[base + k]), acc);
+  return acc;
+}
+
 // x = A^-1 b for one point per CTA, with the lazily applied pivots; Tc is the arithmetic type.
+// With mass.m the right-hand side is (I (x) M_v) b.
 // Column chunks of 32: the 32 x 32 diagonal block is staged in shared memory and solved by one
 // warp, then every thread updates whole rows below (forward) or above (backward) the chunk.
 template <typename T, typename Tc>
 __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fac, const int* __restrict__ piv,
                                                         const double* __restrict__ b, double* __restrict__ x,
                                                         int n, int nb, const int* __restrict__ conv,
-                                                        int accumulate) {
+                                                        int accumulate, MassBand mass) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Tc* s = reinterpret_cast<Tc*>(smraw);
   __shared__ Tc dblk[32][33];
@@ -1799,7 +1812,8 @@ __global__ void __launch_bounds__(1024) lu_solve_kernel(const T* __restrict__ fa
   const T* A = fac + static_cast<size_t>(mat) * n * n;
   const int* ip = piv + static_cast<size_t>(mat) * n;
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int r = tid; r < n; r += bd) s[r] = static_cast<Tc>(b[static_cast<size_t>(mat) * n + r]);
+  const double* bp = b + static_cast<size_t>(mat) * n;
+  for (int r = tid; r < n; r += bd) s[r] = static_cast<Tc>(mass.m ? mass_row(mass, bp, r) : bp[r]);
   __syncthreads();
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int kb = min(nb, n - k0);
@@ -1897,7 +1911,7 @@ __device__ void colblock_dots(const double* A, int n, int j0, int cw, int r0, in
 
 __global__ void __launch_bounds__(1024) lu_solve_t_kernel(const double* __restrict__ fac, const int* __restrict__ piv,
                                                           const double* __restrict__ b, double* __restrict__ x,
-                                                          int n, int nb) {
+                                                          int n, int nb, MassBand mass) {
   extern __shared__ __align__(16) unsigned char smraw[];
   double* s = reinterpret_cast<double*>(smraw);
   __shared__ double red[32][33];
@@ -1968,7 +1982,7 @@ __global__ void __launch_bounds__(1024) lu_solve_t_kernel(const double* __restri
       }
     __syncthreads();
   }
-  for (int r = tid; r < n; r += bd) x[static_cast<size_t>(mat) * n + r] = s[r];
+  for (int r = tid; r < n; r += bd) x[static_cast<size_t>(mat) * n + r] = mass.m ? mass_row(mass, s, r) : s[r];
 }
 
 
@@ -2045,7 +2059,8 @@ __device__ __forceinline__ void rows_dot(const T* __restrict__ M, size_t ld, int
   rows_dot_any(M, ld, r0, r1, kb, v, warp, nwarp, lane, out);
 }
 
-// x = A^-1 b (or x += A^-1 b) for one point per CTA with the per-panel block inverses: forward,
+// x = A^-1 c (or x += A^-1 c), c = b or (I (x) M_v) b, for one point per CTA with the per-panel
+// block inverses: forward,
 // per panel p: permute the right-hand side with the panel's row record, y = inv(L11_p) b_p, then
 // b[below] -= L21_p y; backward, per panel from the last: y = inv(U11_p) b_p, b[above] -= U_p y.
 // Every product is a batch of row dot products (rows_dot): the stored inverses are zero outside
@@ -2055,7 +2070,7 @@ __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restr
                                                                 const T* __restrict__ linv, const T* __restrict__ uinv,
                                                                 const double* __restrict__ b, double* __restrict__ x,
                                                                 int n, int nb, const int* __restrict__ conv,
-                                                                int accumulate) {
+                                                                int accumulate, MassBand mass) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* s = reinterpret_cast<T*>(smraw);   // n (rounded up to 4)
   T* y = s + ((n + 3) & ~3);             // nb
@@ -2065,7 +2080,8 @@ __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restr
   const T* A = fac + static_cast<size_t>(mat) * n * n;
   const int npan = (n + nb - 1) / nb;
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = bd >> 5;
-  for (int r = tid; r < n; r += bd) s[r] = static_cast<T>(b[static_cast<size_t>(mat) * n + r]);
+  const double* bp = b + static_cast<size_t>(mat) * n;
+  for (int r = tid; r < n; r += bd) s[r] = static_cast<T>(mass.m ? mass_row(mass, bp, r) : bp[r]);
   __syncthreads();
   auto set_y = [&](int r, T v) { y[r] = v; };
   auto sub_s = [&](int r, T v) { s[r] -= v; };
@@ -2102,6 +2118,9 @@ __global__ void __launch_bounds__(1024) lu_solve_blocked_kernel(const T* __restr
 }
 
 }  // namespace
+
+// dynamic shared memory cap of lu_panel_kernel
+constexpr int kPanelDynSmemMax = 226 * 1024;
 
 // sub-panel width: largest power of two <= 32 whose shared-memory plan fits the budget
 template <typename T>
@@ -2209,7 +2228,10 @@ void launch_lu_panel(T* fac, int* piv, int* perm, T* linv, T* uinv, int nx, int 
   const size_t smem = panel_smem_bytes<T>(n - k0, nb, nbmax, Wf);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    // 226 KB: with the kernel's static shared memory (a few hundred bytes) within the 227 KB a CTA
+    // may opt in to. The narrowest plan (W = 2) of the largest accepted order, nv = 7936 in FP64,
+    // takes 225,336 bytes.
+    cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelDynSmemMax);
     attr_set = true;
   }
   lu_panel_kernel<T><<<nx, 1024, smem, st>>>(fac, piv, perm, linv, n, k0, nb, nbmax, Wf, status, wh, ws_lo, lh, li_lo);
@@ -2283,7 +2305,7 @@ void launch_lu_gemm_simt(T* fac, int nx, int n, int k0, int nb, cudaStream_t st)
 
 template <typename T>
 void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
-                     const int* conv, int accumulate, cudaStream_t st) {
+                     const int* conv, int accumulate, cudaStream_t st, MassBand mass) {
   using Tc = T;
   const size_t smem = static_cast<size_t>(n) * sizeof(Tc);
   static bool attr_set = false;
@@ -2291,7 +2313,7 @@ void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, i
     cudaFuncSetAttribute(lu_solve_kernel<T, Tc>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     attr_set = true;
   }
-  lu_solve_kernel<T, Tc><<<nx, 1024, smem, st>>>(fac, piv, b, x, n, nb, conv, accumulate);
+  lu_solve_kernel<T, Tc><<<nx, 1024, smem, st>>>(fac, piv, b, x, n, nb, conv, accumulate, mass);
 }
 
 int perm_record_ints(int nbmax) { return perm_stride(nbmax); }
@@ -2309,26 +2331,27 @@ void launch_lu_uinv(const T* fac, T* uinv, int nx, int n, int nbmax, cudaStream_
 }
 
 void launch_lu_solve_t(const double* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
-                       cudaStream_t st) {
+                       cudaStream_t st, MassBand mass) {
   const size_t smem = sizeof(double) * n;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_solve_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  lu_solve_t_kernel<<<nx, 1024, smem, st>>>(fac, piv, b, x, n, nb);
+  lu_solve_t_kernel<<<nx, 1024, smem, st>>>(fac, piv, b, x, n, nb, mass);
 }
 
 template <typename T>
 void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const T* uinv, const double* b,
-                             double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st) {
+                             double* x, int nx, int n, int nb, const int* conv, int accumulate, cudaStream_t st,
+                             MassBand mass) {
   const size_t smem = (static_cast<size_t>((n + 3) & ~3) + 3 * nb) * sizeof(T);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(lu_solve_blocked_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     attr_set = true;
   }
-  lu_solve_blocked_kernel<T><<<nx, 1024, smem, st>>>(fac, perm, linv, uinv, b, x, n, nb, conv, accumulate);
+  lu_solve_blocked_kernel<T><<<nx, 1024, smem, st>>>(fac, perm, linv, uinv, b, x, n, nb, conv, accumulate, mass);
 }
 
 #define BTE_INST(T)                                                                                 \
@@ -2337,12 +2360,13 @@ void launch_lu_solve_blocked(const T* fac, const int* perm, const T* linv, const
   template bool lu_panel_fuses_uinv<T>(int, int, int);                                              \
   template void launch_lu_uinv<T>(const T*, T*, int, int, int, cudaStream_t);                        \
   template void launch_lu_solve_blocked<T>(const T*, const int*, const T*, const T*, const double*,  \
-                                           double*, int, int, int, const int*, int, cudaStream_t);  \
+                                           double*, int, int, int, const int*, int, cudaStream_t,   \
+                                           MassBand);                                               \
   template void launch_lu_swap_trsm<T>(T*, const int*, const T*, int, int, int, int, int, float*, float*, \
                                        cudaStream_t);                                               \
   template void launch_lu_gemm_simt<T>(T*, int, int, int, int, cudaStream_t);                       \
   template void launch_lu_solve<T>(const T*, const int*, const double*, double*, int, int, int,     \
-                                   const int*, int, cudaStream_t);
+                                   const int*, int, cudaStream_t, MassBand);
 BTE_INST(double)
 BTE_INST(float)
 #undef BTE_INST

@@ -227,14 +227,15 @@ __global__ void __launch_bounds__(kST) vsolve_struct_kernel(const double* __rest
 }
 
 // ---- the reduced dense system (N_l < N_theta): the same identity with I - dt B_i factored as a
-// dense m x m matrix, m = N_l Nr, by the LU kernels of the full system. Row and column (l, k) of
-// B_i sit at l Nr + k: block (l, l) = Cs_l, block (l, l - 1) = E_i As_lo[l], block (l, l + 1) =
-// E_i As_up[l], zero elsewhere.
+// dense m x m matrix, m = N_l Nr, by the LU kernels of the full system, in its unscaled form
+// (I (x) M_v)(I - dt B_i) (LU with partial pivoting on the mass-scaled form meets large element
+// growth on fine speed grids). Row and column (l, k) sit at l Nr + k: block (l, l) = M_v - dt Cg_l,
+// block (l, l - 1) = -dt E_i Aglo[l], block (l, l + 1) = -dt E_i Agup[l], zero elsewhere.
 
-// G_i = I - dt B_i, one CTA per row (point i, row (l, p)); columns in blocks of Nr.
+// (I (x) M_v) G_i, one CTA per row (point i, row (l, p)); columns in blocks of Nr.
 template <typename T>
-__global__ void v_form_reduced_kernel(const double* __restrict__ Cs, const double* __restrict__ Alo,
-                                      const double* __restrict__ Aup, const double* __restrict__ E,
+__global__ void v_form_reduced_kernel(const double* __restrict__ Cg, const double* __restrict__ Aglo,
+                                      const double* __restrict__ Agup, MassBand mass, const double* __restrict__ E,
                                       double E_uniform, double dt, T* __restrict__ G, int nr, int nl) {
   const int m = nl * nr;
   const size_t rowg = blockIdx.x;  // i * m + row
@@ -243,12 +244,15 @@ __global__ void v_form_reduced_kernel(const double* __restrict__ Cs, const doubl
   const double Ei = E ? E[i] : E_uniform;
   const size_t off = (static_cast<size_t>(l) * nr + p) * nr;
   T* out = G + rowg * m;
+  const int bw = 2 * mass.w + 1;
   for (int lc = 0; lc < nl; ++lc) {
-    const double* src = lc == l ? Cs : lc == l - 1 ? Alo : lc == l + 1 ? Aup : nullptr;
+    const double* src = lc == l ? Cg : lc == l - 1 ? Aglo : lc == l + 1 ? Agup : nullptr;
     const double w = lc == l ? 1.0 : Ei;
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
       const double b = src ? w * __ldg(src + off + k) : 0.0;
-      out[lc * nr + k] = static_cast<T>((lc == l && k == p ? 1.0 : 0.0) - dt * b);
+      const int dk = k - p;
+      const double d = lc == l && dk >= -mass.w && dk <= mass.w ? __ldg(mass.m + p * bw + dk + mass.w) : 0.0;
+      out[lc * nr + k] = static_cast<T>(d - dt * b);
     }
   }
 }
@@ -292,15 +296,15 @@ __global__ void reduce_lift_kernel(const double* __restrict__ F, const double* _
 }  // namespace
 
 template <typename T>
-void launch_v_form_reduced(const double* Cs, const double* Alo, const double* Aup, const double* E, double E_uniform,
-                           double dt, T* G, int nx, int nr, int nl, cudaStream_t st) {
+void launch_v_form_reduced(const double* Cg, const double* Aglo, const double* Agup, MassBand mass, const double* E,
+                           double E_uniform, double dt, T* G, int nx, int nr, int nl, cudaStream_t st) {
   const unsigned rows = static_cast<unsigned>(nx) * nl * nr;
-  v_form_reduced_kernel<T><<<rows, nr >= 128 ? 128 : 64, 0, st>>>(Cs, Alo, Aup, E, E_uniform, dt, G, nr, nl);
+  v_form_reduced_kernel<T><<<rows, nr >= 128 ? 128 : 64, 0, st>>>(Cg, Aglo, Agup, mass, E, E_uniform, dt, G, nr, nl);
 }
-template void launch_v_form_reduced<float>(const double*, const double*, const double*, const double*, double, double,
-                                           float*, int, int, int, cudaStream_t);
-template void launch_v_form_reduced<double>(const double*, const double*, const double*, const double*, double,
-                                            double, double*, int, int, int, cudaStream_t);
+template void launch_v_form_reduced<float>(const double*, const double*, const double*, MassBand, const double*,
+                                           double, double, float*, int, int, int, cudaStream_t);
+template void launch_v_form_reduced<double>(const double*, const double*, const double*, MassBand, const double*,
+                                            double, double, double*, int, int, int, cudaStream_t);
 
 void launch_reduce_project(const double* F, const double* TS, double* Yr, const int* conv, int nx, int nt, int nr,
                            int nl, cudaStream_t st) {

@@ -139,14 +139,18 @@ __global__ void x_from_eigen_kernel(const double* __restrict__ Y2, const double*
 }
 
 template <typename T>
-__global__ void v_form_kernel(const double* __restrict__ KC, const double* __restrict__ KA,
+__global__ void v_form_kernel(const double* __restrict__ KCg, const double* __restrict__ KAg, MassBand mass,
                               const double* __restrict__ E, double E_uniform, double dt,
                               T* __restrict__ fac, int nx, int nv) {
   const size_t nn = static_cast<size_t>(nv) * nv;
+  const int nr = mass.nr, bw = 2 * mass.w + 1;
   for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < nn;
        e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const double kc = KC[e], ka = KA[e];
-    const double d = (e / nv == e % nv) ? 1.0 : 0.0;
+    const double kc = KCg[e], ka = KAg[e];
+    // (I (x) M_v)[(a,p),(b,k)] = M_v[p][k] when a == b and |p - k| <= w
+    const int row = static_cast<int>(e / nv), col = static_cast<int>(e % nv);
+    const int p = row % nr, k = col % nr, dk = k - p;
+    const double d = (row - p == col - k && dk >= -mass.w && dk <= mass.w) ? __ldg(mass.m + p * bw + dk + mass.w) : 0.0;
     for (int i = 0; i < nx; ++i) {
       const double Ei = E ? E[i] : E_uniform;
       fac[static_cast<size_t>(i) * nn + e] = static_cast<T>(d - dt * (kc + Ei * ka));
@@ -352,14 +356,14 @@ void launch_check_field(const double* E, int nx, unsigned* status, cudaStream_t 
 }
 
 template <typename T>
-void launch_v_form(const double* KC, const double* KA, const double* E, double E_uniform, double dt,
-                   T* fac, int nx, int nv, cudaStream_t st) {
+void launch_v_form(const double* KCg, const double* KAg, MassBand mass, const double* E, double E_uniform,
+                   double dt, T* fac, int nx, int nv, cudaStream_t st) {
   const size_t nn = static_cast<size_t>(nv) * nv;
-  v_form_kernel<T><<<grid_for(nn, 256), 256, 0, st>>>(KC, KA, E, E_uniform, dt, fac, nx, nv);
+  v_form_kernel<T><<<grid_for(nn, 256), 256, 0, st>>>(KCg, KAg, mass, E, E_uniform, dt, fac, nx, nv);
 }
-template void launch_v_form<double>(const double*, const double*, const double*, double, double,
+template void launch_v_form<double>(const double*, const double*, MassBand, const double*, double, double,
                                     double*, int, int, cudaStream_t);
-template void launch_v_form<float>(const double*, const double*, const double*, double, double,
+template void launch_v_form<float>(const double*, const double*, MassBand, const double*, double, double,
                                    float*, int, int, cudaStream_t);
 
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,

@@ -153,10 +153,12 @@ def test_strong_field_parity(e0, path):
     print("strong field %s e0=%.1e: status %s, cond %.2e, forward %.3e, backward max %.3e"
           % (path, e0, bte.STATUS_NAMES[status], kappa, fwd, max(bwd)))
     assert status == bte.OK
-    # backward errors: pivoted FP64 LU at rounding level; the structured FP64 solve (block
-    # elimination without pivoting) and the mixed paths (refinement to a 1e-12 relative residual,
-    # FP64 structured solves for points whose FP32 refinement stalls) within 1e-11
-    assert max(bwd) <= (1e-14 if path == "fp64" else 1e-11), bwd
+    # backward errors: the dense FP64 path refines through its factors of (I (x) M_v) A_i until
+    # the normwise backward error is at 256 eps (measured up to 2.6e-14 here), within 1e-13; the
+    # structured FP64 solve (block elimination without pivoting) and the mixed paths (refinement to
+    # a 1e-12 relative residual, FP64 structured solves for points whose FP32 refinement stalls)
+    # within 1e-11
+    assert max(bwd) <= (1e-13 if path == "fp64" else 1e-11), bwd
     # forward error within what the conditioning allows (two exact-arithmetic-equivalent FP64
     # solves differ by up to ~cond * 1e-16 here)
     assert fwd <= max(1e-9, 1e-14 * kappa), (fwd, kappa)
@@ -245,6 +247,46 @@ def test_largest_workload_one_step_sampled_points():
     assert rel_l2(Fm, F.cpu().numpy()) <= 1e-9
 
 
+# ------------------------------------------------------------------ the grid limits of bte_create
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_largest_velocity_grid(precision):
+    """nv = nr * ntheta = 7936, the largest bte_create accepts (nr = 124, ntheta = 64): the panels
+    taller than 4096 rows take the general panel kernel, the others the mark-pivoting one; the mixed
+    path runs its trailing updates on the tensor cores. One step against the oracle."""
+    cfg = W.scaled(W.SMALL, nx=3, nr=124, ntheta=64)
+    ops = O.Operators(cfg)
+    F0 = W.random_state(ops.nx, ops.nt, ops.nr, seed=45)
+    t = 0.23 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t)
+    s = solver(cfg, precision)
+    F = to_dev(F0)
+    s.step(F, t)
+    err = rel_l2(F.cpu().numpy(), ref)
+    assert err <= (1e-10 if precision == "fp64" else 1e-9), err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("E", [235.0, 1.0e4])
+def test_most_bsplines(precision, E):
+    """nr = 880, the largest bte_create accepts (the eigen-basis transforms stage nr x 33 doubles per
+    CTA, at the shared-memory limit). At E = 235 V/m, dt e E / (m_e dv) is near 0.8 on this grid: LU
+    with partial pivoting on the mass-scaled A_i meets element growth of order 1e61 there (no correct
+    digit); the library factors (I (x) M_v) A_i instead. 1e4 V/m is a strong field on the same grid
+    (four correction sweeps with FP32 factors). One step against the oracle."""
+    import torch
+    cfg = W.scaled(W.SMALL, nx=3, nr=880, ntheta=2)
+    ops = O.Operators(cfg)
+    F0 = W.random_state(ops.nx, ops.nt, ops.nr, seed=46)
+    t = 0.23 / W.RF_FREQ_HZ
+    ref = ops.step(F0, t, E=np.full(ops.nx, E))
+    s = solver(cfg, precision)
+    F = to_dev(F0)
+    s.step(F, t, E=torch.full((ops.nx,), E, dtype=torch.float64, device="cuda"))
+    err = rel_l2(F.cpu().numpy(), ref)
+    assert err <= 1e-10, err
+
+
 # ------------------------------------------------------------------ tensor-core trailing update
 
 @pytest.mark.parametrize("shape", [(4, 32, 8), (6, 24, 16), (5, 40, 13)])
@@ -292,9 +334,9 @@ def test_tensor_core_panel_pairs_match_single_panels(shape):
             out[single, rmax] = F.cpu().numpy()
     e_pair, e_single = rel_l2(out[False, 0], ref), rel_l2(out[True, 0], ref)
     print("unrefined rel. error: pairs %.3e single panels %.3e" % (e_pair, e_single))
-    # the FP32 factors' own accuracy on these inputs (measured on GB300: 1.1e-4, 3.1e-3, 1.6e-4 for
+    # the FP32 factors' own accuracy on these inputs (measured on GB300: 2.6e-4, 2.0e-2, 6.9e-4 for
     # single panels), with a factor 4 of headroom: a regression of the factors by 10x fails here
-    bound = {(5, 40, 13): 4.5e-4, (4, 64, 12): 1.25e-2, (3, 36, 20): 6.5e-4}[shape]
+    bound = {(5, 40, 13): 1.05e-3, (4, 64, 12): 8.0e-2, (3, 36, 20): 2.8e-3}[shape]
     assert e_single <= bound, (e_single, bound)
     assert e_pair <= 4 * e_single + 1e-9, (e_pair, e_single)
     assert rel_l2(out[False, 0], out[True, 0]) <= 4 * e_single + 1e-9

@@ -81,6 +81,25 @@ def test_host_assembly_matches_oracle(name, cfg):
     assert rel(out, ops.x_halfstep(F)) < 1e-12
 
 
+@pytest.mark.parametrize("cfg", [W.scaled(W.SMALL, nx=5, nr=12, ntheta=6),
+                                 W.scaled(W.SMALL, nx=5, nr=9, ntheta=5)])
+def test_unscaled_operators_of_the_factored_form(cfg):
+    """The dense path factors (I (x) M_v) A_i = I (x) M_v - dt (KCg + E KAg): KCg and KAg must equal
+    the oracle's mass-scaled K_C, K_A multiplied by I (x) M_v, and a handle that factors the reduced
+    system does not form them."""
+    from paper_2502_16555_gb300 import bte
+    s = _solver(cfg)
+    ops = O.Operators(cfg)
+    Mh = np.kron(np.eye(ops.nt), ops.M)
+    for name, K in (("KCg", ops.KC), ("KAg", ops.KA)):
+        want = Mh @ K
+        assert np.max(np.abs(s.operator(name) - want)) <= 1e-11 * np.max(np.abs(want)), name
+    red = _solver(dict(cfg, nl=2))
+    with pytest.raises(bte.BteError) as e:
+        red.operator("KCg")
+    assert e.value.status == bte.ESTATE
+
+
 def test_create_rejects_bad_configs(lib):
     from paper_2502_16555_gb300 import bte
     bad = [dict(nx=2), dict(nr=3), dict(ntheta=1), dict(nl=9, ntheta=8), dict(dt_s=0.0), dict(p_Torr=-1.0),
