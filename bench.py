@@ -206,7 +206,8 @@ def algorithmic(cfg, precision, kernel, tc, pair=True):
                    panels' two diagonal-block inverses, esz * (n^2 + n * nb) (n = the order factored);
       x_apply_q    the FP64 Q stream (8 B Nv Nx^2) plus Y in/out, per half step;
       v_form       write of the per-point matrices plus the K_C/K_A read;
-      residual     FP64 flops of the structured residual (Algorithm 2) per point evaluation.
+      residual     FP64 flops of the structured residual (Algorithm 2) per point evaluation,
+                   banded products and the banded Cholesky substitutions of M_v.
     The refinement kernels skip converged points, so those two count point-solves and point
     evaluations (the library's exact count of residual evaluations per point and step)."""
     nx, nr, nt = cfg["nx"], cfg["nr"], cfg["ntheta"]
@@ -240,7 +241,13 @@ def algorithmic(cfg, precision, kernel, tc, pair=True):
     if kernel == "v_form":
         return float(esz) * nx * nv * nv + 16.0 * nv * nv, "byte", "hbm"
     if kernel == "residual":
-        return 2.0 * (2 * nl * nt * nr + 3 * nl * nr * nr), "flop/point", "alu"
+        # P_S and P_O projections, C_0 dense, the loss band of C_l (l >= 1), the field blocks as
+        # banded combinations of Dv and M1 (two neighbours), the two banded Cholesky substitutions
+        # of M_v (half bandwidth w = 3 for cubic B-splines)
+        w = 3
+        fma = (2 * nl * nt * nr + nr * nr + (nl - 1) * nr * (2 * w + 1) + 2 * (nl - 1) * nr * (2 * w + 1)
+               + 2 * nl * nr * w)
+        return 2.0 * fma, "flop/point", "alu"
     return None, None, None
 
 

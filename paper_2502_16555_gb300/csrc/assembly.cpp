@@ -576,6 +576,30 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       for (int k = std::max(i, j); k < nr; ++k) s += Ri[k * nr + i] * Ri[k * nr + j];
       Minv[i * nr + j] = s;
     }
+  // the refinement residual's banded operators (bands of the loss part of C, of Dv and of M1, and
+  // of the Cholesky factor of M); B-spline products of degree 3 couple only indices within mw
+  {
+    const int w = o.mw, bw = 2 * w + 1;
+    o.rband.assign(static_cast<size_t>(3) * nr * bw, 0.0);
+    o.rchol.assign(static_cast<size_t>(nr) * (w + 1), 0.0);
+    o.rcinv.assign(nr, 0.0);
+    const std::vector<double>* src[3] = {&loss, &o.Dv, &o.M1};
+    for (int m = 0; m < 3; ++m)
+      for (int p = 0; p < nr; ++p)
+        for (int k = 0; k < nr; ++k) {
+          const double v = (*src[m])[p * nr + k];
+          if (v == 0.0) continue;
+          if (std::abs(p - k) > w) return "a radial operator is wider than the band of M_v";
+          o.rband[(static_cast<size_t>(m) * nr + p) * bw + k - p + w] = v;
+        }
+    for (int p = 0; p < nr; ++p) {
+      for (int j = 0; j <= w; ++j) {
+        const int k = p - w + j;
+        if (k >= 0) o.rchol[static_cast<size_t>(p) * (w + 1) + j] = R[p * nr + k];
+      }
+      o.rcinv[p] = 1.0 / R[p * nr + p];
+    }
+  }
   auto mscale = [&](const double* A, double* out) {
     for (int i = 0; i < nr; ++i)
       for (int j = 0; j < nr; ++j) {
@@ -604,19 +628,24 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
   o.As_up.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   o.Ag_lo.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   o.Ag_up.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
+  o.fcoef.assign(static_cast<size_t>(4) * nl, 0.0);
   {
     const double em = kE / kMe;
     for (int q = 0; q < nl; ++q) {
       if (q >= 1) {
         const double aq = q / std::sqrt(4.0 * q * q - 1.0);
+        const double cd = em * aq, cm = -em * aq * (q - 1);
+        o.fcoef[4 * q + 0] = cd, o.fcoef[4 * q + 1] = cm;
         double* blk = o.Ag_lo.data() + static_cast<size_t>(q) * nr * nr;
-        for (int i = 0; i < nr * nr; ++i) blk[i] = em * aq * (o.Dv[i] - (q - 1) * o.M1[i]);
+        for (int i = 0; i < nr * nr; ++i) blk[i] = cd * o.Dv[i] + cm * o.M1[i];
         mscale(blk, o.As_lo.data() + static_cast<size_t>(q) * nr * nr);
       }
       if (q + 1 < nl) {
         const double aq = (q + 1) / std::sqrt(4.0 * (q + 1) * (q + 1) - 1.0);
+        const double cd = em * aq, cm = em * aq * (q + 2);
+        o.fcoef[4 * q + 2] = cd, o.fcoef[4 * q + 3] = cm;
         double* blk = o.Ag_up.data() + static_cast<size_t>(q) * nr * nr;
-        for (int i = 0; i < nr * nr; ++i) blk[i] = em * aq * (o.Dv[i] + (q + 2) * o.M1[i]);
+        for (int i = 0; i < nr * nr; ++i) blk[i] = cd * o.Dv[i] + cm * o.M1[i];
         mscale(blk, o.As_up.data() + static_cast<size_t>(q) * nr * nr);
       }
     }
@@ -721,6 +750,7 @@ std::string assemble_kc_only(const HostOps& o, const std::vector<Process>& procs
   t.nx = o.nx, t.nr = o.nr, t.nt = o.nt, t.nl = o.nl, t.nv = o.nv;
   t.L = o.L, t.vmax = o.vmax, t.n0 = o.n0, t.T0 = o.T0, t.m0 = o.m0, t.dt = o.dt;
   t.mu = o.mu, t.wmu = o.wmu, t.knots = o.knots, t.M = o.M, t.G = o.G, t.Dv = o.Dv, t.M1 = o.M1;
+  t.mw = o.mw, t.Mband = o.Mband;
   t.TO = o.TO, t.TS = o.TS;
   std::string e = assemble_v(t, procs);
   if (e.empty()) KC.swap(t.KC);

@@ -59,6 +59,13 @@ bte_status upload(bte_handle* h, T* dst, const std::vector<T>& src) {
   return BTE_OK;
 }
 
+// the first n elements of a host array (n > 0)
+template <typename T>
+bte_status upload_n(bte_handle* h, T* dst, const T* src, size_t n) {
+  BTE_CUDA(h, cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, h->st));
+  return BTE_OK;
+}
+
 cudaEvent_t next_event(bte_handle* h) {
   if (h->pool_used == h->pool.size()) {
     cudaEvent_t e;
@@ -307,11 +314,13 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   }
   // FP64 iterative refinement: residual through Algorithm 2, correction through the factors
   if (h->refine_max > 0) {
+    bte::ResidualOps ro;
+    ro.c0 = h->rc0, ro.band = h->rband, ro.fcoef = h->rfcoef, ro.chol = h->rchol, ro.cinv = h->rcinv, ro.w = o.mw;
     BTE_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(int) * nx, st));
     for (int s = 0; s <= h->refine_max; ++s) {
-      BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
-                                                      h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, o.kc_inf, o.ka_inf, nx,
-                                                      nt, nr, nl, h->status, st));
+      BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, ro, h->TO, h->TS, h->R, h->ratio,
+                                                      h->conv, h->tol, o.kc_inf, o.ka_inf, nx, nt, nr, nl, h->status,
+                                                      st));
       if (s == h->refine_max) break;
       if (h->structured && h->precision == BTE_FP64)
         BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->R, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
@@ -332,9 +341,9 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
                                                                    h->TO, h->TS, h->xs64, nx, nt, nr, nl, h->conv, 0,
                                                                    nullptr, st));
       for (int s = 0; s < kEscalationSweeps; ++s) {
-        BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, h->Cs, h->Alo, h->Aup,
-                                                        h->TO, h->TS, h->R, h->ratio, h->conv, h->tol, o.kc_inf, o.ka_inf, nx,
-                                                        nt, nr, nl, h->status, st));
+        BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, ro, h->TO, h->TS, h->R,
+                                                        h->ratio, h->conv, h->tol, o.kc_inf, o.ka_inf, nx, nt, nr, nl,
+                                                        h->status, st));
         if (s + 1 == kEscalationSweeps) break;
         BTE_LAUNCH(BTE_K_LU_SOLVE, bte::launch_vsolve_struct<double>(h->R, h->Fb, E_dev, Eu, o.dt, h->Cs, h->Alo,
                                                                      h->Aup, h->TO, h->TS, h->xs64, nx, nt, nr, nl,
@@ -523,6 +532,10 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
               (!h->reduced || (chk(dalloc(h, &h->Cg, blk)) && chk(dalloc(h, &h->Aglo, blk)) &&
                                chk(dalloc(h, &h->Agup, blk)))) &&
               (h->structured || chk(dalloc(h, &h->Mband, o.Mband.size()))) &&
+              chk(dalloc(h, &h->rc0, static_cast<size_t>(o.nr) * o.nr)) &&
+              chk(dalloc(h, &h->rband, static_cast<size_t>(3) * o.nr * (2 * o.mw + 1))) &&
+              chk(dalloc(h, &h->rfcoef, static_cast<size_t>(4) * o.nl)) &&
+              chk(dalloc(h, &h->rchol, static_cast<size_t>(o.nr) * (o.mw + 1))) && chk(dalloc(h, &h->rcinv, o.nr)) &&
               chk(dalloc(h, &h->Cs, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Alo, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Aup, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
@@ -643,6 +656,9 @@ bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* 
   if ((h->KCg && (s = upload(h, h->KCg, o.KCg)) != BTE_OK) || (h->KAg && (s = upload(h, h->KAg, o.KAg)) != BTE_OK) ||
       (h->Cg && (s = upload(h, h->Cg, o.Cg)) != BTE_OK) || (h->Aglo && (s = upload(h, h->Aglo, o.Ag_lo)) != BTE_OK) ||
       (h->Agup && (s = upload(h, h->Agup, o.Ag_up)) != BTE_OK) ||
+      (s = upload_n(h, h->rc0, o.Cg.data(), static_cast<size_t>(o.nr) * o.nr)) != BTE_OK ||
+      (s = upload(h, h->rband, o.rband)) != BTE_OK || (s = upload(h, h->rfcoef, o.fcoef)) != BTE_OK ||
+      (s = upload(h, h->rchol, o.rchol)) != BTE_OK || (s = upload(h, h->rcinv, o.rcinv)) != BTE_OK ||
       (s = upload(h, h->Cs, o.Cs)) != BTE_OK || (s = upload(h, h->Alo, o.As_lo)) != BTE_OK ||
       (s = upload(h, h->Aup, o.As_up)) != BTE_OK || (s = upload(h, h->mom_n, o.mom_n)) != BTE_OK ||
       (s = upload(h, h->mom_e, o.mom_e)) != BTE_OK || (o.n_proc > 0 && (s = upload(h, h->mom_r, o.mom_r)) != BTE_OK))

@@ -43,6 +43,8 @@ struct bte_handle {
   // Cg, Aglo, Agup the same blocks before the mass scaling (reduced form only), Mband the band of M
   double *KCg = nullptr, *KAg = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
   double *Cg = nullptr, *Aglo = nullptr, *Agup = nullptr, *Mband = nullptr;
+  // the refinement residual's banded operators (bte::ResidualOps)
+  double *rc0 = nullptr, *rband = nullptr, *rfcoef = nullptr, *rchol = nullptr, *rcinv = nullptr;
   double *TO = nullptr, *TS = nullptr;
   double *mom_n = nullptr, *mom_e = nullptr, *mom_r = nullptr;
   // work

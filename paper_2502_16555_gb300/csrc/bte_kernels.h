@@ -152,12 +152,27 @@ template <typename T>
 void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, int nx, int n, int nb,
                      const int* conv, int accumulate, cudaStream_t st, MassBand mass = {});
 
-// FP64 residual r = b - (x - dt P_O (C + E_i A_v) P_S x) through the structured operators
-// (Algorithm 2), per-point ratio max|r|/max|b|; marks conv[i] = 1 when ratio <= tol.
+// The operators of the FP64 refinement residual, all before the mass scaling: C_0 dense ([nr][nr]);
+// the bands ([3][nr][2 w + 1], band[p][k - p + w]) of the loss part of C (the whole C_l for
+// l >= 1), of Dv and of M1; the field blocks as coefficients of Dv and M1 ([nl][4] = lo_d, lo_m,
+// up_d, up_m: block (q, q - 1) = lo_d Dv + lo_m M1, block (q, q + 1) = up_d Dv + up_m M1); the band
+// of the Cholesky factor R of M_v ([nr][w + 1], chol[p][j] = R[p][p - w + j]) and 1 / R[p][p].
+struct ResidualOps {
+  const double* c0 = nullptr;
+  const double* band = nullptr;
+  const double* fcoef = nullptr;
+  const double* chol = nullptr;
+  const double* cinv = nullptr;
+  int w = 0;
+};
+// FP64 residual r = b - (x - dt P_O M_v^-1 (C + E_i A_v) P_S x) (Algorithm 2's structured
+// evaluation: the products with C and A_v are banded except C_0, and M_v^-1 is applied by banded
+// Cholesky substitution), per-point ratio max|r|/max|b|; marks conv[i] = 1 when ratio <= tol or the
+// normwise backward error is at FP64 rounding level.
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
-                     const double* Cs, const double* Alo, const double* Aup, const double* TO,
-                     const double* TS, double* r, double* ratio, int* conv, double tol, double kc_inf,
-                     double ka_inf, int nx, int nt, int nr, int nl, unsigned* status, cudaStream_t st);
+                     const ResidualOps& ro, const double* TO, const double* TS, double* r, double* ratio, int* conv,
+                     double tol, double kc_inf, double ka_inf, int nx, int nt, int nr, int nl, unsigned* status,
+                     cudaStream_t st);
 void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st);
 
 // ---- misc

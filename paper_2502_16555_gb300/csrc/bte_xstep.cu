@@ -159,7 +159,10 @@ __global__ void v_form_kernel(const double* __restrict__ KCg, const double* __re
 }
 
 // Refinement residual of one point (CTA per point), Algorithm 2 with the structured operators:
-// xS = P_S x, g = (C_s + E_i A_s) xS, r = b - x + dt P_O g. The point has converged when
+// xS = P_S x, g = M_v^-1 (C + E_i A_v) xS, r = b - x + dt P_O g. The products with C and A_v run
+// over the bands of the loss part of C, of Dv and of M1 (C_0 carries the gain and the
+// heavy-temperature term and is dense); M_v^-1 is a forward and a backward substitution with the
+// banded Cholesky factor of M_v along the B-spline index. The point has converged when
 // max|r| <= tol max|b|, or when max|r| is already at the rounding level of an FP64 product A_i x,
 // max|r| <= min(kBackwardFloor, tol) (|A_i| max|x| + max|b|) with |A_i| <= 1 + dt (|K_C| +
 // |E_i| |K_A|) (infinity norms): a normwise backward error no refinement can improve on. The second
@@ -169,10 +172,8 @@ __global__ void v_form_kernel(const double* __restrict__ KCg, const double* __re
 constexpr double kBackwardFloor = 256.0 * 1.1102230246251565e-16;
 
 __global__ void residual_kernel(const double* __restrict__ X, const double* __restrict__ B,
-                                const double* __restrict__ E, double E_uniform, double dt,
-                                const double* __restrict__ Cs, const double* __restrict__ Alo,
-                                const double* __restrict__ Aup, const double* __restrict__ TO,
-                                const double* __restrict__ TS, double* __restrict__ R,
+                                const double* __restrict__ E, double E_uniform, double dt, ResidualOps ro,
+                                const double* __restrict__ TO, const double* __restrict__ TS, double* __restrict__ R,
                                 double* __restrict__ ratio, int* __restrict__ conv, double tol,
                                 double kc_inf, double ka_inf, int nt, int nr, int nl,
                                 unsigned* __restrict__ status) {
@@ -197,16 +198,49 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
     xS[idx] = s;
   }
   __syncthreads();
+  const int w = ro.w, bw = 2 * w + 1;
   for (int idx = threadIdx.x; idx < nl * nr; idx += blockDim.x) {
     const int l = idx / nr, p = idx % nr;
-    const size_t off = (static_cast<size_t>(l) * nr + p) * nr;
+    const int k0 = max(0, p - w), k1 = min(nr - 1, p + w);
     double c = 0.0, f = 0.0;
-    for (int k = 0; k < nr; ++k) c = fma(__ldg(Cs + off + k), xS[l * nr + k], c);
-    if (l >= 1)
-      for (int k = 0; k < nr; ++k) f = fma(__ldg(Alo + off + k), xS[(l - 1) * nr + k], f);
-    if (l + 1 < nl)
-      for (int k = 0; k < nr; ++k) f = fma(__ldg(Aup + off + k), xS[(l + 1) * nr + k], f);
+    if (l == 0) {
+      const double* row = ro.c0 + static_cast<size_t>(p) * nr;
+      for (int k = 0; k < nr; ++k) c = fma(__ldg(row + k), xS[k], c);
+    } else {
+      const double* row = ro.band + static_cast<size_t>(p) * bw + w - p;   // row[k] = loss[p][k]
+      for (int k = k0; k <= k1; ++k) c = fma(__ldg(row + k), xS[l * nr + k], c);
+    }
+    const double* drow = ro.band + static_cast<size_t>(nr + p) * bw + w - p;      // Dv[p][k]
+    const double* mrow = ro.band + static_cast<size_t>(2 * nr + p) * bw + w - p;  // M1[p][k]
+    if (l >= 1) {
+      const double cd = __ldg(ro.fcoef + 4 * l), cm = __ldg(ro.fcoef + 4 * l + 1);
+      const double* y = xS + (l - 1) * nr;
+      for (int k = k0; k <= k1; ++k) f = fma(fma(cd, __ldg(drow + k), cm * __ldg(mrow + k)), y[k], f);
+    }
+    if (l + 1 < nl) {
+      const double cd = __ldg(ro.fcoef + 4 * l + 2), cm = __ldg(ro.fcoef + 4 * l + 3);
+      const double* y = xS + (l + 1) * nr;
+      for (int k = k0; k <= k1; ++k) f = fma(fma(cd, __ldg(drow + k), cm * __ldg(mrow + k)), y[k], f);
+    }
     g[idx] = c + Ei * f;
+  }
+  __syncthreads();
+  // g_l <- M_v^-1 g_l, M_v = R R^T: R y = g_l (p ascending), then R^T z = y (p descending), one
+  // thread per harmonic
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    double* gl = g + l * nr;
+    for (int p = 0; p < nr; ++p) {
+      const double* rrow = ro.chol + static_cast<size_t>(p) * (w + 1);   // rrow[j] = R[p][p - w + j]
+      double s = gl[p];
+      for (int j = max(0, w - p); j < w; ++j) s = fma(-__ldg(rrow + j), gl[p - w + j], s);
+      gl[p] = s * __ldg(ro.cinv + p);
+    }
+    for (int p = nr - 1; p >= 0; --p) {
+      double s = gl[p];
+      const int kmax = min(nr - 1, p + w);
+      for (int k = p + 1; k <= kmax; ++k) s = fma(-__ldg(ro.chol + static_cast<size_t>(k) * (w + 1) + p - k + w), gl[k], s);
+      gl[p] = s * __ldg(ro.cinv + p);
+    }
   }
   __syncthreads();
   double mr = 0.0, mb = 0.0, mx = 0.0;
@@ -367,17 +401,17 @@ template void launch_v_form<float>(const double*, const double*, MassBand, const
                                    float*, int, int, cudaStream_t);
 
 void launch_residual(const double* x, const double* b, const double* E, double E_uniform, double dt,
-                     const double* Cs, const double* Alo, const double* Aup, const double* TO,
-                     const double* TS, double* r, double* ratio, int* conv, double tol, double kc_inf,
-                     double ka_inf, int nx, int nt, int nr, int nl, unsigned* status, cudaStream_t st) {
+                     const ResidualOps& ro, const double* TO, const double* TS, double* r, double* ratio, int* conv,
+                     double tol, double kc_inf, double ka_inf, int nx, int nt, int nr, int nl, unsigned* status,
+                     cudaStream_t st) {
   const size_t smem = sizeof(double) * (static_cast<size_t>(nt) * nr + 2 * nl * nr);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  residual_kernel<<<nx, 256, smem, st>>>(x, b, E, E_uniform, dt, Cs, Alo, Aup, TO, TS, r, ratio,
-                                         conv, tol, kc_inf, ka_inf, nt, nr, nl, status);
+  residual_kernel<<<nx, 256, smem, st>>>(x, b, E, E_uniform, dt, ro, TO, TS, r, ratio, conv, tol, kc_inf, ka_inf, nt,
+                                         nr, nl, status);
 }
 
 void launch_check_conv(const int* conv, int nx, unsigned* status, cudaStream_t st) {
