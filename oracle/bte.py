@@ -22,6 +22,9 @@ Readings of points the paper leaves open:
   - ionization releases two electrons, each at (eps - eps_ion)/2, gain factor 2;
   - excitation: one electron at eps - eps_th;
   - heavy-temperature term: -(n0 kB T0/m0) int v^3 sigma_el phi_p' phi_k' dv on the (0,0) block;
+  - f(vmax) = 0: the Nr radial functions are the clamped cubic B-splines of an Nr + 1 function
+    basis without the last one (the paper states no condition at vmax; without one the field
+    term lets f flow in at vmax unchecked and the step grows like exp(c e E t / (m_e dv)));
   - field operator derived from the strong form (eE/m_e)[mu d_v f + (1-mu^2)/v d_mu f]
     with the Legendre recurrences (only A_M(l) = l/sqrt(4l^2-1) of the printed table survives);
   - T_S carries the azimuthal 2*pi, so T_S T_O = I;
@@ -388,17 +391,20 @@ class Operators:
         self.x = cheb_points(nx, self.L)
         self.Dx = cheb_diff(self.x)
         self.mu, self.wmu, self.T_O, self.T_S = angular_ops(nt, nl)
-        self.knots = bspline_knots(nr, self.vmax)
-        M, G, Dv, M1 = radial_matrices(self.knots)
+        # f(vmax) = 0: the clamped cubic basis of Nr + 1 functions without its last member, the only
+        # one nonzero at vmax. Trial and test spaces lose the same function, so every Galerkin
+        # matrix is the leading Nr x Nr block of the one over all Nr + 1 functions.
+        self.knots = bspline_knots(nr + 1, self.vmax)
+        M, G, Dv, M1 = (X[:nr, :nr] for X in radial_matrices(self.knots))
         self.M, self.G, self.Dv, self.M1 = M, G, Dv, M1
 
         # collisions: C[l] (l-block diagonal); gain and T0 term only on l = 0
         loss = np.zeros((nr, nr))
         gain = np.zeros((nr, nr))
         for p in self.procs:
-            loss += collision_loss(self.knots, p, self.n0)
-            gain += collision_gain(self.knots, p, self.n0, self.m0, nq=nq_gain)
-        cT = collision_T0(self.knots, self.procs, self.n0, self.T0, self.m0)
+            loss += collision_loss(self.knots, p, self.n0)[:nr, :nr]
+            gain += collision_gain(self.knots, p, self.n0, self.m0, nq=nq_gain)[:nr, :nr]
+        cT = collision_T0(self.knots, self.procs, self.n0, self.T0, self.m0)[:nr, :nr]
         self.C_raw = np.array([loss + (gain + cT if l == 0 else 0.0) for l in range(nl)])
         self.A_raw = field_blocks(Dv, M1, nl)
 
@@ -424,7 +430,7 @@ class Operators:
 
         # moment vectors (per x point: n_e = sum_{a,k} u[a,k] F[a,k], etc.)
         vq, wq = gauss_composite(self.knots, 16)
-        P = bspline_eval(self.knots, vq)
+        P = bspline_eval(self.knots, vq)[:, :nr]
         ang = 2.0 * np.pi * self.wmu
         self.mom_n = np.outer(ang, (P * (wq * vq**2)[:, None]).sum(0))
         self.mom_e = np.outer(ang, (P * (wq * vq**2 * energy_of_speed(vq))[:, None]).sum(0))
@@ -432,7 +438,7 @@ class Operators:
         for p in self.procs:
             br = [b for b in list(self.knots) + _sigma_breaks(p) if 0 <= b <= self.vmax]
             vr, wr = gauss_composite(br, 32)
-            Pr = bspline_eval(self.knots, vr)
+            Pr = bspline_eval(self.knots, vr)[:, :nr]
             self.mom_r.append(np.outer(ang, (Pr * (wr * vr**3 * sigma_of_speed(p, vr))[:, None]).sum(0)))
 
     # ---- field
@@ -510,7 +516,7 @@ class Operators:
         """Galerkin (v^2-weighted) projection of a unit-density Maxwellian at Te onto the splines."""
         vth = np.sqrt(2.0 * E_CHARGE * Te_eV / M_E)
         v, w = gauss_composite(self.knots, 32)
-        P = bspline_eval(self.knots, v)
+        P = bspline_eval(self.knots, v)[:, :self.nr]
         fM = np.exp(-(v / vth) ** 2) / (np.pi**1.5 * vth**3)
         b = (P * (w * v**2 * fM)[:, None]).sum(0)
         return np.linalg.solve(self.M, b)

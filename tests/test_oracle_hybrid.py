@@ -165,9 +165,11 @@ def test_ion_source_is_the_ionization_rate_of_the_electrons():
     """No ion mobility, uniform ions and a uniform 3 eV Maxwellian electron state: the flux
     vanishes (walls included), so one step adds dt n0 k_ion n_e everywhere. k_ion is the
     Maxwellian average of v sigma_ion (sigma = 3e-21 ln(eps/15.76)/(eps/15.76) above threshold)
-    by adaptive quadrature, truncated at vmax; agreement to the B-spline projection error."""
+    by adaptive quadrature, truncated at vmax; agreement to the B-spline projection error. vmax =
+    60 eV keeps the ionization tail far from vmax, where the radial functions must vanish."""
     from scipy import integrate
     cfg = tiny(nx=9, nr=48, nt=4)
+    cfg["vmax_eV"] = 60.0
     ops = O.Operators(cfg)
     h = H.Hybrid(ops, n0_mu_i=0.0)
     Te, ne = 3.0, 2.0e15

@@ -149,20 +149,45 @@ def _ops(cfg):
     return O.Operators(cfg)
 
 
-def test_collision_particle_conservation_elastic_excitation():
-    cfg = tiny_cfg(nr=12, procs=[W.P1_ELASTIC, W.P2_EXC, W.P4_EXC])
+def _full_C0(ops):
+    """The l = 0 collision block over all Nr + 1 clamped functions of the oracle's knots (loss, gain
+    and the heavy-temperature term): the building blocks before the last function is dropped."""
+    C = O.collision_T0(ops.knots, ops.procs, ops.n0, ops.T0, ops.m0)
+    for p in ops.procs:
+        C = C + O.collision_loss(ops.knots, p, ops.n0) + O.collision_gain(ops.knots, p, ops.n0, ops.m0)
+    return C
+
+
+def test_operators_are_leading_blocks_of_the_clamped_basis():
+    """f(vmax) = 0: the Nr radial functions are the first Nr of the Nr + 1 clamped cubic B-splines of
+    the oracle's knots; they all vanish at vmax and the dropped one is 1 there. Every radial matrix
+    and moment vector is the leading block of the one over all Nr + 1 functions."""
+    cfg = tiny_cfg(nx=3, nr=11, nt=4, procs=[W.P1_ELASTIC, W.P2_EXC, W.P3_ION])
     ops = _ops(cfg)
-    C0 = ops.C_raw[0]
-    scale = np.abs(C0).max()
-    assert np.max(np.abs(C0.sum(0))) < 1e-12 * scale
+    nr = ops.nr
+    assert ops.knots.size - 4 == nr + 1
+    end = O.bspline_eval(ops.knots, [ops.vmax])[0]
+    assert np.all(end[:nr] == 0.0) and end[nr] == 1.0
+    M, G, Dv, M1 = O.radial_matrices(ops.knots)
+    for a, b in ((ops.M, M), (ops.G, G), (ops.Dv, Dv), (ops.M1, M1)):
+        np.testing.assert_array_equal(a, b[:nr, :nr])
+    np.testing.assert_allclose(ops.C_raw[0], _full_C0(ops)[:nr, :nr], rtol=1e-13, atol=1e-13 * np.abs(ops.C_raw[0]).max())
+
+
+def test_collision_particle_conservation_elastic_excitation():
+    """1^T C = 0 over the whole clamped basis (sum_p phi_p = 1 is then a test function)."""
+    cfg = tiny_cfg(nr=12, procs=[W.P1_ELASTIC, W.P2_EXC, W.P4_EXC])
+    C0 = _full_C0(_ops(cfg))
+    assert np.max(np.abs(C0.sum(0))) < 1e-12 * np.abs(C0).max()
 
 
 def test_collision_ionization_source_is_rate():
-    """1^T C_ion = n0 int v^3 sigma_ion phi_k (two out, one in), i.e. minus the loss column sum."""
+    """1^T C_ion = n0 int v^3 sigma_ion phi_k (two out, one in), i.e. minus the loss column sum,
+    over the whole clamped basis."""
     cfg = tiny_cfg(nr=12, procs=[W.P3_ION])
     ops = _ops(cfg)
     loss = O.collision_loss(ops.knots, W.P3_ION, ops.n0)
-    assert np.allclose(ops.C_raw[0].sum(0), -loss.sum(0), rtol=1e-11, atol=1e-12 * np.abs(loss).max())
+    assert np.allclose(_full_C0(ops).sum(0), -loss.sum(0), rtol=1e-11, atol=1e-12 * np.abs(loss).max())
 
 
 @pytest.mark.parametrize("proc", [W.P1_ELASTIC, W.P2_EXC, W.P3_ION, W.P4_EXC])
@@ -173,8 +198,8 @@ def test_collision_energy_moment(proc):
     cfg = tiny_cfg(nr=14, procs=[proc])
     ops = _ops(cfg)
     vq, wq = O.gauss_composite(ops.knots, 16)
-    P = O.bspline_eval(ops.knots, vq)
-    w = np.linalg.solve(ops.M, (P * (wq * vq**4)[:, None]).sum(0))
+    P = O.bspline_eval(ops.knots, vq)                     # the whole clamped basis
+    w = np.linalg.solve(O.radial_matrices(ops.knots)[0], (P * (wq * vq**4)[:, None]).sum(0))
     loss = O.collision_loss(ops.knots, proc, ops.n0)     # -n0 int v^3 sigma phi_p phi_k
     gain = O.collision_gain(ops.knots, proc, ops.n0, ops.m0)
     lhs = w @ (loss + gain)
@@ -238,11 +263,11 @@ def test_elastic_energy_relaxation_toward_T0(T0):
     n0 = O.neutral_density(1.0, T0)
     proc = W.process("elastic", "nu", nu / n0)
     ops = _ops(tiny_cfg(nx=3, nr=24, procs=[proc], T0_K=T0))
-    w = _energy_weights(ops.knots)
-    F = ops.maxwellian_coeffs(2.0)
+    w = _energy_weights(ops.knots)                         # over the whole clamped basis
+    F = np.append(ops.maxwellian_coeffs(2.0), 0.0)         # the dropped function's coefficient is 0
     dens = _int_v2_phi(ops.knots) @ F
-    eps = 0.5 * O.M_E * (w @ ops.M @ F) / dens
-    rate = 0.5 * O.M_E * (w @ ops.C_raw[0] @ F) / dens
+    eps = 0.5 * O.M_E * (w @ O.radial_matrices(ops.knots)[0] @ F) / dens
+    rate = 0.5 * O.M_E * (w @ _full_C0(ops) @ F) / dens
     expect = -2.0 * O.M_E / ops.m0 * nu * (eps - 1.5 * O.K_B * T0)
     assert abs(rate / expect - 1.0) < 1e-5, (rate, expect)
 
@@ -254,7 +279,7 @@ def test_maxwellian_at_T0_is_null_vector_of_elastic_operator():
     T0 = O.E_CHARGE / O.K_B
     ops = _ops(tiny_cfg(nx=3, nr=48, procs=[W.P1_ELASTIC], T0_K=T0))
     F = ops.maxwellian_coeffs(1.0)
-    CT = O.collision_T0(ops.knots, [W.P1_ELASTIC], ops.n0, ops.T0, ops.m0)
+    CT = O.collision_T0(ops.knots, [W.P1_ELASTIC], ops.n0, ops.T0, ops.m0)[:ops.nr, :ops.nr]
     r = ops.C_raw[0] @ F
     assert np.linalg.norm(r) < 1e-4 * np.linalg.norm(CT @ F)
 
@@ -287,26 +312,36 @@ def test_gain_quadrature_converged():
         assert np.max(np.abs(a - b)) < 1e-13 * np.abs(b).max()
 
 
+def _smooth_state(ops, seed):
+    """A 2 eV Maxwellian in speed with random positive weights per point and ordinate."""
+    rng = np.random.default_rng(seed)
+    return ops.maxwellian_coeffs(2.0)[None, None, :] * (1.0 + 0.3 * rng.random((ops.nx, ops.nt, 1)))
+
+
 def test_vstep_conserves_particles_without_field():
-    cfg = tiny_cfg(nx=3, nr=10, nt=6, procs=[W.P1_ELASTIC, W.P2_EXC])
+    """Collisions keep the particle count. The splines that vanish at vmax hold the constant 1 only
+    away from vmax, so the count is kept to the size of the state there: a 2 eV Maxwellian on a
+    60 eV grid (measured 6e-12; 1e-8 on a 16-function, 30 eV grid)."""
+    cfg = tiny_cfg(nx=3, nr=32, nt=6, procs=[W.P1_ELASTIC, W.P2_EXC], vmax_eV=60.0)
     ops = _ops(cfg)
-    F = W.random_state(3, 6, 10, seed=3)
+    F = _smooth_state(ops, 3)
     F1 = ops.v_step(F, np.zeros(3))
     ne0, _, _ = ops.moments(F)
     ne1, _, _ = ops.moments(F1)
-    assert np.allclose(ne1, ne0, rtol=1e-12)
+    assert np.allclose(ne1, ne0, rtol=1e-10)
 
 
 def test_vstep_ionization_growth():
-    """Backward Euler: n_e(F*) - n_e(F) = dt * n0 * (ionization-rate moment of F*)."""
-    cfg = tiny_cfg(nx=3, nr=10, nt=6, procs=[W.P1_ELASTIC, W.P3_ION])
+    """Backward Euler: n_e(F*) - n_e(F) = dt * n0 * (ionization-rate moment of F*), on the grid of
+    the conservation test (the source is small, so the identity is checked relative to it)."""
+    cfg = tiny_cfg(nx=3, nr=32, nt=6, procs=[W.P1_ELASTIC, W.P3_ION], vmax_eV=60.0)
     ops = _ops(cfg)
-    F = W.random_state(3, 6, 10, seed=4)
+    F = _smooth_state(ops, 4)
     F1 = ops.v_step(F, np.zeros(3))
     ne0, _, _ = ops.moments(F)
     ne1, _, k1 = ops.moments(F1)
     src = ops.dt * ops.n0 * k1[1] * ne1
-    assert np.allclose(ne1 - ne0, src, rtol=1e-9)
+    assert np.allclose(ne1 - ne0, src, rtol=1e-6)
     assert np.all(ne1 > ne0)
 
 
@@ -332,15 +367,20 @@ def test_relaxation_constant_frequency(nt, nl):
 # ------------------------------------------------------------------------------------ field
 
 def test_field_number_balance_is_boundary_flux():
-    """Only the l=1 -> l=0 coupling changes the particle count, and it equals the speed-space flux
-    through vmax: sum_p A[0,1][p,k] = (e/m_e) a_1 vmax^2 phi_k(vmax)."""
+    """Over the whole clamped basis only the l=1 -> l=0 coupling changes the particle count, and it
+    equals the speed-space flux through vmax: sum_p A[0,1][p,k] = (e/m_e) a_1 vmax^2 phi_k(vmax),
+    zero for every kept function (they vanish at vmax)."""
     cfg = tiny_cfg(nr=9, nt=6)
     ops = _ops(cfg)
-    col = ops.A_raw[0, 1].sum(0)
+    _, _, Dv, M1 = O.radial_matrices(ops.knots)
+    A = O.field_blocks(Dv, M1, ops.nl)
+    col = A[0, 1].sum(0)
     phi_end = O.bspline_eval(ops.knots, [ops.vmax])[0]
     expect = O.E_CHARGE / O.M_E * (1 / np.sqrt(3)) * ops.vmax**2 * phi_end
     assert np.allclose(col, expect, rtol=1e-11, atol=1e-12 * np.abs(expect).max())
+    assert np.all(expect[:ops.nr] == 0.0) and expect[ops.nr] != 0.0
     for l in range(2, ops.nl):
+        assert np.all(A[0, l] == 0.0)
         assert np.all(ops.A_raw[0, l] == 0.0)
 
 
@@ -352,8 +392,8 @@ def test_field_operator_matches_strong_form_projection():
     ops = _ops(cfg)
     vq, wv = O.gauss_composite(ops.knots, 12)
     mq, wm = np.polynomial.legendre.leggauss(24)
-    P = O.bspline_eval(ops.knots, vq)
-    dP = O.bspline_eval(ops.knots, vq, deriv=1)
+    P = O.bspline_eval(ops.knots, vq)[:, :nr]               # the kept functions
+    dP = O.bspline_eval(ops.knots, vq, deriv=1)[:, :nr]
     leg = [np.polynomial.legendre.Legendre.basis(l) for l in range(nl)]
     c = np.sqrt((2 * np.arange(nl) + 1) / (4 * np.pi))
     Y = np.array([c[l] * leg[l](mq) for l in range(nl)])
@@ -375,7 +415,7 @@ def test_field_drift_sign():
     F = ops.initial_state()
     F1 = ops.v_step(F, np.full(3, 5e3))
     vq, wq = O.gauss_composite(ops.knots, 16)
-    P = O.bspline_eval(ops.knots, vq)
+    P = O.bspline_eval(ops.knots, vq)[:, :ops.nr]
     m3 = (P * (wq * vq**3)[:, None]).sum(0)
     flux = np.einsum("a,xak,k->x", 2 * np.pi * ops.wmu * ops.mu, F1, m3)
     assert flux[1] < 0
@@ -499,11 +539,13 @@ def _truncated_rates(Te, emax, proc):
 
 def test_moments_of_maxwellian_closed_forms():
     """Mean energy -> 3/2 Te and Maxwellian rate coefficients of the analytic cross sections,
-    truncated at vmax, up to the B-spline projection error (which must shrink with Nr)."""
+    truncated at vmax, up to the B-spline projection error (which must shrink with Nr). vmax = 60 eV:
+    at 2 eV the Maxwellian is e^-30 there, so f(vmax) = 0 costs nothing (with 30 eV the constrained
+    projection of the e^-15 tail limits the ionization rate to 1e-4, converging at first order)."""
     Te = 2.0
     res = []
     for nr in (24, 48, 96):
-        cfg = tiny_cfg(nx=3, nr=nr, nt=4, procs=[W.P1_ELASTIC, W.P2_EXC, W.P3_ION])
+        cfg = tiny_cfg(nx=3, nr=nr, nt=4, procs=[W.P1_ELASTIC, W.P2_EXC, W.P3_ION], vmax_eV=60.0)
         ops = _ops(cfg)
         F = np.broadcast_to(ops.maxwellian_coeffs(Te), (3, 4, nr)).copy()
         ne, mean, rates = ops.moments(F)
@@ -627,3 +669,65 @@ def test_velocity_solve_meets_the_definition(nr, nt, E):
     else:
         assert growth < 1e4 and backward(direct) <= 1e-12
         assert np.abs(direct - x).max() <= 1e-9 * np.abs(x).max()
+
+
+# ------------------------------------------------------------------------------------ speed boundary
+
+def _harmonic_field_matrix(ops):
+    nl, nr = ops.nl, ops.nr
+    B = np.zeros((nl * nr, nl * nr))
+    for q in range(nl):
+        for l in range(nl):
+            B[q * nr:(q + 1) * nr, l * nr:(l + 1) * nr] = ops.A_raw[q, l]
+    return B
+
+
+@pytest.mark.parametrize("nr,nl", [(9, 4), (16, 6), (24, 8)])
+def test_field_operator_conserves_the_square_integral(nr, nl):
+    """With f(vmax) = 0 the acceleration term (eE/m_e)[mu d_v f + (1 - mu^2)/v d_mu f] conserves
+    int f^2 d^3v (a divergence-free flow in velocity space; the boundary term at vmax vanishes), so
+    its Galerkin matrix over the kept functions is skew-symmetric: A + A^T = 0 to rounding. Over
+    all Nr + 1 clamped functions A + A^T is not zero, and only its entries between the last radial
+    functions are: the inflow through vmax that made the step grow without bound."""
+    ops = O.Operators(tiny_cfg(nx=3, nr=nr, nt=nl, nl=nl, procs=[W.P1_ELASTIC]))
+    B = _harmonic_field_matrix(ops)
+    assert np.abs(B + B.T).max() <= 1e-13 * np.abs(B).max()
+    # the whole clamped basis of the same knots
+    Mf, Gf, Dvf, M1f = O.radial_matrices(ops.knots)
+    Af = O.field_blocks(Dvf, M1f, nl)
+    n1 = nr + 1
+    Bf = np.zeros((nl * n1, nl * n1))
+    for q in range(nl):
+        for l in range(nl):
+            Bf[q * n1:(q + 1) * n1, l * n1:(l + 1) * n1] = Af[q, l]
+    S = Bf + Bf.T
+    big = np.argwhere(np.abs(S) > 1e-10 * np.abs(Bf).max())
+    assert big.size > 0
+    assert all(i % n1 == nr and j % n1 == nr for i, j in big)
+
+
+def test_field_operator_spectrum_is_imaginary():
+    """A skew A against the SPD mass matrix: the eigenvalues of M^-1 A are purely imaginary, so the
+    semi-discrete field term neither grows nor damps (backward Euler then damps every mode)."""
+    ops = O.Operators(tiny_cfg(nx=3, nr=20, nt=6, nl=6, procs=[W.P1_ELASTIC]))
+    nl, nr = ops.nl, ops.nr
+    Mh = np.kron(np.eye(nl), ops.M)
+    lam = np.linalg.eigvals(np.linalg.solve(Mh, _harmonic_field_matrix(ops)))
+    assert np.abs(lam.real).max() <= 1e-9 * np.abs(lam).max()
+
+
+def test_quarter_cycle_stays_bounded():
+    """The 2000-step discharge's time step (T_RF/2000) and field amplitude (150 V) on a small grid,
+    500 steps from the Maxwellian to the field maximum: the state stays bounded and n_e stays
+    positive. With all Nr + 1 functions kept, the velocity operator of this grid has an eigenvalue
+    of real part 1.8e9 s^-1 at the field maximum (the inflow through vmax), and the same run grows
+    by about e^20."""
+    cfg = W.scaled(W.MEDIUM, nx=5, nr=16, ntheta=8)
+    ops = O.Operators(cfg)
+    F = ops.initial_state()
+    n0 = np.linalg.norm(F)
+    for n in range(500):
+        F = ops.step(F, n * ops.dt)
+    ne, _, _ = ops.moments(F)
+    assert np.linalg.norm(F) <= 2.0 * n0
+    assert np.all(ne[1:-1] > 0.0)
