@@ -481,6 +481,26 @@ def run_ours(args, rank, world):
             structured[prec] = entry
             del ss
 
+    # ---- accuracy over the configured run (one RF cycle of 2000 steps for the default discharge):
+    # the mixed path against FP64. The dense FP64 path takes about 0.65 s per step here, so the
+    # reference is the FP64 block-tridiagonal solve of the same systems (refined in FP64), which
+    # matches the dense FP64 path to ~1e-15 over the steps compared above (structured_solve).
+    cycle = None
+    if not args.no_cycle and cfg["nr"] <= 64 and cfg.get("steps"):
+        n_cyc = int(cfg["steps"])
+        Fm = F0.clone()
+        Gs = F0.clone()
+        s.run(Fm, n_cyc, 0.0)
+        ref = bte.Solver(cfg, precision="fp64", structured=True)
+        ref.run(Gs, n_cyc, 0.0)
+        ne_m, _, _ = s.moments(Fm)
+        ne_r, _, _ = ref.moments(Gs)
+        torch.cuda.synchronize()
+        cycle = {"steps": n_cyc, "reference": "FP64 block-tridiagonal solve (BTE_FLAG_STRUCTURED), same start state",
+                 "rel_l2_f": float(torch.linalg.norm(Fm - Gs) / torch.linalg.norm(Gs)),
+                 "rel_l2_ne": float(torch.linalg.norm(ne_m - ne_r) / torch.linalg.norm(ne_r))}
+        del ref, Fm, Gs
+
     # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region:
     # the device-timed plain run's steps again, from its start state at its times
     e2e = None
@@ -537,6 +557,7 @@ def run_ours(args, rank, world):
         "fp64": fp64,
         "speedup_mixed_over_fp64": (fp64["ms_per_step"] / ms) if fp64 else None,
         "structured_solve": structured,
+        "cycle_accuracy": cycle,
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": int(launches),
@@ -923,6 +944,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-structured", action="store_true", help="skip the block-tridiagonal solve legs")
+    ap.add_argument("--no-cycle", action="store_true",
+                    help="skip the accuracy leg over the configured run (mixed against FP64)")
     ap.add_argument("--peaks", action="store_true", help="only measure library GEMM peaks (FP64, FP32, TF32, BF16)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, LARGEST, "batched64_uneven", "adjoint_nx64_nr32_nt16", HYBRID, HYBRID_TABLE],

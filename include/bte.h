@@ -90,7 +90,10 @@ typedef enum {
 
 typedef struct {
   int nx;            /* Chebyshev-Gauss-Lobatto points, >= 3 */
-  int nr;            /* cubic B-splines in speed, >= 4 */
+  int nr;            /* cubic B-splines in speed, >= 4: the first nr of the nr + 1 clamped cubic
+                        B-splines on a uniform grid over [0, vmax], so f(vmax) = 0 (the last one,
+                        the only one nonzero at vmax, is left out: without it the field term has no
+                        inflow through vmax and conserves int f^2 d^3v) */
   int ntheta;        /* Gauss-Legendre ordinates in mu = cos(theta), >= 2 */
   int nl;            /* spherical harmonics Y_l0 kept, 1 <= nl <= ntheta (0 means ntheta) */
   double L_m;        /* electrode gap [m] */

@@ -407,8 +407,11 @@ std::string assemble_x(const bte_config& cfg, HostOps& o) {
     }
   }
 
-  // radial Galerkin matrices (polynomial integrands: 8 Gauss points per knot interval are exact)
-  Spline sp(nr, o.vmax);
+  // radial Galerkin matrices (polynomial integrands: 8 Gauss points per knot interval are exact).
+  // f(vmax) = 0: the radial functions are the first nr of the nr + 1 clamped cubic B-splines; the
+  // last one, the only one nonzero at vmax, is left out of trial and test spaces, so every matrix
+  // and vector below accumulates only indices < nr.
+  Spline sp(nr + 1, o.vmax);
   o.knots = sp.t;
   o.M.assign(nr * nr, 0.0);
   o.G = o.M;
@@ -422,6 +425,7 @@ std::string assemble_x(const bte_config& cfg, HostOps& o) {
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b) {
         const int p = s - 3 + a, k = s - 3 + b;
+        if (p >= nr || k >= nr) continue;
         o.M[p * nr + k] += w * v * v * Nv[a] * Nv[b];
         o.G[p * nr + k] += w * v * v * v * Nv[a] * Nv[b];
         o.Dv[p * nr + k] += w * v * v * Nv[a] * dN[b];
@@ -507,7 +511,7 @@ bool assemble_q(const HostOps& o, double tau, std::vector<double>& Q) {
 
 std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
   const int nr = o.nr, nt = o.nt, nl = o.nl, nv = o.nv;
-  Spline sp(nr, o.vmax);
+  Spline sp(nr + 1, o.vmax);  // the last function is left out (f(vmax) = 0)
   const double vmax = o.vmax;
   Rule rq(24);
 
@@ -525,7 +529,8 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       if (!sp.eval(v, s, Nv, dN)) return;
       const double f = -o.n0 * w * v * v * v * sg;
       for (int a = 0; a < 4; ++a)
-        for (int b = 0; b < 4; ++b) loss[(s - 3 + a) * nr + (s - 3 + b)] += f * Nv[a] * Nv[b];
+        for (int b = 0; b < 4; ++b)
+          if (s - 3 + a < nr && s - 3 + b < nr) loss[(s - 3 + a) * nr + (s - 3 + b)] += f * Nv[a] * Nv[b];
     });
     // heavy-temperature correction from the elastic (momentum transfer) cross sections
     if (p.kind == BTE_ELASTIC && o.T0 > 0) {
@@ -537,7 +542,8 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
         if (!sp.eval(v, s, Nv, dN)) return;
         const double f = cf * w * v * v * v * sg;
         for (int a = 0; a < 4; ++a)
-          for (int b = 0; b < 4; ++b) cT[(s - 3 + a) * nr + (s - 3 + b)] += f * dN[a] * dN[b];
+          for (int b = 0; b < 4; ++b)
+            if (s - 3 + a < nr && s - 3 + b < nr) cT[(s - 3 + a) * nr + (s - 3 + b)] += f * dN[a] * dN[b];
       });
     }
     // gain, (0,0) block: g n0 int v^3 sigma(v) phi_k(v) phi_p(u(v)) dv, integrated in u
@@ -561,7 +567,8 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
         if (!sp.eval(u, su, Nu, d1) || !sp.eval(v, sv, Nvv, d2)) return;
         const double f = col.g * o.n0 * w * dvdu * v * v * v * sg;
         for (int a = 0; a < 4; ++a)
-          for (int b = 0; b < 4; ++b) gain[(su - 3 + a) * nr + (sv - 3 + b)] += f * Nu[a] * Nvv[b];
+          for (int b = 0; b < 4; ++b)
+            if (su - 3 + a < nr && sv - 3 + b < nr) gain[(su - 3 + a) * nr + (sv - 3 + b)] += f * Nu[a] * Nvv[b];
       });
     }
   }
@@ -580,9 +587,10 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
   // of the Cholesky factor of M); B-spline products of degree 3 couple only indices within mw
   {
     const int w = o.mw, bw = 2 * w + 1;
-    o.rband.assign(static_cast<size_t>(3) * nr * bw, 0.0);
+    o.rband.assign(static_cast<size_t>(nr) * bw, 0.0);
     o.rchol.assign(static_cast<size_t>(nr) * (w + 1), 0.0);
     o.rcinv.assign(nr, 0.0);
+    // loss, Dv and M1 must lie within the band (the field blocks are combinations of Dv and M1)
     const std::vector<double>* src[3] = {&loss, &o.Dv, &o.M1};
     for (int m = 0; m < 3; ++m)
       for (int p = 0; p < nr; ++p)
@@ -590,7 +598,7 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
           const double v = (*src[m])[p * nr + k];
           if (v == 0.0) continue;
           if (std::abs(p - k) > w) return "a radial operator is wider than the band of M_v";
-          o.rband[(static_cast<size_t>(m) * nr + p) * bw + k - p + w] = v;
+          if (m == 0) o.rband[static_cast<size_t>(p) * bw + k - p + w] = v;
         }
     for (int p = 0; p < nr; ++p) {
       for (int j = 0; j <= w; ++j) {
@@ -628,14 +636,12 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
   o.As_up.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   o.Ag_lo.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
   o.Ag_up.assign(static_cast<size_t>(nl) * nr * nr, 0.0);
-  o.fcoef.assign(static_cast<size_t>(4) * nl, 0.0);
   {
     const double em = kE / kMe;
     for (int q = 0; q < nl; ++q) {
       if (q >= 1) {
         const double aq = q / std::sqrt(4.0 * q * q - 1.0);
         const double cd = em * aq, cm = -em * aq * (q - 1);
-        o.fcoef[4 * q + 0] = cd, o.fcoef[4 * q + 1] = cm;
         double* blk = o.Ag_lo.data() + static_cast<size_t>(q) * nr * nr;
         for (int i = 0; i < nr * nr; ++i) blk[i] = cd * o.Dv[i] + cm * o.M1[i];
         mscale(blk, o.As_lo.data() + static_cast<size_t>(q) * nr * nr);
@@ -643,12 +649,23 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       if (q + 1 < nl) {
         const double aq = (q + 1) / std::sqrt(4.0 * (q + 1) * (q + 1) - 1.0);
         const double cd = em * aq, cm = em * aq * (q + 2);
-        o.fcoef[4 * q + 2] = cd, o.fcoef[4 * q + 3] = cm;
         double* blk = o.Ag_up.data() + static_cast<size_t>(q) * nr * nr;
         for (int i = 0; i < nr * nr; ++i) blk[i] = cd * o.Dv[i] + cm * o.M1[i];
         mscale(blk, o.As_up.data() + static_cast<size_t>(q) * nr * nr);
       }
     }
+  }
+  // bands of the field blocks for the refinement residual (zero where a block does not exist)
+  {
+    const int w = o.mw, bw = 2 * w + 1;
+    o.rfband.assign(static_cast<size_t>(2) * nl * nr * bw, 0.0);
+    for (int side = 0; side < 2; ++side)
+      for (int q = 0; q < nl; ++q) {
+        const double* blk = (side == 0 ? o.Ag_lo : o.Ag_up).data() + static_cast<size_t>(q) * nr * nr;
+        double* out = o.rfband.data() + (static_cast<size_t>(side) * nl + q) * nr * bw;
+        for (int p = 0; p < nr; ++p)
+          for (int k = std::max(0, p - w); k <= std::min(nr - 1, p + w); ++k) out[p * bw + k - p + w] = blk[p * nr + k];
+      }
   }
 
   // K_C[(a,p),(b,k)] = sum_l T_O[a][l] Cs_l[p][k] T_S[l][b];  K_A likewise over (q, l = q -+ 1).
@@ -713,6 +730,7 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       double Nv[4], dN[4];
       if (!sp.eval(v, s, Nv, dN)) return;
       for (int a = 0; a < 4; ++a) {
+        if (s - 3 + a >= nr) continue;
         mn[s - 3 + a] += w * v * v * Nv[a];
         me[s - 3 + a] += w * v * v * energy_eV(v) * Nv[a];
       }
@@ -736,7 +754,8 @@ std::string assemble_v(HostOps& o, const std::vector<Process>& procs) {
       double Nv[4], dN[4];
       if (!sp.eval(v, s, Nv, dN)) return;
       const double f = w * v * v * v * sigma(procs[j], v);
-      for (int a = 0; a < 4; ++a) mr[s - 3 + a] += f * Nv[a];
+      for (int a = 0; a < 4; ++a)
+        if (s - 3 + a < nr) mr[s - 3 + a] += f * Nv[a];
     });
     for (int a = 0; a < nt; ++a)
       for (int k = 0; k < nr; ++k) o.mom_r[static_cast<size_t>(j) * nv + a * nr + k] = 2.0 * kPi * o.wmu[a] * mr[k];
@@ -788,7 +807,7 @@ std::string assemble_field(const HostOps& o, std::vector<double>& Lop, std::vect
 
 std::vector<double> maxwellian_coeffs(const HostOps& o, double Te_eV) {
   const int nr = o.nr;
-  Spline sp(nr, o.vmax);
+  Spline sp(nr + 1, o.vmax);  // the last function is left out (f(vmax) = 0)
   const double vth = std::sqrt(2.0 * kE * Te_eV / kMe);
   std::vector<double> b(nr, 0.0);
   Rule r(24);
@@ -797,7 +816,8 @@ std::vector<double> maxwellian_coeffs(const HostOps& o, double Te_eV) {
     double Nv[4], dN[4];
     if (!sp.eval(v, s, Nv, dN)) return;
     const double f = std::exp(-(v / vth) * (v / vth)) / (std::pow(kPi, 1.5) * vth * vth * vth);
-    for (int a = 0; a < 4; ++a) b[s - 3 + a] += w * v * v * f * Nv[a];
+    for (int a = 0; a < 4; ++a)
+      if (s - 3 + a < nr) b[s - 3 + a] += w * v * v * f * Nv[a];
   });
   std::vector<double> R = o.M;
   cholesky(R, nr);

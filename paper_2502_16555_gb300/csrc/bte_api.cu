@@ -315,7 +315,7 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   // FP64 iterative refinement: residual through Algorithm 2, correction through the factors
   if (h->refine_max > 0) {
     bte::ResidualOps ro;
-    ro.c0 = h->rc0, ro.band = h->rband, ro.fcoef = h->rfcoef, ro.chol = h->rchol, ro.cinv = h->rcinv, ro.w = o.mw;
+    ro.c0 = h->rc0, ro.band = h->rband, ro.fband = h->rfband, ro.chol = h->rchol, ro.cinv = h->rcinv, ro.w = o.mw;
     BTE_CUDA(h, cudaMemsetAsync(h->conv, 0, sizeof(int) * nx, st));
     for (int s = 0; s <= h->refine_max; ++s) {
       BTE_LAUNCH(BTE_K_RESIDUAL, bte::launch_residual(h->Fb, h->Fa, E_dev, Eu, o.dt, ro, h->TO, h->TS, h->R, h->ratio,
@@ -533,8 +533,8 @@ bte_status bte_create(const bte_config* cfg, bte_handle** out) {
                                chk(dalloc(h, &h->Agup, blk)))) &&
               (h->structured || chk(dalloc(h, &h->Mband, o.Mband.size()))) &&
               chk(dalloc(h, &h->rc0, static_cast<size_t>(o.nr) * o.nr)) &&
-              chk(dalloc(h, &h->rband, static_cast<size_t>(3) * o.nr * (2 * o.mw + 1))) &&
-              chk(dalloc(h, &h->rfcoef, static_cast<size_t>(4) * o.nl)) &&
+              chk(dalloc(h, &h->rband, static_cast<size_t>(o.nr) * (2 * o.mw + 1))) &&
+              chk(dalloc(h, &h->rfband, static_cast<size_t>(2) * o.nl * o.nr * (2 * o.mw + 1))) &&
               chk(dalloc(h, &h->rchol, static_cast<size_t>(o.nr) * (o.mw + 1))) && chk(dalloc(h, &h->rcinv, o.nr)) &&
               chk(dalloc(h, &h->Cs, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
               chk(dalloc(h, &h->Alo, static_cast<size_t>(o.nl) * o.nr * o.nr)) &&
@@ -657,7 +657,8 @@ bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* 
       (h->Cg && (s = upload(h, h->Cg, o.Cg)) != BTE_OK) || (h->Aglo && (s = upload(h, h->Aglo, o.Ag_lo)) != BTE_OK) ||
       (h->Agup && (s = upload(h, h->Agup, o.Ag_up)) != BTE_OK) ||
       (s = upload_n(h, h->rc0, o.Cg.data(), static_cast<size_t>(o.nr) * o.nr)) != BTE_OK ||
-      (s = upload(h, h->rband, o.rband)) != BTE_OK || (s = upload(h, h->rfcoef, o.fcoef)) != BTE_OK ||
+      (s = upload(h, h->rband, o.rband)) != BTE_OK ||
+      (s = upload(h, h->rfband, o.rfband)) != BTE_OK ||
       (s = upload(h, h->rchol, o.rchol)) != BTE_OK || (s = upload(h, h->rcinv, o.rcinv)) != BTE_OK ||
       (s = upload(h, h->Cs, o.Cs)) != BTE_OK || (s = upload(h, h->Alo, o.As_lo)) != BTE_OK ||
       (s = upload(h, h->Aup, o.As_up)) != BTE_OK || (s = upload(h, h->mom_n, o.mom_n)) != BTE_OK ||

@@ -44,7 +44,7 @@ struct bte_handle {
   double *KCg = nullptr, *KAg = nullptr, *Cs = nullptr, *Alo = nullptr, *Aup = nullptr;
   double *Cg = nullptr, *Aglo = nullptr, *Agup = nullptr, *Mband = nullptr;
   // the refinement residual's banded operators (bte::ResidualOps)
-  double *rc0 = nullptr, *rband = nullptr, *rfcoef = nullptr, *rchol = nullptr, *rcinv = nullptr;
+  double *rc0 = nullptr, *rband = nullptr, *rfband = nullptr, *rchol = nullptr, *rcinv = nullptr;
   double *TO = nullptr, *TS = nullptr;
   double *mom_n = nullptr, *mom_e = nullptr, *mom_r = nullptr;
   // work

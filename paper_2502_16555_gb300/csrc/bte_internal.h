@@ -50,11 +50,11 @@ struct HostOps {
   std::vector<double> KC, KA;           // [nv][nv]  P_O M^-1 C P_S, P_O M^-1 A_v P_S
   double kc_inf = 0.0, ka_inf = 0.0;    // their infinity norms (largest absolute row sums)
   // the refinement residual's operators: C_0 dense ([nr][nr], C before the mass scaling, l = 0);
-  // bands ([3][nr][2 mw + 1]) of the loss part of C (the whole of C for l >= 1), of Dv and of M1;
-  // the band of the Cholesky factor R of M ([nr][mw + 1], R[p][p - mw + j]) and 1 / R[p][p];
-  // the field blocks as coefficients of Dv and M1: [nl][4] = (lo_d, lo_m, up_d, up_m) with
-  // block (q, q - 1) = lo_d Dv + lo_m M1 and block (q, q + 1) = up_d Dv + up_m M1
-  std::vector<double> rband, rchol, rcinv, fcoef;
+  // bands ([nr][2 mw + 1]) of the loss part of C (the whole of C for l >= 1); bands of the field
+  // blocks ([2][nl][nr][2 mw + 1]: (q, q - 1) = lo_d Dv + lo_m M1, then (q, q + 1) = up_d Dv +
+  // up_m M1, zero where the block does not exist); the band of the Cholesky factor R of M
+  // ([nr][mw + 1], R[p][p - mw + j]) and 1 / R[p][p].
+  std::vector<double> rband, rfband, rchol, rcinv;
   bool want_kg = false;                 // also form KCg, KAg (handles that factor the Nv x Nv form)
   std::vector<double> KCg, KAg;         // [nv][nv]  P_O C P_S, P_O A_v P_S (no mass scaling)
   std::vector<double> mom_n, mom_e;     // [nv]

@@ -153,14 +153,14 @@ void launch_lu_solve(const T* fac, const int* piv, const double* b, double* x, i
                      const int* conv, int accumulate, cudaStream_t st, MassBand mass = {});
 
 // The operators of the FP64 refinement residual, all before the mass scaling: C_0 dense ([nr][nr]);
-// the bands ([3][nr][2 w + 1], band[p][k - p + w]) of the loss part of C (the whole C_l for
-// l >= 1), of Dv and of M1; the field blocks as coefficients of Dv and M1 ([nl][4] = lo_d, lo_m,
-// up_d, up_m: block (q, q - 1) = lo_d Dv + lo_m M1, block (q, q + 1) = up_d Dv + up_m M1); the band
-// of the Cholesky factor R of M_v ([nr][w + 1], chol[p][j] = R[p][p - w + j]) and 1 / R[p][p].
+// the band ([nr][2 w + 1], band[p][k - p + w]) of the loss part of C (the whole C_l for l >= 1);
+// the bands of the field blocks (A_v)_{q,q-1} and (A_v)_{q,q+1} ([2][nl][nr][2 w + 1], zero where
+// a block does not exist); the band of the Cholesky factor R of M_v ([nr][w + 1],
+// chol[p][j] = R[p][p - w + j]) and 1 / R[p][p].
 struct ResidualOps {
   const double* c0 = nullptr;
   const double* band = nullptr;
-  const double* fcoef = nullptr;
+  const double* fband = nullptr;
   const double* chol = nullptr;
   const double* cinv = nullptr;
   int w = 0;

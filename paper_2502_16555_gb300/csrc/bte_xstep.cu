@@ -160,9 +160,9 @@ __global__ void v_form_kernel(const double* __restrict__ KCg, const double* __re
 
 // Refinement residual of one point (CTA per point), Algorithm 2 with the structured operators:
 // xS = P_S x, g = M_v^-1 (C + E_i A_v) xS, r = b - x + dt P_O g. The products with C and A_v run
-// over the bands of the loss part of C, of Dv and of M1 (C_0 carries the gain and the
-// heavy-temperature term and is dense); M_v^-1 is a forward and a backward substitution with the
-// banded Cholesky factor of M_v along the B-spline index. The point has converged when
+// over bands (the loss part of C, the field blocks; C_0 carries the gain and the heavy-temperature
+// term and is dense); M_v^-1 is a forward and a backward substitution with the banded Cholesky
+// factor of M_v along the B-spline index. The point has converged when
 // max|r| <= tol max|b|, or when max|r| is already at the rounding level of an FP64 product A_i x,
 // max|r| <= min(kBackwardFloor, tol) (|A_i| max|x| + max|b|) with |A_i| <= 1 + dt (|K_C| +
 // |E_i| |K_A|) (infinity norms): a normwise backward error no refinement can improve on. The second
@@ -210,17 +210,15 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
       const double* row = ro.band + static_cast<size_t>(p) * bw + w - p;   // row[k] = loss[p][k]
       for (int k = k0; k <= k1; ++k) c = fma(__ldg(row + k), xS[l * nr + k], c);
     }
-    const double* drow = ro.band + static_cast<size_t>(nr + p) * bw + w - p;      // Dv[p][k]
-    const double* mrow = ro.band + static_cast<size_t>(2 * nr + p) * bw + w - p;  // M1[p][k]
     if (l >= 1) {
-      const double cd = __ldg(ro.fcoef + 4 * l), cm = __ldg(ro.fcoef + 4 * l + 1);
+      const double* row = ro.fband + (static_cast<size_t>(l) * nr + p) * bw + w - p;   // (A_v)_{l,l-1}[p][k]
       const double* y = xS + (l - 1) * nr;
-      for (int k = k0; k <= k1; ++k) f = fma(fma(cd, __ldg(drow + k), cm * __ldg(mrow + k)), y[k], f);
+      for (int k = k0; k <= k1; ++k) f = fma(__ldg(row + k), y[k], f);
     }
     if (l + 1 < nl) {
-      const double cd = __ldg(ro.fcoef + 4 * l + 2), cm = __ldg(ro.fcoef + 4 * l + 3);
+      const double* row = ro.fband + (static_cast<size_t>(nl + l) * nr + p) * bw + w - p;   // (A_v)_{l,l+1}[p][k]
       const double* y = xS + (l + 1) * nr;
-      for (int k = k0; k <= k1; ++k) f = fma(fma(cd, __ldg(drow + k), cm * __ldg(mrow + k)), y[k], f);
+      for (int k = k0; k <= k1; ++k) f = fma(__ldg(row + k), y[k], f);
     }
     g[idx] = c + Ei * f;
   }
@@ -263,8 +261,8 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
   if ((threadIdx.x & 31) == 0) red_r[threadIdx.x >> 5] = mr, red_b[threadIdx.x >> 5] = mb, red_x[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w)
-      mr = fmax(mr, red_r[w]), mb = fmax(mb, red_b[w]), mx = fmax(mx, red_x[w]);
+    for (int wi = 1; wi < static_cast<int>(blockDim.x >> 5); ++wi)
+      mr = fmax(mr, red_r[wi]), mb = fmax(mb, red_b[wi]), mx = fmax(mx, red_x[wi]);
     const double q = mb > 0.0 ? mr / mb : (mr > 0.0 ? INFINITY : 0.0);
     const double nA = 1.0 + dt * (kc_inf + fabs(Ei) * ka_inf);
     ratio[i] = q;
@@ -410,7 +408,7 @@ void launch_residual(const double* x, const double* b, const double* E, double E
     cudaFuncSetAttribute(residual_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  residual_kernel<<<nx, 256, smem, st>>>(x, b, E, E_uniform, dt, ro, TO, TS, r, ratio, conv, tol, kc_inf, ka_inf, nt,
+  residual_kernel<<<nx, 512, smem, st>>>(x, b, E, E_uniform, dt, ro, TO, TS, r, ratio, conv, tol, kc_inf, ka_inf, nt,
                                          nr, nl, status);
 }
 
