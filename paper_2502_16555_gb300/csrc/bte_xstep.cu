@@ -203,10 +203,7 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
     const int l = idx / nr, p = idx % nr;
     const int k0 = max(0, p - w), k1 = min(nr - 1, p + w);
     double c = 0.0, f = 0.0;
-    if (l == 0) {
-      const double* row = ro.c0 + static_cast<size_t>(p) * nr;
-      for (int k = 0; k < nr; ++k) c = fma(__ldg(row + k), xS[k], c);
-    } else {
+    if (l > 0) {   // C_0 (dense) is added in the next stage
       const double* row = ro.band + static_cast<size_t>(p) * bw + w - p;   // row[k] = loss[p][k]
       for (int k = k0; k <= k1; ++k) c = fma(__ldg(row + k), xS[l * nr + k], c);
     }
@@ -223,21 +220,62 @@ __global__ void residual_kernel(const double* __restrict__ X, const double* __re
     g[idx] = c + Ei * f;
   }
   __syncthreads();
+  // the dense C_0 rows (l = 0): eight lanes per row, each a strided part of the dot product, summed
+  // over the lane group by shuffles (every thread runs the same number of rounds)
+  {
+    const int sub = threadIdx.x & 7, rows = blockDim.x >> 3;
+    for (int pb = 0; pb < nr; pb += rows) {
+      const int p = pb + (threadIdx.x >> 3);
+      double c = 0.0;
+      if (p < nr) {
+        const double* row = ro.c0 + static_cast<size_t>(p) * nr;
+        for (int k = sub; k < nr; k += 8) c = fma(__ldg(row + k), xS[k], c);
+      }
+      c += __shfl_down_sync(0xffffffffu, c, 4, 8);
+      c += __shfl_down_sync(0xffffffffu, c, 2, 8);
+      c += __shfl_down_sync(0xffffffffu, c, 1, 8);
+      if (p < nr && sub == 0) g[p] += c;
+    }
+  }
+  __syncthreads();
   // g_l <- M_v^-1 g_l, M_v = R R^T: R y = g_l (p ascending), then R^T z = y (p descending), one
-  // thread per harmonic
+  // thread per harmonic; for the cubic band (w = 3) the last three values stay in registers
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     double* gl = g + l * nr;
-    for (int p = 0; p < nr; ++p) {
-      const double* rrow = ro.chol + static_cast<size_t>(p) * (w + 1);   // rrow[j] = R[p][p - w + j]
-      double s = gl[p];
-      for (int j = max(0, w - p); j < w; ++j) s = fma(-__ldg(rrow + j), gl[p - w + j], s);
-      gl[p] = s * __ldg(ro.cinv + p);
-    }
-    for (int p = nr - 1; p >= 0; --p) {
-      double s = gl[p];
-      const int kmax = min(nr - 1, p + w);
-      for (int k = p + 1; k <= kmax; ++k) s = fma(-__ldg(ro.chol + static_cast<size_t>(k) * (w + 1) + p - k + w), gl[k], s);
-      gl[p] = s * __ldg(ro.cinv + p);
+    if (w == 3) {
+      double y1 = 0.0, y2 = 0.0, y3 = 0.0;   // y[p-1], y[p-2], y[p-3]
+      for (int p = 0; p < nr; ++p) {
+        const double* rrow = ro.chol + static_cast<size_t>(p) * 4;   // R[p][p-3], R[p][p-2], R[p][p-1], R[p][p]
+        double s = fma(-__ldg(rrow + 2), y1, gl[p]);
+        s = fma(-__ldg(rrow + 1), y2, s);
+        s = fma(-__ldg(rrow), y3, s);
+        const double y = s * __ldg(ro.cinv + p);
+        gl[p] = y;
+        y3 = y2, y2 = y1, y1 = y;
+      }
+      double z1 = 0.0, z2 = 0.0, z3 = 0.0;   // z[p+1], z[p+2], z[p+3]
+      for (int p = nr - 1; p >= 0; --p) {
+        double s = gl[p];
+        if (p + 1 < nr) s = fma(-__ldg(ro.chol + static_cast<size_t>(p + 1) * 4 + 2), z1, s);
+        if (p + 2 < nr) s = fma(-__ldg(ro.chol + static_cast<size_t>(p + 2) * 4 + 1), z2, s);
+        if (p + 3 < nr) s = fma(-__ldg(ro.chol + static_cast<size_t>(p + 3) * 4), z3, s);
+        const double z = s * __ldg(ro.cinv + p);
+        gl[p] = z;
+        z3 = z2, z2 = z1, z1 = z;
+      }
+    } else {
+      for (int p = 0; p < nr; ++p) {
+        const double* rrow = ro.chol + static_cast<size_t>(p) * (w + 1);   // rrow[j] = R[p][p - w + j]
+        double s = gl[p];
+        for (int j = max(0, w - p); j < w; ++j) s = fma(-__ldg(rrow + j), gl[p - w + j], s);
+        gl[p] = s * __ldg(ro.cinv + p);
+      }
+      for (int p = nr - 1; p >= 0; --p) {
+        double s = gl[p];
+        const int kmax = min(nr - 1, p + w);
+        for (int k = p + 1; k <= kmax; ++k) s = fma(-__ldg(ro.chol + static_cast<size_t>(k) * (w + 1) + p - k + w), gl[k], s);
+        gl[p] = s * __ldg(ro.cinv + p);
+      }
     }
   }
   __syncthreads();
