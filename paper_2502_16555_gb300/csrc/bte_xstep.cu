@@ -142,6 +142,18 @@ template <typename T>
 __global__ void v_form_kernel(const double* __restrict__ KCg, const double* __restrict__ KAg, MassBand mass,
                               const double* __restrict__ E, double E_uniform, double dt,
                               T* __restrict__ fac, int nx, int nv) {
+  // Per element, base = M - dt KCg and slope = -dt KAg once in FP64; per point, one FMA in the
+  // factor precision, base + E_i slope (for FP32 factors an FP32 FMA: GB300's FP64 rate would bound
+  // the Nx FP64 operations per element at about eight times the store time). A per-point field is
+  // staged in shared memory in that precision; the uniform field takes the same arithmetic, so
+  // equal fields give equal factors on both paths.
+  extern __shared__ __align__(8) unsigned char vf_smem[];
+  T* Es = reinterpret_cast<T*>(vf_smem);
+  if (E) {
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) Es[i] = static_cast<T>(E[i]);
+    __syncthreads();
+  }
+  const T Eu = static_cast<T>(E_uniform);
   const size_t nn = static_cast<size_t>(nv) * nv;
   const int nr = mass.nr, bw = 2 * mass.w + 1;
   for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < nn;
@@ -151,9 +163,12 @@ __global__ void v_form_kernel(const double* __restrict__ KCg, const double* __re
     const int row = static_cast<int>(e / nv), col = static_cast<int>(e % nv);
     const int p = row % nr, k = col % nr, dk = k - p;
     const double d = (row - p == col - k && dk >= -mass.w && dk <= mass.w) ? __ldg(mass.m + p * bw + dk + mass.w) : 0.0;
-    for (int i = 0; i < nx; ++i) {
-      const double Ei = E ? E[i] : E_uniform;
-      fac[static_cast<size_t>(i) * nn + e] = static_cast<T>(d - dt * (kc + Ei * ka));
+    const T base = static_cast<T>(d - dt * kc), slope = static_cast<T>(-dt * ka);
+    if (E) {
+      for (int i = 0; i < nx; ++i) fac[static_cast<size_t>(i) * nn + e] = Es[i] * slope + base;
+    } else {
+      const T v = Eu * slope + base;
+      for (int i = 0; i < nx; ++i) fac[static_cast<size_t>(i) * nn + e] = v;
     }
   }
 }
@@ -429,7 +444,8 @@ template <typename T>
 void launch_v_form(const double* KCg, const double* KAg, MassBand mass, const double* E, double E_uniform,
                    double dt, T* fac, int nx, int nv, cudaStream_t st) {
   const size_t nn = static_cast<size_t>(nv) * nv;
-  v_form_kernel<T><<<grid_for(nn, 256), 256, 0, st>>>(KCg, KAg, mass, E, E_uniform, dt, fac, nx, nv);
+  const size_t smem = E ? sizeof(T) * static_cast<size_t>(nx) : 0;   // nx <= 4096: at most 32 KB
+  v_form_kernel<T><<<grid_for(nn, 256), 256, smem, st>>>(KCg, KAg, mass, E, E_uniform, dt, fac, nx, nv);
 }
 template void launch_v_form<double>(const double*, const double*, MassBand, const double*, double, double,
                                     double*, int, int, cudaStream_t);
