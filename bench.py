@@ -419,12 +419,16 @@ def run_ours(args, rank, world):
     F_e2e = F.clone()
     t_q = (args.warmup + args.steps + 1) * dt
     barrier()
+    launches1 = s.info()["launches"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    s.run(Fq, args.steps, t_q)
+    s.run(Fq, args.steps, t_q)   # replays the library's CUDA graph of one step (no event bracketing)
     e1.record()
     barrier()
     ms_plain = e0.elapsed_time(e1) / args.steps
+    launches_plain = s.info()["launches"] - launches1
+    if ms_plain <= ms:
+        launches = launches_plain   # the kernels of the run the value is taken from
     ms = max_over_ranks(min(ms, ms_plain), dist)
     value = world * dof / (ms / 1e3)
 

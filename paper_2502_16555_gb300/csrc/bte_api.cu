@@ -361,6 +361,22 @@ bte_status enqueue_step(bte_handle* h, const double* F_in, double* F_out, const 
   return BTE_OK;
 }
 
+// bte_run's graph: the step's field from the call's sequence of uniform fields, and the counter
+__global__ void run_field_kernel(const double* __restrict__ seq, const int* __restrict__ idx, double* __restrict__ E,
+                                 int nx) {
+  const double e = seq[*idx];
+  for (int x = threadIdx.x; x < nx; x += blockDim.x) E[x] = e;
+}
+__global__ void run_advance_kernel(int* idx) { *idx += 1; }
+
+void release_run_graph(bte_handle* h) {
+  if (h->run_exec) cudaGraphExecDestroy(h->run_exec);
+  if (h->run_graph) cudaGraphDestroy(h->run_graph);
+  h->run_exec = nullptr;
+  h->run_graph = nullptr;
+  h->run_F = nullptr;
+}
+
 bte_status read_status(bte_handle* h, int steps = 1) {
   BTE_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
   BTE_CUDA(h, cudaStreamSynchronize(h->st));
@@ -455,6 +471,7 @@ unsigned long long handle_launches(const bte_handle* h) { return h->launches; }
 void handle_add_launches(bte_handle* h, unsigned long long n) { h->launches += n; }
 bool handle_has_tc(const bte_handle* h) { return h->have_tc; }
 void handle_set_variant(bte_handle* h, const Variant& v) {
+  release_run_graph(h);
   h->use_tc = v.tc && h->have_tc;
   h->panel_w = v.panel_w;
   h->tc_pair = v.pair;
@@ -642,6 +659,8 @@ bte_status bte_set_cross_sections(bte_handle* h, int n_proc, const bte_process* 
   }
   std::string e = bte::assemble_v(h->ops, ps);
   if (!e.empty()) return fail(h, BTE_EINVAL, e);
+  // bte_run's graph holds the previous operators' norms as kernel arguments
+  if (!h->host_only) release_run_graph(h);
   h->procs = ps;
   if (h->host_only) return BTE_OK;
   const HostOps& o = h->ops;
@@ -696,11 +715,74 @@ bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || n_steps < 0) return fail(h, BTE_EINVAL, "bad arguments");
   BTE_TRY(device_status(h));
+  const HostOps& o = h->ops;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  BTE_CUDA(h, cudaStreamIsCapturing(h->st, &cs));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
-  for (int i = 0; i < n_steps; ++i) {
-    bte_status s = enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * h->ops.dt, V0, freq_Hz);
-    if (s != BTE_OK) return s;
+  // one step at a time: a single step, event profiling (per-launch records), or a stream that the
+  // caller is capturing
+  if (n_steps < 2 || h->prof || cs != cudaStreamCaptureStatusNone) {
+    for (int i = 0; i < n_steps; ++i) {
+      bte_status s = enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * o.dt, V0, freq_Hz);
+      if (s != BTE_OK) return s;
+    }
+    return read_status(h, n_steps);
   }
+  // the steps' uniform fields, formed exactly as enqueue_step forms them; through the per-point
+  // field array they give the same factors and residuals, so the result equals n_steps bte_step calls
+  std::vector<double> seq(n_steps);
+  for (int i = 0; i < n_steps; ++i) {
+    const double t = t_s + i * o.dt;
+    seq[i] = V0 / o.L * std::sin(2.0 * bte::kPi * freq_Hz * (t + 0.5 * o.dt));
+    if (!std::isfinite(seq[i])) return fail(h, BTE_ENONFINITE, "non-finite field (V0, freq_Hz or t_s)");
+  }
+  if (!h->run_E) BTE_TRY(dalloc(h, &h->run_E, o.nx));
+  if (!h->run_idx) BTE_TRY(dalloc(h, &h->run_idx, 1));
+  if (h->run_cap < n_steps) {
+    release_run_graph(h);
+    if (h->run_seq) cudaFree(h->run_seq);
+    h->run_seq = nullptr;
+    h->run_cap = 0;
+    const int cap = std::max(n_steps, 256);
+    BTE_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->run_seq), sizeof(double) * cap));
+    h->run_cap = cap;
+  }
+  if (!h->run_exec || h->run_F != F_dev) {
+    release_run_graph(h);
+    // captured on a private stream (the caller's may be the legacy default stream, which cannot be
+    // captured); the graph is then launched on the handle's own stream
+    if (!h->cap_st) BTE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    const unsigned long long before = h->launches;
+    cudaStream_t own = h->st;
+    // relaxed: a launcher's first use may set a kernel attribute or encode a tensor map
+    BTE_CUDA(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed));
+    h->st = h->cap_st;
+    run_field_kernel<<<1, 256, 0, h->st>>>(h->run_seq, h->run_idx, h->run_E, o.nx);
+    const bte_status s = enqueue_step(h, F_dev, F_dev, h->run_E, 0.0, 0.0, 0.0);
+    run_advance_kernel<<<1, 1, 0, h->st>>>(h->run_idx);
+    h->st = own;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->cap_st, &g);
+    h->run_launches = h->launches - before + 2;   // the step's kernels, the field and the counter
+    h->launches = before;                         // captured, not launched: counted per replay
+    if (s != BTE_OK || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();   // a failed capture must not leave an error behind for the caller
+      if (s != BTE_OK) return s;
+      return fail(h, BTE_ECUDA, std::string("capturing the step: ") + cudaGetErrorString(ee));
+    }
+    h->run_graph = g;
+    const cudaError_t ie = cudaGraphInstantiate(&h->run_exec, g, 0);
+    if (ie != cudaSuccess) {
+      release_run_graph(h);
+      return fail(h, BTE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    h->run_F = F_dev;
+  }
+  BTE_CUDA(h, cudaMemcpyAsync(h->run_seq, seq.data(), sizeof(double) * n_steps, cudaMemcpyHostToDevice, h->st));
+  BTE_CUDA(h, cudaMemsetAsync(h->run_idx, 0, sizeof(int), h->st));
+  for (int i = 0; i < n_steps; ++i) BTE_CUDA(h, cudaGraphLaunch(h->run_exec, h->st));
+  h->launches += h->run_launches * static_cast<unsigned long long>(n_steps);
   return read_status(h, n_steps);
 }
 
@@ -818,6 +900,9 @@ bte_status bte_destroy(bte_handle* h) {
   if (!h) return BTE_OK;
   if (!h->host_only) {
     cudaStreamSynchronize(h->st);
+    release_run_graph(h);
+    if (h->run_seq) cudaFree(h->run_seq);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
     for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
     for (void* p : h->allocs) cudaFree(p);
     if (h->mom_r) cudaFree(h->mom_r);

@@ -76,6 +76,18 @@ struct bte_handle {
   double last_resid = 0.0;
   unsigned last_flags = 0;
   unsigned long long launches = 0;
+  // bte_run's CUDA graph of one step: the field of each step comes from run_seq[*run_idx] (the
+  // uniform fields of the call, uploaded from the host) through run_E; captured for the state
+  // pointer run_F, dropped when the operators or the variant change
+  cudaGraph_t run_graph = nullptr;
+  cudaGraphExec_t run_exec = nullptr;
+  double* run_F = nullptr;
+  double* run_E = nullptr;
+  double* run_seq = nullptr;   // run_cap doubles, owned apart from allocs (it grows)
+  int run_cap = 0;
+  int* run_idx = nullptr;
+  unsigned long long run_launches = 0;   // kernels per replayed step
+  cudaStream_t cap_st = nullptr;         // private stream the step is captured on (non-blocking)
   // profiling: events around every launch while enabled
   struct Rec {
     int kind;

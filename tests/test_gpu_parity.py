@@ -406,6 +406,34 @@ def test_tensor_core_panel_left_looking(shape):
 
 # ------------------------------------------------------------------ entry points and errors
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_run_replays_a_graph_equal_to_single_steps(precision):
+    """bte_run with n >= 2 replays a CUDA graph of one step (each step's uniform field formed on the
+    host and passed through the per-point field array): the state equals n bte_step calls bitwise.
+    A second state tensor makes it capture again, and new cross sections drop the graph."""
+    cfg = W.scaled(W.SMALL, nx=6, nr=12, ntheta=6)
+    F0 = W.random_state(6, 6, 12, seed=51)
+    dt = cfg["dt_s"]
+    t0 = 0.13 / W.RF_FREQ_HZ
+    s = solver(cfg, precision)
+
+    def both(n):
+        A, B = to_dev(F0), to_dev(F0)
+        s.run(A, n, t0)
+        for k in range(n):
+            s.step(B, t0 + k * dt)
+        return A, B
+
+    A, B = both(5)
+    assert torch.equal(A, B)
+    A, B = both(3)
+    assert torch.equal(A, B)
+    s.set_cross_sections(cfg["processes"][:1])
+    A, B = both(4)
+    assert torch.equal(A, B)
+    assert not torch.equal(A, to_dev(F0))
+
+
 def test_step_host_matches_device_step():
     cfg = W.scaled(W.SMALL, nx=10, nr=12, ntheta=6)
     F0 = W.random_state(10, 6, 12, seed=21)
