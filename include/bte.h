@@ -200,11 +200,13 @@ bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_
                     double freq_Hz);
 
 /* Same as bte_step, but n_steps steps from t_s without any host synchronisation between them
- * (the status word is read once at the end). E is the uniform sinusoidal field. With n_steps >= 2
- * the steps replay a CUDA graph of one step, captured on the first such call and again when F_dev,
- * the cross sections or the solver variant change; the field of each step is formed on the host as
- * for bte_step, so the result equals n_steps bte_step calls. One step at a time instead while
- * bte_profile records, or when the handle's stream is being captured by the caller. */
+ * (the status word is read once at the end). E is the uniform sinusoidal field.
+ * Launching: bte_run, bte_step with E_dev == NULL and bte_step_host replay a CUDA graph of one step,
+ * captured for the state pointer (again when it, the cross sections or the solver variant change;
+ * bte_step_host steps the handle's own device copy). Each step's field is formed on the host as for
+ * a step launched kernel by kernel and passed through the per-point field array, which gives the
+ * same factors: the results are identical. Kernel by kernel instead while bte_profile records, when
+ * the caller is capturing the handle's stream, and for bte_step with a field array. */
 bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double V0, double freq_Hz);
 
 /* bte_step on HOST buffers: copies F_host (nx*nv doubles) to the device, steps, copies the result

@@ -377,6 +377,78 @@ void release_run_graph(bte_handle* h) {
   h->run_F = nullptr;
 }
 
+// The step graph applies unless bte_profile records (per-launch events) or the caller is capturing
+// the handle's stream.
+bte_status graph_allowed(bte_handle* h, bool& ok) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  BTE_CUDA(h, cudaStreamIsCapturing(h->st, &cs));
+  ok = !h->prof && cs == cudaStreamCaptureStatusNone;
+  return BTE_OK;
+}
+
+// n_steps > 0 steps of F_dev with the uniform sinusoidal field as replays of a CUDA graph of one
+// step, captured for F_dev (again when F_dev, the cross sections or the variant change). The steps'
+// fields are formed exactly as enqueue_step forms them and reach the step through the per-point
+// field array, which gives the same factors and residuals: the result equals the steps launched
+// one kernel at a time.
+bte_status enqueue_graph_steps(bte_handle* h, double* F_dev, int n_steps, double t_s, double V0, double freq_Hz) {
+  const HostOps& o = h->ops;
+  std::vector<double> seq(n_steps);
+  for (int i = 0; i < n_steps; ++i) {
+    const double t = t_s + i * o.dt;
+    seq[i] = V0 / o.L * std::sin(2.0 * bte::kPi * freq_Hz * (t + 0.5 * o.dt));
+    if (!std::isfinite(seq[i])) return fail(h, BTE_ENONFINITE, "non-finite field (V0, freq_Hz or t_s)");
+  }
+  if (!h->run_E) BTE_TRY(dalloc(h, &h->run_E, o.nx));
+  if (!h->run_idx) BTE_TRY(dalloc(h, &h->run_idx, 1));
+  if (h->run_cap < n_steps) {
+    release_run_graph(h);
+    if (h->run_seq) cudaFree(h->run_seq);
+    h->run_seq = nullptr;
+    h->run_cap = 0;
+    const int cap = std::max(n_steps, 256);
+    BTE_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->run_seq), sizeof(double) * cap));
+    h->run_cap = cap;
+  }
+  if (!h->run_exec || h->run_F != F_dev) {
+    release_run_graph(h);
+    // captured on a private stream (the caller's may be the legacy default stream, which cannot be
+    // captured); the graph is then launched on the handle's own stream
+    if (!h->cap_st) BTE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+    const unsigned long long before = h->launches;
+    cudaStream_t own = h->st;
+    // relaxed: a launcher's first use may set a kernel attribute or encode a tensor map
+    BTE_CUDA(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed));
+    h->st = h->cap_st;
+    run_field_kernel<<<1, 256, 0, h->st>>>(h->run_seq, h->run_idx, h->run_E, o.nx);
+    const bte_status s = enqueue_step(h, F_dev, F_dev, h->run_E, 0.0, 0.0, 0.0);
+    run_advance_kernel<<<1, 1, 0, h->st>>>(h->run_idx);
+    h->st = own;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->cap_st, &g);
+    h->run_launches = h->launches - before + 2;   // the step's kernels, the field and the counter
+    h->launches = before;                         // captured, not launched: counted per replay
+    if (s != BTE_OK || ee != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();   // a failed capture must not leave an error behind for the caller
+      if (s != BTE_OK) return s;
+      return fail(h, BTE_ECUDA, std::string("capturing the step: ") + cudaGetErrorString(ee));
+    }
+    h->run_graph = g;
+    const cudaError_t ie = cudaGraphInstantiate(&h->run_exec, g, 0);
+    if (ie != cudaSuccess) {
+      release_run_graph(h);
+      return fail(h, BTE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    h->run_F = F_dev;
+  }
+  BTE_CUDA(h, cudaMemcpyAsync(h->run_seq, seq.data(), sizeof(double) * n_steps, cudaMemcpyHostToDevice, h->st));
+  BTE_CUDA(h, cudaMemsetAsync(h->run_idx, 0, sizeof(int), h->st));
+  for (int i = 0; i < n_steps; ++i) BTE_CUDA(h, cudaGraphLaunch(h->run_exec, h->st));
+  h->launches += h->run_launches * static_cast<unsigned long long>(n_steps);
+  return BTE_OK;
+}
+
 bte_status read_status(bte_handle* h, int steps = 1) {
   BTE_CUDA(h, cudaMemcpyAsync(h->status_host, h->status, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
   BTE_CUDA(h, cudaStreamSynchronize(h->st));
@@ -705,9 +777,13 @@ bte_status bte_step(bte_handle* h, double* F_dev, const double* E_dev, double t_
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev) return fail(h, BTE_EINVAL, "F_dev is NULL");
   BTE_TRY(device_status(h));
+  bool graph = false;
+  BTE_TRY(graph_allowed(h, graph));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
-  bte_status s = enqueue_step(h, F_dev, F_dev, E_dev, t_s, V0, freq_Hz);
-  if (s != BTE_OK) return s;
+  if (graph && !E_dev)
+    BTE_TRY(enqueue_graph_steps(h, F_dev, 1, t_s, V0, freq_Hz));
+  else
+    BTE_TRY(enqueue_step(h, F_dev, F_dev, E_dev, t_s, V0, freq_Hz));
   return read_status(h);
 }
 
@@ -715,74 +791,14 @@ bte_status bte_run(bte_handle* h, double* F_dev, int n_steps, double t_s, double
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_dev || n_steps < 0) return fail(h, BTE_EINVAL, "bad arguments");
   BTE_TRY(device_status(h));
-  const HostOps& o = h->ops;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  BTE_CUDA(h, cudaStreamIsCapturing(h->st, &cs));
+  bool graph = false;
+  BTE_TRY(graph_allowed(h, graph));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
-  // one step at a time: a single step, event profiling (per-launch records), or a stream that the
-  // caller is capturing
-  if (n_steps < 2 || h->prof || cs != cudaStreamCaptureStatusNone) {
-    for (int i = 0; i < n_steps; ++i) {
-      bte_status s = enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * o.dt, V0, freq_Hz);
-      if (s != BTE_OK) return s;
-    }
-    return read_status(h, n_steps);
+  if (graph && n_steps > 0) {
+    BTE_TRY(enqueue_graph_steps(h, F_dev, n_steps, t_s, V0, freq_Hz));
+  } else {
+    for (int i = 0; i < n_steps; ++i) BTE_TRY(enqueue_step(h, F_dev, F_dev, nullptr, t_s + i * h->ops.dt, V0, freq_Hz));
   }
-  // the steps' uniform fields, formed exactly as enqueue_step forms them; through the per-point
-  // field array they give the same factors and residuals, so the result equals n_steps bte_step calls
-  std::vector<double> seq(n_steps);
-  for (int i = 0; i < n_steps; ++i) {
-    const double t = t_s + i * o.dt;
-    seq[i] = V0 / o.L * std::sin(2.0 * bte::kPi * freq_Hz * (t + 0.5 * o.dt));
-    if (!std::isfinite(seq[i])) return fail(h, BTE_ENONFINITE, "non-finite field (V0, freq_Hz or t_s)");
-  }
-  if (!h->run_E) BTE_TRY(dalloc(h, &h->run_E, o.nx));
-  if (!h->run_idx) BTE_TRY(dalloc(h, &h->run_idx, 1));
-  if (h->run_cap < n_steps) {
-    release_run_graph(h);
-    if (h->run_seq) cudaFree(h->run_seq);
-    h->run_seq = nullptr;
-    h->run_cap = 0;
-    const int cap = std::max(n_steps, 256);
-    BTE_CUDA(h, cudaMalloc(reinterpret_cast<void**>(&h->run_seq), sizeof(double) * cap));
-    h->run_cap = cap;
-  }
-  if (!h->run_exec || h->run_F != F_dev) {
-    release_run_graph(h);
-    // captured on a private stream (the caller's may be the legacy default stream, which cannot be
-    // captured); the graph is then launched on the handle's own stream
-    if (!h->cap_st) BTE_CUDA(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
-    const unsigned long long before = h->launches;
-    cudaStream_t own = h->st;
-    // relaxed: a launcher's first use may set a kernel attribute or encode a tensor map
-    BTE_CUDA(h, cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeRelaxed));
-    h->st = h->cap_st;
-    run_field_kernel<<<1, 256, 0, h->st>>>(h->run_seq, h->run_idx, h->run_E, o.nx);
-    const bte_status s = enqueue_step(h, F_dev, F_dev, h->run_E, 0.0, 0.0, 0.0);
-    run_advance_kernel<<<1, 1, 0, h->st>>>(h->run_idx);
-    h->st = own;
-    cudaGraph_t g = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(h->cap_st, &g);
-    h->run_launches = h->launches - before + 2;   // the step's kernels, the field and the counter
-    h->launches = before;                         // captured, not launched: counted per replay
-    if (s != BTE_OK || ee != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      cudaGetLastError();   // a failed capture must not leave an error behind for the caller
-      if (s != BTE_OK) return s;
-      return fail(h, BTE_ECUDA, std::string("capturing the step: ") + cudaGetErrorString(ee));
-    }
-    h->run_graph = g;
-    const cudaError_t ie = cudaGraphInstantiate(&h->run_exec, g, 0);
-    if (ie != cudaSuccess) {
-      release_run_graph(h);
-      return fail(h, BTE_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
-    }
-    h->run_F = F_dev;
-  }
-  BTE_CUDA(h, cudaMemcpyAsync(h->run_seq, seq.data(), sizeof(double) * n_steps, cudaMemcpyHostToDevice, h->st));
-  BTE_CUDA(h, cudaMemsetAsync(h->run_idx, 0, sizeof(int), h->st));
-  for (int i = 0; i < n_steps; ++i) BTE_CUDA(h, cudaGraphLaunch(h->run_exec, h->st));
-  h->launches += h->run_launches * static_cast<unsigned long long>(n_steps);
   return read_status(h, n_steps);
 }
 
@@ -790,11 +806,15 @@ bte_status bte_step_host(bte_handle* h, double* F_host, double t_s, double V0, d
   if (!h) return fail(nullptr, BTE_EINVAL, "handle is NULL");
   if (!F_host) return fail(h, BTE_EINVAL, "F_host is NULL");
   BTE_TRY(device_status(h));
+  bool graph = false;
+  BTE_TRY(graph_allowed(h, graph));
   const size_t bytes = sizeof(double) * h->ops.nx * h->ops.nv;
   BTE_CUDA(h, cudaMemcpyAsync(h->Fhost_dev, F_host, bytes, cudaMemcpyHostToDevice, h->st));
   BTE_CUDA(h, cudaMemsetAsync(h->status, 0, 2 * sizeof(unsigned), h->st));
-  bte_status s = enqueue_step(h, h->Fhost_dev, h->Fhost_dev, nullptr, t_s, V0, freq_Hz);
-  if (s != BTE_OK) return s;
+  if (graph)
+    BTE_TRY(enqueue_graph_steps(h, h->Fhost_dev, 1, t_s, V0, freq_Hz));
+  else
+    BTE_TRY(enqueue_step(h, h->Fhost_dev, h->Fhost_dev, nullptr, t_s, V0, freq_Hz));
   BTE_CUDA(h, cudaMemcpyAsync(F_host, h->Fhost_dev, bytes, cudaMemcpyDeviceToHost, h->st));
   return read_status(h);
 }

@@ -408,9 +408,10 @@ def test_tensor_core_panel_left_looking(shape):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_run_replays_a_graph_equal_to_single_steps(precision):
-    """bte_run with n >= 2 replays a CUDA graph of one step (each step's uniform field formed on the
-    host and passed through the per-point field array): the state equals n bte_step calls bitwise.
-    A second state tensor makes it capture again, and new cross sections drop the graph."""
+    """bte_run (and bte_step, bte_step_host) replay a CUDA graph of one step, each step's uniform
+    field formed on the host and passed through the per-point field array: the state equals the
+    same steps launched kernel by kernel (forced here by recording with bte_profile) bitwise. A
+    second state tensor makes it capture again, and new cross sections drop the graph."""
     cfg = W.scaled(W.SMALL, nx=6, nr=12, ntheta=6)
     F0 = W.random_state(6, 6, 12, seed=51)
     dt = cfg["dt_s"]
@@ -420,14 +421,28 @@ def test_run_replays_a_graph_equal_to_single_steps(precision):
     def both(n):
         A, B = to_dev(F0), to_dev(F0)
         s.run(A, n, t0)
+        s.profile_start()
         for k in range(n):
             s.step(B, t0 + k * dt)
+        s.profile_stop()
         return A, B
 
     A, B = both(5)
     assert torch.equal(A, B)
     A, B = both(3)
     assert torch.equal(A, B)
+    # single graph steps and the host-buffer step
+    C = to_dev(F0)
+    for k in range(3):
+        s.step(C, t0 + k * dt)
+    assert torch.equal(C, B)
+    H = F0.copy()
+    s.step_host(H, t0)
+    D = to_dev(F0)
+    s.profile_start()
+    s.step(D, t0)
+    s.profile_stop()
+    assert np.array_equal(H, D.cpu().numpy())
     s.set_cross_sections(cfg["processes"][:1])
     A, B = both(4)
     assert torch.equal(A, B)
