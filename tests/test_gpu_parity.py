@@ -46,6 +46,10 @@ CASES = {
     "tiny": W.scaled(W.SMALL, nx=3, nr=4, ntheta=2),
     # nr > 186: the eigen-basis transforms stage more than 48 KB of shared memory per CTA
     "many_bsplines": W.scaled(W.SMALL, nx=5, nr=256, ntheta=2),
+    # one harmonic: the reduced system of order nr, no field coupling
+    "nl_one": W.scaled(W.SMALL, nx=5, nr=10, ntheta=4, nl=1),
+    # more collocation points than SMs (152): two waves of the per-point kernels
+    "many_points": W.scaled(W.SMALL, nx=200, nr=8, ntheta=4),
 }
 
 
