@@ -453,6 +453,27 @@ def test_run_replays_a_graph_equal_to_single_steps(precision):
     assert not torch.equal(A, to_dev(F0))
 
 
+def test_run_graph_follows_a_variant_change():
+    """The batch autotuner sets each handle's solver variant; a step graph captured before must be
+    dropped, so bte_run afterwards still equals the steps launched kernel by kernel."""
+    from paper_2502_16555_gb300 import bte
+    cfg = W.scaled(W.SMALL, nx=6, nr=24, ntheta=16)   # nv = 384: three panels in the mixed path
+    F0 = W.random_state(6, 16, 24, seed=52)
+    dt = cfg["dt_s"]
+    s = solver(cfg, "mixed")
+    A = to_dev(F0)
+    s.run(A, 2, 0.0)                       # captures the graph
+    b = bte.Batch([s], autotune=True)      # may switch the variant
+    b.close()
+    A, B = to_dev(F0), to_dev(F0)
+    s.run(A, 3, 0.0)
+    s.profile_start()
+    for k in range(3):
+        s.step(B, k * dt)
+    s.profile_stop()
+    assert torch.equal(A, B)
+
+
 def test_step_host_matches_device_step():
     cfg = W.scaled(W.SMALL, nx=10, nr=12, ntheta=6)
     F0 = W.random_state(10, 6, 12, seed=21)
